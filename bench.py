@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Lloyd-iteration throughput of the GB300 k-means hot path.
+
+Workload (the high-dimensional plain-vs-precision configuration): n = 200,000 points, d = 1,024,
+k = 100, seeded Gaussian mixture with 100 components (weights Dirichlet(1), means U[-10,10]^d,
+sigma log-uniform in [0.5, 2]).  A step is one Lloyd iteration: kmeans_assign (distance GEMM +
+fused top-2 epilogue + exact recheck of certified near-ties) followed by kmeans_update
+(stable counting sort + segmented CF sums + FP64 centroids and costs).  k-means++ seeding,
+the row norms and the operand copy of X are per-dataset preparation, done before the timed
+region.  X (819 MB FP32 + 410 MB BF16) is larger than L2 (129 MB), so no flush is needed.
+
+Metric: assign+update GFLOP/s with the algorithmic flop count 2nkd + nd per iteration.
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "assign+update GFLOP/s (Lloyd iteration, 200k x 1024, k=100)"
+UNIT = "GFLOP/s"
+# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
+FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense ratio, applied to the measured BF16 peak
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gbkm", choices=["gbkm", "reference"])
+    ap.add_argument("--form", default="auto", choices=["auto", "f32", "bf16"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tcgen05"])
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--d", type=int, default=1024)
+    ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return {"hbm_gbs": j["hbm_gbs"], "bf16_tflops": j["bf16_tflops"],
+                "bf16_tflops_sustained": j.get("bf16_tflops_sustained", j["bf16_tflops"]),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(X, C, cpu_seconds, threads=None):
+    """Time the FP64 oracle's assign + update on a bounded row sample; GFLOP/s of the sample."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    cores = oracle.set_threads(threads or os.cpu_count() or 1)
+    n, d = X.shape
+    k = C.shape[0]
+    Cd = C.astype(np.float64)
+    rows = min(n, 2048)
+    t0 = time.perf_counter()
+    lab, _, _ = oracle.assign(X[:rows], Cd)
+    oracle.update(X[:rows], lab, Cd)
+    dt = time.perf_counter() - t0
+    rows = int(min(n, max(rows, rows * cpu_seconds / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    lab, _, _ = oracle.assign(X[:rows], Cd)
+    oracle.update(X[:rows], lab, Cd)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * rows * k * d + rows * d
+    return {"value": flops / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {rows} of {n} rows, assign over all k={k} + update, FP64 C loops, "
+                      f"{dt:.1f} s"}
+
+
+def make_workload(n, d, k, seed):
+    from paper_1502_04265_gb300 import synth
+
+    X, _ = synth.gaussian_mixture(n, d, k, seed=seed)
+    return X, synth.seed_uniforms(k, seed=seed)
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores, on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    X, u = make_workload(args.n, args.d, args.k, 0)
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    # fixed centers for timing: rows picked by the seeding uniforms (assign work does not depend
+    # on which centers are used)
+    C = X[(u * args.n).astype(np.int64) % args.n].astype(np.float64)
+    rows = min(args.n, 2048)
+    t0 = time.perf_counter()
+    lab, _, _ = oracle.assign(X[:rows], C)
+    oracle.update(X[:rows], lab, C)
+    dt = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    rows = int(min(args.n, max(256, rows * budget / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        lab, _, _ = oracle.assign(X[:rows], C)
+        oracle.update(X[:rows], lab, C)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lab, _, _ = oracle.assign(X[:rows], C)
+        oracle.update(X[:rows], lab, C)
+    dt = (time.perf_counter() - t0) / args.steps
+    flops = 2.0 * rows * args.k * args.d + rows * args.d
+    val = flops / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"gaussian mixture n={args.n} d={args.d} "
+                                                       f"k={args.k}; oracle on a {rows}-row sample per step"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {rows} of {args.n} rows per step, assign + update"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1502_04265_gb300 import _binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    B.load(build_if_missing=True)
+    n, d, k = args.n, args.d, args.k
+    F_step = 2.0 * n * k * d + n * d
+    # independent replica per rank (the path has no exchange step): seed = rank
+    X, u = make_workload(n, d, k, seed=rank)
+    Xg = torch.from_numpy(X).to(dev)
+    ug = torch.from_numpy(u).to(dev)
+    ctx = B.Context(local)
+
+    form = args.form
+    engine = args.engine
+    xnorm = B.kmeans_row_norms(Xg, ctx=ctx)
+    idx, C0 = B.kmeans_seed_pp(Xg, k, ug, ctx=ctx)
+    Xop = None
+    if form in ("auto", "bf16"):
+        Xb, _ = B.kmeans_quantize(Xg, "bf16", ctx=ctx)
+        try:
+            B.kmeans_assign(Xg, C0, Xop=Xb, xnorm=xnorm, compute="bf16", engine=engine, ctx=ctx)
+            form, Xop = "bf16", Xb
+        except B.GbkmError:
+            if form == "bf16":
+                raise
+            form = "f32"
+            del Xb
+    else:
+        form = "f32"
+    ctx.sync()
+
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    C = C0.clone()
+    Cn = torch.empty_like(C)
+    cost = torch.zeros((max(args.steps, 1) + args.warmup, 2), dtype=torch.float64, device=dev)
+    nre = torch.zeros(max(args.steps, 1) + args.warmup, dtype=torch.int64, device=dev)
+
+    def step(i):
+        nonlocal C, Cn
+        B.kmeans_assign(Xg, C, Xop=Xop, xnorm=xnorm, compute=form, engine=engine, labels=labels,
+                        n_rechecked=nre[i:i + 1], ctx=ctx)
+        B.kmeans_update(Xg, labels, C, C_new=Cn, cost_old=cost[i, 0:1], cost_new=cost[i, 1:2], ctx=ctx)
+        C, Cn = Cn, C
+
+    for i in range(args.warmup):
+        step(i)
+    ctx.sync()
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(local) if (rank == 0 and not args.no_clocks) else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    ctx.profile(True)
+    l0 = ctx.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clocks = sampler.stop() if sampler else None
+    ms_step = ms_total / max(args.steps, 1)
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * F_step / (ms_step * 1e-3) / 1e9
+    ctx.sync()
+    costs = cost.cpu().numpy()
+    rechecked = nre.cpu().numpy()
+
+    # ---- dominant kernel roofline
+    peaks = load_peaks()
+    kname = "assign_tc" if "assign_tc" in prof else "assign_simt"
+    kl, kms = prof.get(kname, (1, float("nan")))
+    k_avg_s = kms / max(kl, 1) * 1e-3
+    if form == "bf16":
+        bytes_k = n * d * 2 + k * d * 2 + n * 4
+        t_hbm = bytes_k / (peaks["hbm_gbs"] * 1e9)
+        t_tc = 2.0 * n * k * d / (peaks["bf16_tflops"] * 1e12)
+        if t_hbm >= t_tc:
+            ach = bytes_k / k_avg_s / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None}
+        else:
+            ach = 2.0 * n * k * d / k_avg_s / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / peaks["bf16_tflops"], "traffic": None}
+    elif kname == "assign_tc":
+        peak = peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0
+        ach = 2.0 * n * k * d / k_avg_s / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "note": "3xTF32: measured BF16 burst x nominal TF32/BF16 ratio / 3"}
+    else:
+        ach = 2.0 * n * k * d / k_avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FFMA_PEAK_TFLOPS, "traffic": None,
+                "note": "FFMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+    roof["kernel"] = kname
+    roof["kernel_ms"] = k_avg_s * 1e3
+    roof["peak_source"] = peaks["source"]
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        Xh = torch.from_numpy(X).pin_memory()
+        Ch_out = torch.empty((k, d), dtype=torch.float32).pin_memory()
+        cost_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        Xd = torch.empty_like(Xg)
+        xn2 = torch.empty(n, dtype=torch.float32, device=dev)
+        Xb2 = torch.empty((n, d), dtype=torch.bfloat16, device=dev) if form == "bf16" else None
+        Ce = C.clone()
+        Cen = torch.empty_like(Ce)
+        lab2 = torch.empty(n, dtype=torch.int32, device=dev)
+        co2 = torch.empty(2, dtype=torch.float64, device=dev)
+
+        def e2e_step():
+            nonlocal Ce, Cen
+            Xd.copy_(Xh, non_blocking=True)
+            B.kmeans_row_norms(Xd, xnorm=xn2, ctx=ctx)
+            if Xb2 is not None:
+                B.kmeans_quantize(Xd, "bf16", Xq=Xb2, ctx=ctx)
+            B.kmeans_assign(Xd, Ce, Xop=Xb2, xnorm=xn2, compute=form, engine=engine, labels=lab2, ctx=ctx)
+            B.kmeans_update(Xd, lab2, Ce, C_new=Cen, cost_old=co2[0:1], cost_new=co2[1:2], ctx=ctx)
+            Ch_out.copy_(Cen, non_blocking=True)
+            cost_h.copy_(co2[1:2], non_blocking=True)
+            Ce, Cen = Cen, Ce
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = a.elapsed_time(b) / args.e2e_steps
+        e2e = {"value": world * F_step / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * d * 4 + 8),
+               "ms_per_step": e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(X, C.cpu().numpy(), args.cpu_seconds)
+
+    if rank == 0:
+        kept = [name for name in prof]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": form, "data": "synthetic",
+            "config": {"workload": f"gaussian mixture n={n} d={d} k={k} (100 components, seed rank), "
+                                   f"one Lloyd iteration per step",
+                       "form": form, "engine": engine,
+                       "l2": "inputs larger than L2 (X is 819 MB FP32 / 410 MB BF16)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks,
+            "kernels_ms": {name: prof[name][1] / max(prof[name][0], 1) for name in kept},
+            "points_per_s": world * n / (ms_step * 1e-3),
+            "rechecked_per_step": float(np.mean(rechecked[args.warmup:args.warmup + args.steps])),
+            "cost_last": float(costs[args.warmup + args.steps - 1, 1]) if args.steps else None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

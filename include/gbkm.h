@@ -1,0 +1,200 @@
+/*
+ * gbkm.h -- C ABI of the GB300 (sm_103a) k-means hot-path library.
+ *
+ * The library computes the data-parallel core of the high-dimensional k-means
+ * pipeline of "Solving k-means on High-dimensional Big Data" (Kappmeier,
+ * Schmidt, Schmidt): projection of point blocks onto a low-rank subspace
+ * (Section 2.2), k-means++ D^2 seeding (Section 1), Lloyd's assignment and
+ * centroid steps (Section 1), clustering-feature sums and the k-means cost
+ * (Section 2.1, Section 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Points are the ROWS of a row-major n x d matrix (leading dimension d).
+ *    Centers are a row-major k x d FP32 matrix.  Labels are int32 in [0, k).
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *    argument's comment says "host".  Scalar outputs (costs, counters) are
+ *    device pointers too, so that a whole Lloyd loop runs without a host
+ *    synchronisation.  Optional outputs may be NULL.
+ *  - Calls are asynchronous on the context's stream (gbkm_create /
+ *    gbkm_set_stream).  The library allocates only its own grow-only
+ *    workspace; the first call of a given size may allocate (and synchronise
+ *    the stream while it grows), later calls of the same or smaller size do not.
+ *  - Return value: GBKM_OK, or a negative gbkm_status.  Argument errors are
+ *    detected before any launch and leave every output untouched;
+ *    gbkm_last_error() then holds a message.  Conditions detected on the
+ *    device (a bounded wait that timed out, a degenerate seeding input) are
+ *    recorded in a device status word and reported by the next gbkm_sync().
+ *  - n, d, k >= 1 unless stated otherwise; n * d < 2^40; k <= 65536.
+ *  - Arithmetic: see each call.  Only cluster sums and costs use FP64.
+ */
+#ifndef GBKM_H
+#define GBKM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbkm_ctx gbkm_ctx;
+
+typedef enum {
+    GBKM_OK = 0,
+    GBKM_EINVAL = -1,         /* bad argument (size, NULL, alignment, dtype) */
+    GBKM_ENOMEM = -2,         /* workspace allocation failed */
+    GBKM_ECUDA = -3,          /* a CUDA runtime call failed (message in gbkm_last_error) */
+    GBKM_ETIMEOUT = -4,       /* a bounded device-side wait gave up */
+    GBKM_EUNSUPPORTED = -5,   /* shape or dtype outside what this build supports */
+    GBKM_EDEGENERATE = -6     /* k-means++: fewer than k points with positive D^2 */
+} gbkm_status;
+
+typedef enum {
+    GBKM_F32 = 0,       /* float */
+    GBKM_BF16 = 1,      /* bfloat16, round to nearest even */
+    GBKM_FP8E4M3 = 2    /* E4M3 (no inf, max 448) with one power-of-two FP32 scale per row block */
+} gbkm_dtype;
+
+typedef enum {
+    GBKM_ENGINE_AUTO = 0,     /* tcgen05 where the shape allows it, else SIMT */
+    GBKM_ENGINE_SIMT = 1,     /* CUDA-core FFMA tiles (FP32 operands only) */
+    GBKM_ENGINE_TCGEN05 = 2   /* tensor-core tiles: TMA -> SMEM -> tcgen05.mma -> TMEM */
+} gbkm_engine;
+
+/* options of kmeans_assign */
+typedef struct {
+    int32_t compute;    /* gbkm_dtype of the distance-GEMM operands */
+    int32_t engine;     /* gbkm_engine */
+    int32_t recheck;    /* 1 (default): re-resolve certified near-ties exactly from FP32 data */
+    int32_t reserved;
+} gbkm_assign_opts;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context; the caller destroys it with gbkm_destroy. */
+int gbkm_create(gbkm_ctx **out, int device, void *cuda_stream);
+int gbkm_destroy(gbkm_ctx *ctx);
+int gbkm_set_stream(gbkm_ctx *ctx, void *cuda_stream);
+/* Message of the last error on this context ("" if none).  Owned by ctx. */
+const char *gbkm_last_error(const gbkm_ctx *ctx);
+/* Wait for the context's stream, then report (and clear) the device status
+ * word: GBKM_OK, GBKM_ETIMEOUT, GBKM_EDEGENERATE or GBKM_ECUDA. */
+int gbkm_sync(gbkm_ctx *ctx);
+/* Number of this library's kernel launches issued on ctx since creation. */
+int64_t gbkm_launch_count(const gbkm_ctx *ctx);
+/* Library version as major*10000 + minor*100 + patch. */
+int gbkm_version(void);
+
+/* ------------------------------------------------------------------ A1: row norms */
+
+/* xnorm[i] = ||x_i||^2 (Section 2.1: the sum-of-squares term of a clustering
+ * feature), FP32 output from FP32 products summed in FP32 per lane and a warp
+ * tree.  X: n x d FP32.  xnorm: n FP32. */
+int kmeans_row_norms(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, float *xnorm);
+
+/* ------------------------------------------------------------------ A0: operand quantisation */
+
+/* Copy of X in a lower-precision operand format (precision form of the
+ * distance and projection GEMMs; no paper counterpart).
+ *   dtype == GBKM_BF16:    Xq is n x d bfloat16 (round to nearest even); scales unused.
+ *   dtype == GBKM_FP8E4M3: Xq is n x d E4M3 bytes; scales is n x ceil(d/128) FP32,
+ *     scale = 2^e with e the smallest integer such that the block's max |x| * 2^-e
+ *     <= 448 (1 for an all-zero block); x ~= scale * e4m3(q), round to nearest even.
+ * X: n x d FP32.  Xq must be 16-byte aligned. */
+int kmeans_quantize(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, int32_t dtype,
+                    void *Xq, float *scales);
+
+/* ------------------------------------------------------------------ A2: block projection */
+
+/* Projection of a block of points onto the span of V (Section 2.2: the best-fit
+ * subspace projection A_l = U D_l V^T; here V is given, d x r with orthonormal
+ * columns, for example the top-r right singular vectors of a piece):
+ *   Y = X V         (n x r FP32, the r-dimensional coordinates)
+ *   X_lift = Y V^T  (n x d FP32, the paper's d-dimensional A_l; NULL to skip).
+ * X is n x d in dtype xt (GBKM_F32: the tensor cores read it as TF32;
+ * GBKM_BF16: bfloat16) and V is d x r FP32 (rounded to xt's format for the
+ * product).  Accumulation is FP32.  r must be a multiple of 16 and <= 256 for
+ * the tensor-core engine; other r use the SIMT engine (FP32 X only). */
+int kmeans_project_block(gbkm_ctx *ctx, const void *X, int32_t xt, int64_t n, int64_t d,
+                         const float *V, int64_t r, float *Y, float *X_lift);
+
+/* ------------------------------------------------------------------ A3: k-means++ seeding */
+
+/* k-means++ seeding (Section 1).  The first center is row floor(u[0] * n), or,
+ * when weights w are given, the first row whose inclusive prefix sum of w
+ * exceeds u[0] * sum(w).  Center j >= 1 is the smallest i whose inclusive
+ * prefix of p_i = w_i * D^2_i exceeds u[j] * sum(p), D^2_i being the squared
+ * distance of x_i to its closest chosen center (if rounding leaves no such i,
+ * the last i with p_i > 0).  D^2 is evaluated from direct differences with
+ * error-free FP32 transformations (accurate to ~2^-44 relative) and summed in
+ * FP64 by a two-level block scan; no host synchronisation between rounds.
+ *   X: n x d FP32; w: n FP32 or NULL; u: k FP64 uniforms in [0, 1) (device);
+ *   idx_out: k int64 (device); C_out: k x d FP32 (device), the chosen rows.
+ * If fewer than k rows have positive w * D^2 the remaining idx_out entries
+ * are -1, their C_out rows are left unchanged and gbkm_sync reports
+ * GBKM_EDEGENERATE.  Requires k <= n. */
+int kmeans_seed_pp(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const float *w,
+                   int64_t k, const double *u, int64_t *idx_out, float *C_out);
+
+/* ------------------------------------------------------------------ A4 + A5: assignment */
+
+/* Assignment step of Lloyd's algorithm (Section 1): labels[i] = argmin_j
+ * ||x_i - c_j||^2, ties to the lowest j.  Scores ||c_j||^2 - 2 x_i . c_j come
+ * from a distance GEMM in the operand format opts->compute:
+ *   GBKM_F32:     Xop == X (FP32); SIMT FFMA or tcgen05 3xTF32 (split hi/lo);
+ *   GBKM_BF16:    Xop is the bfloat16 copy of X; tcgen05 kind::f16;
+ *   GBKM_FP8E4M3: Xop is the E4M3 copy with per-row scales (d <= 128 only);
+ *                 tcgen05 kind::f8f6f4, scales applied in the epilogue.
+ * The fused epilogue keeps the best and second-best score per row.  A row is a
+ * certified near-tie when the computed gap is within the worst-case error
+ * bound of the operand format; such rows (opts->recheck != 0) are re-resolved
+ * over all k centers from the FP32 data with error-free transformations, so
+ * every label equals the exact nearest center except where two centers lie
+ * within ~1e-12 relative of each other.
+ *   Xop_scales: per-row scales of an FP8 Xop (n x ceil(d/128)), else NULL.
+ *   X: n x d FP32 (always required: recheck and bounds).
+ *   xnorm: ||x_i||^2 FP32 from kmeans_row_norms, or NULL (then computed here).
+ *   C: k x d FP32.  labels: n int32.  min_d2: n FP32 or NULL, the squared
+ *   distance to the chosen center (expanded form, clamped at 0; exact form on
+ *   rechecked rows).  n_rechecked: 1 int64 or NULL (device), rows rechecked.
+ *   opts: host pointer or NULL (F32, AUTO, recheck on). */
+int kmeans_assign(gbkm_ctx *ctx, const void *Xop, const float *Xop_scales, const float *X,
+                  const float *xnorm, int64_t n, int64_t d, const float *C, int64_t k,
+                  const gbkm_assign_opts *opts, int32_t *labels, float *min_d2,
+                  int64_t *n_rechecked);
+
+/* ------------------------------------------------------------------ A6 + A7: update and cost */
+
+/* Centroid step of Lloyd's algorithm (Section 1; Section 2: mu(P) = sum x/|P|)
+ * through clustering features (Section 2.1): for every cluster j,
+ * N_j = sum w_i, S_j = sum w_i x_i, Q_j = sum w_i ||x_i||^2 over rows labelled j;
+ * C_new[j] = S_j / N_j, or C_old[j] when N_j == 0 (empty cluster keeps its center).
+ * The rows are grouped by a stable counting sort of the labels (per-segment
+ * histograms with warp-aggregated match_any counting, a device-wide scan, a
+ * stable scatter), then each cluster's rows are summed in fixed-size chunks
+ * with error-free FP32 transformations and the chunks combined in FP64 in
+ * chunk order: no floating-point atomics, bit-reproducible.
+ * Costs from the CF identity (Section 2.1), in FP64:
+ *   cost_old = sum_j Q_j - 2 c_old_j . S_j + N_j ||c_old_j||^2 = cost(C_old, labels)
+ *   cost_new = sum_j Q_j - ||S_j||^2 / N_j                      = cost(C_new, labels)
+ *   X: n x d FP32; w: n FP32 or NULL; labels: n int32 in [0, k);
+ *   C_old, C_new: k x d FP32 (may not alias); counts: k FP64 (N_j) or NULL;
+ *   cost_old, cost_new: 1 FP64 each or NULL; n_empty: 1 int64 or NULL.
+ * Labels outside [0, k) are reported as GBKM_EINVAL by gbkm_sync. */
+int kmeans_update(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const float *w,
+                  const int32_t *labels, int64_t k, const float *C_old, float *C_new,
+                  double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
+
+/* k-means objective (Section 1): cost = sum_i w_i min_j ||x_i - c_j||^2 (FP64),
+ * evaluated as an exact FP32-operand assignment followed by the CF identity of
+ * Section 2.1 on the resulting clusters.  X: n x d FP32; w: n FP32 or NULL;
+ * C: k x d FP32; cost: 1 FP64 (device). */
+int kmeans_cost(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const float *w,
+                const float *C, int64_t k, double *cost);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBKM_H */

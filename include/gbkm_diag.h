@@ -1,0 +1,33 @@
+/*
+ * gbkm_diag.h -- diagnostics of the GB300 k-means library (no paper counterpart).
+ *
+ * Per-kernel timing with CUDA events recorded on the context's own stream, so
+ * that a caller can measure one kernel's device time inside a longer sequence
+ * without a profiler.  Host-side calls; ctx as in gbkm.h.
+ */
+#ifndef GBKM_DIAG_H
+#define GBKM_DIAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct gbkm_ctx;
+
+/* enable (1) or disable (0) event timing around the library's main kernels:
+ * "assign_simt", "assign_tc", "recheck", "update", "seed", "project", "center_prep".
+ * Enabling clears earlier records. */
+int gbkm_profile_enable(struct gbkm_ctx *ctx, int enable);
+
+/* Synchronise the stream, then write one line per kernel name,
+ * "<name> <launches> <total_ms>\n", into buf (host, len bytes, NUL-terminated,
+ * truncated if short) and clear the records.  Returns the number of names or a
+ * negative gbkm_status. */
+int gbkm_profile_read(struct gbkm_ctx *ctx, char *buf, int64_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBKM_DIAG_H */

@@ -1,0 +1,318 @@
+"""Thin ctypes binding of libgbkm.so (include/gbkm.h).
+
+Argument marshalling only: every function takes torch CUDA tensors, passes
+their device pointers and the current torch stream to the C ABI call of the
+same name, and returns the output tensors.  There is no CPU path: if the
+library is not built, or a tensor is not on the GPU, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+GBKM_OK, GBKM_EINVAL, GBKM_ENOMEM, GBKM_ECUDA, GBKM_ETIMEOUT, GBKM_EUNSUPPORTED, GBKM_EDEGENERATE = (
+    0, -1, -2, -3, -4, -5, -6)
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
+ENGINES = {"auto": 0, "simt": 1, "tcgen05": 2}
+STATUS_NAMES = {0: "GBKM_OK", -1: "GBKM_EINVAL", -2: "GBKM_ENOMEM", -3: "GBKM_ECUDA",
+                -4: "GBKM_ETIMEOUT", -5: "GBKM_EUNSUPPORTED", -6: "GBKM_EDEGENERATE"}
+
+
+class GbkmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class AssignOpts(ct.Structure):
+    _fields_ = [("compute", ct.c_int32), ("engine", ct.c_int32), ("recheck", ct.c_int32),
+                ("reserved", ct.c_int32)]
+
+
+_vp, _i64, _i32 = ct.c_void_p, ct.c_int64, ct.c_int32
+_SIGS = {
+    "gbkm_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, _vp]),
+    "gbkm_destroy": (ct.c_int, [_vp]),
+    "gbkm_set_stream": (ct.c_int, [_vp, _vp]),
+    "gbkm_last_error": (ct.c_char_p, [_vp]),
+    "gbkm_sync": (ct.c_int, [_vp]),
+    "gbkm_launch_count": (ct.c_int64, [_vp]),
+    "gbkm_version": (ct.c_int, []),
+    "gbkm_profile_enable": (ct.c_int, [_vp, ct.c_int]),
+    "gbkm_profile_read": (ct.c_int, [_vp, ct.c_char_p, _i64]),
+    "kmeans_row_norms": (ct.c_int, [_vp, _vp, _i64, _i64, _vp]),
+    "kmeans_quantize": (ct.c_int, [_vp, _vp, _i64, _i64, _i32, _vp, _vp]),
+    "kmeans_project_block": (ct.c_int, [_vp, _vp, _i32, _i64, _i64, _vp, _i64, _vp, _vp]),
+    "kmeans_seed_pp": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp, _vp]),
+    "kmeans_assign": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _vp, _i64,
+                                 ct.POINTER(AssignOpts), _vp, _vp, _vp]),
+    "kmeans_update": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "kmeans_cost": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libgbkm.so (building it first if asked).  Raises if it is not there."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgbkm.so is not built ({path}); run paper_1502_04265_gb300.build.build()")
+        L = ct.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("libgbkm takes CUDA tensors only (no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous (row-major)")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _req(t, dtype, shape=None, name="tensor"):
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class Context:
+    """Owns one gbkm_ctx on a device; every call binds it to torch's current stream."""
+
+    def __init__(self, device=None):
+        L = load()
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        h = ct.c_void_p()
+        with torch.cuda.device(dev):
+            stream = torch.cuda.current_stream(dev).cuda_stream
+            rc = L.gbkm_create(ct.byref(h), dev.index, ct.c_void_p(stream))
+        if rc != GBKM_OK:
+            raise GbkmError(rc, "gbkm_create failed")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bind_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        load().gbkm_set_stream(self._h, ct.c_void_p(s))
+
+    def check(self, rc):
+        if rc != GBKM_OK:
+            msg = load().gbkm_last_error(self._h).decode()
+            raise GbkmError(rc, msg)
+
+    def sync(self):
+        """Wait for the stream and raise on a device-reported status."""
+        self.bind_stream()
+        self.check(load().gbkm_sync(self._h))
+
+    def launch_count(self) -> int:
+        return int(load().gbkm_launch_count(self._h))
+
+    def profile(self, enable: bool = True):
+        """Turn on per-kernel CUDA-event timing on this context's stream."""
+        self.check(load().gbkm_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total ms)} since the last read; synchronises the stream."""
+        self.bind_stream()
+        buf = ct.create_string_buffer(1 << 14)
+        rc = load().gbkm_profile_read(self._h, buf, len(buf))
+        if rc < 0:
+            self.check(rc)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, n, ms = line.split()
+            out[name] = (int(n), float(ms))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gbkm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context(device=None) -> Context:
+    idx = torch.cuda.current_device() if device is None else torch.device(device).index
+    if idx not in _default_ctx:
+        _default_ctx[idx] = Context(idx)
+    return _default_ctx[idx]
+
+
+def _ctx(ctx, ref):
+    c = ctx or default_context(ref.device)
+    c.bind_stream()
+    return c
+
+
+def gbkm_sync(ctx=None):
+    (ctx or default_context()).sync()
+
+
+def gbkm_version() -> int:
+    return int(load().gbkm_version())
+
+
+# ------------------------------------------------------------------ A1
+def kmeans_row_norms(X, xnorm=None, ctx=None):
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    if xnorm is None:
+        xnorm = torch.empty(n, dtype=torch.float32, device=X.device)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_row_norms(c.handle, _ptr(X), n, d, _ptr(xnorm)))
+    return xnorm
+
+
+# ------------------------------------------------------------------ A0
+def kmeans_quantize(X, dtype="bf16", Xq=None, scales=None, ctx=None):
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    if dtype == "bf16":
+        Xq = Xq if Xq is not None else torch.empty((n, d), dtype=torch.bfloat16, device=X.device)
+    elif dtype == "fp8":
+        Xq = Xq if Xq is not None else torch.empty((n, d), dtype=torch.uint8, device=X.device)
+        nb = (d + 127) // 128
+        scales = scales if scales is not None else torch.empty((n, nb), dtype=torch.float32, device=X.device)
+    else:
+        raise ValueError("dtype must be 'bf16' or 'fp8'")
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_quantize(c.handle, _ptr(X), n, d, DTYPES[dtype], _ptr(Xq), _ptr(scales)))
+    return Xq, scales
+
+
+# ------------------------------------------------------------------ A2
+def kmeans_project_block(X, V, Y=None, X_lift=None, lift=False, ctx=None):
+    if X.dtype == torch.float32:
+        xt = 0
+    elif X.dtype == torch.bfloat16:
+        xt = 1
+    else:
+        raise TypeError("X must be float32 or bfloat16")
+    n, d = X.shape
+    _req(V, torch.float32, name="V")
+    r = V.shape[1]
+    if V.shape[0] != d:
+        raise ValueError("V must be d x r")
+    if Y is None:
+        Y = torch.empty((n, r), dtype=torch.float32, device=X.device)
+    if lift and X_lift is None:
+        X_lift = torch.empty((n, d), dtype=torch.float32, device=X.device)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_project_block(c.handle, _ptr(X), xt, n, d, _ptr(V), r, _ptr(Y), _ptr(X_lift)))
+    return (Y, X_lift) if X_lift is not None else Y
+
+
+# ------------------------------------------------------------------ A3
+def kmeans_seed_pp(X, k, u, w=None, idx_out=None, C_out=None, ctx=None):
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    _req(u, torch.float64, name="u")
+    if u.numel() < k:
+        raise ValueError("u needs k uniforms")
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
+    idx_out = idx_out if idx_out is not None else torch.empty(k, dtype=torch.int64, device=X.device)
+    C_out = C_out if C_out is not None else torch.empty((k, d), dtype=torch.float32, device=X.device)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_seed_pp(c.handle, _ptr(X), n, d, _ptr(w), k, _ptr(u), _ptr(idx_out), _ptr(C_out)))
+    return idx_out, C_out
+
+
+# ------------------------------------------------------------------ A4 + A5
+def kmeans_assign(X, C, Xop=None, Xop_scales=None, xnorm=None, compute="f32", engine="auto",
+                  recheck=True, labels=None, min_d2=None, n_rechecked=None, ctx=None):
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    _req(C, torch.float32, name="C")
+    k = C.shape[0]
+    if C.shape[1] != d:
+        raise ValueError("C must be k x d")
+    if compute == "bf16":
+        _req(Xop, torch.bfloat16, (n, d), "Xop")
+    elif compute == "fp8":
+        _req(Xop, torch.uint8, (n, d), "Xop")
+    if xnorm is not None:
+        _req(xnorm, torch.float32, (n,), "xnorm")
+    labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=X.device)
+    opts = AssignOpts(DTYPES[compute], ENGINES[engine], 1 if recheck else 0, 0)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_assign(c.handle, _ptr(Xop), _ptr(Xop_scales), _ptr(X), _ptr(xnorm), n, d,
+                                 _ptr(C), k, ct.byref(opts), _ptr(labels), _ptr(min_d2),
+                                 _ptr(n_rechecked)))
+    return labels
+
+
+# ------------------------------------------------------------------ A6 + A7
+def kmeans_update(X, labels, C_old, w=None, C_new=None, counts=None, cost_old=None, cost_new=None,
+                  n_empty=None, ctx=None):
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    _req(labels, torch.int32, (n,), "labels")
+    _req(C_old, torch.float32, name="C_old")
+    k = C_old.shape[0]
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
+    dev = X.device
+    C_new = C_new if C_new is not None else torch.empty_like(C_old)
+    counts = counts if counts is not None else torch.empty(k, dtype=torch.float64, device=dev)
+    cost_old = cost_old if cost_old is not None else torch.empty(1, dtype=torch.float64, device=dev)
+    cost_new = cost_new if cost_new is not None else torch.empty(1, dtype=torch.float64, device=dev)
+    n_empty = n_empty if n_empty is not None else torch.empty(1, dtype=torch.int64, device=dev)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_update(c.handle, _ptr(X), n, d, _ptr(w), _ptr(labels), k, _ptr(C_old),
+                                 _ptr(C_new), _ptr(counts), _ptr(cost_old), _ptr(cost_new),
+                                 _ptr(n_empty)))
+    return {"C_new": C_new, "counts": counts, "cost_old": cost_old, "cost_new": cost_new,
+            "n_empty": n_empty}
+
+
+def kmeans_cost(X, C, w=None, cost=None, ctx=None):
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    _req(C, torch.float32, name="C")
+    cost = cost if cost is not None else torch.empty(1, dtype=torch.float64, device=X.device)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_cost(c.handle, _ptr(X), n, d, _ptr(w), _ptr(C), C.shape[0], _ptr(cost)))
+    return cost

@@ -1,0 +1,393 @@
+// api.cu -- the C ABI declared in include/gbkm.h: context, workspace, argument checks and the
+// orchestration of the kernels of one call on the context's stream.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.cuh"
+
+#define GBKM_VERSION 10000
+
+int set_error(gbkm_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_check(gbkm_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return GBKM_OK;
+    return set_error(c, GBKM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *ws_reserve(gbkm_ctx *c, size_t bytes, int *rc) {
+    if (bytes <= c->ws_bytes) return c->ws;
+    cudaError_t e = cudaStreamSynchronize(c->stream);  // the old block may still be in use
+    if (e != cudaSuccess) {
+        *rc = cuda_check(c, e, "workspace sync");
+        return nullptr;
+    }
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    size_t want = bytes + (bytes >> 3) + (1 << 20);
+    e = cudaMalloc(&c->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *rc = set_error(c, GBKM_ENOMEM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+        return nullptr;
+    }
+    c->ws_bytes = want;
+    return c->ws;
+}
+
+void prof_begin(gbkm_ctx *c, const char *name) {
+    if (!c->prof) return;
+    while (c->pool.size() < c->pool_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        c->pool.push_back(e);
+    }
+    ProfRec r{name, c->pool[c->pool_used], c->pool[c->pool_used + 1]};
+    c->pool_used += 2;
+    cudaEventRecord(r.a, c->stream);
+    c->recs.push_back(r);
+}
+
+void prof_end(gbkm_ctx *c) {
+    if (!c->prof || c->recs.empty()) return;
+    cudaEventRecord(c->recs.back().b, c->stream);
+}
+
+namespace {
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// worst-case relative error coefficients of the distance scores of each operand format:
+// |score_err| <= err_rel ||x|| max||c|| + err_abs max||c||^2 (see the certified near-tie rule)
+void score_error_coeffs(int dtype, int engine_tc, int64_t d, float &err_rel, float &err_abs) {
+    const double u = ldexp(1.0, -24);
+    double dot;
+    if (!engine_tc) {
+        // FP32 FFMA chain: gamma_d = d u / (1 - d u)
+        dot = (double)d * u / (1.0 - (double)d * u);
+    } else if (dtype == GBKM_F32) {
+        // 3xTF32: representation error 3.01 * 2^-20, accumulation of 3d terms at 2^-22 each
+        dot = 3.01 * ldexp(1.0, -20) + 3.0 * (double)d * ldexp(1.0, -22) * 1.003;
+    } else if (dtype == GBKM_BF16) {
+        const double uq = ldexp(1.0, -8);
+        dot = 2 * uq + uq * uq + (double)d * ldexp(1.0, -22) * (1 + uq) * (1 + uq);
+    } else {
+        // E4M3 with power-of-two per-row scales, d <= 128: normal range 2^-4, subnormal absolute
+        // term folded in via max|x|/448 <= ||x||/224; accumulation assumed no better than 14 bits
+        const double uq = ldexp(1.0, -4);
+        dot = 2 * uq + uq * uq + 2.0 * ldexp(1.0, -10) * sqrt((double)d) / 224.0 * (1 + uq) +
+              ldexp(1.0, -20) * (double)d / (224.0 * 224.0) + (double)d * ldexp(1.0, -13) * 1.3;
+    }
+    err_rel = (float)((2.0 * dot + 2.0 * u) * (1.0 + 1e-3));
+    err_abs = (float)(3.0 * u * (1.0 + 1e-3));
+}
+}  // namespace
+
+extern "C" {
+
+int gbkm_version(void) { return GBKM_VERSION; }
+
+int gbkm_create(gbkm_ctx **out, int device, void *cuda_stream) {
+    if (!out) return GBKM_EINVAL;
+    *out = nullptr;
+    gbkm_ctx *c = new (std::nothrow) gbkm_ctx();
+    if (!c) return GBKM_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(device);
+    cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->status, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (c->status) cudaFree(c->status);
+        delete c;
+        return GBKM_ECUDA;
+    }
+    *out = c;
+    return GBKM_OK;
+}
+
+int gbkm_profile_enable(gbkm_ctx *c, int enable) {
+    if (!c) return GBKM_EINVAL;
+    c->prof = enable != 0;
+    c->recs.clear();
+    c->pool_used = 0;
+    return GBKM_OK;
+}
+
+int gbkm_profile_read(gbkm_ctx *c, char *buf, int64_t len) {
+    if (!c || !buf || len < 1) return GBKM_EINVAL;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "profile sync");
+    struct Acc {
+        const char *name;
+        int64_t launches;
+        double ms;
+    };
+    std::vector<Acc> acc;
+    for (const ProfRec &r : c->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        size_t q = 0;
+        while (q < acc.size() && strcmp(acc[q].name, r.name) != 0) ++q;
+        if (q == acc.size()) acc.push_back({r.name, 0, 0.0});
+        acc[q].launches += 1;
+        acc[q].ms += ms;
+    }
+    c->recs.clear();
+    c->pool_used = 0;
+    int64_t off = 0;
+    buf[0] = 0;
+    for (const Acc &a : acc) {
+        int w = snprintf(buf + off, (size_t)(len - off), "%s %lld %.6f\n", a.name, (long long)a.launches, a.ms);
+        if (w < 0 || off + w >= len) break;
+        off += w;
+    }
+    return (int)acc.size();
+}
+
+int gbkm_destroy(gbkm_ctx *c) {
+    if (!c) return GBKM_OK;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->ws) cudaFree(c->ws);
+    if (c->status) cudaFree(c->status);
+    if (c->tmap_scratch) cudaFree(c->tmap_scratch);
+    delete c;
+    return GBKM_OK;
+}
+
+int gbkm_set_stream(gbkm_ctx *c, void *cuda_stream) {
+    if (!c) return GBKM_EINVAL;
+    c->stream = (cudaStream_t)cuda_stream;
+    return GBKM_OK;
+}
+
+const char *gbkm_last_error(const gbkm_ctx *c) { return c ? c->err : "null context"; }
+
+int64_t gbkm_launch_count(const gbkm_ctx *c) { return c ? c->launches : 0; }
+
+int gbkm_sync(gbkm_ctx *c) {
+    if (!c) return GBKM_EINVAL;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "stream synchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_check(c, e, "status read");
+    if (st & ST_TIMEOUT) return set_error(c, GBKM_ETIMEOUT, "a bounded device wait timed out");
+    if (st & ST_BADLABEL) return set_error(c, GBKM_EINVAL, "a label outside [0, k) reached kmeans_update");
+    if (st & ST_BOUNDS) return set_error(c, GBKM_ECUDA, "an internal index check failed");
+    if (st & ST_DEGENERATE)
+        return set_error(c, GBKM_EDEGENERATE, "k-means++: fewer than k points with positive D^2");
+    return GBKM_OK;
+}
+
+int kmeans_row_norms(gbkm_ctx *c, const float *X, int64_t n, int64_t d, float *xnorm) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || !X || !xnorm) return set_error(c, GBKM_EINVAL, "row_norms: bad arguments");
+    DeviceGuard g(c->device);
+    return gbkm::launch_row_norms(c, X, n, d, xnorm);
+}
+
+int kmeans_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int32_t dtype, void *Xq,
+                    float *scales) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || !X || !Xq) return set_error(c, GBKM_EINVAL, "quantize: bad arguments");
+    if (dtype != GBKM_BF16 && dtype != GBKM_FP8E4M3)
+        return set_error(c, GBKM_EINVAL, "quantize: dtype must be BF16 or FP8E4M3");
+    if (dtype == GBKM_FP8E4M3 && !scales) return set_error(c, GBKM_EINVAL, "quantize: FP8 needs scales");
+    if (!aligned16(Xq)) return set_error(c, GBKM_EINVAL, "quantize: Xq must be 16-byte aligned");
+    DeviceGuard g(c->device);
+    return gbkm::launch_quantize(c, X, n, d, dtype, Xq, scales);
+}
+
+int kmeans_project_block(gbkm_ctx *c, const void *X, int32_t xt, int64_t n, int64_t d,
+                         const float *V, int64_t r, float *Y, float *X_lift) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || r < 1 || r > d || !X || !V || !Y)
+        return set_error(c, GBKM_EINVAL, "project_block: bad arguments");
+    if (xt != GBKM_F32 && xt != GBKM_BF16)
+        return set_error(c, GBKM_EINVAL, "project_block: X dtype must be F32 or BF16");
+    DeviceGuard g(c->device);
+    int rc;
+    prof_begin(c, "project");
+    if (gbkm::tc_project_supported(xt, d, r) && aligned16(X)) {
+        rc = gbkm::launch_project_tc(c, xt, X, n, d, V, r, Y);
+    } else if (xt == GBKM_F32) {
+        // Y[n x r] = X V: B addressed as V[kk * r + nn]
+        rc = gbkm::launch_gemm_simt_strided(c, (const float *)X, V, n, r, d, 1, r, Y);
+    } else {
+        prof_end(c);
+        return set_error(c, GBKM_EUNSUPPORTED, "project_block: BF16 X needs r %% 16 == 0, r <= 256, d %% 64 == 0");
+    }
+    prof_end(c);
+    if (rc != GBKM_OK || !X_lift) return rc;
+    // X_lift[n x d] = Y V^T: B = V as an N x K (d x r) row-major matrix
+    return gbkm::launch_gemm_simt_strided(c, Y, V, n, d, r, r, 1, X_lift);
+}
+
+int kmeans_seed_pp(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, int64_t k,
+                   const double *u, int64_t *idx_out, float *C_out) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || k < 1 || k > n || !X || !u || !idx_out || !C_out)
+        return set_error(c, GBKM_EINVAL, "seed_pp: bad arguments (need 1 <= k <= n)");
+    DeviceGuard g(c->device);
+    prof_begin(c, "seed");
+    int rc = gbkm::seed_impl(c, X, n, d, w, k, u, idx_out, C_out);
+    prof_end(c);
+    return rc;
+}
+
+int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const float *X,
+                  const float *xnorm, int64_t n, int64_t d, const float *C, int64_t k,
+                  const gbkm_assign_opts *opts, int32_t *labels, float *min_d2, int64_t *n_rechecked) {
+    if (!c) return GBKM_EINVAL;
+    gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 0};
+    if (opts) o = *opts;
+    if (n < 1 || d < 1 || k < 1 || k > 65536 || !X || !C || !labels)
+        return set_error(c, GBKM_EINVAL, "assign: bad arguments");
+    if (o.compute != GBKM_F32 && o.compute != GBKM_BF16 && o.compute != GBKM_FP8E4M3)
+        return set_error(c, GBKM_EINVAL, "assign: unknown compute dtype %d", o.compute);
+    if (o.compute != GBKM_F32 && !Xop) return set_error(c, GBKM_EINVAL, "assign: Xop required");
+    if (o.compute == GBKM_FP8E4M3 && (!Xop_scales || d > 128))
+        return set_error(c, GBKM_EINVAL, "assign: FP8 needs per-row scales and d <= 128");
+    if (!Xop) Xop = X;
+    const bool tc_ok = gbkm::tc_assign_supported(o.compute, d, k) && aligned16(Xop);
+    bool use_tc;
+    if (o.engine == GBKM_ENGINE_SIMT) {
+        if (o.compute != GBKM_F32) return set_error(c, GBKM_EUNSUPPORTED, "assign: SIMT engine is FP32 only");
+        use_tc = false;
+    } else if (o.engine == GBKM_ENGINE_TCGEN05) {
+        if (!tc_ok) return set_error(c, GBKM_EUNSUPPORTED, "assign: shape/dtype not supported by tcgen05 engine");
+        use_tc = true;
+    } else {
+        use_tc = tc_ok;
+        if (!use_tc && o.compute != GBKM_F32)
+            return set_error(c, GBKM_EUNSUPPORTED, "assign: low-precision forms need the tcgen05 engine");
+    }
+    DeviceGuard g(c->device);
+    const int64_t k_pad = use_tc ? ceil_div(k, 16) * 16 : k;
+    const size_t esz = o.compute == GBKM_BF16 ? 2 : (o.compute == GBKM_FP8E4M3 ? 1 : 4);
+    WsPlan p;
+    size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(1),
+           o_cop = p.take<char>(use_tc ? k_pad * d * esz : 0),
+           o_clo = p.take<float>(use_tc && o.compute == GBKM_F32 ? k_pad * d : 0),
+           o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_fc = p.take<int32_t>(1);
+    int rc = GBKM_OK;
+    void *ws = ws_reserve(c, p.off, &rc);
+    if (!ws) return rc;
+    float *xn = xnorm ? const_cast<float *>(xnorm) : ws_at<float>(ws, o_xn);
+    if (!xnorm && (rc = gbkm::launch_row_norms(c, X, n, d, xn)) != GBKM_OK) return rc;
+    gbkm::CenterPrep cp;
+    cp.cnorm = ws_at<float>(ws, o_cn);
+    cp.cmax = ws_at<unsigned>(ws, o_cm);
+    cp.cop = use_tc ? ws_at<void>(ws, o_cop) : nullptr;
+    cp.cop_lo = (use_tc && o.compute == GBKM_F32) ? ws_at<void>(ws, o_clo) : nullptr;
+    cp.cscale = ws_at<float>(ws, o_cs);
+    prof_begin(c, "center_prep");
+    rc = gbkm::launch_center_prep(c, C, k, d, o.compute, k_pad, cp);
+    prof_end(c);
+    if (rc != GBKM_OK) return rc;
+    gbkm::AssignOut out;
+    out.labels = labels;
+    out.min_d2 = min_d2;
+    out.flag_list = o.recheck ? ws_at<int32_t>(ws, o_fl) : nullptr;
+    out.flag_count = ws_at<int32_t>(ws, o_fc);
+    cudaError_t e = cudaMemsetAsync(out.flag_count, 0, sizeof(int32_t), c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "memset flag count");
+    float err_rel, err_abs;
+    score_error_coeffs(o.compute, use_tc, d, err_rel, err_abs);
+    prof_begin(c, use_tc ? "assign_tc" : "assign_simt");
+    if (use_tc)
+        rc = gbkm::launch_assign_tc(c, o.compute, Xop, Xop_scales, X, xn, n, d, cp, k, k_pad, err_rel,
+                                    err_abs, out);
+    else
+        rc = gbkm::launch_assign_simt(c, X, xn, n, d, C, cp.cnorm, cp.cmax, k, err_rel, err_abs, out);
+    prof_end(c);
+    if (rc != GBKM_OK) return rc;
+    if (o.recheck) {
+        prof_begin(c, "recheck");
+        rc = gbkm::launch_recheck(c, X, n, d, C, k, out, n_rechecked);
+        prof_end(c);
+        return rc;
+    }
+    if (n_rechecked) {
+        e = cudaMemsetAsync(n_rechecked, 0, sizeof(int64_t), c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "memset n_rechecked");
+    }
+    return GBKM_OK;
+}
+
+int kmeans_update(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
+                  const int32_t *labels, int64_t k, const float *C_old, float *C_new, double *counts,
+                  double *cost_old, double *cost_new, int64_t *n_empty) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || k < 1 || k > 65536 || !X || !labels || !C_old || !C_new || C_old == C_new)
+        return set_error(c, GBKM_EINVAL, "update: bad arguments");
+    if (n >= ((int64_t)1 << 31)) return set_error(c, GBKM_EUNSUPPORTED, "update: n >= 2^31");
+    DeviceGuard g(c->device);
+    prof_begin(c, "update");
+    int rc = gbkm::update_impl(c, X, n, d, w, labels, k, C_old, C_new, counts, cost_old, cost_new, n_empty);
+    prof_end(c);
+    return rc;
+}
+
+int kmeans_cost(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, const float *C,
+                int64_t k, double *cost) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || k < 1 || k > 65536 || !X || !C || !cost)
+        return set_error(c, GBKM_EINVAL, "cost: bad arguments");
+    DeviceGuard g(c->device);
+    // private scratch for the labels and a throwaway center copy, kept in its own allocation so
+    // that the update's workspace plan does not overlap it
+    int32_t *labels = nullptr;
+    float *Cn = nullptr;
+    cudaError_t e = cudaMallocAsync(&labels, sizeof(int32_t) * n, c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&Cn, sizeof(float) * k * d, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (labels) cudaFreeAsync(labels, c->stream);
+        return set_error(c, GBKM_ENOMEM, "cost: scratch allocation failed");
+    }
+    gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 0};
+    int rc = kmeans_assign(c, X, nullptr, X, nullptr, n, d, C, k, &o, labels, nullptr, nullptr);
+    if (rc == GBKM_OK) rc = kmeans_update(c, X, n, d, w, labels, k, C, Cn, nullptr, cost, nullptr, nullptr);
+    cudaFreeAsync(labels, c->stream);
+    cudaFreeAsync(Cn, c->stream);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// internal.cuh -- context, workspace and device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/gbkm.h"
+#include "../../include/gbkm_diag.h"
+
+// ---------------------------------------------------------------- device status word bits
+enum : int {
+    ST_TIMEOUT = 1,      // a bounded wait gave up
+    ST_DEGENERATE = 2,   // k-means++ ran out of points with positive D^2
+    ST_BADLABEL = 4,     // a label outside [0, k) reached the update
+    ST_BOUNDS = 8,       // an internal index check failed (access skipped)
+};
+
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+struct gbkm_ctx {
+    int device = 0;
+    bool prof = false;              // per-kernel CUDA-event timing on the context's stream
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    cudaStream_t stream = nullptr;
+    char err[512] = {0};
+    void *ws = nullptr;          // grow-only workspace
+    size_t ws_bytes = 0;
+    int *status = nullptr;       // device status word
+    int sm_count = 0;
+    int64_t launches = 0;
+    void *tmap_scratch = nullptr;  // device copy of tensor maps (128 B aligned, 16 slots)
+};
+
+int set_error(gbkm_ctx *c, int code, const char *fmt, ...);
+int cuda_check(gbkm_ctx *c, cudaError_t e, const char *what);
+// returns a pointer to >= bytes of workspace (grows, synchronising the stream, if needed)
+void *ws_reserve(gbkm_ctx *c, size_t bytes, int *rc);
+
+// bump sub-allocator over a workspace block, 256-byte aligned slices
+struct WsPlan {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count) {
+        size_t o = off;
+        off += ((count * sizeof(T) + 255) / 256) * 256;
+        return o;
+    }
+};
+template <class T>
+static inline T *ws_at(void *base, size_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+#define GBKM_LAUNCHED(ctx) ((ctx)->launches += 1)
+
+// bracket a kernel (or a short sequence of kernels) with events when profiling is on
+void prof_begin(gbkm_ctx *c, const char *name);
+void prof_end(gbkm_ctx *c);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void status_raise(int *status, int bit) {
+    if (status) atomicOr(status, bit);
+}
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// double-float accumulator: hi + lo carries the running sum
+struct DF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float s, e;
+        two_sum(hi, v, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    // add the exact product a*b (TwoProd via fma)
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        float p = __fmul_rn(a, b);
+        float pe = __fmaf_rn(a, b, -p);
+        add(p);
+        lo = __fadd_rn(lo, pe);
+    }
+    // add (x - c)^2 with the difference and the square resolved error-free
+    __device__ __forceinline__ void add_sqdiff(float x, float c) {
+        float s, e;
+        two_sum(x, -c, s, e);           // x - c == s + e exactly
+        float p = __fmul_rn(s, s);
+        float pe = __fmaf_rn(s, s, -p);  // s*s == p + pe exactly
+        float q = __fmul_rn(__fmul_rn(2.f, s), e);
+        add(p);
+        lo = __fadd_rn(lo, __fadd_rn(pe, q));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- host-side launch helpers
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// kernel entry points implemented in the .cu files (host launchers)
+namespace gbkm {
+int launch_row_norms(gbkm_ctx *c, const float *X, int64_t n, int64_t d, float *xnorm);
+int launch_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int dtype, void *Xq,
+                    float *scales);
+// center preparation: ||c||^2 (FP32 from FP64 sums), max ||c|| (as float bits), optional
+// operand copies (bf16 / fp8 with per-row scale / tf32 hi-lo split)
+struct CenterPrep {
+    float *cnorm;       // k
+    unsigned *cmax;     // 1: max ||c_j|| as float bits
+    void *cop;          // operand copy (k_pad x d) or null
+    void *cop_lo;       // tf32 low part or null
+    float *cscale;      // fp8 per-row scales or null
+};
+int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dtype,
+                       int64_t k_pad, const CenterPrep &cp);
+
+struct AssignOut {
+    int32_t *labels;
+    float *min_d2;
+    int32_t *flag_list;   // n entries max
+    int32_t *flag_count;  // 1
+};
+int launch_assign_simt(gbkm_ctx *c, const float *X, const float *xnorm, int64_t n, int64_t d,
+                       const float *C, const float *cnorm, const unsigned *cmax, int64_t k,
+                       float err_rel, float err_abs, const AssignOut &o);
+// Out[M x N] = A[M x K] B^T with B[nn * sbn + kk * sbk]
+int launch_gemm_simt_strided(gbkm_ctx *c, const float *A, const float *B, int64_t M, int64_t N,
+                             int64_t K, int64_t sbn, int64_t sbk, float *Out);
+int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
+                   const AssignOut &o, int64_t *n_rechecked);
+
+int update_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
+                const int32_t *labels, int64_t k, const float *C_old, float *C_new,
+                double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
+int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, int64_t k,
+              const double *u, int64_t *idx_out, float *C_out);
+bool tc_assign_supported(int dtype, int64_t d, int64_t k);
+int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscales,
+                     const float *X, const float *xnorm, int64_t n, int64_t d,
+                     const CenterPrep &cp, int64_t k, int64_t k_pad, float err_rel,
+                     float err_abs, const AssignOut &o);
+bool tc_project_supported(int dtype, int64_t d, int64_t r);
+int launch_project_tc(gbkm_ctx *c, int dtype, const void *X, int64_t n, int64_t d,
+                      const float *V, int64_t r, float *Y);
+}  // namespace gbkm

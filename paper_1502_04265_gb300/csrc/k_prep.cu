@@ -1,0 +1,211 @@
+// k_prep.cu -- A1 row norms, A0 operand quantisation, per-call center preparation.
+#include "internal.cuh"
+
+namespace gbkm {
+
+// ---------------------------------------------------------------- A1: ||x_i||^2
+// One warp per row (grid-stride), 128-bit loads when rows are 16-byte aligned.
+__global__ void __launch_bounds__(256) k_row_norms(const float *__restrict__ X, int64_t n,
+                                                   int64_t d, float *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const float *x = X + i * d;
+        float s = 0.f;
+        if (vec) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(x);
+            for (int64_t t = lane; t < d / 4; t += 32) {
+                float4 v = __ldg(x4 + t);
+                s = fmaf(v.x, v.x, s);
+                s = fmaf(v.y, v.y, s);
+                s = fmaf(v.z, v.z, s);
+                s = fmaf(v.w, v.w, s);
+            }
+        } else {
+            for (int64_t t = lane; t < d; t += 32) s = fmaf(x[t], x[t], s);
+        }
+        s = warp_sum_f(s);
+        if (lane == 0) out[i] = s;
+    }
+}
+
+int launch_row_norms(gbkm_ctx *c, const float *X, int64_t n, int64_t d, float *xnorm) {
+    if (n == 0) return GBKM_OK;
+    int64_t blocks = ceil_div(n, 8);
+    int64_t cap = (int64_t)c->sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    k_row_norms<<<(unsigned)blocks, 256, 0, c->stream>>>(X, n, d, xnorm);
+    GBKM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "row_norms launch");
+}
+
+// ---------------------------------------------------------------- A0: bf16 copy
+__global__ void __launch_bounds__(256) k_to_bf16(const float *__restrict__ X, int64_t m,
+                                                 __nv_bfloat16 *__restrict__ out) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nth = gridDim.x * (int64_t)blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+    int64_t m8 = vec ? m / 8 : 0;
+    for (int64_t g = tid; g < m8; g += nth) {
+        const float4 *src = reinterpret_cast<const float4 *>(X) + 2 * g;
+        float4 a = __ldg(src), b = __ldg(src + 1);
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(a.x, a.y);
+        __nv_bfloat162 p1 = __floats2bfloat162_rn(a.z, a.w);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(b.x, b.y);
+        __nv_bfloat162 p3 = __floats2bfloat162_rn(b.z, b.w);
+        uint4 o;
+        o.x = *reinterpret_cast<uint32_t *>(&p0);
+        o.y = *reinterpret_cast<uint32_t *>(&p1);
+        o.z = *reinterpret_cast<uint32_t *>(&p2);
+        o.w = *reinterpret_cast<uint32_t *>(&p3);
+        reinterpret_cast<uint4 *>(out)[g] = o;
+    }
+    for (int64_t e = m8 * 8 + tid; e < m; e += nth) out[e] = __float2bfloat16_rn(X[e]);
+}
+
+// smallest e with amax * 2^-e <= 448 (e = 0 when amax == 0)
+__device__ __forceinline__ int e4m3_scale_exp(float amax) {
+    if (!(amax > 0.f)) return 0;
+    int e = ilogbf(amax) - 9;
+    while (!(ldexpf(amax, -e) <= 448.f)) ++e;
+    return e;
+}
+
+// ---------------------------------------------------------------- A0: E4M3 copy, one scale per
+// 128-element row block.  One warp per (row, block).
+__global__ void __launch_bounds__(256) k_to_e4m3(const float *__restrict__ X, int64_t n, int64_t d,
+                                                 uint8_t *__restrict__ out, float *__restrict__ scales) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = (d + 127) / 128;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    for (int64_t wb = warp; wb < n * nb; wb += nwarps) {
+        const int64_t i = wb / nb, b = wb % nb;
+        const int64_t t0 = b * 128;
+        float v[4];
+        float amax = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int64_t t = t0 + lane * 4 + q;
+            v[q] = (t < d) ? X[i * d + t] : 0.f;
+            amax = fmaxf(amax, fabsf(v[q]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        const int e = e4m3_scale_exp(amax);
+        if (lane == 0) scales[i * nb + b] = ldexpf(1.f, e);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int64_t t = t0 + lane * 4 + q;
+            if (t < d)
+                out[i * d + t] = (uint8_t)__nv_cvt_float_to_fp8(ldexpf(v[q], -e), __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
+int launch_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int dtype, void *Xq,
+                    float *scales) {
+    if (n == 0) return GBKM_OK;
+    int64_t cap = (int64_t)c->sm_count * 8;
+    if (dtype == GBKM_BF16) {
+        int64_t blocks = ceil_div(n * d, 256 * 8);
+        if (blocks > cap) blocks = cap;
+        k_to_bf16<<<(unsigned)blocks, 256, 0, c->stream>>>(X, n * d, (__nv_bfloat16 *)Xq);
+    } else {
+        int64_t blocks = ceil_div(n * ceil_div(d, 128), 8);
+        if (blocks > cap) blocks = cap;
+        k_to_e4m3<<<(unsigned)blocks, 256, 0, c->stream>>>(X, n, d, (uint8_t *)Xq, scales);
+    }
+    GBKM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "quantize launch");
+}
+
+// ---------------------------------------------------------------- center preparation
+// One CTA per (padded) center row: ||c_j||^2 from error-free FP32 sums (stored FP32),
+// max_j ||c_j|| (rounded up) as float bits, and the operand copy of the row in the
+// GEMM's format.  Rows k..k_pad-1 are zero operands with ||c||^2 = +inf so they never win.
+__global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C, int64_t k,
+                                                     int64_t d, int dtype, CenterPrep cp) {
+    const int64_t j = blockIdx.x;
+    __shared__ double red[8];
+    __shared__ float amax_s[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (j >= k) {
+        for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+            if (dtype == GBKM_BF16 && cp.cop) ((__nv_bfloat16 *)cp.cop)[j * d + t] = __float2bfloat16_rn(0.f);
+            if (dtype == GBKM_FP8E4M3 && cp.cop) ((uint8_t *)cp.cop)[j * d + t] = 0;
+            if (dtype == GBKM_F32 && cp.cop) {
+                ((float *)cp.cop)[j * d + t] = 0.f;
+                ((float *)cp.cop_lo)[j * d + t] = 0.f;
+            }
+        }
+        if (threadIdx.x == 0) {
+            cp.cnorm[j] = __int_as_float(0x7f800000);
+            if (cp.cscale) cp.cscale[j] = 1.f;
+        }
+        return;
+    }
+    const float *c = C + j * d;
+    DF acc;
+    float amax = 0.f;
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+        float v = c[t];
+        acc.add_prod(v, v);
+        amax = fmaxf(amax, fabsf(v));
+    }
+    double s = warp_sum_d(acc.value());
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) {
+        red[wid] = s;
+        amax_s[wid] = amax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        float am = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            tot += red[w];
+            am = fmaxf(am, amax_s[w]);
+        }
+        cp.cnorm[j] = (float)tot;
+        float nrm = (float)sqrt(tot) * (1.f + 1.0e-6f);
+        atomicMax(cp.cmax, __float_as_uint(nrm));
+        amax_s[0] = am;
+    }
+    __syncthreads();
+    if (!cp.cop) return;
+    if (dtype == GBKM_BF16) {
+        for (int64_t t = threadIdx.x; t < d; t += blockDim.x)
+            ((__nv_bfloat16 *)cp.cop)[j * d + t] = __float2bfloat16_rn(c[t]);
+    } else if (dtype == GBKM_FP8E4M3) {
+        const int e = e4m3_scale_exp(amax_s[0]);
+        if (threadIdx.x == 0) cp.cscale[j] = ldexpf(1.f, e);
+        for (int64_t t = threadIdx.x; t < d; t += blockDim.x)
+            ((uint8_t *)cp.cop)[j * d + t] =
+                (uint8_t)__nv_cvt_float_to_fp8(ldexpf(c[t], -e), __NV_SATFINITE, __NV_E4M3);
+    } else {
+        // 3xTF32 split: hi = c truncated to TF32 (19 bits), lo = (c - hi) truncated to TF32
+        for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+            float v = c[t];
+            float hi = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+            float lo = __uint_as_float(__float_as_uint(__fsub_rn(v, hi)) & 0xffffe000u);
+            ((float *)cp.cop)[j * d + t] = hi;
+            ((float *)cp.cop_lo)[j * d + t] = lo;
+        }
+    }
+}
+
+int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dtype,
+                       int64_t k_pad, const CenterPrep &cp) {
+    cudaError_t e = cudaMemsetAsync(cp.cmax, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "memset cmax");
+    k_center_prep<<<(unsigned)k_pad, 256, 0, c->stream>>>(C, k, d, dtype, cp);
+    GBKM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "center_prep launch");
+}
+
+}  // namespace gbkm

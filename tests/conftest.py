@@ -20,3 +20,17 @@ def orc():
     oracle.build()
     oracle.set_threads(min(8, os.cpu_count() or 1))
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gb():
+    """The CUDA binding, built in-tree; skips only when this machine has no GPU at all."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device on this machine")
+    from paper_1502_04265_gb300 import _binding, build
+
+    build.build()
+    _binding.load()
+    return _binding
