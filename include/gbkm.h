@@ -46,7 +46,8 @@ typedef enum {
     GBKM_ECUDA = -3,          /* a CUDA runtime call failed (message in gbkm_last_error) */
     GBKM_ETIMEOUT = -4,       /* a bounded device-side wait gave up */
     GBKM_EUNSUPPORTED = -5,   /* shape or dtype outside what this build supports */
-    GBKM_EDEGENERATE = -6     /* k-means++: fewer than k points with positive D^2 */
+    GBKM_EDEGENERATE = -6,    /* k-means++: fewer than k points with positive D^2 */
+    GBKM_ETOOBIG = -7         /* kmeans_update_noalloc: the problem needs more than its fixed scratch */
 } gbkm_status;
 
 typedef enum {
@@ -186,6 +187,40 @@ int kmeans_assign(gbkm_ctx *ctx, const void *Xop, const float *Xop_scales, const
 int kmeans_update(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const float *w,
                   const int32_t *labels, int64_t k, const float *C_old, float *C_new,
                   double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
+
+/* Fixed device scratch of kmeans_update_noalloc, in bytes (64 MiB). */
+#define GBKM_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* kmeans_update for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this exists for callers that must not call cudaMalloc, for
+ * example code running while the CUDA caching allocator of a host framework is
+ * locked, a memory-capped or pre-reserved serving process, or a real-time loop
+ * in which an allocation (and the synchronisation it can bring) is not allowed.
+ * It computes exactly what kmeans_update computes, with the same kernels and
+ * the same results, but needs no gbkm_ctx and allocates nothing: its scratch is
+ * a fixed GBKM_NOALLOC_SCRATCH_BYTES block compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *  - cuda_stream: a cudaStream_t of the CURRENT device (NULL = legacy stream);
+ *    the work is queued there, asynchronously.  All other pointers are device
+ *    pointers as in kmeans_update and are owned by the caller.
+ *  - The first call on a device looks up the scratch block's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    outside any stream capture.
+ *  - Every call on a device shares the one scratch block, and the block keeps
+ *    the last call's contents (what must start at zero is cleared by the call
+ *    itself).  Calls whose work overlaps on the GPU (two streams, two threads)
+ *    race on the block and corrupt each other: serialise them.
+ *  - Scratch needed (bytes, each term rounded up to 256): 8 k S + 4 ceil(kS/4096)
+ *    + 8 (k+1) + 4 n + 8 (ceil(n/256) + k)(d + 2) + 24 k, with S = ceil(n/R) and
+ *    R the smallest power of two >= 1024 with k ceil(n/R) <= 2^23.  A problem
+ *    that needs more than GBKM_NOALLOC_SCRATCH_BYTES - 256 returns GBKM_ETOOBIG
+ *    before anything is queued (n = 200,000, d = 1,024, k = 100 needs ~8 MB).
+ *  - Labels must lie in [0, k); rows with other labels are left out of the sums
+ *    (no status word is reported, since there is no context).
+ * Returns GBKM_OK, GBKM_EINVAL, GBKM_EUNSUPPORTED, GBKM_ETOOBIG or GBKM_ECUDA. */
+int kmeans_update_noalloc(void *cuda_stream, const float *X, int64_t n, int64_t d, const float *w,
+                          const int32_t *labels, int64_t k, const float *C_old, float *C_new,
+                          double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
 
 /* k-means objective (Section 1): cost = sum_i w_i min_j ||x_i - c_j||^2 (FP64),
  * evaluated as an exact FP32-operand assignment followed by the CF identity of

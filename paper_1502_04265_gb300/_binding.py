@@ -17,10 +17,12 @@ from . import build as _build
 
 GBKM_OK, GBKM_EINVAL, GBKM_ENOMEM, GBKM_ECUDA, GBKM_ETIMEOUT, GBKM_EUNSUPPORTED, GBKM_EDEGENERATE = (
     0, -1, -2, -3, -4, -5, -6)
+GBKM_ETOOBIG = -7
+NOALLOC_SCRATCH_BYTES = 64 << 20
 DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
 ENGINES = {"auto": 0, "simt": 1, "tcgen05": 2}
 STATUS_NAMES = {0: "GBKM_OK", -1: "GBKM_EINVAL", -2: "GBKM_ENOMEM", -3: "GBKM_ECUDA",
-                -4: "GBKM_ETIMEOUT", -5: "GBKM_EUNSUPPORTED", -6: "GBKM_EDEGENERATE"}
+                -4: "GBKM_ETIMEOUT", -5: "GBKM_EUNSUPPORTED", -6: "GBKM_EDEGENERATE", -7: "GBKM_ETOOBIG"}
 
 
 class GbkmError(RuntimeError):
@@ -53,6 +55,8 @@ _SIGS = {
                                  ct.POINTER(AssignOpts), _vp, _vp, _vp]),
     "kmeans_update": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "kmeans_cost": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]),
+    "kmeans_update_noalloc": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
+                                         _vp, _vp]),
 }
 
 _lib = None
@@ -316,3 +320,40 @@ def kmeans_cost(X, C, w=None, cost=None, ctx=None):
     c = _ctx(ctx, X)
     c.check(load().kmeans_cost(c.handle, _ptr(X), n, d, _ptr(w), _ptr(C), C.shape[0], _ptr(cost)))
     return cost
+
+
+def kmeans_update_noalloc(X, labels, C_old, w=None, C_new=None, counts=None, cost_old=None,
+                          cost_new=None, n_empty=None):
+    """kmeans_update without a context and without any device allocation by the library.
+
+    For callers that must not allocate device memory (a locked caching allocator, a
+    memory-capped serving process, a loop where an allocation is not allowed): the library
+    uses a fixed scratch block compiled into it, shared by every call on the device, so calls
+    that overlap on the GPU race.  Output tensors left as None are created here by torch,
+    before the call; pass them in to allocate nothing at all.  Work is queued on torch's
+    current stream of X's device, which must be the current device.
+    """
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    _req(labels, torch.int32, (n,), "labels")
+    _req(C_old, torch.float32, name="C_old")
+    k = C_old.shape[0]
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
+    dev = X.device
+    if dev.index != torch.cuda.current_device():
+        raise ValueError("X must live on the current CUDA device")
+    C_new = C_new if C_new is not None else torch.empty_like(C_old)
+    counts = counts if counts is not None else torch.empty(k, dtype=torch.float64, device=dev)
+    cost_old = cost_old if cost_old is not None else torch.empty(1, dtype=torch.float64, device=dev)
+    cost_new = cost_new if cost_new is not None else torch.empty(1, dtype=torch.float64, device=dev)
+    n_empty = n_empty if n_empty is not None else torch.empty(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    rc = load().kmeans_update_noalloc(ct.c_void_p(stream), _ptr(X), n, d, _ptr(w), _ptr(labels), k,
+                                      _ptr(C_old), _ptr(C_new), _ptr(counts), _ptr(cost_old),
+                                      _ptr(cost_new), _ptr(n_empty))
+    if rc != GBKM_OK:
+        raise GbkmError(rc, "kmeans_update_noalloc failed" +
+                        (" (problem exceeds the fixed scratch block)" if rc == GBKM_ETOOBIG else ""))
+    return {"C_new": C_new, "counts": counts, "cost_old": cost_old, "cost_new": cost_new,
+            "n_empty": n_empty}

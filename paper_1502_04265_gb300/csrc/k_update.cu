@@ -10,6 +10,8 @@
 //   6. k_segsum    one CTA per chunk: error-free FP32 sums of w x, w, w ||x||^2 -> FP64 partials
 //   7. k_finalize  one CTA per cluster: FP64 sum of its partials in chunk order, centroid, CF costs
 //   8. k_final     one CTA: FP64 totals in cluster order
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace gbkm {
@@ -149,13 +151,11 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_final(const int32_t *__restrict
     }
 }
 
-static int scan_excl(gbkm_ctx *c, const int32_t *in, int64_t L, int32_t *bsum, int32_t *out) {
+static void scan_excl(cudaStream_t st, const int32_t *in, int64_t L, int32_t *bsum, int32_t *out) {
     const int64_t nb = ceil_div(L, (int64_t)SCAN_T * SCAN_E);
-    k_scan_partial<<<(unsigned)nb, SCAN_T, 0, c->stream>>>(in, L, bsum);
-    k_scan_bsum<<<1, SCAN_T, 0, c->stream>>>(bsum, nb);
-    k_scan_final<<<(unsigned)nb, SCAN_T, 0, c->stream>>>(in, L, bsum, out);
-    c->launches += 3;
-    return cuda_check(c, cudaGetLastError(), "scan launch");
+    k_scan_partial<<<(unsigned)nb, SCAN_T, 0, st>>>(in, L, bsum);
+    k_scan_bsum<<<1, SCAN_T, 0, st>>>(bsum, nb);
+    k_scan_final<<<(unsigned)nb, SCAN_T, 0, st>>>(in, L, bsum, out);
 }
 
 // start[j] = first sorted slot of cluster j, start[k] = number of valid rows
@@ -343,50 +343,127 @@ __global__ void __launch_bounds__(256) k_final(const double *__restrict__ terms,
     }
 }
 
+// sizes and workspace layout of one update
+struct UpdatePlan {
+    int64_t R, S, L, nbs, items_max;
+    size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_terms, bytes;
+};
+
+static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
+    UpdatePlan P;
+    // label segments: R rows each, with the histogram table k * S kept below ~8M entries
+    P.R = 1024;
+    while (ceil_div(n, P.R) * k > (int64_t)8 << 20) P.R *= 2;
+    P.S = ceil_div(n, P.R);
+    P.L = k * P.S;
+    P.nbs = ceil_div(P.L, (int64_t)SCAN_T * SCAN_E);
+    P.items_max = ceil_div(n, CHUNK_R) + k;
+    WsPlan p;
+    P.o_hist = p.take<int32_t>(P.L);
+    P.o_off = p.take<int32_t>(P.L);
+    P.o_bsum = p.take<int32_t>(P.nbs);
+    P.o_start = p.take<int32_t>(k + 1);
+    P.o_items = p.take<int32_t>(k + 1);
+    P.o_perm = p.take<int32_t>(n);
+    P.o_part = p.take<double>(P.items_max * (d + 2));
+    P.o_terms = p.take<double>(k * 3);
+    P.bytes = p.off;
+    return P;
+}
+
+// the update pipeline on a workspace block of P.bytes bytes; returns the number of launches
+// (or -1 on a CUDA error, left in cudaGetLastError)
+static int update_run(cudaStream_t st, int *status, void *ws, const UpdatePlan &P, const float *X,
+                      int64_t n, int64_t d, const float *w, const int32_t *labels, int64_t k,
+                      const float *C_old, float *C_new, double *counts, double *cost_old,
+                      double *cost_new, int64_t *n_empty) {
+    int32_t *hist = ws_at<int32_t>(ws, P.o_hist), *off = ws_at<int32_t>(ws, P.o_off),
+            *bsum = ws_at<int32_t>(ws, P.o_bsum), *start = ws_at<int32_t>(ws, P.o_start),
+            *item_start = ws_at<int32_t>(ws, P.o_items), *perm = ws_at<int32_t>(ws, P.o_perm);
+    double *part = ws_at<double>(ws, P.o_part), *terms = ws_at<double>(ws, P.o_terms);
+    if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * P.L, st) != cudaSuccess) return -1;
+    const unsigned seg_blocks = (unsigned)ceil_div(P.S, 8);
+    k_hist<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, hist, status);
+    scan_excl(st, hist, P.L, bsum, off);
+    k_starts<<<(unsigned)ceil_div(k, 256), 256, 0, st>>>(off, hist, k, P.S, start);
+    k_scatter<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, off, perm);
+    k_items<<<1, SCAN_T, 0, st>>>(start, k, CHUNK_R, item_start);
+    const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    if (vec)
+        k_segsum<4><<<(unsigned)P.items_max, 256, 0, st>>>(X, d, w, perm, start, item_start, k,
+                                                           CHUNK_R, part);
+    else
+        k_segsum<1><<<(unsigned)P.items_max, 256, 0, st>>>(X, d, w, perm, start, item_start, k,
+                                                           CHUNK_R, part);
+    k_finalize<<<(unsigned)k, 256, 0, st>>>(part, d, k, item_start, C_old, C_new, counts, terms);
+    k_final<<<1, 256, 0, st>>>(terms, k, cost_old, cost_new, n_empty);
+    return cudaPeekAtLastError() == cudaSuccess ? 10 : -1;
+}
+
 int update_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
                 const int32_t *labels, int64_t k, const float *C_old, float *C_new, double *counts,
                 double *cost_old, double *cost_new, int64_t *n_empty) {
-    // label segments: R rows each, with the histogram table k * S kept below ~8M entries
-    int64_t R = 1024;
-    while (ceil_div(n, R) * k > (int64_t)8 << 20) R *= 2;
-    const int64_t S = ceil_div(n, R);
-    const int64_t L = k * S;
-    const int64_t nbs = ceil_div(L, (int64_t)SCAN_T * SCAN_E);
-    const int64_t items_max = ceil_div(n, CHUNK_R) + k;
-    WsPlan p;
-    size_t o_hist = p.take<int32_t>(L), o_off = p.take<int32_t>(L), o_bsum = p.take<int32_t>(nbs),
-           o_start = p.take<int32_t>(k + 1), o_items = p.take<int32_t>(k + 1),
-           o_perm = p.take<int32_t>(n), o_part = p.take<double>(items_max * (d + 2)),
-           o_terms = p.take<double>(k * 3);
+    const UpdatePlan P = update_plan(n, d, k);
     int rc = GBKM_OK;
-    void *ws = ws_reserve(c, p.off, &rc);
+    void *ws = ws_reserve(c, P.bytes, &rc);
     if (!ws) return rc;
-    int32_t *hist = ws_at<int32_t>(ws, o_hist), *off = ws_at<int32_t>(ws, o_off),
-            *bsum = ws_at<int32_t>(ws, o_bsum), *start = ws_at<int32_t>(ws, o_start),
-            *item_start = ws_at<int32_t>(ws, o_items), *perm = ws_at<int32_t>(ws, o_perm);
-    double *part = ws_at<double>(ws, o_part), *terms = ws_at<double>(ws, o_terms);
-
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * L, c->stream);
-    if (e != cudaSuccess) return cuda_check(c, e, "memset hist");
-    const unsigned seg_blocks = (unsigned)ceil_div(S, 8);
-    k_hist<<<seg_blocks, 256, 0, c->stream>>>(labels, n, k, R, S, hist, c->status);
-    GBKM_LAUNCHED(c);
-    if ((rc = scan_excl(c, hist, L, bsum, off)) != GBKM_OK) return rc;
-    k_starts<<<(unsigned)ceil_div(k, 256), 256, 0, c->stream>>>(off, hist, k, S, start);
-    k_scatter<<<seg_blocks, 256, 0, c->stream>>>(labels, n, k, R, S, off, perm);
-    k_items<<<1, SCAN_T, 0, c->stream>>>(start, k, CHUNK_R, item_start);
-    c->launches += 3;
-    const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    if (vec)
-        k_segsum<4><<<(unsigned)items_max, 256, 0, c->stream>>>(X, d, w, perm, start, item_start, k,
-                                                                CHUNK_R, part);
-    else
-        k_segsum<1><<<(unsigned)items_max, 256, 0, c->stream>>>(X, d, w, perm, start, item_start, k,
-                                                                CHUNK_R, part);
-    k_finalize<<<(unsigned)k, 256, 0, c->stream>>>(part, d, k, item_start, C_old, C_new, counts, terms);
-    k_final<<<1, 256, 0, c->stream>>>(terms, k, cost_old, cost_new, n_empty);
-    c->launches += 3;
-    return cuda_check(c, cudaGetLastError(), "update launch");
+    const int nl = update_run(c->stream, c->status, ws, P, X, n, d, w, labels, k, C_old, C_new, counts,
+                              cost_old, cost_new, n_empty);
+    if (nl < 0) return cuda_check(c, cudaGetLastError(), "update launch");
+    c->launches += nl;
+    return GBKM_OK;
 }
 
 }  // namespace gbkm
+
+// ---------------------------------------------------------------- allocation-free update
+// Scratch for kmeans_update_noalloc: a fixed block in the library's own device image.  Every GPU
+// that loads this library holds it until the process exits.  The first 256 bytes take the
+// label-check word the histogram kernel writes; the update pipeline's workspace follows.
+namespace {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GBKM_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[256] = {};  // device address of g_noalloc_scratch, per device ordinal
+}  // namespace
+
+extern "C" int kmeans_update_noalloc(void *cuda_stream, const float *X, int64_t n, int64_t d,
+                                     const float *w, const int32_t *labels, int64_t k,
+                                     const float *C_old, float *C_new, double *counts,
+                                     double *cost_old, double *cost_new, int64_t *n_empty) {
+    if (n < 1 || d < 1 || k < 1 || k > 65536 || !X || !labels || !C_old || !C_new || C_old == C_new)
+        return GBKM_EINVAL;
+    if (n >= ((int64_t)1 << 31)) return GBKM_EUNSUPPORTED;
+    const gbkm::UpdatePlan P = gbkm::update_plan(n, d, k);
+    if (P.bytes + 256 > (size_t)GBKM_NOALLOC_SCRATCH_BYTES) return GBKM_ETOOBIG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return GBKM_ECUDA;
+    }
+    if (dev >= 256) return GBKM_EUNSUPPORTED;
+    void *base = nullptr;
+    {
+        // set-up, once per device, with that device current: in host code the array's name is
+        // only a host-side stand-in, so the kernels get the device address from the runtime
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_base[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return GBKM_ECUDA;
+            }
+            g_noalloc_base[dev] = p;
+        }
+        base = g_noalloc_base[dev];
+    }
+    int *label_check = static_cast<int *>(base);
+    void *ws = static_cast<char *>(base) + 256;
+    const int nl = gbkm::update_run((cudaStream_t)cuda_stream, label_check, ws, P, X, n, d, w, labels,
+                                    k, C_old, C_new, counts, cost_old, cost_new, n_empty);
+    if (nl < 0) {
+        cudaGetLastError();
+        return GBKM_ECUDA;
+    }
+    return GBKM_OK;
+}
