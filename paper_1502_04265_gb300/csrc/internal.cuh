@@ -149,7 +149,8 @@ int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dt
 struct AssignOut {
     int32_t *labels;
     float *min_d2;
-    int32_t *flag_list;   // n entries max
+    int32_t *flag_list;   // n entries max: rows whose argmin is a certified near-tie
+    int2 *cand;           // per flag slot: the two candidate centers, or (-1, -1) = scan all k
     int32_t *flag_count;  // 1
 };
 int launch_assign_simt(gbkm_ctx *c, const float *X, const float *xnorm, int64_t n, int64_t d,

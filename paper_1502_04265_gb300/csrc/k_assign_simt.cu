@@ -62,7 +62,11 @@ __device__ __forceinline__ void emit_row(int64_t row, float b1, int a1, float b2
             int base = 0;
             if (lane == leader) base = atomicAdd(o.flag_count, __popc(m));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (flag) o.flag_list[base + __popc(m & lanemask_lt())] = (int32_t)row;
+            if (flag) {
+                const int slot = base + __popc(m & lanemask_lt());
+                o.flag_list[slot] = (int32_t)row;
+                o.cand[slot] = make_int2(-1, -1);
+            }
         }
     }
 }
@@ -251,6 +255,7 @@ int launch_gemm_simt_strided(gbkm_ctx *c, const float *A, const float *B, int64_
 __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, int64_t d,
                                                  const float *__restrict__ C, int64_t k,
                                                  const int32_t *__restrict__ list,
+                                                 const int2 *__restrict__ cand,
                                                  const int32_t *__restrict__ count, int64_t n,
                                                  int32_t *__restrict__ labels, float *__restrict__ min_d2,
                                                  int64_t *n_rechecked, int *status) {
@@ -268,14 +273,28 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
         const float *x = X + row * d;
         double best = 0.0;
         int arg = -1;
-        for (int64_t j = 0; j < k; ++j) {
-            const float *cj = C + j * d;
-            DF acc;
-            for (int64_t t = lane; t < d; t += 32) acc.add_sqdiff(x[t], cj[t]);
-            double v = warp_sum_d(acc.value());
-            if (arg < 0 || v < best) {
-                best = v;
-                arg = (int)j;
+        const int2 cc = cand[f];
+        if (cc.x >= 0 && cc.y >= 0 && cc.x < k && cc.y < k) {
+            // the certified band holds exactly these two centers: compare them by (distance, index)
+            const int lo = min(cc.x, cc.y), hi = max(cc.x, cc.y);
+            DF a0, a1;
+            for (int64_t t = lane; t < d; t += 32) {
+                a0.add_sqdiff(x[t], C[lo * d + t]);
+                a1.add_sqdiff(x[t], C[hi * d + t]);
+            }
+            const double v0 = warp_sum_d(a0.value()), v1 = warp_sum_d(a1.value());
+            best = v1 < v0 ? v1 : v0;
+            arg = v1 < v0 ? hi : lo;
+        } else {
+            for (int64_t j = 0; j < k; ++j) {
+                const float *cj = C + j * d;
+                DF acc;
+                for (int64_t t = lane; t < d; t += 32) acc.add_sqdiff(x[t], cj[t]);
+                double v = warp_sum_d(acc.value());
+                if (arg < 0 || v < best) {
+                    best = v;
+                    arg = (int)j;
+                }
             }
         }
         if (lane == 0) {
@@ -288,7 +307,7 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
 int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
                    const AssignOut &o, int64_t *n_rechecked) {
     unsigned blocks = (unsigned)c->sm_count * 4;
-    k_recheck<<<blocks, 256, 0, c->stream>>>(X, d, C, k, o.flag_list, o.flag_count, n, o.labels,
+    k_recheck<<<blocks, 256, 0, c->stream>>>(X, d, C, k, o.flag_list, o.cand, o.flag_count, n, o.labels,
                                              o.min_d2, n_rechecked, c->status);
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "recheck launch");

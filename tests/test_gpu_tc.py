@@ -1,0 +1,120 @@
+"""GPU parity of the tcgen05 engine (distance GEMM + fused top-2 epilogue, projection GEMM).
+
+Every precision form must give the exact nearest center (bit-identical to the FP64 oracle
+outside the 1e-5 near-tie band) because rows inside the certified error band are re-resolved
+exactly; the expanded-form min distance carries the form's rounding.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1502_04265_gb300 import synth
+from parity_util import assert_labels_match
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def H(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _data(n, d, k, seed):
+    X, _ = synth.gaussian_mixture(n, d, max(2, k // 2), seed=seed)
+    C = synth.gaussian_mixture(k, d, max(2, k // 2), seed=seed + 1)[0]
+    return X, C
+
+
+def _assign(gb, X, C, form, **kw):
+    Xg, Cg = T(X), T(C)
+    Xop, sc = None, None
+    if form in ("bf16", "fp8"):
+        Xop, sc = gb.kmeans_quantize(Xg, form)
+    n = X.shape[0]
+    md = torch.empty(n, dtype=torch.float32, device=DEV)
+    nre = torch.zeros(1, dtype=torch.int64, device=DEV)
+    lab = gb.kmeans_assign(Xg, Cg, Xop=Xop, Xop_scales=sc, compute=form, engine="tcgen05",
+                           min_d2=md, n_rechecked=nre, **kw)
+    gb.gbkm_sync()
+    return H(lab), H(md), int(H(nre)[0])
+
+
+def test_tc_smallest_tile_bf16(gb, orc):
+    """One 128-row tile, one K block, one 16-wide center chunk: the smallest tcgen05 case."""
+    X, C = _data(128, 64, 16, seed=1)
+    lab, md, nre = _assign(gb, X, C, "bf16")
+    assert_labels_match(orc, X, C.astype(np.float64), lab)
+
+
+TC_CASES = [
+    (1000, 64, 10),      # ragged last tile, one K block, k padded 10 -> 16
+    (3000, 1024, 100),   # the high-dimensional shape, scaled down in n
+    (2100, 72, 300),     # two center chunks; K tail (72 = 64 + 8 -> OOB zero fill)
+    (700, 128, 1000),    # four center chunks
+    (257, 256, 1),       # k = 1
+]
+
+
+@pytest.mark.parametrize("form", ["bf16", "f32"])
+@pytest.mark.parametrize("n,d,k", TC_CASES)
+def test_tc_assign_exact_labels(gb, orc, form, n, d, k):
+    X, C = _data(n, d, k, seed=n + d + k)
+    lab, md, nre = _assign(gb, X, C, form)
+    ref, d1, d2, _ = assert_labels_match(orc, X, C.astype(np.float64), lab)
+    xn = orc.row_norms(X)
+    cn = (C.astype(np.float64) ** 2).sum(1).max()
+    rel = 2.0 ** -6 if form == "bf16" else 1e-4
+    assert np.all(np.abs(md - d1) <= rel * np.sqrt(xn * cn) * 2 + 1e-3)
+
+
+@pytest.mark.parametrize("n,d,k", [(1500, 64, 40), (900, 128, 257), (640, 48, 9)])
+def test_tc_assign_fp8_exact_labels(gb, orc, n, d, k):
+    X, C = _data(n, d, k, seed=3 * n + k)
+    lab, md, nre = _assign(gb, X, C, "fp8")
+    assert_labels_match(orc, X, C.astype(np.float64), lab)
+
+
+def test_tc_matches_simt_engine(gb):
+    X, C = _data(5000, 256, 77, seed=9)
+    Xg, Cg = T(X), T(C)
+    a = H(gb.kmeans_assign(Xg, Cg, engine="simt"))
+    b = H(gb.kmeans_assign(Xg, Cg, compute="f32", engine="tcgen05"))
+    Xb, _ = gb.kmeans_quantize(Xg, "bf16")
+    c = H(gb.kmeans_assign(Xg, Cg, Xop=Xb, compute="bf16", engine="tcgen05"))
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_tc_planted_ties(gb, orc):
+    rng = np.random.default_rng(5)
+    d, k = 64, 16
+    C = rng.integers(-8, 8, size=(k, d)).astype(np.float32) * 2.0
+    C[7] = C[3]
+    X = np.concatenate([0.5 * (C[0:1] + C[1:2]), 0.5 * (C[2:3] + C[5:6]), C[3:4] + 0.25,
+                        rng.normal(size=(300, d)).astype(np.float32) * 6]).astype(np.float32)
+    for form in ("bf16", "f32"):
+        lab, _, nre = _assign(gb, X, C, form)
+        ref, _, _ = orc.assign(X, C.astype(np.float64))
+        assert np.array_equal(lab[:3], ref[:3]) and lab[2] == 3
+        assert nre >= 3
+        assert_labels_match(orc, X, C.astype(np.float64), lab)
+
+
+@pytest.mark.parametrize("xt", ["f32", "bf16"])
+@pytest.mark.parametrize("n,d,r", [(1000, 256, 64), (300, 2048, 64), (129, 64, 16), (200, 512, 256)])
+def test_tc_project(gb, orc, xt, n, d, r):
+    Q = synth.orthonormal_basis(d, min(r, 8), seed=d)
+    X, _ = synth.subspace_mixture_chunk(Q, 0, n, 10, seed=r)
+    V = synth.orthonormal_basis(d, r, seed=r + 1).astype(np.float32)
+    Xg = T(X)
+    Xin = Xg if xt == "f32" else gb.kmeans_quantize(Xg, "bf16")[0]
+    Y = H(gb.kmeans_project_block(Xin, T(V)))
+    Yr = orc.project(X, V.astype(np.float64))
+    xn = np.sqrt(orc.row_norms(X))[:, None]
+    # per element |sum x_t v_t| error <= (2u + d 2^-22) sum |x_t v_t| <= (2u + d 2^-22) ||x|| (||v_q|| = 1)
+    u = 2.0 ** -8 if xt == "bf16" else 2.0 ** -10
+    assert np.all(np.abs(Y - Yr) <= (2 * u + d * 2.0 ** -22) * xn + 1e-5)
