@@ -305,7 +305,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(1),
            o_cop = p.take<char>(use_tc ? k_pad * d * esz : 0),
            o_clo = p.take<float>(use_tc && o.compute == GBKM_F32 ? k_pad * d : 0),
-           o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_cd = p.take<int2>(n),
+           o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_cd = p.take<int32_t>(n * gbkm::CAND_STRIDE),
            o_fc = p.take<int32_t>(1);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
@@ -326,7 +326,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     out.labels = labels;
     out.min_d2 = min_d2;
     out.flag_list = o.recheck ? ws_at<int32_t>(ws, o_fl) : nullptr;
-    out.cand = ws_at<int2>(ws, o_cd);
+    out.cand = ws_at<int32_t>(ws, o_cd);
     out.flag_count = ws_at<int32_t>(ws, o_fc);
     cudaError_t e = cudaMemsetAsync(out.flag_count, 0, sizeof(int32_t), c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "memset flag count");

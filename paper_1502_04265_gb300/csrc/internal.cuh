@@ -115,6 +115,35 @@ struct DF {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// warp-wide sum of double-float values with error-free TwoSum at every butterfly step; the result
+// is bitwise identical on every lane (TwoSum's error term is exact whichever operand comes first)
+__device__ __forceinline__ double warp_sum_df(DF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        float s, e;
+        two_sum(a.hi, h2, s, e);
+        a.hi = s;
+        a.lo = __fadd_rn(__fadd_rn(a.lo, l2), e);
+    }
+    return a.value();
+}
+
+// deterministic tree sum of blockDim.x doubles in shared memory (blockDim.x a power of two);
+// every thread must call it; returns the total to every thread
+__device__ __forceinline__ double block_tree_sum_d(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -146,11 +175,14 @@ struct CenterPrep {
 int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dtype,
                        int64_t k_pad, const CenterPrep &cp);
 
+constexpr int CAND_MAX = 8, CAND_STRIDE = CAND_MAX + 1;
+
 struct AssignOut {
     int32_t *labels;
     float *min_d2;
     int32_t *flag_list;   // n entries max: rows whose argmin is a certified near-tie
-    int2 *cand;           // per flag slot: the two candidate centers, or (-1, -1) = scan all k
+    int32_t *cand;        // per flag slot, CAND_STRIDE ints: count (-1 = scan all k), then the
+                          // centers inside the certified band in increasing index order
     int32_t *flag_count;  // 1
 };
 int launch_assign_simt(gbkm_ctx *c, const float *X, const float *xnorm, int64_t n, int64_t d,

@@ -65,7 +65,7 @@ __device__ __forceinline__ void emit_row(int64_t row, float b1, int a1, float b2
             if (flag) {
                 const int slot = base + __popc(m & lanemask_lt());
                 o.flag_list[slot] = (int32_t)row;
-                o.cand[slot] = make_int2(-1, -1);
+                o.cand[(int64_t)slot * CAND_STRIDE] = -1;
             }
         }
     }
@@ -249,13 +249,43 @@ int launch_gemm_simt_strided(gbkm_ctx *c, const float *A, const float *B, int64_
 }
 
 // ---------------------------------------------------------------- A5: exact recheck
-// One warp per flagged row (grid-stride over the device-side count).  Every center's
-// distance is summed from direct differences with error-free FP32 transformations; lanes are
-// combined in FP64 by a butterfly (identical on every lane).  Ties go to the lower index.
+// Squared distance of row x to center c from direct differences in FP32, summed by the whole warp
+// (same value on every lane).  Each lane keeps 4 interleaved accumulators (<= ceil(d/128)
+// terms each), combined pairwise, then a 5-level butterfly: the relative error is at most
+// (ceil(d/128) + 10) * 2^-24 (about 1e-6 for d = 1024), far inside the 1e-5 near-tie band, so
+// the order of two centers is resolved exactly whenever their gap exceeds that band.
+__device__ __forceinline__ float warp_direct_d2(const float *__restrict__ x, const float *__restrict__ c,
+                                                int64_t d, bool vec) {
+    const int lane = threadIdx.x & 31;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (vec) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(x);
+        const float4 *c4 = reinterpret_cast<const float4 *>(c);
+#pragma unroll 4
+        for (int64_t t = lane; t < d / 4; t += 32) {
+            const float4 a = __ldg(x4 + t), b = __ldg(c4 + t);
+            const float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+            a0 = fmaf(e0, e0, a0);
+            a1 = fmaf(e1, e1, a1);
+            a2 = fmaf(e2, e2, a2);
+            a3 = fmaf(e3, e3, a3);
+        }
+    } else {
+        for (int64_t t = lane; t < d; t += 32) {
+            const float e = x[t] - c[t];
+            a0 = fmaf(e, e, a0);
+        }
+    }
+    float v = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, int64_t d,
                                                  const float *__restrict__ C, int64_t k,
                                                  const int32_t *__restrict__ list,
-                                                 const int2 *__restrict__ cand,
+                                                 const int32_t *__restrict__ cand,
                                                  const int32_t *__restrict__ count, int64_t n,
                                                  int32_t *__restrict__ labels, float *__restrict__ min_d2,
                                                  int64_t *n_rechecked, int *status) {
@@ -271,26 +301,29 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
             continue;
         }
         const float *x = X + row * d;
-        double best = 0.0;
+        const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                         ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+        float best = 0.f;
         int arg = -1;
-        const int2 cc = cand[f];
-        if (cc.x >= 0 && cc.y >= 0 && cc.x < k && cc.y < k) {
-            // the certified band holds exactly these two centers: compare them by (distance, index)
-            const int lo = min(cc.x, cc.y), hi = max(cc.x, cc.y);
-            DF a0, a1;
-            for (int64_t t = lane; t < d; t += 32) {
-                a0.add_sqdiff(x[t], C[lo * d + t]);
-                a1.add_sqdiff(x[t], C[hi * d + t]);
+        const int32_t *cf = cand + f * CAND_STRIDE;
+        const int nc = cf[0];
+        if (nc > 0 && nc <= CAND_MAX) {
+            // the certified band holds these centers (increasing index): exact compare by (distance, index)
+            for (int q = 0; q < nc; ++q) {
+                const int j = cf[1 + q];
+                if (j < 0 || j >= k) {
+                    if (lane == 0) status_raise(status, ST_BOUNDS);
+                    continue;
+                }
+                const float v = warp_direct_d2(x, C + (int64_t)j * d, d, vec);
+                if (arg < 0 || v < best || (v == best && j < arg)) {
+                    best = v;
+                    arg = j;
+                }
             }
-            const double v0 = warp_sum_d(a0.value()), v1 = warp_sum_d(a1.value());
-            best = v1 < v0 ? v1 : v0;
-            arg = v1 < v0 ? hi : lo;
         } else {
             for (int64_t j = 0; j < k; ++j) {
-                const float *cj = C + j * d;
-                DF acc;
-                for (int64_t t = lane; t < d; t += 32) acc.add_sqdiff(x[t], cj[t]);
-                double v = warp_sum_d(acc.value());
+                const float v = warp_direct_d2(x, C + j * d, d, vec);
                 if (arg < 0 || v < best) {
                     best = v;
                     arg = (int)j;
@@ -299,7 +332,7 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
         }
         if (lane == 0) {
             labels[row] = arg;
-            if (min_d2) min_d2[row] = (float)best;
+            if (min_d2) min_d2[row] = best;
         }
     }
 }

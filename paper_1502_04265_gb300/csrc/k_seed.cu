@@ -6,7 +6,7 @@
 namespace gbkm {
 
 namespace {
-constexpr int SB = 1024;   // rows per sampling block
+constexpr int SB = 128;    // rows per sampling block (one CTA of 8 warps, 16 rows per warp)
 constexpr int PICK_T = 1024;
 }  // namespace
 
@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, 
         if constexpr (VW == 4) {
             const float4 *x4 = reinterpret_cast<const float4 *>(x);
             const float4 *c4 = reinterpret_cast<const float4 *>(c);
+#pragma unroll 4
             for (int64_t t = lane; t < d / 4; t += 32) {
                 float4 a = __ldg(x4 + t), b = __ldg(c4 + t);
                 acc.add_sqdiff(a.x, b.x);
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, 
         } else {
             for (int64_t t = lane; t < d; t += 32) acc.add_sqdiff(x[t], c[t]);
         }
-        const double dist = warp_sum_d(acc.value());
+        const double dist = warp_sum_df(acc);
         double nd = dist;
         if (!init) nd = fmin(D2[i], dist);
         if (lane == 0) D2[i] = nd;
@@ -157,10 +158,11 @@ __global__ void __launch_bounds__(PICK_T) k_pick(const float *__restrict__ X, in
         __syncthreads();
         const double base = s_base;
         const int64_t i = blk * SB + tid;
+        const bool in_blk = tid < SB && i < n;
         double p = 0.0;
-        if (i < n) p = (w ? (double)w[i] : 1.0) * (mode_w ? 1.0 : D2[i]);
+        if (in_blk) p = (w ? (double)w[i] : 1.0) * (mode_w ? 1.0 : D2[i]);
         const double pin = block_incl_scan_d(p, sh);
-        if (i < n && base + pin > t) atomicMin((unsigned long long *)&s_idx, (unsigned long long)i);
+        if (in_blk && base + pin > t) atomicMin((unsigned long long *)&s_idx, (unsigned long long)i);
         __syncthreads();
         if (s_idx == INT64_MAX) fallback = true;
         __syncthreads();

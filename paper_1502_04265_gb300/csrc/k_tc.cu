@@ -43,7 +43,7 @@ struct Args {
     int32_t *labels;
     float *min_d2;
     int32_t *flag_list;
-    int2 *cand;
+    int32_t *cand;
     int32_t *flag_count;
     // store epilogue
     float *Y;
@@ -145,6 +145,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// wait for the thread's TMEM loads, with the loaded registers as operands so that no use of them
+// can be scheduled before the wait
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
 
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle: rows of 128 B, 8-row
 // atoms of 1024 B (stride byte offset 1024), tile base 1024-byte aligned, descriptor version 1.
@@ -345,13 +355,12 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                 if (!mbar_wait(&accf[ab], aph, abort_flag)) goto epi_done;
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * bn_alloc);
-                for (int c = 0; c < a.bn; c += 16) {
-                    uint32_t r[16];
-                    tmem_ld16(tbase + (uint32_t)c, r);
-                    tmem_wait_ld();
+                // 16 accumulator columns per tcgen05.ld; the load of the next group is in flight
+                // while the current group is processed
+                auto process = [&](const uint32_t (&r)[16], int c) {
                     const int64_t j0 = (int64_t)nc * a.bn + c;
                     if constexpr (EPI == E_ARGMIN) {
-                        if (j0 >= a.k) continue;
+                        if (j0 >= a.k) return;
                         float cn[16], ms[16];
                         if (j0 + 16 <= a.k_pad) {
 #pragma unroll
@@ -394,6 +403,99 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                                                 __uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3]));
                         }
                     }
+                };
+                uint32_t ra[16], rb[16];
+                tmem_ld16(tbase, ra);
+                tmem_wait_ld(ra);
+                for (int c = 0; c < a.bn; c += 32) {
+                    const bool has_b = c + 16 < a.bn;
+                    if (has_b) tmem_ld16(tbase + (uint32_t)(c + 16), rb);
+                    process(ra, c);
+                    if (has_b) {
+                        tmem_wait_ld(rb);
+                        if (c + 32 < a.bn) tmem_ld16(tbase + (uint32_t)(c + 32), ra);
+                        process(rb, c + 16);
+                        if (c + 32 < a.bn) tmem_wait_ld(ra);
+                    }
+                }
+                if constexpr (EPI == E_ARGMIN) {
+                    if (nc == units_per_tile - 1) {
+                        // the point's final top-2: label, expanded min distance, certified near-tie flag
+                        const float xn = valid ? a.xnorm[row] : 0.f;
+                        const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
+                        const float E2 = 2.f * (a.err_rel * xr * cm + a.err_abs * cm * cm);
+                        const bool flag = valid && !((v1 - v0) > E2);
+                        if (valid) {
+                            a.labels[row] = i0;
+                            if (a.min_d2) a.min_d2[row] = fmaxf(0.f, xn + v0);
+                        }
+                        if (a.flag_list) {
+                            const unsigned m = __ballot_sync(0xffffffffu, flag);
+                            if (m) {
+                                const int leader = __ffs(m) - 1;
+                                int b0 = 0;
+                                if (lane == leader) b0 = atomicAdd(a.flag_count, __popc(m));
+                                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                                const int slot = b0 + __popc(m & lanemask_lt());
+                                int32_t *cf = a.cand + (int64_t)slot * CAND_STRIDE;
+                                if (flag) a.flag_list[slot] = (int32_t)row;
+                                // two candidates when every other center is certified worse (v2 is
+                                // the third best score); otherwise the band must be listed
+                                const bool pair = flag && (v2 - v0) > E2;
+                                const bool need_band = flag && !pair;
+                                if (pair) {
+                                    cf[0] = 2;
+                                    cf[1] = min(i0, i1);
+                                    cf[2] = max(i0, i1);
+                                }
+                                if (units_per_tile == 1 && __any_sync(0xffffffffu, need_band)) {
+                                    // a second pass over the accumulator, still resident in TMEM: every
+                                    // center whose score lies inside the band is a candidate
+                                    int cnt = 0;
+                                    auto band = [&](const uint32_t (&r)[16], int c) {
+                                        if (!need_band || c >= a.k) return;
+                                        float cn[16];
+#pragma unroll
+                                        for (int g = 0; g < 4; ++g) {
+                                            const float4 t4 = __ldg(reinterpret_cast<const float4 *>(a.cnorm + c) + g);
+                                            cn[4 * g] = t4.x, cn[4 * g + 1] = t4.y, cn[4 * g + 2] = t4.z, cn[4 * g + 3] = t4.w;
+                                        }
+                                        uint32_t inband = 0;
+#pragma unroll
+                                        for (int g = 0; g < 16; ++g) {
+                                            float ms = -2.f;
+                                            if constexpr (FORM == F_FP8) ms = (c + g < a.k) ? -2.f * sx * a.cscale[c + g] : 0.f;
+                                            const float sc = fmaf(ms, __uint_as_float(r[g]), cn[g]);
+                                            if (c + g < a.k && sc - v0 <= E2) inband |= 1u << g;
+                                        }
+                                        while (inband) {
+                                            const int g = __ffs(inband) - 1;
+                                            inband &= inband - 1;
+                                            if (cnt < CAND_MAX) cf[1 + cnt] = c + g;
+                                            ++cnt;
+                                        }
+                                    };
+                                    uint32_t ra[16], rb[16];
+                                    tmem_ld16(tbase, ra);
+                                    tmem_wait_ld(ra);
+                                    for (int c = 0; c < a.bn; c += 32) {
+                                        const bool has_b = c + 16 < a.bn;
+                                        if (has_b) tmem_ld16(tbase + (uint32_t)(c + 16), rb);
+                                        band(ra, c);
+                                        if (has_b) {
+                                            tmem_wait_ld(rb);
+                                            if (c + 32 < a.bn) tmem_ld16(tbase + (uint32_t)(c + 32), ra);
+                                            band(rb, c + 16);
+                                            if (c + 32 < a.bn) tmem_wait_ld(ra);
+                                        }
+                                    }
+                                    if (need_band) cf[0] = cnt <= CAND_MAX ? cnt : -1;
+                                } else if (need_band) {
+                                    cf[0] = -1;
+                                }
+                            }
+                        }
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -401,31 +503,6 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                 if (++ab == 2) {
                     ab = 0;
                     aph ^= 1;
-                }
-            }
-            if constexpr (EPI == E_ARGMIN) {
-                const float xn = valid ? a.xnorm[row] : 0.f;
-                const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
-                const float E2 = 2.f * (a.err_rel * xr * cm + a.err_abs * cm * cm);
-                const bool flag = valid && !((v1 - v0) > E2);
-                if (valid) {
-                    a.labels[row] = i0;
-                    if (a.min_d2) a.min_d2[row] = fmaxf(0.f, xn + v0);
-                }
-                if (a.flag_list) {
-                    const unsigned m = __ballot_sync(0xffffffffu, flag);
-                    if (m) {
-                        const int leader = __ffs(m) - 1;
-                        int b0 = 0;
-                        if (lane == leader) b0 = atomicAdd(a.flag_count, __popc(m));
-                        b0 = __shfl_sync(0xffffffffu, b0, leader);
-                        if (flag) {
-                            const int slot = b0 + __popc(m & lanemask_lt());
-                            a.flag_list[slot] = (int32_t)row;
-                            // candidates are {i0, i1} when every other center is certified worse
-                            a.cand[slot] = ((v2 - v0) > E2) ? make_int2(i0, i1) : make_int2(-1, -1);
-                        }
-                    }
                 }
             }
         }

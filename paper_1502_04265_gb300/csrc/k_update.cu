@@ -7,7 +7,8 @@
 //   3. k_starts    first slot of every cluster
 //   4. k_scatter   one warp per segment: stable rank inside the warp + running slot -> perm
 //   5. k_items     chunks of R rows per cluster, exclusive scan -> work-item table
-//   6. k_segsum    one CTA per chunk: error-free FP32 sums of w x, w, w ||x||^2 -> FP64 partials
+//   6. k_segsum    one CTA per chunk: sums of w (x - s), w, w ||x - s||^2 with s the chunk's first
+//                  row, rebased in FP64 to S = sum w x and sum w ||x - c_old||^2
 //   7. k_finalize  one CTA per cluster: FP64 sum of its partials in chunk order, centroid, CF costs
 //   8. k_final     one CTA: FP64 totals in cluster order
 #include <mutex>
@@ -18,7 +19,8 @@ namespace gbkm {
 
 namespace {
 constexpr int SCAN_T = 1024, SCAN_E = 4;           // scan block: 1024 threads x 4 elements
-constexpr int64_t CHUNK_R = 256;                    // rows per segmented-sum work item
+constexpr int64_t CHUNK_R = 512;                    // rows per segmented-sum work item
+constexpr int64_t SMEM_HIST_MAX_K = 2048;           // per-warp histograms in shared memory up to here
 
 __device__ __forceinline__ unsigned lanemask_lt_u() {
     unsigned m;
@@ -68,6 +70,63 @@ __global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ lab
             perm[pos] = (int32_t)i;
             __syncwarp(act);
             if (lane == __ffs(grp) - 1) *slot = *slot + __popc(grp);
+        }
+        __syncwarp();
+    }
+}
+
+// Shared-memory forms of the two label walks (k <= SMEM_HIST_MAX_K): each warp keeps its
+// segment's counts (k_hist_sm) or running output slots (k_scatter_sm) in its own slice of shared
+// memory, so the per-step read-modify-write never leaves the SM; every table entry is written
+// (no clearing pass needed).
+__global__ void __launch_bounds__(256) k_hist_sm(const int32_t *__restrict__ labels, int64_t n, int64_t k,
+                                                 int64_t R, int64_t S, int32_t *__restrict__ hist,
+                                                 int *status) {
+    extern __shared__ int32_t hsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (s >= S) return;
+    volatile int32_t *mine = hsm + (int64_t)wib * k;
+    for (int64_t j = lane; j < k; j += 32) mine[j] = 0;
+    __syncwarp();
+    const int64_t r0 = s * R, r1 = min(n, r0 + R);
+    for (int64_t base = r0; base < r1; base += 32) {
+        const int64_t i = base + lane;
+        const int32_t l = (i < r1) ? labels[i] : -1;
+        const bool ok = (i < r1) && l >= 0 && l < k;
+        if (i < r1 && !ok) status_raise(status, ST_BADLABEL);
+        const unsigned act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const unsigned grp = __match_any_sync(act, l);
+            if (lane == __ffs(grp) - 1) mine[l] = mine[l] + __popc(grp);
+        }
+        __syncwarp();
+    }
+    for (int64_t j = lane; j < k; j += 32) hist[j * S + s] = mine[j];
+}
+
+__global__ void __launch_bounds__(256) k_scatter_sm(const int32_t *__restrict__ labels, int64_t n, int64_t k,
+                                                    int64_t R, int64_t S, const int32_t *__restrict__ off,
+                                                    int32_t *__restrict__ perm) {
+    extern __shared__ int32_t hsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (s >= S) return;
+    volatile int32_t *mine = hsm + (int64_t)wib * k;
+    for (int64_t j = lane; j < k; j += 32) mine[j] = off[j * S + s];
+    __syncwarp();
+    const int64_t r0 = s * R, r1 = min(n, r0 + R);
+    for (int64_t base = r0; base < r1; base += 32) {
+        const int64_t i = base + lane;
+        const int32_t l = (i < r1) ? labels[i] : -1;
+        const bool ok = (i < r1) && l >= 0 && l < k;
+        const unsigned act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const unsigned grp = __match_any_sync(act, l);
+            const int32_t pos = mine[l] + __popc(grp & lanemask_lt_u());
+            perm[pos] = (int32_t)i;
+            __syncwarp(act);
+            if (lane == __ffs(grp) - 1) mine[l] = mine[l] + __popc(grp);
         }
         __syncwarp();
     }
@@ -184,16 +243,27 @@ __global__ void __launch_bounds__(SCAN_T) k_items(const int32_t *__restrict__ st
 }
 
 // ---------------------------------------------------------------- segmented CF sums
-// One CTA (256 threads) per work item = up to R rows of one cluster in sorted order.
-// Columns are processed in passes of 256 vectors (float4 when rows are 16-byte aligned);
-// threads form G = 256 / tpr row groups; group partials are combined in FP64 in group order.
+// One CTA (256 threads) per work item = up to R rows of one cluster j in sorted order.  The item's
+// sums are taken of its rows shifted by the item's first row s (a point of the same cluster, so
+// the shifted values are of the size of the cluster's spread): S'_c = sum w (x - s),
+// Q'_c = sum w ||x - s||^2, N_c = sum w.  The item then moves its sums to the reference c_old
+// exactly in FP64 (the CF identity of Section 2.1), so no cancellation larger than the
+// cluster's own scatter ever happens in FP32.  Each thread keeps 8 row loads in flight (row
+// indices staged in shared memory), sums 4-row blocks in FP32 and adds every block into a
+// double-float accumulator (error-free TwoSum); the G = 256 / tpr row groups are combined in
+// FP64 in group order.
+constexpr int SEG_UNROLL = 8, SEG_BLOCK = 4;
+
 template <int VW>
 __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int64_t d,
                                                 const float *__restrict__ w,
                                                 const int32_t *__restrict__ perm,
                                                 const int32_t *__restrict__ start,
                                                 const int32_t *__restrict__ item_start, int64_t k,
-                                                int64_t R, double *__restrict__ part) {
+                                                int64_t R, const float *__restrict__ C_old,
+                                                double *__restrict__ part) {
+    __shared__ int32_t rows_s[CHUNK_R];
+    __shared__ float w_s[CHUNK_R];
     __shared__ double red[256 * VW];
     __shared__ double qred[256];
     const int64_t item = blockIdx.x;
@@ -208,9 +278,19 @@ __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int
     }
     const int64_t j = lo;
     const int64_t row0 = start[j] + (item - item_start[j]) * R;
-    const int64_t rows = min((int64_t)start[j + 1] - row0, R);
-    double *out = part + item * (d + 2);
+    const int rows = (int)min((int64_t)start[j + 1] - row0, R);
     const int tid = threadIdx.x;
+    for (int r = tid; r < rows; r += 256) {
+        rows_s[r] = perm[row0 + r];
+        w_s[r] = w ? w[rows_s[r]] : 1.f;
+    }
+    __syncthreads();
+    double wpart = 0.0;
+    for (int r = tid; r < rows; r += 256) wpart += (double)w_s[r];
+    const double wsum_s = block_tree_sum_d(wpart, qred);
+    double rebase = 0.0;
+    double *out = part + item * (d + 2);
+    const float *ref = X + (int64_t)rows_s[0] * d;
     const int64_t ncv = d / VW;
     DF qacc;
     for (int64_t cb = 0; cb < ncv; cb += 256) {
@@ -219,141 +299,177 @@ __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int
         while (tpr < pass) tpr <<= 1;
         const int G = 256 / tpr, g = tid / tpr, cv = tid % tpr;
         const bool active = cv < pass;
-        DF acc[VW];
+        DF sacc[VW];
         if (active) {
-            for (int64_t r = g; r < rows; r += G) {
-                const int64_t i = perm[row0 + r];
-                const float wi = w ? w[i] : 1.f;
-                const float *xr = X + i * d + (cb + cv) * VW;
-                float v[VW];
-                if constexpr (VW == 4) {
-                    float4 q = __ldg(reinterpret_cast<const float4 *>(xr));
-                    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-                } else {
-                    v[0] = xr[0];
+            float c[VW];
+            if constexpr (VW == 4) {
+                const float4 c4 = __ldg(reinterpret_cast<const float4 *>(ref + (cb + cv) * 4));
+                c[0] = c4.x, c[1] = c4.y, c[2] = c4.z, c[3] = c4.w;
+            } else {
+                c[0] = __ldg(ref + cb + cv);
+            }
+            for (int r = g; r < rows; r += G * SEG_UNROLL) {
+                float v[SEG_UNROLL][VW];
+#pragma unroll
+                for (int u = 0; u < SEG_UNROLL; ++u) {
+                    const int rr = r + u * G;
+                    if (rr < rows) {
+                        const float *xr = X + (int64_t)rows_s[rr] * d + (cb + cv) * VW;
+                        if constexpr (VW == 4) {
+                            const float4 q4 = __ldg(reinterpret_cast<const float4 *>(xr));
+                            v[u][0] = q4.x, v[u][1] = q4.y, v[u][2] = q4.z, v[u][3] = q4.w;
+                        } else {
+                            v[u][0] = __ldg(xr);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < VW; ++q) v[u][q] = c[q];  // t = 0
+                    }
                 }
 #pragma unroll
-                for (int q = 0; q < VW; ++q) {
-                    acc[q].add_prod(wi, v[q]);
-                    const float p = __fmul_rn(v[q], v[q]);
-                    const float pe = __fmaf_rn(v[q], v[q], -p);
-                    qacc.add_prod(wi, p);
-                    qacc.lo = __fmaf_rn(wi, pe, qacc.lo);
+                for (int b = 0; b < SEG_UNROLL; b += SEG_BLOCK) {
+                    float sb[VW], qb[VW];
+#pragma unroll
+                    for (int q = 0; q < VW; ++q) sb[q] = qb[q] = 0.f;
+#pragma unroll
+                    for (int u = b; u < b + SEG_BLOCK; ++u) {
+                        const int rr = r + u * G;
+                        const float wt = (rr < rows) ? w_s[rr] : 0.f;
+#pragma unroll
+                        for (int q = 0; q < VW; ++q) {
+                            const float t = __fsub_rn(v[u][q], c[q]);
+                            const float wtt = __fmul_rn(wt, t);
+                            sb[q] = __fadd_rn(sb[q], wtt);
+                            qb[q] = __fmaf_rn(wtt, t, qb[q]);
+                        }
+                    }
+                    float qs = qb[0];
+#pragma unroll
+                    for (int q = 0; q < VW; ++q) {
+                        sacc[q].add(sb[q]);
+                        if (q > 0) qs = __fadd_rn(qs, qb[q]);
+                    }
+                    qacc.add(qs);
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < VW; ++q) red[tid * VW + q] = active ? acc[q].value() : 0.0;
+        for (int q = 0; q < VW; ++q) red[tid * VW + q] = active ? sacc[q].value() : 0.0;
         __syncthreads();
+        // combine the row groups in FP64, then move the item's sums from the reference row s to
+        // the cluster's old center c (CF identity, FP64):  S = S' + N s,
+        // sum w ||x - c||^2 = Q' + sum_t 2 (s_t - c_t) S'_t + N (s_t - c_t)^2
         for (int e = tid; e < pass * VW; e += 256) {
             const int cvv = e / VW, q = e % VW;
-            double s = 0.0;
-            for (int gg = 0; gg < G; ++gg) s += red[(gg * tpr + cvv) * VW + q];
-            out[(cb + cvv) * VW + q] = s;
+            double sp = 0.0;
+            for (int gg = 0; gg < G; ++gg) sp += red[(gg * tpr + cvv) * VW + q];
+            const int64_t t = (cb + cvv) * VW + q;
+            const double sref = (double)ref[t], co = (double)C_old[j * d + t], e0 = sref - co;
+            out[t] = sp + wsum_s * sref;
+            rebase += 2.0 * e0 * sp + wsum_s * e0 * e0;
         }
         __syncthreads();
     }
-    qred[tid] = qacc.value();
-    __syncthreads();
+    const double qtot = block_tree_sum_d(qacc.value() + rebase, qred);
     if (tid == 0) {
-        double q = 0.0, nsum = 0.0;
-        for (int t = 0; t < 256; ++t) q += qred[t];
-        for (int64_t r = 0; r < rows; ++r) nsum += w ? (double)w[perm[row0 + r]] : 1.0;
-        out[d] = nsum;
-        out[d + 1] = q;
+        out[d] = wsum_s;
+        out[d + 1] = qtot;
     }
 }
 
-// one CTA per cluster: FP64 sums of its partials in item order, centroid, CF cost terms
+// One CTA per (cluster j, block of 256 columns): FP64 sums of the cluster's items in item order
+// give N_j, S_j = sum w x and cost(c_old) = sum w ||x - c_old||^2; the centroid is S_j / N_j and,
+// by the CF identity of Section 2.1 with reference c_old, cost(mu) = cost(c_old) - N_j ||mu - c_old||^2,
+// whose second term is summed per column block here and across blocks by k_final.
 __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ part, int64_t d, int64_t k,
                                                   const int32_t *__restrict__ item_start,
                                                   const float *__restrict__ C_old, float *__restrict__ C_new,
-                                                  double *__restrict__ counts, double *__restrict__ terms) {
-    __shared__ double r_old[256], r_new[256];
-    __shared__ double NQ[2];
-    const int64_t j = blockIdx.x;
+                                                  double *__restrict__ counts, double *__restrict__ nq,
+                                                  double *__restrict__ mvb) {
+    __shared__ double sh[256];
+    const int64_t j = blockIdx.x, cb = blockIdx.y;
     const int32_t i0 = item_start[j], i1 = item_start[j + 1];
-    if (threadIdx.x == 0) {
-        double N = 0.0, Q = 0.0;
-        for (int32_t it = i0; it < i1; ++it) {
-            N += part[(int64_t)it * (d + 2) + d];
-            Q += part[(int64_t)it * (d + 2) + d + 1];
-        }
-        NQ[0] = N;
-        NQ[1] = Q;
+    const int64_t P = d + 2;
+    double n_part = 0.0, q_part = 0.0;
+    for (int32_t it = i0 + (int32_t)threadIdx.x; it < i1; it += (int32_t)blockDim.x) {
+        n_part += part[(int64_t)it * P + d];
+        if (cb == 0) q_part += part[(int64_t)it * P + d + 1];
     }
-    __syncthreads();
-    const double N = NQ[0], Q = NQ[1];
-    double t_old = 0.0, t_new = 0.0;
-    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
-        double S = 0.0;
-        for (int32_t it = i0; it < i1; ++it) S += part[(int64_t)it * (d + 2) + t];
-        const double co = (double)C_old[j * d + t];
-        t_old += co * (N * co - 2.0 * S);
+    const double N = block_tree_sum_d(n_part, sh);
+    double mv = 0.0;
+    const int64_t t = cb * 256 + threadIdx.x;
+    if (t < d) {
+        double S0 = 0.0, S1 = 0.0;
+        int32_t it = i0;
+        for (; it + 1 < i1; it += 2) {
+            S0 += part[(int64_t)it * P + t];
+            S1 += part[(int64_t)(it + 1) * P + t];
+        }
+        if (it < i1) S0 += part[(int64_t)it * P + t];
+        const double S = S0 + S1;
+        const float co = C_old[j * d + t];
         if (N > 0.0) {
-            t_new += S * S;
-            C_new[j * d + t] = (float)(S / N);
+            const double mu = S / N, e = mu - (double)co;
+            mv = e * e;
+            C_new[j * d + t] = (float)mu;
         } else {
-            C_new[j * d + t] = C_old[j * d + t];
+            C_new[j * d + t] = co;
         }
     }
-    r_old[threadIdx.x] = t_old;
-    r_new[threadIdx.x] = t_new;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            r_old[threadIdx.x] += r_old[threadIdx.x + o];
-            r_new[threadIdx.x] += r_new[threadIdx.x + o];
+    const double mvt = block_tree_sum_d(mv, sh);
+    if (cb == 0) {
+        const double Q = block_tree_sum_d(q_part, sh);
+        if (threadIdx.x == 0) {
+            if (counts) counts[j] = N;
+            nq[j * 2] = N;
+            nq[j * 2 + 1] = Q;
         }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        if (counts) counts[j] = N;
-        terms[j * 3 + 0] = Q + r_old[0];                      // Q - 2 c.S + N ||c||^2
-        terms[j * 3 + 1] = N > 0.0 ? Q - r_new[0] / N : 0.0;  // Q - ||S||^2 / N
-        terms[j * 3 + 2] = N > 0.0 ? 0.0 : 1.0;
-    }
+    if (threadIdx.x == 0) mvb[j * gridDim.y + cb] = mvt;
 }
 
-__global__ void __launch_bounds__(256) k_final(const double *__restrict__ terms, int64_t k,
-                                               double *cost_old, double *cost_new, int64_t *n_empty) {
-    __shared__ double a[256], b[256], e[256];
+// one CTA: cost(C_old) = sum_j Q_j, cost(C_new) = sum_j Q_j - N_j ||mu_j - c_old_j||^2, empty count
+__global__ void __launch_bounds__(256) k_final(const double *__restrict__ nq, const double *__restrict__ mvb,
+                                               int64_t k, int64_t ncb, double *cost_old, double *cost_new,
+                                               int64_t *n_empty) {
+    __shared__ double sh[256];
     double x = 0.0, y = 0.0, z = 0.0;
-    const int64_t per = (k + 255) / 256;
-    const int64_t j0 = (int64_t)threadIdx.x * per, j1 = min(k, j0 + per);
-    for (int64_t j = j0; j < j1; ++j) {
-        x += terms[j * 3];
-        y += terms[j * 3 + 1];
-        z += terms[j * 3 + 2];
-    }
-    a[threadIdx.x] = x;
-    b[threadIdx.x] = y;
-    e[threadIdx.x] = z;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sx = 0.0, sy = 0.0, sz = 0.0;
-        for (int t = 0; t < 256; ++t) {
-            sx += a[t];
-            sy += b[t];
-            sz += e[t];
+    for (int64_t j = threadIdx.x; j < k; j += 256) {
+        const double N = nq[j * 2], Q = nq[j * 2 + 1];
+        double mv = 0.0;
+        for (int64_t b = 0; b < ncb; ++b) mv += mvb[j * ncb + b];
+        if (N > 0.0) {
+            x += Q;
+            y += Q - N * mv;
+        } else {
+            z += 1.0;
         }
-        if (cost_old) *cost_old = sx;
-        if (cost_new) *cost_new = sy;
-        if (n_empty) *n_empty = (int64_t)sz;
+    }
+    x = block_tree_sum_d(x, sh);
+    y = block_tree_sum_d(y, sh);
+    z = block_tree_sum_d(z, sh);
+    if (threadIdx.x == 0) {
+        if (cost_old) *cost_old = x;
+        if (cost_new) *cost_new = y;
+        if (n_empty) *n_empty = (int64_t)z;
     }
 }
 
 // sizes and workspace layout of one update
 struct UpdatePlan {
-    int64_t R, S, L, nbs, items_max;
+    int64_t R, S, L, nbs, items_max, ncb;
+    bool smem_hist;
     size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_terms, bytes;
 };
 
 static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     UpdatePlan P;
-    // label segments: R rows each, with the histogram table k * S kept below ~8M entries
-    P.R = 1024;
+    // label segments: R rows each (one warp per segment), with the histogram table k * S kept
+    // below ~8M entries
+    P.smem_hist = k <= SMEM_HIST_MAX_K;
+    P.R = P.smem_hist ? 512 : 128;
     while (ceil_div(n, P.R) * k > (int64_t)8 << 20) P.R *= 2;
+    P.ncb = ceil_div(d, 256);
     P.S = ceil_div(n, P.R);
     P.L = k * P.S;
     P.nbs = ceil_div(P.L, (int64_t)SCAN_T * SCAN_E);
@@ -366,7 +482,7 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     P.o_items = p.take<int32_t>(k + 1);
     P.o_perm = p.take<int32_t>(n);
     P.o_part = p.take<double>(P.items_max * (d + 2));
-    P.o_terms = p.take<double>(k * 3);
+    P.o_terms = p.take<double>(k * (2 + P.ncb));
     P.bytes = p.off;
     return P;
 }
@@ -381,22 +497,35 @@ static int update_run(cudaStream_t st, int *status, void *ws, const UpdatePlan &
             *bsum = ws_at<int32_t>(ws, P.o_bsum), *start = ws_at<int32_t>(ws, P.o_start),
             *item_start = ws_at<int32_t>(ws, P.o_items), *perm = ws_at<int32_t>(ws, P.o_perm);
     double *part = ws_at<double>(ws, P.o_part), *terms = ws_at<double>(ws, P.o_terms);
-    if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * P.L, st) != cudaSuccess) return -1;
     const unsigned seg_blocks = (unsigned)ceil_div(P.S, 8);
-    k_hist<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, hist, status);
+    const size_t hsm = P.smem_hist ? sizeof(int32_t) * 8 * (size_t)k : 0;
+    if (P.smem_hist) {
+        if (hsm > 48 * 1024) {
+            cudaFuncSetAttribute(k_hist_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+            cudaFuncSetAttribute(k_scatter_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        }
+        k_hist_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, hist, status);
+    } else {
+        if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * P.L, st) != cudaSuccess) return -1;
+        k_hist<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, hist, status);
+    }
     scan_excl(st, hist, P.L, bsum, off);
     k_starts<<<(unsigned)ceil_div(k, 256), 256, 0, st>>>(off, hist, k, P.S, start);
-    k_scatter<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, off, perm);
+    if (P.smem_hist)
+        k_scatter_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, off, perm);
+    else
+        k_scatter<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, off, perm);
     k_items<<<1, SCAN_T, 0, st>>>(start, k, CHUNK_R, item_start);
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     if (vec)
         k_segsum<4><<<(unsigned)P.items_max, 256, 0, st>>>(X, d, w, perm, start, item_start, k,
-                                                           CHUNK_R, part);
+                                                           CHUNK_R, C_old, part);
     else
         k_segsum<1><<<(unsigned)P.items_max, 256, 0, st>>>(X, d, w, perm, start, item_start, k,
-                                                           CHUNK_R, part);
-    k_finalize<<<(unsigned)k, 256, 0, st>>>(part, d, k, item_start, C_old, C_new, counts, terms);
-    k_final<<<1, 256, 0, st>>>(terms, k, cost_old, cost_new, n_empty);
+                                                           CHUNK_R, C_old, part);
+    k_finalize<<<dim3((unsigned)k, (unsigned)P.ncb), 256, 0, st>>>(part, d, k, item_start, C_old, C_new,
+                                                                  counts, terms, terms + 2 * k);
+    k_final<<<1, 256, 0, st>>>(terms, terms + 2 * k, k, P.ncb, cost_old, cost_new, n_empty);
     return cudaPeekAtLastError() == cudaSuccess ? 10 : -1;
 }
 

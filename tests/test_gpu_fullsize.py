@@ -1,0 +1,95 @@
+"""Parity at the full sizes of the workloads, in the configuration bench.py times.
+
+High-dimensional workload: n = 200,000, d = 1,024, k = 100 (100-component mixture, seed 0).
+The oracle checks seeding indices over the whole set, labels on a sample of rows (recomputed
+one by one in FP64), and the whole update step (FP64 CF sums over all rows).
+Small workload: n = 10,000, d = 64, k = 10, 20 Lloyd iterations in every precision form.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1502_04265_gb300 import synth
+from parity_util import COST_REL_F32, CENTROID_REL, assert_labels_match, centroid_err
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def highdim():
+    X, _ = synth.gaussian_mixture(200_000, 1024, 100, seed=0)
+    u = synth.seed_uniforms(100, seed=0)
+    return X, u
+
+
+def test_highdim_seeding_matches_oracle(gb, orc, highdim):
+    X, u = highdim
+    Xg = torch.from_numpy(X).to(DEV)
+    idx, C = gb.kmeans_seed_pp(Xg, 100, torch.from_numpy(u).to(DEV))
+    gb.gbkm_sync()
+    ref_idx, _, _, rc = orc.seed_pp(X, 100, u)
+    assert rc == 0
+    assert np.array_equal(idx.cpu().numpy(), ref_idx)
+
+
+@pytest.mark.parametrize("form", ["bf16", "f32"])
+def test_highdim_lloyd_step_matches_oracle(gb, orc, highdim, form):
+    X, u = highdim
+    n, d, k = X.shape[0], X.shape[1], 100
+    Xg = torch.from_numpy(X).to(DEV)
+    _, C = gb.kmeans_seed_pp(Xg, k, torch.from_numpy(u).to(DEV))
+    xn = gb.kmeans_row_norms(Xg)
+    Xop = gb.kmeans_quantize(Xg, "bf16")[0] if form == "bf16" else None
+    labels = torch.empty(n, dtype=torch.int32, device=DEV)
+    for _ in range(3):  # a few iterations so that clusters are split and ties appear
+        Ch = C.cpu().numpy().astype(np.float64)
+        nre = torch.zeros(1, dtype=torch.int64, device=DEV)
+        gb.kmeans_assign(Xg, C, Xop=Xop, xnorm=xn, compute=form, labels=labels, n_rechecked=nre)
+        out = gb.kmeans_update(Xg, labels, C)
+        gb.gbkm_sync()
+        L = labels.cpu().numpy()
+        rows = np.random.default_rng(1).choice(n, 4000, replace=False)
+        assert_labels_match(orc, X[rows], Ch, L[rows])
+        ref = orc.update(X, L, Ch)
+        assert np.array_equal(out["counts"].cpu().numpy(), ref["N"])
+        assert centroid_err(out["C_new"].cpu().numpy(), ref["C_new"], X, L) <= CENTROID_REL
+        assert float(out["cost_old"].item()) == pytest.approx(ref["cost_old"], rel=COST_REL_F32)
+        assert float(out["cost_new"].item()) == pytest.approx(ref["cost_new"], rel=COST_REL_F32)
+        C = out["C_new"]
+
+
+@pytest.mark.parametrize("form,engine", [("f32", "simt"), ("f32", "tcgen05"), ("bf16", "auto"),
+                                         ("fp8", "auto")])
+def test_small_workload_full_run(gb, orc, form, engine):
+    """10,000 x 64, k = 10: seeding + 20 iterations on the GPU in each precision form.  The seeding
+    is bit-exact; the final state is checked stepwise (the oracle takes the GPU's centers); the
+    independent oracle trajectory reaches the same cost up to near-tie drift."""
+    from paper_1502_04265_gb300 import driver
+
+    X, _ = synth.gaussian_mixture(10_000, 64, 10, seed=0)
+    u = synth.seed_uniforms(10, seed=0)
+    Xg = torch.from_numpy(X).to(DEV)
+    out = driver.lloyd(Xg, 10, 20, torch.from_numpy(u).to(DEV), compute=form, engine=engine,
+                       return_trace=True)
+    gb.gbkm_sync()
+    ref_idx, C0, _, _ = orc.seed_pp(X, 10, u)
+    assert np.array_equal(out["seed_idx"].cpu().numpy(), ref_idx)
+    C = out["C"].cpu().numpy().astype(np.float64)
+    trace = out["trace"].cpu().numpy()
+    assert np.all(np.diff(trace.reshape(-1)) <= 1e-9 * trace[0, 0])
+    # stepwise parity at the final state: one more step from the GPU's centers on both sides
+    Cg = out["C"]
+    Xop, sc = gb.kmeans_quantize(Xg, form) if form in ("bf16", "fp8") else (None, None)
+    lab = gb.kmeans_assign(Xg, Cg, Xop=Xop, Xop_scales=sc, compute=form, engine=engine)
+    step = gb.kmeans_update(Xg, lab, Cg)
+    L = lab.cpu().numpy()
+    assert_labels_match(orc, X, C, L)
+    ref = orc.update(X, L, C)
+    assert centroid_err(step["C_new"].cpu().numpy(), ref["C_new"], X, L) <= CENTROID_REL
+    assert float(step["cost_old"].item()) == pytest.approx(ref["cost_old"], rel=COST_REL_F32)
+    assert float(step["cost_new"].item()) == pytest.approx(ref["cost_new"], rel=COST_REL_F32)
+    # the independent oracle trajectory from the same seeds: the same local optimum up to the
+    # drift a near-tie flip causes (trajectories are compared on cost only)
+    ref_C, ref_L, ref_trace, _ = orc.lloyd(X, C0, 20)
+    assert trace[-1, 1] == pytest.approx(ref_trace[-1], rel=1e-4)

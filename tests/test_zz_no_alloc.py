@@ -55,11 +55,12 @@ def test_noalloc_update_matches_update_on_two_calls(gb):
 
 
 def test_noalloc_update_rejects_problems_beyond_its_scratch(gb):
-    """A problem whose scratch would exceed the fixed block is refused before anything is queued:
-    (ceil(600000/256) + 8) * 4098 * 8 bytes of partial sums alone are 77 MB > 64 MiB.  The size
-    check precedes every launch, so the small buffers passed here are never read."""
+    """A problem whose scratch would exceed the fixed block is refused before anything is queued.
+    With n = 20,000,000 the row permutation alone takes 4 n = 80 MB > 64 MiB, whatever the other
+    terms; the size check precedes every launch, so the small buffers passed here are never read."""
     torch.cuda.set_device(0)
-    n, d, k = 600_000, 4096, 8
+    n, d, k = 20_000_000, 16, 8
+    assert 4 * n > gb.NOALLOC_SCRATCH_BYTES  # refused by the permutation term alone
     small = torch.empty(16, dtype=torch.float32, device=DEV)
     out = torch.empty(16, dtype=torch.float32, device=DEV)
     lab = torch.zeros(16, dtype=torch.int32, device=DEV)
