@@ -211,9 +211,9 @@ int kmeans_update(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const flo
  *    itself).  Calls whose work overlaps on the GPU (two streams, two threads)
  *    race on the block and corrupt each other: serialise them.
  *  - Scratch needed (bytes, each term rounded up to 256): 8 k S + 4 ceil(kS/4096)
- *    + 8 (k+1) + 4 n + 8 (ceil(n/512) + k)(d + 2) + 8 k (2 + ceil(d/256)), with
+ *    + 8 (k+1) + 4 n + 8 (ceil(n/128) + k)(d + 2) + 8 k (2 + 2 ceil(d/256)), with
  *    S = ceil(n/R) and R the smallest power of two >= R0 with k ceil(n/R) <= 2^23,
- *    R0 = 512 for k <= 2048 and 128 above.  A problem
+ *    R0 = 256 for k <= 2048 and 128 above.  A problem
  *    that needs more than GBKM_NOALLOC_SCRATCH_BYTES - 256 returns GBKM_ETOOBIG
  *    before anything is queued (n = 200,000, d = 1,024, k = 100 needs ~8 MB).
  *  - Labels must lie in [0, k); rows with other labels are left out of the sums

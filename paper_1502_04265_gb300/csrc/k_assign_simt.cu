@@ -282,6 +282,30 @@ __device__ __forceinline__ float warp_direct_d2(const float *__restrict__ x, con
     return v;
 }
 
+// the same distance with the row x already held in registers (d <= 1024, d % 4 == 0, aligned):
+// lane l owns float4 columns l, l + 32, ..., and the 8 center loads are issued together
+__device__ __forceinline__ float warp_direct_d2_rx(const float4 (&xr)[8], const float *__restrict__ c,
+                                                   int64_t nv) {
+    const int lane = threadIdx.x & 31;
+    const float4 *c4 = reinterpret_cast<const float4 *>(c);
+    float4 cv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cv[q] = (lane + 32 * q < nv) ? __ldg(c4 + lane + 32 * q) : xr[q];
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float e0 = xr[q].x - cv[q].x, e1 = xr[q].y - cv[q].y, e2 = xr[q].z - cv[q].z, e3 = xr[q].w - cv[q].w;
+        a0 = fmaf(e0, e0, a0);
+        a1 = fmaf(e1, e1, a1);
+        a2 = fmaf(e2, e2, a2);
+        a3 = fmaf(e3, e3, a3);
+    }
+    float v = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, int64_t d,
                                                  const float *__restrict__ C, int64_t k,
                                                  const int32_t *__restrict__ list,
@@ -307,15 +331,26 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
         int arg = -1;
         const int32_t *cf = cand + f * CAND_STRIDE;
         const int nc = cf[0];
+        const bool cached = vec && d <= 1024;
+        float4 xr[8];
+        if (cached) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(x);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                xr[q] = (lane + 32 * q < d / 4) ? __ldg(x4 + lane + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        auto dist = [&](int64_t j) -> float {
+            return cached ? warp_direct_d2_rx(xr, C + j * d, d / 4) : warp_direct_d2(x, C + j * d, d, vec);
+        };
         if (nc > 0 && nc <= CAND_MAX) {
-            // the certified band holds these centers (increasing index): exact compare by (distance, index)
+            // the certified band holds these centers (increasing index): compare by (distance, index)
             for (int q = 0; q < nc; ++q) {
                 const int j = cf[1 + q];
                 if (j < 0 || j >= k) {
                     if (lane == 0) status_raise(status, ST_BOUNDS);
                     continue;
                 }
-                const float v = warp_direct_d2(x, C + (int64_t)j * d, d, vec);
+                const float v = dist(j);
                 if (arg < 0 || v < best || (v == best && j < arg)) {
                     best = v;
                     arg = j;
@@ -323,7 +358,7 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
             }
         } else {
             for (int64_t j = 0; j < k; ++j) {
-                const float v = warp_direct_d2(x, C + j * d, d, vec);
+                const float v = dist(j);
                 if (arg < 0 || v < best) {
                     best = v;
                     arg = (int)j;

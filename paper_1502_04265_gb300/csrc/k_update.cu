@@ -7,9 +7,10 @@
 //   3. k_starts    first slot of every cluster
 //   4. k_scatter   one warp per segment: stable rank inside the warp + running slot -> perm
 //   5. k_items     chunks of R rows per cluster, exclusive scan -> work-item table
-//   6. k_segsum    one CTA per chunk: sums of w (x - s), w, w ||x - s||^2 with s the chunk's first
-//                  row, rebased in FP64 to S = sum w x and sum w ||x - c_old||^2
-//   7. k_finalize  one CTA per cluster: FP64 sum of its partials in chunk order, centroid, CF costs
+//   6. k_segsum    one CTA per chunk of 128 rows: sums of w (x - s), w, w ||x - s||^2 with s the
+//                  cluster's first row -> FP64 partials
+//   7. k_finalize  one CTA per (cluster, 256 columns): FP64 sums of the partials in chunk order,
+//                  centroid and CF cost terms
 //   8. k_final     one CTA: FP64 totals in cluster order
 #include <mutex>
 
@@ -19,8 +20,9 @@ namespace gbkm {
 
 namespace {
 constexpr int SCAN_T = 1024, SCAN_E = 4;           // scan block: 1024 threads x 4 elements
-constexpr int64_t CHUNK_R = 512;                    // rows per segmented-sum work item
+constexpr int64_t CHUNK_R = 128;                    // rows per segmented-sum work item
 constexpr int64_t SMEM_HIST_MAX_K = 2048;           // per-warp histograms in shared memory up to here
+constexpr int HIST_PF = 8;                          // label steps a warp loads ahead
 
 __device__ __forceinline__ unsigned lanemask_lt_u() {
     unsigned m;
@@ -90,17 +92,25 @@ __global__ void __launch_bounds__(256) k_hist_sm(const int32_t *__restrict__ lab
     for (int64_t j = lane; j < k; j += 32) mine[j] = 0;
     __syncwarp();
     const int64_t r0 = s * R, r1 = min(n, r0 + R);
-    for (int64_t base = r0; base < r1; base += 32) {
-        const int64_t i = base + lane;
-        const int32_t l = (i < r1) ? labels[i] : -1;
-        const bool ok = (i < r1) && l >= 0 && l < k;
-        if (i < r1 && !ok) status_raise(status, ST_BADLABEL);
-        const unsigned act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const unsigned grp = __match_any_sync(act, l);
-            if (lane == __ffs(grp) - 1) mine[l] = mine[l] + __popc(grp);
+    for (int64_t base = r0; base < r1; base += 32 * HIST_PF) {
+        int32_t lab[HIST_PF];  // the next 32 * HIST_PF labels, loaded together
+#pragma unroll
+        for (int q = 0; q < HIST_PF; ++q) {
+            const int64_t i = base + q * 32 + lane;
+            lab[q] = (i < r1) ? labels[i] : INT32_MIN;
         }
-        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < HIST_PF; ++q) {
+            const int32_t l = lab[q];
+            const bool ok = l >= 0 && l < k;
+            if (l != INT32_MIN && !ok) status_raise(status, ST_BADLABEL);
+            const unsigned act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const unsigned grp = __match_any_sync(act, l);
+                if (lane == __ffs(grp) - 1) mine[l] = mine[l] + __popc(grp);
+            }
+            __syncwarp();
+        }
     }
     for (int64_t j = lane; j < k; j += 32) hist[j * S + s] = mine[j];
 }
@@ -116,19 +126,27 @@ __global__ void __launch_bounds__(256) k_scatter_sm(const int32_t *__restrict__ 
     for (int64_t j = lane; j < k; j += 32) mine[j] = off[j * S + s];
     __syncwarp();
     const int64_t r0 = s * R, r1 = min(n, r0 + R);
-    for (int64_t base = r0; base < r1; base += 32) {
-        const int64_t i = base + lane;
-        const int32_t l = (i < r1) ? labels[i] : -1;
-        const bool ok = (i < r1) && l >= 0 && l < k;
-        const unsigned act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const unsigned grp = __match_any_sync(act, l);
-            const int32_t pos = mine[l] + __popc(grp & lanemask_lt_u());
-            perm[pos] = (int32_t)i;
-            __syncwarp(act);
-            if (lane == __ffs(grp) - 1) mine[l] = mine[l] + __popc(grp);
+    for (int64_t base = r0; base < r1; base += 32 * HIST_PF) {
+        int32_t lab[HIST_PF];
+#pragma unroll
+        for (int q = 0; q < HIST_PF; ++q) {
+            const int64_t i = base + q * 32 + lane;
+            lab[q] = (i < r1) ? labels[i] : INT32_MIN;
         }
-        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < HIST_PF; ++q) {
+            const int32_t l = lab[q];
+            const bool ok = l >= 0 && l < k;
+            const unsigned act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const unsigned grp = __match_any_sync(act, l);
+                const int32_t pos = mine[l] + __popc(grp & lanemask_lt_u());
+                perm[pos] = (int32_t)(base + q * 32 + lane);
+                __syncwarp(act);
+                if (lane == __ffs(grp) - 1) mine[l] = mine[l] + __popc(grp);
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -243,28 +261,38 @@ __global__ void __launch_bounds__(SCAN_T) k_items(const int32_t *__restrict__ st
 }
 
 // ---------------------------------------------------------------- segmented CF sums
-// One CTA (256 threads) per work item = up to R rows of one cluster j in sorted order.  The item's
-// sums are taken of its rows shifted by the item's first row s (a point of the same cluster, so
-// the shifted values are of the size of the cluster's spread): S'_c = sum w (x - s),
-// Q'_c = sum w ||x - s||^2, N_c = sum w.  The item then moves its sums to the reference c_old
-// exactly in FP64 (the CF identity of Section 2.1), so no cancellation larger than the
-// cluster's own scatter ever happens in FP32.  Each thread keeps 8 row loads in flight (row
-// indices staged in shared memory), sums 4-row blocks in FP32 and adds every block into a
-// double-float accumulator (error-free TwoSum); the G = 256 / tpr row groups are combined in
-// FP64 in group order.
-constexpr int SEG_UNROLL = 8, SEG_BLOCK = 4;
+// One CTA (256 threads) per work item = up to R rows of one cluster j in sorted order.  Sums are
+// taken of the rows shifted by the cluster's reference row s_j (its first row in sorted order, a
+// point of the same cluster, so the shifted values are of the size of the cluster's spread):
+// S'_c = sum w (x - s_j), Q'_c = sum w ||x - s_j||^2, N_c = sum w.  Every FP32 cancellation is
+// therefore bounded by the cluster's own scatter; k_finalize moves the cluster's sums to other
+// references exactly.  Each thread keeps 8 row loads in flight (row offsets staged in shared
+// memory, the tail padded with the reference row at weight 0), sums S over 8-row blocks and Q
+// over 4-row blocks in FP32 and adds every block into a double-float accumulator (error-free
+// TwoSum); the G = 256 / tpr row groups are combined in double-float in group order.  The item's
+// S' is stored as (hi, lo) float pairs, its N and Q' in FP64.  Small items (R = 128 rows) keep
+// every SM busy to the end.
+constexpr int SEG_UNROLL = 8;
 
-template <int VW>
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    a.hi = s;
+    a.lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    return a;
+}
+
+template <int VW, bool WEIGHTED>
 __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int64_t d,
                                                 const float *__restrict__ w,
                                                 const int32_t *__restrict__ perm,
                                                 const int32_t *__restrict__ start,
                                                 const int32_t *__restrict__ item_start, int64_t k,
-                                                int64_t R, const float *__restrict__ C_old,
-                                                double *__restrict__ part) {
-    __shared__ int32_t rows_s[CHUNK_R];
-    __shared__ float w_s[CHUNK_R];
-    __shared__ double red[256 * VW];
+                                                int64_t R, float2 *__restrict__ part_s,
+                                                double *__restrict__ part_nq) {
+    __shared__ int64_t roff_s[CHUNK_R + SEG_UNROLL * 256];
+    __shared__ float w_s[CHUNK_R + SEG_UNROLL * 256];
+    __shared__ float2 red[256 * VW];
     __shared__ double qred[256];
     const int64_t item = blockIdx.x;
     const int32_t total = item_start[k];
@@ -280,18 +308,27 @@ __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int
     const int64_t row0 = start[j] + (item - item_start[j]) * R;
     const int rows = (int)min((int64_t)start[j + 1] - row0, R);
     const int tid = threadIdx.x;
-    for (int r = tid; r < rows; r += 256) {
-        rows_s[r] = perm[row0 + r];
-        w_s[r] = w ? w[rows_s[r]] : 1.f;
+    const int64_t ref_off = (int64_t)perm[start[j]] * d;
+    const int64_t ncv = d / VW;
+    // largest row stride any column pass uses (the last pass is the narrowest): rows are padded
+    // up to a multiple of Gmax * SEG_UNROLL, which CHUNK_R + SEG_UNROLL * 256 always covers
+    const int last_pass = (int)(ncv - ((ncv - 1) / 256) * 256);
+    int tpr0 = 1;
+    while (tpr0 < last_pass) tpr0 <<= 1;
+    const int Gmax = 256 / tpr0;
+    const int rows_pad = ((rows + Gmax * SEG_UNROLL - 1) / (Gmax * SEG_UNROLL)) * (Gmax * SEG_UNROLL);
+    for (int r = tid; r < rows_pad; r += 256) {
+        const bool real = r < rows;
+        const int32_t i = real ? perm[row0 + r] : 0;
+        roff_s[r] = real ? (int64_t)i * d : ref_off;
+        w_s[r] = real ? (WEIGHTED ? w[i] : 1.f) : 0.f;
     }
     __syncthreads();
     double wpart = 0.0;
     for (int r = tid; r < rows; r += 256) wpart += (double)w_s[r];
     const double wsum_s = block_tree_sum_d(wpart, qred);
-    double rebase = 0.0;
-    double *out = part + item * (d + 2);
-    const float *ref = X + (int64_t)rows_s[0] * d;
-    const int64_t ncv = d / VW;
+    float2 *out_s = part_s + item * d;
+    const float *ref = X + ref_off;
     DF qacc;
     for (int64_t cb = 0; cb < ncv; cb += 256) {
         const int pass = (int)min((int64_t)256, ncv - cb);
@@ -301,122 +338,149 @@ __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int
         const bool active = cv < pass;
         DF sacc[VW];
         if (active) {
+            const int64_t col = (cb + cv) * VW;
             float c[VW];
             if constexpr (VW == 4) {
-                const float4 c4 = __ldg(reinterpret_cast<const float4 *>(ref + (cb + cv) * 4));
+                const float4 c4 = __ldg(reinterpret_cast<const float4 *>(ref + col));
                 c[0] = c4.x, c[1] = c4.y, c[2] = c4.z, c[3] = c4.w;
             } else {
-                c[0] = __ldg(ref + cb + cv);
+                c[0] = __ldg(ref + col);
             }
             for (int r = g; r < rows; r += G * SEG_UNROLL) {
                 float v[SEG_UNROLL][VW];
 #pragma unroll
                 for (int u = 0; u < SEG_UNROLL; ++u) {
-                    const int rr = r + u * G;
-                    if (rr < rows) {
-                        const float *xr = X + (int64_t)rows_s[rr] * d + (cb + cv) * VW;
-                        if constexpr (VW == 4) {
-                            const float4 q4 = __ldg(reinterpret_cast<const float4 *>(xr));
-                            v[u][0] = q4.x, v[u][1] = q4.y, v[u][2] = q4.z, v[u][3] = q4.w;
-                        } else {
-                            v[u][0] = __ldg(xr);
-                        }
+                    const float *xr = X + roff_s[r + u * G] + col;
+                    if constexpr (VW == 4) {
+                        const float4 q4 = __ldg(reinterpret_cast<const float4 *>(xr));
+                        v[u][0] = q4.x, v[u][1] = q4.y, v[u][2] = q4.z, v[u][3] = q4.w;
                     } else {
-#pragma unroll
-                        for (int q = 0; q < VW; ++q) v[u][q] = c[q];  // t = 0
+                        v[u][0] = __ldg(xr);
                     }
                 }
+                float sb[VW];
 #pragma unroll
-                for (int b = 0; b < SEG_UNROLL; b += SEG_BLOCK) {
-                    float sb[VW], qb[VW];
+                for (int q = 0; q < VW; ++q) sb[q] = 0.f;
 #pragma unroll
-                    for (int q = 0; q < VW; ++q) sb[q] = qb[q] = 0.f;
+                for (int b = 0; b < SEG_UNROLL; b += 4) {
+                    float qb[VW];
 #pragma unroll
-                    for (int u = b; u < b + SEG_BLOCK; ++u) {
-                        const int rr = r + u * G;
-                        const float wt = (rr < rows) ? w_s[rr] : 0.f;
+                    for (int q = 0; q < VW; ++q) qb[q] = 0.f;
 #pragma unroll
-                        for (int q = 0; q < VW; ++q) {
-                            const float t = __fsub_rn(v[u][q], c[q]);
-                            const float wtt = __fmul_rn(wt, t);
-                            sb[q] = __fadd_rn(sb[q], wtt);
-                            qb[q] = __fmaf_rn(wtt, t, qb[q]);
+                    for (int u = b; u < b + 4; ++u) {
+                        if constexpr (WEIGHTED) {
+                            const float wt = w_s[r + u * G];
+#pragma unroll
+                            for (int q = 0; q < VW; ++q) {
+                                const float t = __fsub_rn(v[u][q], c[q]);
+                                const float wtt = __fmul_rn(wt, t);
+                                sb[q] = __fadd_rn(sb[q], wtt);
+                                qb[q] = __fmaf_rn(wtt, t, qb[q]);
+                            }
+                        } else {
+                            // padded rows repeat the reference row, so t = 0 there
+#pragma unroll
+                            for (int q = 0; q < VW; ++q) {
+                                const float t = __fsub_rn(v[u][q], c[q]);
+                                sb[q] = __fadd_rn(sb[q], t);
+                                qb[q] = __fmaf_rn(t, t, qb[q]);
+                            }
                         }
                     }
                     float qs = qb[0];
 #pragma unroll
-                    for (int q = 0; q < VW; ++q) {
-                        sacc[q].add(sb[q]);
-                        if (q > 0) qs = __fadd_rn(qs, qb[q]);
-                    }
+                    for (int q = 1; q < VW; ++q) qs = __fadd_rn(qs, qb[q]);
                     qacc.add(qs);
                 }
+#pragma unroll
+                for (int q = 0; q < VW; ++q) sacc[q].add(sb[q]);
             }
         }
 #pragma unroll
-        for (int q = 0; q < VW; ++q) red[tid * VW + q] = active ? sacc[q].value() : 0.0;
+        for (int q = 0; q < VW; ++q) red[tid * VW + q] = active ? make_float2(sacc[q].hi, sacc[q].lo) : make_float2(0.f, 0.f);
         __syncthreads();
-        // combine the row groups in FP64, then move the item's sums from the reference row s to
-        // the cluster's old center c (CF identity, FP64):  S = S' + N s,
-        // sum w ||x - c||^2 = Q' + sum_t 2 (s_t - c_t) S'_t + N (s_t - c_t)^2
         for (int e = tid; e < pass * VW; e += 256) {
             const int cvv = e / VW, q = e % VW;
-            double sp = 0.0;
-            for (int gg = 0; gg < G; ++gg) sp += red[(gg * tpr + cvv) * VW + q];
-            const int64_t t = (cb + cvv) * VW + q;
-            const double sref = (double)ref[t], co = (double)C_old[j * d + t], e0 = sref - co;
-            out[t] = sp + wsum_s * sref;
-            rebase += 2.0 * e0 * sp + wsum_s * e0 * e0;
+            DF acc;
+            for (int gg = 0; gg < G; ++gg) {
+                const float2 t2 = red[(gg * tpr + cvv) * VW + q];
+                DF o;
+                o.hi = t2.x;
+                o.lo = t2.y;
+                acc = df_add(acc, o);
+            }
+            out_s[(cb + cvv) * VW + q] = make_float2(acc.hi, acc.lo);
         }
         __syncthreads();
     }
-    const double qtot = block_tree_sum_d(qacc.value() + rebase, qred);
+    const double qtot = block_tree_sum_d(qacc.value(), qred);
     if (tid == 0) {
-        out[d] = wsum_s;
-        out[d + 1] = qtot;
+        part_nq[item * 2] = wsum_s;
+        part_nq[item * 2 + 1] = qtot;
     }
 }
 
-// One CTA per (cluster j, block of 256 columns): FP64 sums of the cluster's items in item order
-// give N_j, S_j = sum w x and cost(c_old) = sum w ||x - c_old||^2; the centroid is S_j / N_j and,
-// by the CF identity of Section 2.1 with reference c_old, cost(mu) = cost(c_old) - N_j ||mu - c_old||^2,
-// whose second term is summed per column block here and across blocks by k_final.
-__global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ part, int64_t d, int64_t k,
+// One CTA per (cluster j, block of 256 columns).  Sums of the cluster's items in item order (N_j,
+// Q'_j in FP64; S'_j in double-float) are its CF shifted by the reference row s_j.  Then, in
+// FP64 (Section 2.1's CF identity: sum_x ||x - y||^2 = Q' + 2 (s - y) . S' + N ||s - y||^2):
+//   centroid         mu_j = s_j + S'_j / N_j
+//   cost of c_old    Q'_j + sum_t [2 (s_t - c_t) S'_t + N (s_t - c_t)^2]
+//   cost of mu_j     Q'_j - ||S'_j||^2 / N_j
+// The per-column terms are summed per block here and across blocks by k_final.
+__global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ part_s,
+                                                  const double *__restrict__ part_nq,
+                                                  const float *__restrict__ X, const int32_t *__restrict__ perm,
+                                                  const int32_t *__restrict__ start, int64_t d, int64_t k,
                                                   const int32_t *__restrict__ item_start,
                                                   const float *__restrict__ C_old, float *__restrict__ C_new,
                                                   double *__restrict__ counts, double *__restrict__ nq,
-                                                  double *__restrict__ mvb) {
+                                                  double *__restrict__ blk) {
     __shared__ double sh[256];
     const int64_t j = blockIdx.x, cb = blockIdx.y;
     const int32_t i0 = item_start[j], i1 = item_start[j + 1];
-    const int64_t P = d + 2;
     double n_part = 0.0, q_part = 0.0;
     for (int32_t it = i0 + (int32_t)threadIdx.x; it < i1; it += (int32_t)blockDim.x) {
-        n_part += part[(int64_t)it * P + d];
-        if (cb == 0) q_part += part[(int64_t)it * P + d + 1];
+        n_part += part_nq[(int64_t)it * 2];
+        if (cb == 0) q_part += part_nq[(int64_t)it * 2 + 1];
     }
     const double N = block_tree_sum_d(n_part, sh);
-    double mv = 0.0;
+    double a_old = 0.0, b_sq = 0.0;
     const int64_t t = cb * 256 + threadIdx.x;
     if (t < d) {
-        double S0 = 0.0, S1 = 0.0;
+        // 8 independent double-float accumulators keep 8 partial loads in flight; combined in order
+        DF acc[8];
         int32_t it = i0;
-        for (; it + 1 < i1; it += 2) {
-            S0 += part[(int64_t)it * P + t];
-            S1 += part[(int64_t)(it + 1) * P + t];
+        for (; it + 8 <= i1; it += 8) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 p = part_s[(int64_t)(it + q) * d + t];
+                DF o;
+                o.hi = p.x, o.lo = p.y;
+                acc[q] = df_add(acc[q], o);
+            }
         }
-        if (it < i1) S0 += part[(int64_t)it * P + t];
-        const double S = S0 + S1;
+        for (int q = 0; it < i1; ++it, ++q) {
+            const float2 p = part_s[(int64_t)it * d + t];
+            DF o;
+            o.hi = p.x, o.lo = p.y;
+            acc[q] = df_add(acc[q], o);
+        }
+#pragma unroll
+        for (int q = 1; q < 8; ++q) acc[0] = df_add(acc[0], acc[q]);
+        const double Sp = acc[0].value();
         const float co = C_old[j * d + t];
         if (N > 0.0) {
-            const double mu = S / N, e = mu - (double)co;
-            mv = e * e;
-            C_new[j * d + t] = (float)mu;
+            const double sref = (double)X[(int64_t)perm[start[j]] * d + t];
+            const double e = sref - (double)co;
+            a_old = 2.0 * e * Sp + N * e * e;
+            b_sq = Sp * Sp;
+            C_new[j * d + t] = (float)(sref + Sp / N);
         } else {
             C_new[j * d + t] = co;
         }
     }
-    const double mvt = block_tree_sum_d(mv, sh);
+    const double at = block_tree_sum_d(a_old, sh);
+    const double bt = block_tree_sum_d(b_sq, sh);
     if (cb == 0) {
         const double Q = block_tree_sum_d(q_part, sh);
         if (threadIdx.x == 0) {
@@ -425,22 +489,28 @@ __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ par
             nq[j * 2 + 1] = Q;
         }
     }
-    if (threadIdx.x == 0) mvb[j * gridDim.y + cb] = mvt;
+    if (threadIdx.x == 0) {
+        blk[(j * gridDim.y + cb) * 2] = at;
+        blk[(j * gridDim.y + cb) * 2 + 1] = bt;
+    }
 }
 
-// one CTA: cost(C_old) = sum_j Q_j, cost(C_new) = sum_j Q_j - N_j ||mu_j - c_old_j||^2, empty count
-__global__ void __launch_bounds__(256) k_final(const double *__restrict__ nq, const double *__restrict__ mvb,
+// one CTA: cost(C_old) and cost(C_new) summed over clusters, and the empty-cluster count
+__global__ void __launch_bounds__(256) k_final(const double *__restrict__ nq, const double *__restrict__ blk,
                                                int64_t k, int64_t ncb, double *cost_old, double *cost_new,
                                                int64_t *n_empty) {
     __shared__ double sh[256];
     double x = 0.0, y = 0.0, z = 0.0;
     for (int64_t j = threadIdx.x; j < k; j += 256) {
         const double N = nq[j * 2], Q = nq[j * 2 + 1];
-        double mv = 0.0;
-        for (int64_t b = 0; b < ncb; ++b) mv += mvb[j * ncb + b];
+        double a = 0.0, b = 0.0;
+        for (int64_t c = 0; c < ncb; ++c) {
+            a += blk[(j * ncb + c) * 2];
+            b += blk[(j * ncb + c) * 2 + 1];
+        }
         if (N > 0.0) {
-            x += Q;
-            y += Q - N * mv;
+            x += Q + a;
+            y += Q - b / N;
         } else {
             z += 1.0;
         }
@@ -459,7 +529,7 @@ __global__ void __launch_bounds__(256) k_final(const double *__restrict__ nq, co
 struct UpdatePlan {
     int64_t R, S, L, nbs, items_max, ncb;
     bool smem_hist;
-    size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_terms, bytes;
+    size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_nq, o_terms, bytes;
 };
 
 static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
@@ -467,7 +537,7 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     // label segments: R rows each (one warp per segment), with the histogram table k * S kept
     // below ~8M entries
     P.smem_hist = k <= SMEM_HIST_MAX_K;
-    P.R = P.smem_hist ? 512 : 128;
+    P.R = P.smem_hist ? 256 : 128;
     while (ceil_div(n, P.R) * k > (int64_t)8 << 20) P.R *= 2;
     P.ncb = ceil_div(d, 256);
     P.S = ceil_div(n, P.R);
@@ -481,8 +551,9 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     P.o_start = p.take<int32_t>(k + 1);
     P.o_items = p.take<int32_t>(k + 1);
     P.o_perm = p.take<int32_t>(n);
-    P.o_part = p.take<double>(P.items_max * (d + 2));
-    P.o_terms = p.take<double>(k * (2 + P.ncb));
+    P.o_part = p.take<float2>(P.items_max * d);
+    P.o_nq = p.take<double>(P.items_max * 2);
+    P.o_terms = p.take<double>(k * (2 + 2 * P.ncb));
     P.bytes = p.off;
     return P;
 }
@@ -496,7 +567,8 @@ static int update_run(cudaStream_t st, int *status, void *ws, const UpdatePlan &
     int32_t *hist = ws_at<int32_t>(ws, P.o_hist), *off = ws_at<int32_t>(ws, P.o_off),
             *bsum = ws_at<int32_t>(ws, P.o_bsum), *start = ws_at<int32_t>(ws, P.o_start),
             *item_start = ws_at<int32_t>(ws, P.o_items), *perm = ws_at<int32_t>(ws, P.o_perm);
-    double *part = ws_at<double>(ws, P.o_part), *terms = ws_at<double>(ws, P.o_terms);
+    float2 *part = ws_at<float2>(ws, P.o_part);
+    double *part_nq = ws_at<double>(ws, P.o_nq), *terms = ws_at<double>(ws, P.o_terms);
     const unsigned seg_blocks = (unsigned)ceil_div(P.S, 8);
     const size_t hsm = P.smem_hist ? sizeof(int32_t) * 8 * (size_t)k : 0;
     if (P.smem_hist) {
@@ -517,14 +589,18 @@ static int update_run(cudaStream_t st, int *status, void *ws, const UpdatePlan &
         k_scatter<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, off, perm);
     k_items<<<1, SCAN_T, 0, st>>>(start, k, CHUNK_R, item_start);
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    if (vec)
-        k_segsum<4><<<(unsigned)P.items_max, 256, 0, st>>>(X, d, w, perm, start, item_start, k,
-                                                           CHUNK_R, C_old, part);
+    const unsigned items = (unsigned)P.items_max;
+    if (vec && w)
+        k_segsum<4, true><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+    else if (vec)
+        k_segsum<4, false><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+    else if (w)
+        k_segsum<1, true><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
     else
-        k_segsum<1><<<(unsigned)P.items_max, 256, 0, st>>>(X, d, w, perm, start, item_start, k,
-                                                           CHUNK_R, C_old, part);
-    k_finalize<<<dim3((unsigned)k, (unsigned)P.ncb), 256, 0, st>>>(part, d, k, item_start, C_old, C_new,
-                                                                  counts, terms, terms + 2 * k);
+        k_segsum<1, false><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+    k_finalize<<<dim3((unsigned)k, (unsigned)P.ncb), 256, 0, st>>>(part, part_nq, X, perm, start, d, k,
+                                                                  item_start, C_old, C_new, counts, terms,
+                                                                  terms + 2 * k);
     k_final<<<1, 256, 0, st>>>(terms, terms + 2 * k, k, P.ncb, cost_old, cost_new, n_empty);
     return cudaPeekAtLastError() == cudaSuccess ? 10 : -1;
 }

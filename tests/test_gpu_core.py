@@ -113,7 +113,8 @@ def test_assign_recheck_off_still_valid(gb, orc):
 
 # ------------------------------------------------------------------ A6 + A7
 @pytest.mark.parametrize("n,d,k,weighted", [(3000, 64, 10, False), (2049, 37, 25, True),
-                                            (600, 1030, 7, False), (5, 3, 9, True)])
+                                            (600, 1030, 7, False), (5, 3, 9, True),
+                                            (1500, 1100, 5, True), (900, 4, 3, False)])
 def test_update_matches_oracle(gb, orc, n, d, k, weighted):
     X, z = synth.gaussian_mixture(n, d, k, seed=n + k)
     lab = (z % max(1, k - 2)).astype(np.int32)       # leaves empty clusters when k > 2
