@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 path beside the BF16 form")
     return ap.parse_args()
 
 
@@ -63,6 +64,30 @@ def load_peaks():
                 "source": "measured"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
             "source": "fallback"}
+
+
+def kernel_source_hash():
+    """Hash of the tensor-core kernel source, to tell whether stored ncu counters still apply."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("k_tc.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1502_04265_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel, form, workload):
+    """DRAM bytes per launch from a committed ncu capture, or None if the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        table = json.load(f)
+    e = table.get(f"{kernel}/{form}/{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_launch"]
 
 
 class ClockSampler:
@@ -135,14 +160,19 @@ def cpu_oracle_rate(X, C, cpu_seconds, threads=None):
     oracle.update(X[:rows], lab, Cd)
     dt = time.perf_counter() - t0
     rows = int(min(n, max(rows, rows * cpu_seconds / max(dt, 1e-3))))
-    t0 = time.perf_counter()
-    lab, _, _ = oracle.assign(X[:rows], Cd)
-    oracle.update(X[:rows], lab, Cd)
-    dt = time.perf_counter() - t0
-    flops = 2.0 * rows * k * d + rows * d
+    # repeat the sample until about cpu_seconds of work has been timed
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        lab, _, _ = oracle.assign(X[:rows], Cd)
+        oracle.update(X[:rows], lab, Cd)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= cpu_seconds or reps >= 64:
+            break
+    flops = reps * (2.0 * rows * k * d + rows * d)
     return {"value": flops / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {rows} of {n} rows, assign over all k={k} + update, FP64 C loops, "
-                      f"{dt:.1f} s"}
+            "sample": f"first {rows} of {n} rows x {reps} passes: assign over all k={k} + update, "
+                      f"FP64 C loops (OpenMP over points), {dt:.1f} s"}
 
 
 def make_workload(n, d, k, seed):
@@ -241,54 +271,60 @@ def main():
         form = "f32"
     ctx.sync()
 
-    labels = torch.empty(n, dtype=torch.int32, device=dev)
-    C = C0.clone()
-    Cn = torch.empty_like(C)
-    cost = torch.zeros((max(args.steps, 1) + args.warmup, 2), dtype=torch.float64, device=dev)
-    nre = torch.zeros(max(args.steps, 1) + args.warmup, dtype=torch.int64, device=dev)
+    def timed_run(form_, Xop_, engine_, steps, warmup, sample_clocks):
+        """W warm-up and `steps` timed Lloyd iterations from C0; returns timing and diagnostics."""
+        labels = torch.empty(n, dtype=torch.int32, device=dev)
+        Cs = [C0.clone(), torch.empty_like(C0)]
+        cost = torch.zeros((max(steps, 1) + warmup, 2), dtype=torch.float64, device=dev)
+        nre = torch.zeros(max(steps, 1) + warmup, dtype=torch.int64, device=dev)
 
-    def step(i):
-        nonlocal C, Cn
-        B.kmeans_assign(Xg, C, Xop=Xop, xnorm=xnorm, compute=form, engine=engine, labels=labels,
-                        n_rechecked=nre[i:i + 1], ctx=ctx)
-        B.kmeans_update(Xg, labels, C, C_new=Cn, cost_old=cost[i, 0:1], cost_new=cost[i, 1:2], ctx=ctx)
-        C, Cn = Cn, C
+        def step(i):
+            B.kmeans_assign(Xg, Cs[0], Xop=Xop_, xnorm=xnorm, compute=form_, engine=engine_, labels=labels,
+                            n_rechecked=nre[i:i + 1], ctx=ctx)
+            B.kmeans_update(Xg, labels, Cs[0], C_new=Cs[1], cost_old=cost[i, 0:1], cost_new=cost[i, 1:2],
+                            ctx=ctx)
+            Cs.reverse()
 
-    for i in range(args.warmup):
-        step(i)
-    ctx.sync()
+        for i in range(warmup):
+            step(i)
+        ctx.sync()
+        stream = torch.cuda.current_stream(dev)
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.5)
+        ctx.profile(True)
+        l0 = ctx.launch_count()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        ms_total = e0.elapsed_time(e1)
+        launches = ctx.launch_count() - l0
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        clocks = sampler.stop() if sampler else None
+        ms_step = ms_total / max(steps, 1)
+        if world > 1:
+            t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_step = float(t.item())
+        ctx.sync()
+        return {"ms_step": ms_step, "launches": launches, "prof": prof, "clocks": clocks,
+                "costs": cost.cpu().numpy(), "rechecked": nre.cpu().numpy(), "C": Cs[0]}
+
     stream = torch.cuda.current_stream(dev)
-    sampler = ClockSampler(local) if (rank == 0 and not args.no_clocks) else None
-    if sampler:
-        sampler.start()
-        time.sleep(0.5)
-    ctx.profile(True)
-    l0 = ctx.launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    ms_total = e0.elapsed_time(e1)
-    launches = ctx.launch_count() - l0
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    clocks = sampler.stop() if sampler else None
-    ms_step = ms_total / max(args.steps, 1)
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    R = timed_run(form, Xop, engine, args.steps, args.warmup, rank == 0 and not args.no_clocks)
+    ms_step, launches, prof, clocks = R["ms_step"], R["launches"], R["prof"], R["clocks"]
+    costs, rechecked, C = R["costs"], R["rechecked"], R["C"]
     value = world * F_step / (ms_step * 1e-3) / 1e9
-    ctx.sync()
-    costs = cost.cpu().numpy()
-    rechecked = nre.cpu().numpy()
 
     # ---- dominant kernel roofline
     peaks = load_peaks()
@@ -320,6 +356,18 @@ def main():
     roof["kernel"] = kname
     roof["kernel_ms"] = k_avg_s * 1e3
     roof["peak_source"] = peaks["source"]
+    wl = f"{n}x{d}_k{k}"
+    roof["traffic"] = stored_traffic(kname, form, wl) if kname == "assign_tc" else None
+    roof["algorithmic_bytes"] = (n * d * (2 if form == "bf16" else 4) + k * d * 4 + n * 4)
+    # whole-step roofline of the metric: one read of X at the operand dtype + C + labels + CFs
+    # against HBM, and the distance flops against the unit used
+    B_step = n * d * (2 if form == "bf16" else 4) + k * d * 4 + n * 4 + k * (d + 2) * 8
+    p_unit = (peaks["bf16_tflops"] if form == "bf16" else
+              (peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0 if kname == "assign_tc" else FFMA_PEAK_TFLOPS)) * 1e12
+    t_roof = max(B_step / (peaks["hbm_gbs"] * 1e9), F_step / p_unit)
+    step_roof = {"t_roof_ms": t_roof * 1e3, "frac": t_roof / (ms_step * 1e-3),
+                 "note": "T_roof = max(bytes / HBM, flops / unit peak); the update's FP32 read of X "
+                         "is not counted in the bytes"}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -360,6 +408,24 @@ def main():
                "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * d * 4 + 8),
                "ms_per_step": e_ms}
 
+    forms = None
+    if form == "bf16" and not args.no_compare:
+        s32 = max(3, min(args.steps, args.steps // 2))
+        R32 = timed_run("f32", None, "tcgen05", s32, args.warmup, False)
+        v32 = world * F_step / (R32["ms_step"] * 1e-3) / 1e9
+        # cost after the same number of iterations from the same centers in both forms
+        it = args.warmup + min(s32, args.steps) - 1
+        c16 = float(costs[it, 1]) if args.steps else float("nan")
+        c32 = float(R32["costs"][it, 1])
+        forms = {"bf16": {"value": value, "ms_per_step": ms_step},
+                 "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms_step"],
+                                "assign_ms": R32["prof"].get("assign_tc", (1, float("nan")))[1]
+                                / max(R32["prof"].get("assign_tc", (1, 0))[0], 1)},
+                 "speedup_vs_f32": v32 and value / v32,
+                 "final_cost_rel_gap": abs(c16 - c32) / c32,
+                 "note": "both forms run the same Lloyd iterations from the same seeds; labels are "
+                         "exact in both (certified near-ties re-resolved), so costs agree to rounding"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(X, C.cpu().numpy(), args.cpu_seconds)
@@ -375,7 +441,8 @@ def main():
                        "form": form, "engine": engine,
                        "l2": "inputs larger than L2 (X is 819 MB FP32 / 410 MB BF16)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roof, "step_roofline": step_roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
             "clocks": clocks,
             "kernels_ms": {name: prof[name][1] / max(prof[name][0], 1) for name in kept},
             "points_per_s": world * n / (ms_step * 1e-3),

@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
          const __grid_constant__ CUtensorMap tmB2, const Args a) {
     constexpr bool X3 = (FORM == F_TF32X3);
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned stage base, derived by pointer arithmetic on the shared array so that
+    // accesses through it stay shared-memory accesses
+    uint8_t *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + (size_t)a.stages * a.stage_bytes);
     uint64_t *full = bars, *tfull = bars + MAX_STAGES, *empty = bars + 2 * MAX_STAGES;
     uint64_t *accf = bars + 3 * MAX_STAGES, *acce = accf + 2;
