@@ -223,6 +223,46 @@ int kmeans_update_noalloc(void *cuda_stream, const float *X, int64_t n, int64_t 
                           const int32_t *labels, int64_t k, const float *C_old, float *C_new,
                           double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
 
+/* ------------------------------------------------------------------ A8: batched problems */
+
+/* One problem of a batched run.  All pointers are device pointers owned by the caller. */
+typedef struct {
+    const float *X;      /* n x d FP32 points, 16-byte aligned */
+    int64_t n, d, k;     /* d % 16 == 0, 1 <= k <= min(n, 1024) */
+    const double *u;     /* seeds x k uniforms in [0, 1): row s drives seed s's k-means++ */
+    float *C_out;        /* seeds x k x d: the centers of every seed after the last iteration */
+    int32_t *labels_out; /* seeds x n or NULL: labels of the last assignment */
+    double *cost_out;    /* seeds x 2 or NULL: cost(C_{T-1}, L) and cost(C_T, L) of the last iteration */
+} gbkm_problem;
+
+/* Run k-means++ (Section 1) and then `iters` Lloyd iterations (Section 1) for `count`
+ * independent problems x `seeds` seeds each, with the same rules and results as
+ * kmeans_seed_pp, kmeans_assign (compute = GBKM_F32 or GBKM_BF16, tcgen05 engine,
+ * certified near-ties re-resolved exactly) and kmeans_update.  No paper counterpart
+ * as a batch: it runs many instances of the paper's solver at once.  Every phase is
+ * one launch over all (problem, seed) pairs: the k-means++ rounds, the assignment
+ * (a persistent tcgen05 kernel over the row tiles of all problems, the seeds'
+ * centers side by side so one read of X serves every seed), the recheck, and the
+ * CF update (one label table and one device-wide scan for all pairs).
+ *   probs: host array of `count` problems; 1 <= seeds <= 8; iters >= 0.
+ *   flags: bit 0 (GBKM_BATCH_GRAPH): record the whole run into one CUDA graph and
+ *          launch it; bit 1 (GBKM_BATCH_AUTOTUNE): choose the center-chunk width of
+ *          each problem's shape with kmeans_autotune (else 256).
+ * Asynchronous on the context's stream; workspace and per-problem tables are
+ * allocated (and the stream synchronised) before anything is queued. */
+#define GBKM_BATCH_GRAPH 1
+#define GBKM_BATCH_AUTOTUNE 2
+int kmeans_batch_run(gbkm_ctx *ctx, const gbkm_problem *probs, int64_t count, int64_t seeds,
+                     int64_t iters, int32_t compute, int32_t flags);
+
+/* The project's tile autotuner (no paper counterpart): times the tcgen05
+ * assignment of a synthetic 16,384-point problem of dimension d against ncols
+ * centers with center-chunk widths of 64, 128 and 256 columns and returns the
+ * fastest in *bn_out (host).  Results are cached per (GPU, compute, d, ncols rounded
+ * up to a power of two) for the life of the process and, when the environment
+ * variable GBKM_TUNE_CACHE names a file, across processes.  Synchronises. */
+int kmeans_autotune(gbkm_ctx *ctx, int32_t compute, int64_t d, int64_t ncols, int32_t *bn_out);
+
 /* k-means objective (Section 1): cost = sum_i w_i min_j ||x_i - c_j||^2 (FP64),
  * evaluated as an exact FP32-operand assignment followed by the CF identity of
  * Section 2.1 on the resulting clusters.  X: n x d FP32; w: n FP32 or NULL;

@@ -31,6 +31,12 @@ class GbkmError(RuntimeError):
         self.code = code
 
 
+class Problem(ct.Structure):
+    _fields_ = [("X", ct.c_void_p), ("n", ct.c_int64), ("d", ct.c_int64), ("k", ct.c_int64),
+                ("u", ct.c_void_p), ("C_out", ct.c_void_p), ("labels_out", ct.c_void_p),
+                ("cost_out", ct.c_void_p)]
+
+
 class AssignOpts(ct.Structure):
     _fields_ = [("compute", ct.c_int32), ("engine", ct.c_int32), ("recheck", ct.c_int32),
                 ("reserved", ct.c_int32)]
@@ -57,6 +63,8 @@ _SIGS = {
     "kmeans_cost": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]),
     "kmeans_update_noalloc": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                          _vp, _vp]),
+    "kmeans_batch_run": (ct.c_int, [_vp, ct.POINTER(Problem), _i64, _i64, _i64, _i32, _i32]),
+    "kmeans_autotune": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32)]),
 }
 
 _lib = None
@@ -357,3 +365,40 @@ def kmeans_update_noalloc(X, labels, C_old, w=None, C_new=None, counts=None, cos
                         (" (problem exceeds the fixed scratch block)" if rc == GBKM_ETOOBIG else ""))
     return {"C_new": C_new, "counts": counts, "cost_old": cost_old, "cost_new": cost_new,
             "n_empty": n_empty}
+
+
+# ------------------------------------------------------------------ A8
+def kmeans_batch_run(problems, seeds, iters, compute="bf16", graph=True, autotune=False, ctx=None):
+    """Run k-means++ and `iters` Lloyd iterations for many problems x `seeds` seeds in one call.
+
+    problems: list of dicts with X (n x d float32), k, u (seeds x k float64); optional C_out
+    (seeds x k x d), labels_out (seeds x n int32), cost_out (seeds x 2 float64) are created if absent.
+    Returns the list of dicts with the outputs filled (asynchronously, on the current stream).
+    """
+    arr = (Problem * len(problems))()
+    keep = []
+    for i, pr in enumerate(problems):
+        X = _req(pr["X"], torch.float32, name="X")
+        n, d = X.shape
+        k = int(pr["k"])
+        u = _req(pr["u"], torch.float64, (seeds, k), "u")
+        dev = X.device
+        pr.setdefault("C_out", torch.empty((seeds, k, d), dtype=torch.float32, device=dev))
+        pr.setdefault("labels_out", torch.empty((seeds, n), dtype=torch.int32, device=dev))
+        pr.setdefault("cost_out", torch.empty((seeds, 2), dtype=torch.float64, device=dev))
+        arr[i] = Problem(X.data_ptr(), n, d, k, u.data_ptr(), _ptr(pr["C_out"]).value,
+                         _ptr(pr["labels_out"]).value, _ptr(pr["cost_out"]).value)
+        keep.append(pr)
+    flags = (1 if graph else 0) | (2 if autotune else 0)
+    c = _ctx(ctx, problems[0]["X"])
+    c.check(load().kmeans_batch_run(c.handle, arr, len(problems), seeds, iters, DTYPES[compute], flags))
+    return keep
+
+
+def kmeans_autotune(d, ncols, compute="bf16", ctx=None):
+    """Center-chunk width (64, 128 or 256) the autotuner picks for this shape (synchronises)."""
+    c = ctx or default_context()
+    c.bind_stream()
+    out = ct.c_int32()
+    c.check(load().kmeans_autotune(c.handle, DTYPES[compute], d, ncols, ct.byref(out)))
+    return int(out.value)

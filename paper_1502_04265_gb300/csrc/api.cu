@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -82,6 +83,9 @@ struct DeviceGuard {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+}  // namespace
+
+namespace gbkm {
 // worst-case relative error coefficients of the distance scores of each operand format:
 // |score_err| <= err_rel ||x|| max||c|| + err_abs max||c||^2 (see the certified near-tie rule)
 void score_error_coeffs(int dtype, int engine_tc, int64_t d, float &err_rel, float &err_abs) {
@@ -106,7 +110,7 @@ void score_error_coeffs(int dtype, int engine_tc, int64_t d, float &err_rel, flo
     err_rel = (float)((2.0 * dot + 2.0 * u) * (1.0 + 1e-3));
     err_abs = (float)(3.0 * u * (1.0 + 1e-3));
 }
-}  // namespace
+}  // namespace gbkm
 
 extern "C" {
 
@@ -180,6 +184,8 @@ int gbkm_destroy(gbkm_ctx *c) {
     if (!c) return GBKM_OK;
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
     if (c->status) cudaFree(c->status);
@@ -331,7 +337,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     cudaError_t e = cudaMemsetAsync(out.flag_count, 0, sizeof(int32_t), c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "memset flag count");
     float err_rel, err_abs;
-    score_error_coeffs(o.compute, use_tc, d, err_rel, err_abs);
+    gbkm::score_error_coeffs(o.compute, use_tc, d, err_rel, err_abs);
     prof_begin(c, use_tc ? "assign_tc" : "assign_simt");
     if (use_tc)
         rc = gbkm::launch_assign_tc(c, o.compute, Xop, Xop_scales, X, xn, n, d, cp, k, k_pad, err_rel,
@@ -364,6 +370,49 @@ int kmeans_update(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float
     prof_begin(c, "update");
     int rc = gbkm::update_impl(c, X, n, d, w, labels, k, C_old, C_new, counts, cost_old, cost_new, n_empty);
     prof_end(c);
+    return rc;
+}
+
+int kmeans_batch_run(gbkm_ctx *c, const gbkm_problem *probs, int64_t count, int64_t seeds, int64_t iters,
+                     int32_t compute, int32_t flags) {
+    if (!c) return GBKM_EINVAL;
+    if (!probs || count < 1 || seeds < 1 || seeds > 8 || iters < 0)
+        return set_error(c, GBKM_EINVAL, "batch_run: bad arguments");
+    if (compute != GBKM_F32 && compute != GBKM_BF16)
+        return set_error(c, GBKM_EINVAL, "batch_run: compute must be F32 or BF16");
+    for (int64_t p = 0; p < count; ++p) {
+        const gbkm_problem &q = probs[p];
+        if (!q.X || !q.u || !q.C_out || q.n < 1 || q.k < 1 || q.k > q.n || q.n >= ((int64_t)1 << 31) ||
+            !aligned16(q.X))
+            return set_error(c, GBKM_EINVAL, "batch_run: problem %lld has bad arguments", (long long)p);
+        if (!gbkm::tc_batched_supported(compute, q.d, q.k, seeds))
+            return set_error(c, GBKM_EUNSUPPORTED, "batch_run: problem %lld needs d %% 16 == 0 and k <= 1024",
+                             (long long)p);
+    }
+    DeviceGuard g(c->device);
+    std::vector<int> caps(count, 256);
+    if (flags & GBKM_BATCH_AUTOTUNE) {
+        for (int64_t p = 0; p < count; ++p) {
+            int bn = 256;
+            const int64_t ncols = seeds * ((probs[p].k + 15) / 16 * 16);
+            int rc = gbkm::autotune_bn(c, compute, probs[p].d, ncols, &bn);
+            if (rc != GBKM_OK) return rc;
+            caps[p] = bn;
+        }
+    }
+    prof_begin(c, "batch_run");
+    int rc = gbkm::batch_run(c, probs, count, seeds, iters, compute, flags, caps.data());
+    prof_end(c);
+    return rc;
+}
+
+int kmeans_autotune(gbkm_ctx *c, int32_t compute, int64_t d, int64_t ncols, int32_t *bn_out) {
+    if (!c) return GBKM_EINVAL;
+    if (!bn_out || d < 1 || ncols < 1) return set_error(c, GBKM_EINVAL, "autotune: bad arguments");
+    DeviceGuard g(c->device);
+    int bn = 256;
+    int rc = gbkm::autotune_bn(c, compute, d, ncols, &bn);
+    *bn_out = bn;
     return rc;
 }
 

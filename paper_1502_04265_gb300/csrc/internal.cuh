@@ -40,6 +40,9 @@ struct gbkm_ctx {
     int sm_count = 0;
     int64_t launches = 0;
     void *tmap_scratch = nullptr;  // device copy of tensor maps (128 B aligned, 16 slots)
+    void *graph_exec = nullptr;    // last instantiated batched-run graph (cudaGraphExec_t)
+    cudaStream_t cap_stream = nullptr;  // private stream the batched run is recorded on
+    int bn_cap = 0;                // center-chunk width of the tcgen05 assignment (0: 256); autotuner knob
 };
 
 int set_error(gbkm_ctx *c, int code, const char *fmt, ...);
@@ -155,6 +158,34 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// exclusive scan of one int32 per thread across the block (blockDim.x a multiple of 32, <= 1024);
+// `total` receives the block's sum; sh holds 32 ints
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *sh, int32_t &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const int32_t warp_base = wid > 0 ? sh[wid - 1] : 0;
+    total = sh[nw - 1];
+    __syncthreads();
+    return warp_base + x - v;
+}
+
 // ---------------------------------------------------------------- host-side launch helpers
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -194,11 +225,15 @@ int launch_gemm_simt_strided(gbkm_ctx *c, const float *A, const float *B, int64_
 int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
                    const AssignOut &o, int64_t *n_rechecked);
 
+// device-wide exclusive scan of L int32 (totals < 2^31); bsum holds ceil(L / 4096) ints
+void scan_excl(cudaStream_t st, const int32_t *in, int64_t L, int32_t *bsum, int32_t *out);
 int update_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
                 const int32_t *labels, int64_t k, const float *C_old, float *C_new,
                 double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
 int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, int64_t k,
               const double *u, int64_t *idx_out, float *C_out);
+// worst-case error coefficients of the distance scores of an operand format and engine
+void score_error_coeffs(int dtype, int engine_tc, int64_t d, float &err_rel, float &err_abs);
 bool tc_assign_supported(int dtype, int64_t d, int64_t k);
 int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscales,
                      const float *X, const float *xnorm, int64_t n, int64_t d,
@@ -207,4 +242,40 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
 bool tc_project_supported(int dtype, int64_t d, int64_t r);
 int launch_project_tc(gbkm_ctx *c, int dtype, const void *X, int64_t n, int64_t d,
                       const float *V, int64_t r, float *Y);
+// ---------------------------------------------------------------- batched problems
+// device-side descriptor of one problem of a batched run (all pointers are device pointers)
+struct BProb {
+    const float *X;          // n x d FP32
+    int64_t n, d, k, kps;    // kps: per-seed stride of the centers in the operand (k rounded up to 16)
+    int32_t seeds, m_tiles, n_chunks, bn, kb, nb;  // nb: sampling blocks of 128 rows
+    uint32_t idesc, tx_bytes;
+    float err_rel, err_abs;
+    const void *Xop;         // operand copy of X (BF16) or X itself (FP32)
+    float *xnorm;            // n
+    float *C[2];             // seeds x k x d, ping-pong centers
+    float *cnorm;            // seeds x kps
+    unsigned *cmax;          // 1
+    void *cop, *cop_lo;      // (seeds x kps) x d operand copies of the centers
+    int32_t *labels;         // seeds x n
+    double *D2;              // seeds x n
+    double *bsum;            // seeds x nb
+    int32_t *stop;           // seeds
+    const double *u;         // seeds x k uniforms
+    int64_t pair0;           // index of (this problem, seed 0) among all pairs
+    int64_t crow0;           // first row of this problem among all centers rows (seeds x kps each)
+    int64_t tile0;           // first global row tile
+};
+constexpr int BFLAG_STRIDE = 6;  // flag entry: problem, seed, row, candidate count (-1: all), c0, c1
+
+// batched tcgen05 distance GEMM over the (problem, row tile) work list; maps: 3 tensor maps per
+// problem (X operand, center operand, TF32 low part) in global memory, 64-byte aligned
+int launch_assign_tc_batched(gbkm_ctx *c, int dtype, const void *maps, const BProb *probs, int64_t nprob,
+                             const int32_t *tile_prob, int64_t ntiles, int parity, int bn_max,
+                             int32_t *flags, int32_t *flag_count);
+bool tc_batched_supported(int dtype, int64_t d, int64_t k, int64_t seeds);
+int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds, int64_t iters, int dtype,
+              int flags, const int *bn_caps);
+// fastest center-chunk width (64, 128 or 256 columns) of the tcgen05 assignment for this shape
+int autotune_bn(gbkm_ctx *c, int dtype, int64_t d, int64_t ncols, int *bn_out);
+int make_batch_tmaps(gbkm_ctx *c, int dtype, const BProb &P, void *host_maps3);
 }  // namespace gbkm

@@ -520,6 +520,283 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
     }
 }
 
+// ---------------------------------------------------------------- batched kernel
+// The same pipeline over a work list of (problem, row tile) items: every CTA walks items
+// blockIdx.x, blockIdx.x + gridDim.x, ...; each item runs its problem's center chunks in order with
+// that problem's tensor maps (3 per problem in global memory), K-block count and instruction
+// descriptor.  The centers of a problem's seeds are concatenated along N (seeds x kps columns), so
+// one read of X serves every seed; the epilogue keeps a separate top-2 per seed (seed boundaries
+// fall on 16-column groups) and emits a label and a certified near-tie flag per (seed, point).
+template <int FORM>
+__global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
+    k_tcb(const CUtensorMap *__restrict__ maps, const BProb *__restrict__ probs,
+          const int32_t *__restrict__ tile_prob, int ntiles, int stages, uint32_t a_bytes, uint32_t b_bytes,
+          uint32_t stage_bytes, int32_t *__restrict__ flags, int32_t *__restrict__ flag_count, int *status) {
+    constexpr bool X3 = (FORM == F_TF32X3);
+    constexpr int BKE = 128 / (FORM == F_BF16 ? 2 : (FORM == F_FP8 ? 1 : 4));
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + (size_t)stages * stage_bytes);
+    uint64_t *full = bars, *tfull = bars + MAX_STAGES, *empty = bars + 2 * MAX_STAGES;
+    uint64_t *accf = bars + 3 * MAX_STAGES, *acce = accf + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    constexpr uint32_t TMEM_COLS = 512, BN_ALLOC = 256;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < stages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&tfull[q], 4);
+            mbar_init(&empty[q], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0, issued = 0, last_par = 0;
+            for (int it = blockIdx.x; it < ntiles && !*abort_flag; it += gridDim.x) {
+                const int p = tile_prob[it];
+                const BProb &P = probs[p];
+                const int ltile = it - (int)P.tile0;
+                const CUtensorMap *tm = maps + 3 * p;
+                for (int nc = 0; nc < P.n_chunks; ++nc) {
+                    for (int kb = 0; kb < P.kb; ++kb) {
+                        if (!mbar_wait(&empty[st], ph ^ 1, abort_flag)) goto producer_done;
+                        uint8_t *sb = base + (size_t)st * stage_bytes;
+                        mbar_expect_tx(&full[st], P.tx_bytes);
+                        tma_load_2d(sb, tm, &full[st], kb * BKE, ltile * BM);
+                        uint8_t *bdst = sb + (X3 ? 2 : 1) * a_bytes;
+                        tma_load_2d(bdst, tm + 1, &full[st], kb * BKE, nc * P.bn);
+                        if constexpr (X3) tma_load_2d(bdst + b_bytes, tm + 2, &full[st], kb * BKE, nc * P.bn);
+                        issued |= 1u << st;
+                        last_par = (last_par & ~(1u << st)) | (ph << st);
+                        if (++st == stages) {
+                            st = 0;
+                            ph ^= 1;
+                        }
+                    }
+                }
+            }
+        producer_done:
+            if (*abort_flag)
+                for (int q = 0; q < stages; ++q)
+                    if (issued & (1u << q)) mbar_drain(&full[q], (last_par >> q) & 1, 500000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int st = 0, ab = 0;
+            uint32_t ph = 0, aph = 0;
+            uint64_t *last_bar = nullptr;
+            uint32_t last_parity = 0;
+            for (int it = blockIdx.x; it < ntiles && !*abort_flag; it += gridDim.x) {
+                const BProb &P = probs[tile_prob[it]];
+                for (int nc = 0; nc < P.n_chunks; ++nc) {
+                    if (!mbar_wait(&acce[ab], aph ^ 1, abort_flag)) goto mma_done;
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(ab * BN_ALLOC);
+                    for (int kb = 0; kb < P.kb; ++kb) {
+                        if (!mbar_wait(X3 ? &tfull[st] : &full[st], ph, abort_flag)) goto mma_done;
+                        tc_fence_after();
+                        uint8_t *sb = base + (size_t)st * stage_bytes;
+                        const uint64_t adesc = sw128_desc(sb);
+                        const uint64_t bdesc = sw128_desc(sb + (X3 ? 2 : 1) * a_bytes);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                            const uint64_t off = (uint64_t)(kk * 2);
+                            if constexpr (X3) {
+                                const uint64_t alo = sw128_desc(sb + a_bytes);
+                                const uint64_t blo = sw128_desc(sb + 2 * a_bytes + b_bytes);
+                                tc_mma<FORM>(d_tmem, alo + off, bdesc + off, P.idesc, acc);
+                                tc_mma<FORM>(d_tmem, adesc + off, blo + off, P.idesc, 1u);
+                                tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, P.idesc, 1u);
+                            } else {
+                                tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, P.idesc, acc);
+                            }
+                        }
+                        tc_commit(&empty[st]);
+                        last_bar = &empty[st];
+                        last_parity = ph;
+                        if (++st == stages) {
+                            st = 0;
+                            ph ^= 1;
+                        }
+                    }
+                    tc_commit(&accf[ab]);
+                    last_bar = &accf[ab];
+                    last_parity = aph;
+                    if (++ab == 2) {
+                        ab = 0;
+                        aph ^= 1;
+                    }
+                }
+            }
+        mma_done:
+            if (*abort_flag && last_bar) mbar_drain(last_bar, last_parity, 500000000ull);
+        }
+    } else if (X3 && warp >= 8) {
+        const int t = threadIdx.x - 256;
+        int st = 0;
+        uint32_t ph = 0;
+        for (int it = blockIdx.x; it < ntiles && !*abort_flag; it += gridDim.x) {
+            const BProb &P = probs[tile_prob[it]];
+            for (int nc = 0; nc < P.n_chunks; ++nc) {
+                for (int kb = 0; kb < P.kb; ++kb) {
+                    if (!mbar_wait(&full[st], ph, abort_flag)) goto split_done;
+                    uint8_t *sb = base + (size_t)st * stage_bytes;
+                    uint4 *hi = reinterpret_cast<uint4 *>(sb);
+                    uint4 *lo = reinterpret_cast<uint4 *>(sb + a_bytes);
+#pragma unroll 4
+                    for (int e = t; e < (int)(a_bytes / 16); e += 128) {
+                        uint4 v = hi[e], h, l;
+                        h.x = v.x & 0xffffe000u;
+                        h.y = v.y & 0xffffe000u;
+                        h.z = v.z & 0xffffe000u;
+                        h.w = v.w & 0xffffe000u;
+                        l.x = __float_as_uint(__fsub_rn(__uint_as_float(v.x), __uint_as_float(h.x))) & 0xffffe000u;
+                        l.y = __float_as_uint(__fsub_rn(__uint_as_float(v.y), __uint_as_float(h.y))) & 0xffffe000u;
+                        l.z = __float_as_uint(__fsub_rn(__uint_as_float(v.z), __uint_as_float(h.z))) & 0xffffe000u;
+                        l.w = __float_as_uint(__fsub_rn(__uint_as_float(v.w), __uint_as_float(h.w))) & 0xffffe000u;
+                        hi[e] = h;
+                        lo[e] = l;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tfull[st]);
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+        }
+    split_done:;
+    } else if (warp >= 4 && warp < 8) {
+        const int q = warp - 4;
+        int ab = 0;
+        uint32_t aph = 0;
+        for (int it = blockIdx.x; it < ntiles && !*abort_flag; it += gridDim.x) {
+            const int p = tile_prob[it];
+            const BProb &P = probs[p];
+            const int64_t row = (int64_t)(it - P.tile0) * BM + q * 32 + lane;
+            const bool valid = row < P.n;
+            const float xn = valid ? P.xnorm[row] : 0.f;
+            const float cm = __uint_as_float(*P.cmax);
+            const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
+            const float E2 = 2.f * (P.err_rel * xr * cm + P.err_abs * cm * cm);
+            const int64_t ncols = (int64_t)P.seeds * P.kps;
+            float v0 = __int_as_float(0x7f800000), v1 = v0, v2 = v0;
+            int i0 = 0, i1 = 0, cur = 0;
+            // emit the finished seed s of this point: label, certified near-tie flag, candidates
+            auto finish = [&](int s) {
+                const bool flag = valid && !((v1 - v0) > E2);
+                if (valid) P.labels[(int64_t)s * P.n + row] = i0;
+                const unsigned m = __ballot_sync(0xffffffffu, flag);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    int b0 = 0;
+                    if (lane == leader) b0 = atomicAdd(flag_count, __popc(m));
+                    b0 = __shfl_sync(0xffffffffu, b0, leader);
+                    if (flag) {
+                        int32_t *f = flags + (int64_t)(b0 + __popc(m & lanemask_lt())) * BFLAG_STRIDE;
+                        f[0] = p;
+                        f[1] = s;
+                        f[2] = (int32_t)row;
+                        const bool pair = (v2 - v0) > E2;
+                        f[3] = pair ? 2 : -1;
+                        f[4] = min(i0, i1);
+                        f[5] = max(i0, i1);
+                    }
+                }
+                v0 = v1 = v2 = __int_as_float(0x7f800000);
+                i0 = i1 = 0;
+            };
+            for (int nc = 0; nc < P.n_chunks; ++nc) {
+                if (!mbar_wait(&accf[ab], aph, abort_flag)) goto epi_done;
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN_ALLOC);
+                auto process = [&](const uint32_t (&r)[16], int c) {
+                    const int64_t j0 = (int64_t)nc * P.bn + c;  // column among all seeds' centers
+                    if (j0 >= ncols) return;
+                    const int s = (int)(j0 / P.kps);
+                    const int jl0 = (int)(j0 - (int64_t)s * P.kps);
+                    if (s != cur) {
+                        finish(cur);
+                        cur = s;
+                    }
+                    if (jl0 >= P.k) return;
+                    float cn[16];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        const float4 t4 = __ldg(reinterpret_cast<const float4 *>(P.cnorm + j0) + g);
+                        cn[4 * g] = t4.x, cn[4 * g + 1] = t4.y, cn[4 * g + 2] = t4.z, cn[4 * g + 3] = t4.w;
+                    }
+#pragma unroll
+                    for (int g = 0; g < 16; ++g) {
+                        const int j = jl0 + g;
+                        const float sc = (j < P.k) ? fmaf(-2.f, __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
+                        const bool lt0 = sc < v0, lt1 = sc < v1;
+                        const float m0 = fmaxf(v0, sc), m1 = fmaxf(v1, sc);
+                        v2 = fminf(v2, m1);
+                        v1 = fminf(v1, m0);
+                        v0 = fminf(v0, sc);
+                        i1 = lt0 ? i0 : (lt1 ? j : i1);
+                        i0 = lt0 ? j : i0;
+                    }
+                };
+                uint32_t ra[16], rb[16];
+                tmem_ld16(tbase, ra);
+                tmem_wait_ld(ra);
+                for (int c = 0; c < P.bn; c += 32) {
+                    const bool has_b = c + 16 < P.bn;
+                    if (has_b) tmem_ld16(tbase + (uint32_t)(c + 16), rb);
+                    process(ra, c);
+                    if (has_b) {
+                        tmem_wait_ld(rb);
+                        if (c + 32 < P.bn) tmem_ld16(tbase + (uint32_t)(c + 32), ra);
+                        process(rb, c + 16);
+                        if (c + 32 < P.bn) tmem_wait_ld(ra);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[ab]);
+                if (++ab == 2) {
+                    ab = 0;
+                    aph ^= 1;
+                }
+            }
+            finish(cur);
+        }
+    epi_done:;
+    }
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) status_raise(status, ST_TIMEOUT);
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -574,10 +851,10 @@ struct Plan {
     size_t smem;
 };
 
-static Plan plan(int form, int64_t d, int64_t k_pad) {
+static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256) {
     Plan p;
     const int esize = (form == F_BF16) ? 2 : (form == F_FP8 ? 1 : 4);
-    p.n_chunks = (int)ceil_div(k_pad, 256);
+    p.n_chunks = (int)ceil_div(k_pad, bn_cap);
     p.bn = (int)(ceil_div(ceil_div(k_pad, p.n_chunks), 16) * 16);
     p.kb = (int)ceil_div(d * esize, 128);
     const bool x3 = form == F_TF32X3;
@@ -620,7 +897,7 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
                      float err_rel, float err_abs, const AssignOut &o) {
     using namespace tc;
     const int form = (dtype == GBKM_BF16) ? F_BF16 : (dtype == GBKM_FP8E4M3 ? F_FP8 : F_TF32X3);
-    const Plan p = plan(form, d, k_pad);
+    const Plan p = plan(form, d, k_pad, c->bn_cap > 0 ? c->bn_cap : 256);
     const CUtensorMapDataType dt = (form == F_BF16)  ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                    : (form == F_FP8) ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -693,6 +970,61 @@ int launch_project_tc(gbkm_ctx *c, int dtype, const void *X, int64_t n, int64_t 
     a.status = c->status;
     if (form == F_BF16) return launch<F_BF16, E_STORE>(c, tA, tB, tB, a, p);
     return launch<F_TF32, E_STORE>(c, tA, tB, tB, a, p);
+}
+
+
+bool tc_batched_supported(int dtype, int64_t d, int64_t k, int64_t seeds) {
+    if (!tc::encode_fn()) return false;
+    if (dtype != GBKM_BF16 && dtype != GBKM_F32) return false;
+    if (d % 16 != 0 || k < 1 || k > 1024 || seeds < 1 || seeds > 8) return false;
+    return true;
+}
+
+int make_batch_tmaps(gbkm_ctx *c, int dtype, const BProb &P, void *host_maps3) {
+    using namespace tc;
+    CUtensorMap *m = static_cast<CUtensorMap *>(host_maps3);
+    const bool bf = dtype == GBKM_BF16;
+    const CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const uint32_t es = bf ? 2 : 4;
+    const uint64_t rows_b = (uint64_t)P.seeds * (uint64_t)P.kps;
+    if (!make_tmap(&m[0], dt, P.Xop, (uint64_t)P.d, (uint64_t)P.n, es, BM) ||
+        !make_tmap(&m[1], dt, P.cop, (uint64_t)P.d, rows_b, es, (uint32_t)P.bn))
+        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for a batched problem");
+    m[2] = m[1];
+    if (!bf && !make_tmap(&m[2], dt, P.cop_lo, (uint64_t)P.d, rows_b, es, (uint32_t)P.bn))
+        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for a batched TF32 low part");
+    return GBKM_OK;
+}
+
+int launch_assign_tc_batched(gbkm_ctx *c, int dtype, const void *maps, const BProb *probs, int64_t nprob,
+                             const int32_t *tile_prob, int64_t ntiles, int parity, int bn_max, int32_t *flags,
+                             int32_t *flag_count) {
+    using namespace tc;
+    (void)nprob;
+    (void)parity;
+    const bool x3 = dtype == GBKM_F32;
+    const uint32_t a_bytes = BM * 128, b_bytes = (uint32_t)bn_max * 128;
+    const uint32_t stage_bytes = (x3 ? 2 : 1) * a_bytes + (x3 ? 2 : 1) * b_bytes;
+    const int stages = (int)std::min<int64_t>(MAX_STAGES, SMEM_BUDGET / stage_bytes);
+    const size_t smem = (size_t)stages * stage_bytes + 2048;
+    const int threads = x3 ? 384 : 256;
+    const int grid = (int)std::min<int64_t>(c->sm_count, ntiles);
+    cudaError_t e;
+    if (x3) {
+        e = cudaFuncSetAttribute(k_tcb<F_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_check(c, e, "batched smem attribute");
+        k_tcb<F_TF32X3><<<grid, threads, smem, c->stream>>>(static_cast<const CUtensorMap *>(maps), probs, tile_prob,
+                                                            (int)ntiles, stages, a_bytes, b_bytes, stage_bytes,
+                                                            flags, flag_count, c->status);
+    } else {
+        e = cudaFuncSetAttribute(k_tcb<F_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_check(c, e, "batched smem attribute");
+        k_tcb<F_BF16><<<grid, threads, smem, c->stream>>>(static_cast<const CUtensorMap *>(maps), probs, tile_prob,
+                                                          (int)ntiles, stages, a_bytes, b_bytes, stage_bytes,
+                                                          flags, flag_count, c->status);
+    }
+    GBKM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "batched tcgen05 launch");
 }
 
 }  // namespace gbkm

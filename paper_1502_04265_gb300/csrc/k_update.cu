@@ -152,32 +152,6 @@ __global__ void __launch_bounds__(256) k_scatter_sm(const int32_t *__restrict__ 
 
 // ---------------------------------------------------------------- device-wide exclusive scan
 // (int32; totals < 2^31 because they count rows)
-__device__ int32_t block_excl_scan(int32_t v, int32_t *sh, int32_t &total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int32_t w = lane < nw ? sh[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        sh[lane] = w;  // inclusive over warps
-    }
-    __syncthreads();
-    const int32_t warp_base = wid > 0 ? sh[wid - 1] : 0;
-    total = sh[nw - 1];
-    __syncthreads();
-    return warp_base + x - v;
-}
-
 __global__ void __launch_bounds__(SCAN_T) k_scan_partial(const int32_t *__restrict__ in, int64_t L,
                                                          int32_t *__restrict__ bsum) {
     __shared__ int32_t sh[32];
@@ -228,7 +202,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_final(const int32_t *__restrict
     }
 }
 
-static void scan_excl(cudaStream_t st, const int32_t *in, int64_t L, int32_t *bsum, int32_t *out) {
+void scan_excl(cudaStream_t st, const int32_t *in, int64_t L, int32_t *bsum, int32_t *out) {
     const int64_t nb = ceil_div(L, (int64_t)SCAN_T * SCAN_E);
     k_scan_partial<<<(unsigned)nb, SCAN_T, 0, st>>>(in, L, bsum);
     k_scan_bsum<<<1, SCAN_T, 0, st>>>(bsum, nb);
