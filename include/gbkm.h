@@ -263,6 +263,62 @@ int kmeans_batch_run(gbkm_ctx *ctx, const gbkm_problem *probs, int64_t count, in
  * variable GBKM_TUNE_CACHE names a file, across processes.  Synchronises. */
 int kmeans_autotune(gbkm_ctx *ctx, int32_t compute, int64_t d, int64_t ncols, int32_t *bn_out);
 
+/* ------------------------------------------------------------------ A9: learned candidate proposal */
+
+/* A small MLP d_in -> hidden -> hidden -> k (GELU after the two hidden layers) that scores the k
+ * centers for a point (no paper counterpart).  Parameters are one FP32 vector, layout
+ * W1 (hidden x d_in), b1 (hidden), W2 (hidden x hidden), b2 (hidden), W3 (k x hidden), b3 (k),
+ * rows = output units; params_bf16 is its BF16 copy (what the tensor cores read).  adam_m /
+ * adam_v (same layout, FP32) and wd_mask (same layout, 1 = decayed weight) serve training and may
+ * be NULL for inference.  d_in, hidden and k are multiples of 16.  Device pointers except step. */
+typedef struct {
+    int64_t d_in, hidden, k;
+    float *params;
+    void *params_bf16;
+    float *adam_m, *adam_v;
+    const uint8_t *wd_mask;
+    int64_t step;  /* host: AdamW step counter, advanced by kmeans_mlp_train_step */
+} gbkm_mlp;
+
+/* Number of parameters of the layout above. */
+int64_t kmeans_mlp_param_count(int64_t d_in, int64_t hidden, int64_t k);
+
+/* D = A B^T on the tensor cores with a fused epilogue (building block of the MLP):
+ * A: M x K, B: N x K, BF16 row-major (K % 8 == 0, N % 16 == 0, 16-byte aligned);
+ * Y[i, j] = act(D[i, j] + bias[j]) (act 0: none, 1: GELU), FP32 or BF16 (out_bf16), row stride ldy.
+ * bias may be NULL. */
+int kmeans_gemm_bf16(gbkm_ctx *ctx, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
+                     const float *bias, int32_t act, int32_t out_bf16, void *Y, int64_t ldy);
+
+/* Forward pass on Xh (n x d_in BF16): logits (n x k FP32) and/or the indices of the topm
+ * (1..32) largest logits of every point (n x topm int32, order unspecified, -1 padding), the
+ * latter selected inside the logits GEMM's epilogue so that the logits are never stored. */
+int kmeans_mlp_forward(gbkm_ctx *ctx, const gbkm_mlp *mlp, const void *Xh, int64_t n, float *logits,
+                       int32_t *top_idx, int32_t topm);
+
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8, decoupled decay wd on wd_mask) on the mean
+ * softmax cross-entropy of the batch Xh (B x d_in BF16, B % 8 == 0) against labels (B int32 in
+ * [0, k)).  Every matrix product of the forward and backward passes runs on the tensor cores.
+ * loss_rows (B FP32) and grad_out (param_count FP32, the batch gradient) may be NULL.
+ * mlp->step is advanced on the host. */
+int kmeans_mlp_train_step(gbkm_ctx *ctx, gbkm_mlp *mlp, const void *Xh, const int32_t *labels, int64_t B,
+                          float lr, float wd, float *loss_rows, float *grad_out);
+
+/* s2[j] = (1/4) min_{i != j} ||c_j - c_i||^2 for the k x d centers C (FP32 direct differences):
+ * the squared acceptance radius of kmeans_learned_assign's certificate. */
+int kmeans_center_separation(gbkm_ctx *ctx, const float *C, int64_t k, int64_t d, float *s2);
+
+/* Assignment step (Section 1) with learned candidates: the MLP proposes topm centers per point,
+ * their exact FP32 distances give the best candidate b, and b is accepted when the point lies
+ * certifiably inside the ball of radius s(c_b) (then every other center is strictly farther);
+ * the remaining points get the full scan of kmeans_assign (FP32).  The labels are therefore those
+ * of the exact method.  X: n x d FP32, Xh: its BF16 copy, C: k x d, s2 from
+ * kmeans_center_separation; labels: n int32; n_fallback: 1 int64 (device) or NULL; cand_out:
+ * n x topm int32 or NULL.  Synchronises once (to size the fallback scan). */
+int kmeans_learned_assign(gbkm_ctx *ctx, const gbkm_mlp *mlp, const float *X, const void *Xh, int64_t n,
+                          int64_t d, const float *C, int64_t k, const float *s2, int32_t topm,
+                          int32_t *labels, int64_t *n_fallback, int32_t *cand_out);
+
 /* k-means objective (Section 1): cost = sum_i w_i min_j ||x_i - c_j||^2 (FP64),
  * evaluated as an exact FP32-operand assignment followed by the CF identity of
  * Section 2.1 on the resulting clusters.  X: n x d FP32; w: n FP32 or NULL;

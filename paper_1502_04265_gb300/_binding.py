@@ -37,6 +37,12 @@ class Problem(ct.Structure):
                 ("cost_out", ct.c_void_p)]
 
 
+class MLP(ct.Structure):
+    _fields_ = [("d_in", ct.c_int64), ("hidden", ct.c_int64), ("k", ct.c_int64), ("params", ct.c_void_p),
+                ("params_bf16", ct.c_void_p), ("adam_m", ct.c_void_p), ("adam_v", ct.c_void_p),
+                ("wd_mask", ct.c_void_p), ("step", ct.c_int64)]
+
+
 class AssignOpts(ct.Structure):
     _fields_ = [("compute", ct.c_int32), ("engine", ct.c_int32), ("recheck", ct.c_int32),
                 ("reserved", ct.c_int32)]
@@ -65,6 +71,13 @@ _SIGS = {
                                          _vp, _vp]),
     "kmeans_batch_run": (ct.c_int, [_vp, ct.POINTER(Problem), _i64, _i64, _i64, _i32, _i32]),
     "kmeans_autotune": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32)]),
+    "kmeans_mlp_param_count": (ct.c_int64, [_i64, _i64, _i64]),
+    "kmeans_gemm_bf16": (ct.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i32, _i32, _vp, _i64]),
+    "kmeans_mlp_forward": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _i64, _vp, _vp, _i32]),
+    "kmeans_mlp_train_step": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _vp, _i64, ct.c_float, ct.c_float, _vp, _vp]),
+    "kmeans_center_separation": (ct.c_int, [_vp, _vp, _i64, _i64, _vp]),
+    "kmeans_learned_assign": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i32, _vp,
+                                         _vp, _vp]),
 }
 
 _lib = None
@@ -402,3 +415,73 @@ def kmeans_autotune(d, ncols, compute="bf16", ctx=None):
     out = ct.c_int32()
     c.check(load().kmeans_autotune(c.handle, DTYPES[compute], d, ncols, ct.byref(out)))
     return int(out.value)
+
+
+# ------------------------------------------------------------------ A9
+def kmeans_mlp_param_count(d_in, hidden, k):
+    return int(load().kmeans_mlp_param_count(d_in, hidden, k))
+
+
+def kmeans_gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Y=None, ctx=None):
+    """Y = act(A B^T + bias) on the tensor cores (A: M x K, B: N x K, BF16)."""
+    _req(A, torch.bfloat16, name="A")
+    _req(B, torch.bfloat16, name="B")
+    M, K = A.shape
+    N = B.shape[0]
+    if Y is None:
+        Y = torch.empty((M, N), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=A.device)
+    if bias is not None:
+        _req(bias, torch.float32, (N,), "bias")
+    c = _ctx(ctx, A)
+    c.check(load().kmeans_gemm_bf16(c.handle, _ptr(A), _ptr(B), M, N, K, _ptr(bias), act, 1 if out_bf16 else 0,
+                                    _ptr(Y), Y.shape[1]))
+    return Y
+
+
+def _mlp_struct(net):
+    return MLP(net.d_in, net.hidden, net.k, _ptr(net.params).value, _ptr(net.params_bf16).value,
+               _ptr(net.adam_m).value if net.adam_m is not None else None,
+               _ptr(net.adam_v).value if net.adam_v is not None else None,
+               _ptr(net.wd_mask).value if net.wd_mask is not None else None, net.step)
+
+
+def kmeans_mlp_forward(net, Xh, logits=None, top_idx=None, topm=32, ctx=None):
+    _req(Xh, torch.bfloat16, name="Xh")
+    n = Xh.shape[0]
+    m = _mlp_struct(net)
+    c = _ctx(ctx, Xh)
+    c.check(load().kmeans_mlp_forward(c.handle, ct.byref(m), _ptr(Xh), n, _ptr(logits), _ptr(top_idx), topm))
+    return logits, top_idx
+
+
+def kmeans_mlp_train_step(net, Xh, labels, lr, wd=0.0, loss_rows=None, grad_out=None, ctx=None):
+    _req(Xh, torch.bfloat16, name="Xh")
+    _req(labels, torch.int32, name="labels")
+    B = Xh.shape[0]
+    m = _mlp_struct(net)
+    c = _ctx(ctx, Xh)
+    c.check(load().kmeans_mlp_train_step(c.handle, ct.byref(m), _ptr(Xh), _ptr(labels), B, lr, wd,
+                                         _ptr(loss_rows), _ptr(grad_out)))
+    net.step = int(m.step)
+
+
+def kmeans_center_separation(C, s2=None, ctx=None):
+    _req(C, torch.float32, name="C")
+    k, d = C.shape
+    s2 = s2 if s2 is not None else torch.empty(k, dtype=torch.float32, device=C.device)
+    c = _ctx(ctx, C)
+    c.check(load().kmeans_center_separation(c.handle, _ptr(C), k, d, _ptr(s2)))
+    return s2
+
+
+def kmeans_learned_assign(net, X, Xh, C, s2, topm=32, labels=None, n_fallback=None, cand_out=None, ctx=None):
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    k = C.shape[0]
+    labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=X.device)
+    n_fallback = n_fallback if n_fallback is not None else torch.zeros(1, dtype=torch.int64, device=X.device)
+    m = _mlp_struct(net)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_learned_assign(c.handle, ct.byref(m), _ptr(X), _ptr(Xh), n, d, _ptr(C), k, _ptr(s2), topm,
+                                         _ptr(labels), _ptr(n_fallback), _ptr(cand_out)))
+    return labels, n_fallback

@@ -416,6 +416,63 @@ int kmeans_autotune(gbkm_ctx *c, int32_t compute, int64_t d, int64_t ncols, int3
     return rc;
 }
 
+int64_t kmeans_mlp_param_count(int64_t d_in, int64_t hidden, int64_t k) {
+    gbkm_mlp m{};
+    m.d_in = d_in, m.hidden = hidden, m.k = k;
+    return gbkm::mlp_param_count(&m);
+}
+
+int kmeans_gemm_bf16(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64_t N, int64_t K, const float *bias,
+                     int32_t act, int32_t out_bf16, void *Y, int64_t ldy) {
+    if (!c) return GBKM_EINVAL;
+    if (!A || !B || !Y || M < 1 || ldy < N || !aligned16(A) || !aligned16(B) || !aligned16(Y) || (act != 0 && act != 1))
+        return set_error(c, GBKM_EINVAL, "gemm: bad arguments");
+    DeviceGuard g(c->device);
+    prof_begin(c, "gemm");
+    int rc = gbkm::launch_gemm_bf16_tc(c, A, B, M, N, K, bias, act, out_bf16, Y, ldy, nullptr, 0, nullptr, nullptr, 0);
+    prof_end(c);
+    return rc;
+}
+
+int kmeans_mlp_forward(gbkm_ctx *c, const gbkm_mlp *mlp, const void *Xh, int64_t n, float *logits, int32_t *top_idx,
+                       int32_t topm) {
+    if (!c) return GBKM_EINVAL;
+    DeviceGuard g(c->device);
+    prof_begin(c, "mlp_forward");
+    int rc = gbkm::mlp_forward(c, mlp, Xh, n, logits, top_idx, topm);
+    prof_end(c);
+    return rc;
+}
+
+int kmeans_mlp_train_step(gbkm_ctx *c, gbkm_mlp *mlp, const void *Xh, const int32_t *labels, int64_t B, float lr,
+                          float wd, float *loss_rows, float *grad_out) {
+    if (!c) return GBKM_EINVAL;
+    DeviceGuard g(c->device);
+    prof_begin(c, "mlp_train_step");
+    int rc = gbkm::mlp_train_step(c, mlp, Xh, labels, B, lr, wd, loss_rows, grad_out);
+    prof_end(c);
+    return rc;
+}
+
+int kmeans_center_separation(gbkm_ctx *c, const float *C, int64_t k, int64_t d, float *s2) {
+    if (!c) return GBKM_EINVAL;
+    if (!C || !s2 || k < 2 || d < 1) return set_error(c, GBKM_EINVAL, "center_separation: bad arguments");
+    DeviceGuard g(c->device);
+    return gbkm::center_separation(c, C, k, d, s2);
+}
+
+int kmeans_learned_assign(gbkm_ctx *c, const gbkm_mlp *mlp, const float *X, const void *Xh, int64_t n, int64_t d,
+                          const float *C, int64_t k, const float *s2, int32_t topm, int32_t *labels,
+                          int64_t *n_fallback, int32_t *cand_out) {
+    if (!c) return GBKM_EINVAL;
+    if (!X || !Xh || !C || !s2 || !labels || n < 1) return set_error(c, GBKM_EINVAL, "learned_assign: bad arguments");
+    DeviceGuard g(c->device);
+    prof_begin(c, "learned_assign");
+    int rc = gbkm::learned_assign(c, mlp, X, Xh, n, d, C, k, s2, topm, labels, n_fallback, cand_out);
+    prof_end(c);
+    return rc;
+}
+
 int kmeans_cost(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, const float *C,
                 int64_t k, double *cost) {
     if (!c) return GBKM_EINVAL;

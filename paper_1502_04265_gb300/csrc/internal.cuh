@@ -239,6 +239,17 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
                      const float *X, const float *xnorm, int64_t n, int64_t d,
                      const CenterPrep &cp, int64_t k, int64_t k_pad, float err_rel,
                      float err_abs, const AssignOut &o);
+int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
+                        const float *bias, int act, int out_bf16, void *Y, int64_t ldy, float *Ypre, int64_t ldpre,
+                        int32_t *top_idx, float *top_val, int topm);
+int64_t mlp_param_count(const gbkm_mlp *m);
+int mlp_forward(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n, float *logits, int32_t *top_idx, int topm);
+int mlp_train_step(gbkm_ctx *c, gbkm_mlp *m, const void *Xh, const int32_t *labels, int64_t B, float lr, float wd,
+                   float *loss_rows, float *grad_out);
+int center_separation(gbkm_ctx *c, const float *C, int64_t k, int64_t d, float *s2);
+int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *Xh, int64_t n, int64_t d,
+                   const float *C, int64_t k, const float *s2, int topm, int32_t *labels, int64_t *n_fallback,
+                   int32_t *cand_out);
 bool tc_project_supported(int dtype, int64_t d, int64_t r);
 int launch_project_tc(gbkm_ctx *c, int dtype, const void *X, int64_t n, int64_t d,
                       const float *V, int64_t r, float *Y);

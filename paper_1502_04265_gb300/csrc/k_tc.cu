@@ -29,7 +29,8 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
 constexpr int SMEM_BUDGET = 200 * 1024;
 
 enum Form : int { F_BF16 = 0, F_TF32X3 = 1, F_FP8 = 2, F_TF32 = 3 };
-enum Epi : int { E_ARGMIN = 0, E_STORE = 1 };
+enum Epi : int { E_ARGMIN = 0, E_STORE = 1, E_TOPM = 2 };
+constexpr int TOPBUF = 64;  // per-row candidate buffer of the top-m epilogue (shared memory)
 
 struct Args {
     int64_t n, d, k, k_pad;
@@ -45,11 +46,44 @@ struct Args {
     int32_t *flag_list;
     int32_t *cand;
     int32_t *flag_count;
-    // store epilogue
+    // store epilogue: Y[row, col] = act(acc + bias[col]) in FP32 or BF16; Ypre = acc + bias (FP32)
     float *Y;
     int64_t ldy;
+    const float *bias;
+    int act;       // 0: none, 1: GELU (erf form)
+    int out_bf16;
+    float *Ypre;
+    int64_t ldpre;
+    // top-m epilogue: the m largest (acc + bias) of every row, over all N chunks
+    int32_t *top_idx;
+    float *top_val;
+    int topm;
     int *status;
 };
+
+__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+// order-preserving map of floats to unsigned keys
+__device__ __forceinline__ uint32_t fkey(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// the m-th largest key among a thread's cnt buffered candidates (stride 128 in shared memory):
+// the largest T with #{key >= T} >= m, found bit by bit from the top
+__device__ __forceinline__ uint32_t topm_threshold(const float *bv, int t, int cnt, int m) {
+    uint32_t T = 0;
+    for (int b = 31; b >= 0; --b) {
+        const uint32_t cand = T | (1u << b);
+        int c = 0;
+        for (int i = 0; i < cnt; ++i) c += fkey(bv[i * 128 + t]) >= cand;
+        if (c >= m) T = cand;
+    }
+    return T;
+}
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -353,6 +387,12 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
             int i0 = 0, i1 = 0;
             float sx = 1.f;
             if (EPI == E_ARGMIN && FORM == F_FP8 && valid) sx = a.xscale[row];
+            // top-m state: threshold and this thread's buffer (slot-major, stride 128)
+            float tau = -__int_as_float(0x7f800000);
+            int tcnt = 0;
+            const int et = q * 32 + lane;
+            float *tbv = reinterpret_cast<float *>(base + (size_t)a.stages * a.stage_bytes + 1024);
+            int32_t *tbi = reinterpret_cast<int32_t *>(tbv + TOPBUF * 128);
             for (int nc = 0; nc < units_per_tile; ++nc) {
                 if (!mbar_wait(&accf[ab], aph, abort_flag)) goto epi_done;
                 tc_fence_after();
@@ -395,14 +435,87 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                             i1 = lt0 ? i0 : (lt1 ? j : i1);
                             i0 = lt0 ? j : i0;
                         }
-                    } else {
-                        if (valid) {
-                            float *yr = a.Y + row * a.ldy + c;
+                    } else if constexpr (EPI == E_STORE) {
+                        const int64_t col0 = (int64_t)nc * a.bn + c;
+                        if (valid && col0 < a.k) {
+                            float v[16];
 #pragma unroll
-                            for (int g = 0; g < 4; ++g)
-                                reinterpret_cast<float4 *>(yr)[g] =
-                                    make_float4(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]),
-                                                __uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3]));
+                            for (int g = 0; g < 16; ++g) v[g] = __uint_as_float(r[g]);
+                            if (a.bias) {
+#pragma unroll
+                                for (int g = 0; g < 4; ++g) {
+                                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g);
+                                    v[4 * g] += b4.x, v[4 * g + 1] += b4.y, v[4 * g + 2] += b4.z, v[4 * g + 3] += b4.w;
+                                }
+                            }
+                            if (a.Ypre) {
+                                float4 *pr = reinterpret_cast<float4 *>(a.Ypre + row * a.ldpre + col0);
+#pragma unroll
+                                for (int g = 0; g < 4; ++g) pr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                            }
+                            if (a.act == 1) {
+#pragma unroll
+                                for (int g = 0; g < 16; ++g) v[g] = gelu_erf(v[g]);
+                            }
+                            if (a.out_bf16) {
+                                uint32_t w[8];
+#pragma unroll
+                                for (int g = 0; g < 8; ++g) {
+                                    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * g], v[2 * g + 1]);
+                                    w[g] = *reinterpret_cast<uint32_t *>(&h);
+                                }
+                                uint4 *yr = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.Y) + row * a.ldy + col0);
+                                yr[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                                yr[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                            } else {
+                                float4 *yr = reinterpret_cast<float4 *>(a.Y + row * a.ldy + col0);
+#pragma unroll
+                                for (int g = 0; g < 4; ++g) yr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                            }
+                        }
+                    } else {
+                        // top-m: candidates above the running threshold go to this row's buffer
+                        const int64_t col0 = (int64_t)nc * a.bn + c;
+                        if (col0 >= a.k) return;
+                        float sv[16];
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            const float4 b4 = a.bias ? __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g)
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                            sv[4 * g] = __uint_as_float(r[4 * g]) + b4.x;
+                            sv[4 * g + 1] = __uint_as_float(r[4 * g + 1]) + b4.y;
+                            sv[4 * g + 2] = __uint_as_float(r[4 * g + 2]) + b4.z;
+                            sv[4 * g + 3] = __uint_as_float(r[4 * g + 3]) + b4.w;
+                        }
+                        uint32_t m = 0;
+#pragma unroll
+                        for (int g = 0; g < 16; ++g)
+                            if (sv[g] > tau && col0 + g < a.k) m |= 1u << g;
+                        while (m) {
+                            const int g = __ffs(m) - 1;
+                            m &= m - 1;
+                            float sg = 0.f;
+#pragma unroll
+                            for (int h = 0; h < 16; ++h)
+                                if (h == g) sg = sv[h];
+                            if (tcnt == TOPBUF) {
+                                const uint32_t T = topm_threshold(tbv, et, tcnt, a.topm);
+                                int nw = 0;
+                                for (int i = 0; i < tcnt; ++i) {
+                                    const float bvv = tbv[i * 128 + et];
+                                    if (fkey(bvv) >= T) {
+                                        tbv[nw * 128 + et] = bvv;
+                                        tbi[nw * 128 + et] = tbi[i * 128 + et];
+                                        ++nw;
+                                    }
+                                }
+                                tcnt = nw;
+                                tau = fkey_inv(T);
+                                if (!(sg > tau) || tcnt == TOPBUF) continue;
+                            }
+                            tbv[tcnt * 128 + et] = sg;
+                            tbi[tcnt * 128 + et] = (int32_t)(col0 + g);
+                            ++tcnt;
                         }
                     }
                 };
@@ -505,6 +618,28 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                 if (++ab == 2) {
                     ab = 0;
                     aph ^= 1;
+                }
+            }
+            if constexpr (EPI == E_TOPM) {
+                // exactly m outputs: keys above the m-th largest, then ties at it, -1 padding
+                if (valid) {
+                    const int m = a.topm;
+                    const uint32_t T = tcnt >= m ? topm_threshold(tbv, et, tcnt, m) : 0u;
+                    int w = 0;
+                    for (int pass = 0; pass < 2; ++pass)
+                        for (int i = 0; i < tcnt && w < m; ++i) {
+                            const float bvv = tbv[i * 128 + et];
+                            const uint32_t kk = fkey(bvv);
+                            if ((pass == 0 && kk > T) || (pass == 1 && kk == T)) {
+                                a.top_idx[row * m + w] = tbi[i * 128 + et];
+                                if (a.top_val) a.top_val[row * m + w] = bvv;
+                                ++w;
+                            }
+                        }
+                    for (; w < m; ++w) {
+                        a.top_idx[row * m + w] = -1;
+                        if (a.top_val) a.top_val[row * m + w] = -__int_as_float(0x7f800000);
+                    }
                 }
             }
         }
@@ -851,7 +986,7 @@ struct Plan {
     size_t smem;
 };
 
-static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256) {
+static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra_smem = 0) {
     Plan p;
     const int esize = (form == F_BF16) ? 2 : (form == F_FP8 ? 1 : 4);
     p.n_chunks = (int)ceil_div(k_pad, bn_cap);
@@ -862,9 +997,9 @@ static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256) {
     p.b_bytes = (uint32_t)p.bn * 128;
     p.stage_bytes = (x3 ? 2 : 1) * p.a_bytes + (x3 ? 2 : 1) * p.b_bytes;
     p.tx_bytes = p.a_bytes + (x3 ? 2 : 1) * p.b_bytes;
-    p.stages = (int)std::min<int64_t>(MAX_STAGES, SMEM_BUDGET / p.stage_bytes);
+    p.stages = (int)std::min<int64_t>(MAX_STAGES, (SMEM_BUDGET - extra_smem) / p.stage_bytes);
     p.tmem_cols = (2 * p.bn <= 256) ? 256 : 512;
-    p.smem = (size_t)p.stages * p.stage_bytes + 1024 + 1024;
+    p.smem = (size_t)p.stages * p.stage_bytes + 1024 + 1024 + extra_smem;
     return p;
 }
 
@@ -1025,6 +1160,39 @@ int launch_assign_tc_batched(gbkm_ctx *c, int dtype, const void *maps, const BPr
     }
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "batched tcgen05 launch");
+}
+
+
+// D = A B^T on tcgen05 (BF16 operands, FP32 accumulation) with a fused epilogue: store
+// act(D + bias) in FP32 or BF16 (and optionally the FP32 pre-activation), or, when top_idx is
+// given, the indices of the topm largest entries of every row of D + bias (D never written).
+// A: M x K, B: N x K, row-major BF16, K % 8 == 0, N % 16 == 0, 16-byte aligned.
+int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
+                        const float *bias, int act, int out_bf16, void *Y, int64_t ldy, float *Ypre, int64_t ldpre,
+                        int32_t *top_idx, float *top_val, int topm) {
+    using namespace tc;
+    if (M < 1 || N < 16 || N % 16 || K < 8 || K % 8 || !tc::encode_fn())
+        return set_error(c, GBKM_EUNSUPPORTED, "gemm: shape unsupported by the tcgen05 GEMM");
+    const bool topk = top_idx != nullptr;
+    if (topk && (topm < 1 || topm > TOPBUF / 2)) return set_error(c, GBKM_EINVAL, "gemm: topm must be in [1, 32]");
+    const int extra = topk ? TOPBUF * 128 * 8 : 0;
+    const Plan p = plan(F_BF16, K, N, 256, extra);
+    CUtensorMap tA, tB;
+    if (!make_tmap(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, (uint64_t)K, (uint64_t)M, 2, BM) ||
+        !make_tmap(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, (uint64_t)K, (uint64_t)N, 2, (uint32_t)p.bn))
+        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the GEMM operands");
+    Args a{};
+    a.n = M, a.d = K, a.k = N, a.k_pad = N;
+    a.n_chunks = p.n_chunks, a.bn = p.bn, a.kb = p.kb, a.stages = p.stages, a.tmem_cols = p.tmem_cols;
+    a.m_tiles = (int)ceil_div(M, BM);
+    a.a_bytes = p.a_bytes, a.b_bytes = p.b_bytes, a.stage_bytes = p.stage_bytes, a.tx_bytes = p.tx_bytes;
+    a.idesc = make_idesc(F_BF16, BM, p.bn);
+    a.Y = static_cast<float *>(Y), a.ldy = ldy;
+    a.bias = bias, a.act = act, a.out_bf16 = out_bf16, a.Ypre = Ypre, a.ldpre = ldpre;
+    a.top_idx = top_idx, a.top_val = top_val, a.topm = topm;
+    a.status = c->status;
+    if (topk) return launch<F_BF16, E_TOPM>(c, tA, tB, tB, a, p);
+    return launch<F_BF16, E_STORE>(c, tA, tB, tB, a, p);
 }
 
 }  // namespace gbkm

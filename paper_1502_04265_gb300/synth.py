@@ -32,6 +32,7 @@ __all__ = [
     "orthonormal_basis",
     "subspace_mixture_chunk",
     "batch_problem_list",
+    "mlp_init",
 ]
 
 
@@ -121,3 +122,15 @@ def batch_problem_list(count: int, seed: int = 0, *, n_range=(1_000, 100_000),
         k = max(1, min(k, n))
         out.append({"n": n, "d": d, "k": k, "seed": p})
     return out
+
+
+def mlp_init(d_in: int, hidden: int, k: int, seed: int) -> np.ndarray:
+    """Initial parameters of the candidate-proposal network (FP32 vector, layout W1, b1, W2, b2,
+    W3, b3 with rows = output units): weights uniform in +-1/sqrt(fan_in), biases zero."""
+    rng = np.random.default_rng([seed, 0x31F])
+    parts = []
+    for fan_out, fan_in in ((hidden, d_in), (hidden, hidden), (k, hidden)):
+        bound = 1.0 / math.sqrt(fan_in)
+        parts.append(rng.uniform(-bound, bound, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
