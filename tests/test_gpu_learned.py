@@ -117,14 +117,14 @@ def test_training_lowers_the_loss(gb):
 
 def test_learned_assign_labels_are_exact(gb):
     d, h, k = 64, 64, 64
-    X, z, mu = _clustered(20000, d, k, seed=12)
+    # one mixture: the first 20,000 points are assigned, the last 8,192 (held out) train the net
+    Xall, z, mu = _clustered(28192, d, k, seed=12)
+    X, Xt = Xall[:20000], Xall[20000:]
     C = torch.from_numpy(mu.astype(np.float32)).to(DEV)
-    Xg = torch.from_numpy(X).to(DEV)
+    Xg = torch.from_numpy(np.ascontiguousarray(X)).to(DEV)
     Xh = Xg.to(torch.bfloat16)
     exact = gb.kmeans_assign(Xg, C, compute="f32")
-    # train on held-out points labelled by the exact method
-    Xt, _, _ = _clustered(8192, d, k, seed=13)
-    Xtg = torch.from_numpy(Xt).to(DEV)
+    Xtg = torch.from_numpy(np.ascontiguousarray(Xt)).to(DEV)
     lt = gb.kmeans_assign(Xtg, C, compute="f32")
     net = _net(gb, d, h, k, seed=2)
     net.train(Xtg.to(torch.bfloat16), lt, epochs=6, batch=1024, lr=3e-3)
@@ -132,4 +132,4 @@ def test_learned_assign_labels_are_exact(gb):
     labels, nf = gb.kmeans_learned_assign(net, Xg, Xh, C, s2, topm=8)
     gb.gbkm_sync()
     assert torch.equal(labels, exact)
-    assert int(nf.item()) < 20000 // 2
+    assert int(nf.item()) < 20000 // 10
