@@ -1,16 +1,34 @@
 #!/usr/bin/env python
-"""Lloyd-iteration throughput of the GB300 k-means hot path.
+"""Throughput of the GB300 k-means hot path on five seeded synthetic workloads.
 
-Workload (the high-dimensional plain-vs-precision configuration): n = 200,000 points, d = 1,024,
-k = 100, seeded Gaussian mixture with 100 components (weights Dirichlet(1), means U[-10,10]^d,
-sigma log-uniform in [0.5, 2]).  A step is one Lloyd iteration: kmeans_assign (distance GEMM +
-fused top-2 epilogue + exact recheck of certified near-ties) followed by kmeans_update
-(stable counting sort + segmented CF sums + FP64 centroids and costs).  k-means++ seeding,
-the row norms and the operand copy of X are per-dataset preparation, done before the timed
-region.  X (819 MB FP32 + 410 MB BF16) is larger than L2 (129 MB), so no flush is needed.
+Every workload prints one JSON line (rank 0).  The metric is assign+update GFLOP/s with the
+algorithmic flop count 2nkd + nd per Lloyd iteration (padding, rechecks and fallbacks are not
+counted), and the roofline of the dominant kernel beside it.
 
-Metric: assign+update GFLOP/s with the algorithmic flop count 2nkd + nd per iteration.
-Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+  highdim (default)  n = 200,000 points, d = 1,024, k = 100, 100-component Gaussian mixture
+                     (weights Dirichlet(1), means U[-10,10]^d, sigma log-uniform in [0.5, 2]).
+                     A step is one Lloyd iteration: kmeans_assign (distance GEMM, fused top-2
+                     epilogue, exact recheck of certified near-ties) + kmeans_update (stable
+                     counting sort, segmented CF sums, FP64 centroids and costs).  Seeding, row
+                     norms and the operand copy are per-dataset preparation, timed separately
+                     in "pipeline".  X (819 MB FP32, 410 MB BF16) is larger than L2.
+  small              n = 10,000, d = 64, k = 10, 10 components, FP32: a step is a whole run
+                     (row norms, k-means++, 20 Lloyd iterations); L2 is flushed between steps
+                     (X is 2.56 MB).  Latency-bound.
+  stream             2,000,000 points in d = 2,048 from a 500-component mixture in a random
+                     rank-64 subspace plus N(0, 0.1^2) noise; 31 chunks of 65,536 rows projected
+                     to r = 64 by the BF16 projection GEMM, then k = 1,000 k-means++ and Lloyd on
+                     the coordinates in BF16 (step), FP8 and FP32 (forms), 20 iterations.
+  batch              512 problems (n log-uniform in [1e3, 1e5], d in {32, 128, 512}, k
+                     log-uniform in [4, 256], k components each), 4 k-means++ seeds each,
+                     20 Lloyd iterations, in one recorded CUDA graph; a step is one replay.
+  learned            n = 4,000,000, d = 256, k = 16,384 (16,384 components; 200,000 held-out
+                     points train the proposal network).  Centers: k-means++ on the first
+                     200,000 points, then 5 FP32 Lloyd iterations, frozen.  A step is the learned
+                     assignment (MLP 256-256-256-16384, top-32 candidates, certified exact check,
+                     full-scan fallback) + the CF update; the BF16 and FP32 full scans run beside.
+
+``--impl reference`` times the FP64 CPU oracle on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -27,33 +45,49 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "assign+update GFLOP/s (Lloyd iteration, 200k x 1024, k=100)"
 UNIT = "GFLOP/s"
+METRICS = {
+    "highdim": "assign+update GFLOP/s (Lloyd iteration, 200k x 1024, k=100)",
+    "small": "assign+update GFLOP/s (whole k-means++ + 20-iteration run, 10k x 64, k=10)",
+    "stream": "assign+update GFLOP/s (Lloyd iteration on projected coordinates, 2M x 64, k=1000)",
+    "batch": "assign+update GFLOP/s (512 problems x 4 seeds x 20 iterations per replay)",
+    "learned": "assign+update GFLOP/s, exact-method flops (learned assignment, 4M x 256, k=16384)",
+}
+DEFAULT_STEPS = {"highdim": 30, "small": 20, "stream": 20, "batch": 5, "learned": 5}
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense ratio, applied to the measured BF16 peak
+TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense ratios, applied to the measured BF16 peak
+FP8_OVER_BF16 = 4.5 / 2.25
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbkm", choices=["gbkm", "reference"])
+    ap.add_argument("--workload", default="highdim", choices=list(METRICS))
     ap.add_argument("--form", default="auto", choices=["auto", "f32", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tcgen05"])
-    ap.add_argument("--n", type=int, default=200_000)
-    ap.add_argument("--d", type=int, default=1024)
-    ap.add_argument("--k", type=int, default=100)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--n", type=int, default=None, help="override n (highdim / learned)")
+    ap.add_argument("--d", type=int, default=None, help="override d (highdim)")
+    ap.add_argument("--k", type=int, default=None, help="override k (highdim)")
+    ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
+    ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 path beside the BF16 form")
-    return ap.parse_args()
+    ap.add_argument("--no-compare", action="store_true", help="skip the other forms")
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = DEFAULT_STEPS[a.workload]
+    if a.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return a
 
 
+# ---------------------------------------------------------------------------- shared helpers
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -67,24 +101,27 @@ def load_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the tensor-core kernel source, to tell whether stored ncu counters still apply."""
+    """Hash of the kernel sources, to tell whether stored ncu counters still apply."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("k_tc.cu", "internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1502_04265_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_1502_04265_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel, form, workload):
-    """DRAM bytes per launch from a committed ncu capture, or None if the kernel changed since."""
+def stored_traffic(key):
+    """DRAM bytes per launch of `key` from a committed ncu capture (profiles/traffic.json), or
+    None when the kernels changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         table = json.load(f)
-    e = table.get(f"{kernel}/{form}/{workload}")
+    e = table.get(key)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
     return e["dram_bytes_per_launch"]
@@ -143,8 +180,188 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(X, C, cpu_seconds, threads=None):
-    """Time the FP64 oracle's assign + update on a bounded row sample; GFLOP/s of the sample."""
+class Env:
+    """Rank, device, library context and peaks of this process."""
+
+    def __init__(self, args):
+        import torch
+        import torch.distributed as dist
+
+        from paper_1502_04265_gb300 import _binding as B
+
+        self.args = args
+        self.torch, self.dist, self.B = torch, dist, B
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        if self.world > 1:
+            dist.init_process_group("nccl", device_id=self.dev)
+        B.load(build_if_missing=True)
+        self.ctx = B.Context(self.local)
+        self.peaks = load_peaks()
+
+    @property
+    def stream(self):
+        return self.torch.cuda.current_stream(self.dev)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max_over_ranks(self, v):
+        if self.world == 1:
+            return v
+        t = self.torch.tensor([v], dtype=self.torch.float64, device=self.dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def event(self):
+        return self.torch.cuda.Event(enable_timing=True)
+
+    def timed(self, step, steps, warmup, clocks=False, flush=None):
+        """`warmup` untimed and `steps` timed calls of step(i), CUDA events on the launching
+        stream, barrier + synchronize on both sides; with `flush`, L2 is overwritten before
+        every step and only the steps are timed.  Returns ms per step (max over ranks), our
+        kernel launches in the timed region, the library's per-kernel profile and the clocks."""
+        torch = self.torch
+        for i in range(warmup):
+            if flush:
+                flush()
+            step(i)
+        self.ctx.sync()
+        sampler = ClockSampler(self.local) if clocks and self.rank == 0 and not self.args.no_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.5)
+        self.ctx.profile(True)
+        l0 = self.ctx.launch_count()
+        self.barrier()
+        torch.cuda.synchronize(self.dev)
+        pairs = []
+        if flush is None:
+            a, b = self.event(), self.event()
+            a.record(self.stream)
+            for i in range(steps):
+                step(warmup + i)
+            b.record(self.stream)
+            pairs.append((a, b))
+        else:
+            for i in range(steps):
+                flush()
+                a, b = self.event(), self.event()
+                a.record(self.stream)
+                step(warmup + i)
+                b.record(self.stream)
+                pairs.append((a, b))
+        torch.cuda.synchronize(self.dev)
+        self.barrier()
+        ms_total = sum(a.elapsed_time(b) for a, b in pairs)
+        launches = self.ctx.launch_count() - l0
+        prof = self.ctx.profile_read()
+        self.ctx.profile(False)
+        clk = sampler.stop() if sampler else None
+        return {"ms": self.max_over_ranks(ms_total / max(steps, 1)), "launches": int(launches), "prof": prof,
+                "clocks": clk, "total_s": ms_total * 1e-3}
+
+    def once(self, fn, warmup=1):
+        """Device time of one call of fn() after `warmup` calls, with the per-kernel profile."""
+        for _ in range(warmup):
+            fn()
+        R = self.timed(lambda i: fn(), 1, 0)
+        return R
+
+
+def kernel_avg_s(prof, name):
+    launches, ms = prof.get(name, (0, float("nan")))
+    return ms / max(launches, 1) * 1e-3
+
+
+def roofline(peaks, kernel, avg_s, bytes_, flops, unit_tflops, total_s, bound=None, note=None, traffic=None):
+    """Roofline object of one kernel: algorithmic bytes / flops per launch over its average launch
+    duration, against the measured HBM copy bandwidth or the compute unit's peak (the burst BF16
+    figure for a kernel timed for under a second, the sustained one otherwise)."""
+    if bound is None:
+        t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
+        t_c = flops / (unit_tflops * 1e12) if flops else 0.0
+        bound = "hbm" if t_hbm >= t_c else "tensor"
+    if bound == "hbm":
+        ach, peak, unit = bytes_ / avg_s / 1e9, peaks["hbm_gbs"], "GB/s"
+    else:  # "tensor" or "alu": flops against the compute unit's peak
+        ach, peak, unit = flops / avg_s / 1e12, unit_tflops, "TFLOP/s"
+    r = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak, "traffic": traffic,
+         "kernel": kernel, "kernel_ms": avg_s * 1e3, "algorithmic_bytes": int(bytes_),
+         "algorithmic_flops": float(flops), "peak_source": f"{peaks['source']} ({'of measured' if peaks['source'] == 'measured' else 'of fallback'})"}
+    if note:
+        r["note"] = note
+    return r
+
+
+def bf16_peak(peaks, total_s):
+    return peaks["bf16_tflops_sustained"] if total_s > 1.0 else peaks["bf16_tflops"]
+
+
+def unit_peak(peaks, compute, engine_tc, total_s):
+    b = bf16_peak(peaks, total_s)
+    if compute == "bf16":
+        return b
+    if compute == "fp8":
+        return b * FP8_OVER_BF16
+    return b * TF32_OVER_BF16 / 3.0 if engine_tc else FFMA_PEAK_TFLOPS
+
+
+def gen_pool(jobs, fn, workers=None):
+    """Run the seeded generators of many independent pieces in spawned processes (started before
+    any CUDA use in this process); returns the results in job order."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    workers = workers or max(1, min(8, (os.cpu_count() or 2) - 1))
+    ex = ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    return ex, [ex.submit(fn, j) for j in jobs]
+
+
+def lloyd_timed(env, X, Xop, scales, xnorm, C0, compute, engine, steps, warmup, clocks=False):
+    """`warmup` + `steps` Lloyd iterations from C0 (assign + update per step); the timed steps'
+    ms, launches, profile, the FP64 cost trace and recheck counts."""
+    torch, B = env.torch, env.B
+    n = X.shape[0]
+    labels = torch.empty(n, dtype=torch.int32, device=env.dev)
+    Cs = [C0.clone(), torch.empty_like(C0)]
+    cost = torch.zeros((steps + warmup, 2), dtype=torch.float64, device=env.dev)
+    nre = torch.zeros(steps + warmup, dtype=torch.int64, device=env.dev)
+
+    def step(i):
+        B.kmeans_assign(X, Cs[0], Xop=Xop, Xop_scales=scales, xnorm=xnorm, compute=compute, engine=engine,
+                        labels=labels, n_rechecked=nre[i:i + 1], ctx=env.ctx)
+        B.kmeans_update(X, labels, Cs[0], C_new=Cs[1], cost_old=cost[i, 0:1], cost_new=cost[i, 1:2], ctx=env.ctx)
+        Cs.reverse()
+
+    R = env.timed(step, steps, warmup, clocks=clocks)
+    env.ctx.sync()
+    R.update({"costs": cost.cpu().numpy(), "rechecked": nre.cpu().numpy(), "C": Cs[0], "labels": labels})
+    return R
+
+
+def assign_kernel(prof):
+    return "assign_tc" if "assign_tc" in prof else "assign_simt"
+
+
+def base_line(env, workload, value, ms, steps, warmup, dtype, config):
+    return {"metric": METRICS[workload], "value": value, "unit": UNIT, "n_gpus": env.world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+
+
+def kernels_ms(prof):
+    return {name: prof[name][1] / max(prof[name][0], 1) for name in prof}
+
+
+# ---------------------------------------------------------------------------- CPU oracle samples
+def oracle_assign_update_rate(X, C, cpu_seconds, threads=None, label=""):
+    """The FP64 oracle's assign + update on a bounded row sample of X, repeated for about
+    cpu_seconds; GFLOP/s of the sample (2 m k d + m d per pass)."""
     import numpy as np
 
     import oracle
@@ -153,14 +370,13 @@ def cpu_oracle_rate(X, C, cpu_seconds, threads=None):
     cores = oracle.set_threads(threads or os.cpu_count() or 1)
     n, d = X.shape
     k = C.shape[0]
-    Cd = C.astype(np.float64)
-    rows = min(n, 2048)
+    Cd = np.ascontiguousarray(C, dtype=np.float64)
+    rows = min(n, 512)
     t0 = time.perf_counter()
     lab, _, _ = oracle.assign(X[:rows], Cd)
     oracle.update(X[:rows], lab, Cd)
     dt = time.perf_counter() - t0
-    rows = int(min(n, max(rows, rows * cpu_seconds / max(dt, 1e-3))))
-    # repeat the sample until about cpu_seconds of work has been timed
+    rows = int(min(n, max(rows, rows * cpu_seconds / 3 / max(dt, 1e-3))))
     reps, t0 = 0, time.perf_counter()
     while True:
         lab, _, _ = oracle.assign(X[:rows], Cd)
@@ -171,92 +387,57 @@ def cpu_oracle_rate(X, C, cpu_seconds, threads=None):
             break
     flops = reps * (2.0 * rows * k * d + rows * d)
     return {"value": flops / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {rows} of {n} rows x {reps} passes: assign over all k={k} + update, "
+            "sample": f"{label}first {rows} of {n} rows x {reps} passes: assign over all k={k} + update, "
                       f"FP64 C loops (OpenMP over points), {dt:.1f} s"}
 
 
-def make_workload(n, d, k, seed):
-    from paper_1502_04265_gb300 import synth
-
-    X, _ = synth.gaussian_mixture(n, d, k, seed=seed)
-    return X, synth.seed_uniforms(k, seed=seed)
-
-
-def run_reference(args, rank, world):
-    """The oracle timed on the host cores, on bounded samples of the same workload."""
-    if rank != 0:
-        return
+def oracle_lloyd_rate(problems, iters, cpu_seconds, threads=None, label=""):
+    """The oracle's k-means++ + `iters` Lloyd iterations over (X, k, u) runs until about
+    cpu_seconds; GFLOP/s counting iters x (2nkd + nd) per run."""
     import numpy as np
 
     import oracle
 
-    X, u = make_workload(args.n, args.d, args.k, 0)
     oracle.build()
-    cores = oracle.set_threads(os.cpu_count() or 1)
-    # fixed centers for timing: rows picked by the seeding uniforms (assign work does not depend
-    # on which centers are used)
-    C = X[(u * args.n).astype(np.int64) % args.n].astype(np.float64)
-    rows = min(args.n, 2048)
-    t0 = time.perf_counter()
-    lab, _, _ = oracle.assign(X[:rows], C)
-    oracle.update(X[:rows], lab, C)
+    cores = oracle.set_threads(threads or os.cpu_count() or 1)
+    flops, runs, t0 = 0.0, 0, time.perf_counter()
+    for X, k, u in problems:
+        _, C0, _, _ = oracle.seed_pp(X, k, u)
+        oracle.lloyd(X, C0, iters)
+        n, d = X.shape
+        flops += iters * (2.0 * n * k * d + n * d)
+        runs += 1
+        if time.perf_counter() - t0 >= cpu_seconds:
+            break
     dt = time.perf_counter() - t0
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    rows = int(min(args.n, max(256, rows * budget / max(dt, 1e-3))))
-    for _ in range(args.warmup):
-        lab, _, _ = oracle.assign(X[:rows], C)
-        oracle.update(X[:rows], lab, C)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        lab, _, _ = oracle.assign(X[:rows], C)
-        oracle.update(X[:rows], lab, C)
-    dt = (time.perf_counter() - t0) / args.steps
-    flops = 2.0 * rows * args.k * args.d + rows * args.d
-    val = flops / dt / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"gaussian mixture n={args.n} d={args.d} "
-                                                       f"k={args.k}; oracle on a {rows}-row sample per step"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {rows} of {args.n} rows per step, assign + update"},
-            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    return {"value": flops / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{label}{runs} whole runs (k-means++ + {iters} Lloyd iterations), FP64 C loops, {dt:.1f} s"}
 
 
-def main():
-    args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
+# ---------------------------------------------------------------------------- workloads
+def mixture(n, d, comps, seed):
+    from paper_1502_04265_gb300 import synth
 
+    X, _ = synth.gaussian_mixture(n, d, comps, seed=seed)
+    return X
+
+
+def run_highdim(env, args):
     import numpy as np
-    import torch
-    import torch.distributed as dist
 
-    from paper_1502_04265_gb300 import _binding as B
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import synth
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-    B.load(build_if_missing=True)
-    n, d, k = args.n, args.d, args.k
-    F_step = 2.0 * n * k * d + n * d
-    # independent replica per rank (the path has no exchange step): seed = rank
-    X, u = make_workload(n, d, k, seed=rank)
-    Xg = torch.from_numpy(X).to(dev)
-    ug = torch.from_numpy(u).to(dev)
-    ctx = B.Context(local)
-
-    form = args.form
-    engine = args.engine
+    n, d, k = args.n or 200_000, args.d or 1024, args.k or 100
+    F = 2.0 * n * k * d + n * d
+    X = mixture(n, d, k, seed=env.rank)
+    u = synth.seed_uniforms(k, seed=env.rank)
+    Xg = torch.from_numpy(X).to(env.dev)
+    ug = torch.from_numpy(u).to(env.dev)
+    ctx = env.ctx
     xnorm = B.kmeans_row_norms(Xg, ctx=ctx)
-    idx, C0 = B.kmeans_seed_pp(Xg, k, ug, ctx=ctx)
-    Xop = None
+    _, C0 = B.kmeans_seed_pp(Xg, k, ug, ctx=ctx)
+    form, engine, Xop = args.form, args.engine, None
     if form in ("auto", "bf16"):
         Xb, _ = B.kmeans_quantize(Xg, "bf16", ctx=ctx)
         try:
@@ -271,187 +452,699 @@ def main():
         form = "f32"
     ctx.sync()
 
-    def timed_run(form_, Xop_, engine_, steps, warmup, sample_clocks):
-        """W warm-up and `steps` timed Lloyd iterations from C0; returns timing and diagnostics."""
-        labels = torch.empty(n, dtype=torch.int32, device=dev)
-        Cs = [C0.clone(), torch.empty_like(C0)]
-        cost = torch.zeros((max(steps, 1) + warmup, 2), dtype=torch.float64, device=dev)
-        nre = torch.zeros(max(steps, 1) + warmup, dtype=torch.int64, device=dev)
+    R = lloyd_timed(env, Xg, Xop, None, xnorm, C0, form, engine, args.steps, args.warmup, clocks=True)
+    ms, prof = R["ms"], R["prof"]
+    value = env.world * F / (ms * 1e-3) / 1e9
+    peaks = env.peaks
+    kname = assign_kernel(prof)
+    tc = kname == "assign_tc"
+    es = 2 if form == "bf16" else 4
+    bytes_k = n * d * es + k * d * es + n * 4
+    roof = roofline(peaks, kname, kernel_avg_s(prof, kname), bytes_k, 2.0 * n * k * d,
+                    unit_peak(peaks, form, tc, R["total_s"]), R["total_s"],
+                    bound=None if form == "bf16" else ("tensor" if tc else "alu"),
+                    note=None if form == "bf16" else ("3xTF32: measured BF16 peak x nominal TF32/BF16 ratio / 3" if tc
+                                                      else "FFMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"),
+                    traffic=stored_traffic(f"{kname}/{form}/{n}x{d}_k{k}"))
+    B_step = n * d * es + k * d * 4 + n * 4 + k * (d + 2) * 8
+    p_unit = unit_peak(peaks, form, tc, R["total_s"]) * 1e12
+    t_roof = max(B_step / (peaks["hbm_gbs"] * 1e9), 2.0 * n * k * d / p_unit)
+    step_roof = {"t_roof_ms": t_roof * 1e3, "frac": t_roof / (ms * 1e-3),
+                 "note": "T_roof = max(bytes / HBM, flops / unit peak) over the whole iteration; the "
+                         "update's FP32 read of X is not counted in the bytes"}
 
-        def step(i):
-            B.kmeans_assign(Xg, Cs[0], Xop=Xop_, xnorm=xnorm, compute=form_, engine=engine_, labels=labels,
-                            n_rechecked=nre[i:i + 1], ctx=ctx)
-            B.kmeans_update(Xg, labels, Cs[0], C_new=Cs[1], cost_old=cost[i, 0:1], cost_new=cost[i, 1:2],
-                            ctx=ctx)
-            Cs.reverse()
+    # the whole run (per-dataset preparation included): norms, operand copy, k-means++, 30 iterations
+    iters = 30
+    labels = torch.empty(n, dtype=torch.int32, device=env.dev)
+    Ca, Cb = torch.empty_like(C0), torch.empty_like(C0)
+    tr = torch.zeros((iters, 2), dtype=torch.float64, device=env.dev)
 
-        for i in range(warmup):
-            step(i)
-        ctx.sync()
-        stream = torch.cuda.current_stream(dev)
-        sampler = ClockSampler(local) if sample_clocks else None
-        if sampler:
-            sampler.start()
-            time.sleep(0.5)
-        ctx.profile(True)
-        l0 = ctx.launch_count()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(steps):
-            step(warmup + i)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
-        ms_total = e0.elapsed_time(e1)
-        launches = ctx.launch_count() - l0
-        prof = ctx.profile_read()
-        ctx.profile(False)
-        clocks = sampler.stop() if sampler else None
-        ms_step = ms_total / max(steps, 1)
-        if world > 1:
-            t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_step = float(t.item())
-        ctx.sync()
-        return {"ms_step": ms_step, "launches": launches, "prof": prof, "clocks": clocks,
-                "costs": cost.cpu().numpy(), "rechecked": nre.cpu().numpy(), "C": Cs[0]}
+    def whole():
+        B.kmeans_row_norms(Xg, xnorm=xnorm, ctx=ctx)
+        if form == "bf16":
+            B.kmeans_quantize(Xg, "bf16", Xq=Xop, ctx=ctx)
+        B.kmeans_seed_pp(Xg, k, ug, C_out=Ca, ctx=ctx)
+        cur, nxt = Ca, Cb
+        for t in range(iters):
+            B.kmeans_assign(Xg, cur, Xop=Xop, xnorm=xnorm, compute=form, engine=engine, labels=labels, ctx=ctx)
+            B.kmeans_update(Xg, labels, cur, C_new=nxt, cost_old=tr[t, 0:1], cost_new=tr[t, 1:2], ctx=ctx)
+            cur, nxt = nxt, cur
 
-    stream = torch.cuda.current_stream(dev)
-    R = timed_run(form, Xop, engine, args.steps, args.warmup, rank == 0 and not args.no_clocks)
-    ms_step, launches, prof, clocks = R["ms_step"], R["launches"], R["prof"], R["clocks"]
-    costs, rechecked, C = R["costs"], R["rechecked"], R["C"]
-    value = world * F_step / (ms_step * 1e-3) / 1e9
+    W = env.once(whole)
+    pipeline = {"iterations": iters, "total_ms": W["ms"],
+                "gflops_whole_run": iters * F / (W["ms"] * 1e-3) / 1e9,
+                "stage_ms": {nm: W["prof"][nm][1] for nm in ("row_norms", "quantize", "seed") if nm in W["prof"]},
+                "note": "one whole run from raw X: the k-means++ time is included, its flops are not"}
 
-    # ---- dominant kernel roofline
-    peaks = load_peaks()
-    kname = "assign_tc" if "assign_tc" in prof else "assign_simt"
-    kl, kms = prof.get(kname, (1, float("nan")))
-    k_avg_s = kms / max(kl, 1) * 1e-3
-    if form == "bf16":
-        bytes_k = n * d * 2 + k * d * 2 + n * 4
-        t_hbm = bytes_k / (peaks["hbm_gbs"] * 1e9)
-        t_tc = 2.0 * n * k * d / (peaks["bf16_tflops"] * 1e12)
-        if t_hbm >= t_tc:
-            ach = bytes_k / k_avg_s / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None}
-        else:
-            ach = 2.0 * n * k * d / k_avg_s / 1e12
-            roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                    "frac": ach / peaks["bf16_tflops"], "traffic": None}
-    elif kname == "assign_tc":
-        peak = peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0
-        ach = 2.0 * n * k * d / k_avg_s / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "note": "3xTF32: measured BF16 burst x nominal TF32/BF16 ratio / 3"}
-    else:
-        ach = 2.0 * n * k * d / k_avg_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FFMA_PEAK_TFLOPS, "traffic": None,
-                "note": "FFMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"}
-    roof["kernel"] = kname
-    roof["kernel_ms"] = k_avg_s * 1e3
-    roof["peak_source"] = peaks["source"]
-    wl = f"{n}x{d}_k{k}"
-    roof["traffic"] = stored_traffic(kname, form, wl) if kname == "assign_tc" else None
-    roof["algorithmic_bytes"] = (n * d * (2 if form == "bf16" else 4) + k * d * 4 + n * 4)
-    # whole-step roofline of the metric: one read of X at the operand dtype + C + labels + CFs
-    # against HBM, and the distance flops against the unit used
-    B_step = n * d * (2 if form == "bf16" else 4) + k * d * 4 + n * 4 + k * (d + 2) * 8
-    p_unit = (peaks["bf16_tflops"] if form == "bf16" else
-              (peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0 if kname == "assign_tc" else FFMA_PEAK_TFLOPS)) * 1e12
-    t_roof = max(B_step / (peaks["hbm_gbs"] * 1e9), F_step / p_unit)
-    step_roof = {"t_roof_ms": t_roof * 1e3, "frac": t_roof / (ms_step * 1e-3),
-                 "note": "T_roof = max(bytes / HBM, flops / unit peak); the update's FP32 read of X "
-                         "is not counted in the bytes"}
-
-    # ---- end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e and args.e2e_steps > 0:
+    if not args.no_e2e:
         Xh = torch.from_numpy(X).pin_memory()
         Ch_out = torch.empty((k, d), dtype=torch.float32).pin_memory()
         cost_h = torch.empty(1, dtype=torch.float64).pin_memory()
         Xd = torch.empty_like(Xg)
-        xn2 = torch.empty(n, dtype=torch.float32, device=dev)
-        Xb2 = torch.empty((n, d), dtype=torch.bfloat16, device=dev) if form == "bf16" else None
-        Ce = C.clone()
-        Cen = torch.empty_like(Ce)
-        lab2 = torch.empty(n, dtype=torch.int32, device=dev)
-        co2 = torch.empty(2, dtype=torch.float64, device=dev)
+        xn2 = torch.empty(n, dtype=torch.float32, device=env.dev)
+        Xb2 = torch.empty((n, d), dtype=torch.bfloat16, device=env.dev) if form == "bf16" else None
+        Ce, Cen = R["C"].clone(), torch.empty_like(C0)
+        lab2 = torch.empty(n, dtype=torch.int32, device=env.dev)
+        co2 = torch.empty(2, dtype=torch.float64, device=env.dev)
+        st = {"C": Ce, "Cn": Cen}
 
-        def e2e_step():
-            nonlocal Ce, Cen
+        def e2e_step(i):
             Xd.copy_(Xh, non_blocking=True)
             B.kmeans_row_norms(Xd, xnorm=xn2, ctx=ctx)
             if Xb2 is not None:
                 B.kmeans_quantize(Xd, "bf16", Xq=Xb2, ctx=ctx)
-            B.kmeans_assign(Xd, Ce, Xop=Xb2, xnorm=xn2, compute=form, engine=engine, labels=lab2, ctx=ctx)
-            B.kmeans_update(Xd, lab2, Ce, C_new=Cen, cost_old=co2[0:1], cost_new=co2[1:2], ctx=ctx)
-            Ch_out.copy_(Cen, non_blocking=True)
+            B.kmeans_assign(Xd, st["C"], Xop=Xb2, xnorm=xn2, compute=form, engine=engine, labels=lab2, ctx=ctx)
+            B.kmeans_update(Xd, lab2, st["C"], C_new=st["Cn"], cost_old=co2[0:1], cost_new=co2[1:2], ctx=ctx)
+            Ch_out.copy_(st["Cn"], non_blocking=True)
             cost_h.copy_(co2[1:2], non_blocking=True)
-            Ce, Cen = Cen, Ce
+            st["C"], st["Cn"] = st["Cn"], st["C"]
 
-        e2e_step()
-        torch.cuda.synchronize(dev)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        e_ms = a.elapsed_time(b) / args.e2e_steps
-        e2e = {"value": world * F_step / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+        E = env.timed(e2e_step, args.e2e_steps or 5, 1)
+        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * d * 4 + 8),
-               "ms_per_step": e_ms}
+               "ms_per_step": E["ms"], "note": "H2D of X from pinned memory, norms, operand copy, assign, "
+                                               "update and D2H of the centers and the cost every step"}
 
     forms = None
     if form == "bf16" and not args.no_compare:
         s32 = max(3, min(args.steps, args.steps // 2))
-        R32 = timed_run("f32", None, "tcgen05", s32, args.warmup, False)
-        v32 = world * F_step / (R32["ms_step"] * 1e-3) / 1e9
-        # cost after the same number of iterations from the same centers in both forms
+        R32 = lloyd_timed(env, Xg, None, None, xnorm, C0, "f32", "tcgen05", s32, args.warmup)
+        v32 = env.world * F / (R32["ms"] * 1e-3) / 1e9
         it = args.warmup + min(s32, args.steps) - 1
-        c16 = float(costs[it, 1]) if args.steps else float("nan")
-        c32 = float(R32["costs"][it, 1])
-        forms = {"bf16": {"value": value, "ms_per_step": ms_step},
-                 "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms_step"],
-                                "assign_ms": R32["prof"].get("assign_tc", (1, float("nan")))[1]
-                                / max(R32["prof"].get("assign_tc", (1, 0))[0], 1)},
-                 "speedup_vs_f32": v32 and value / v32,
-                 "final_cost_rel_gap": abs(c16 - c32) / c32,
-                 "note": "both forms run the same Lloyd iterations from the same seeds; labels are "
-                         "exact in both (certified near-ties re-resolved), so costs agree to rounding"}
+        c16, c32 = float(R["costs"][it, 1]), float(R32["costs"][it, 1])
+        forms = {"bf16": {"value": value, "ms_per_step": ms},
+                 "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms"],
+                                "assign_ms": kernel_avg_s(R32["prof"], "assign_tc") * 1e3},
+                 "speedup_vs_f32": value / v32, "final_cost_rel_gap": abs(c16 - c32) / c32,
+                 "note": "both forms run the same Lloyd iterations from the same seeds; labels are exact in "
+                         "both (certified near-ties re-resolved), so costs agree to rounding"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(X, C.cpu().numpy(), args.cpu_seconds)
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_assign_update_rate(X, R["C"].cpu().numpy(), args.cpu_seconds)
 
-    if rank == 0:
-        kept = [name for name in prof]
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": form, "data": "synthetic",
-            "config": {"workload": f"gaussian mixture n={n} d={d} k={k} (100 components, seed rank), "
-                                   f"one Lloyd iteration per step",
-                       "form": form, "engine": engine,
-                       "l2": "inputs larger than L2 (X is 819 MB FP32 / 410 MB BF16)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roof, "step_roofline": step_roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(launches),
-            "clocks": clocks,
-            "kernels_ms": {name: prof[name][1] / max(prof[name][0], 1) for name in kept},
-            "points_per_s": world * n / (ms_step * 1e-3),
-            "rechecked_per_step": float(np.mean(rechecked[args.warmup:args.warmup + args.steps])),
-            "cost_last": float(costs[args.warmup + args.steps - 1, 1]) if args.steps else None,
-        }
+    line = base_line(env, "highdim", value, ms, args.steps, args.warmup, form, {
+        "workload": f"gaussian mixture n={n} d={d} k={k} ({k} components, seed = rank), one Lloyd iteration "
+                    f"per step", "form": form, "engine": engine,
+        "l2": "inputs larger than L2 (X is 819 MB FP32 / 410 MB BF16)",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "step_roofline": step_roof, "pipeline": pipeline, "forms": forms,
+                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["launches"], "clocks": R["clocks"],
+                 "kernels_ms": kernels_ms(prof), "points_per_s": env.world * n / (ms * 1e-3),
+                 "rechecked_per_step": float(np.mean(R["rechecked"][args.warmup:])),
+                 "cost_last": float(R["costs"][-1, 1])})
+    return line
+
+
+def run_small(env, args):
+    import numpy as np
+
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import synth
+
+    n, d, k, iters = 10_000, 64, 10, 20
+    F = iters * (2.0 * n * k * d + n * d)
+    X = mixture(n, d, 10, seed=env.rank)
+    u = synth.seed_uniforms(k, seed=env.rank)
+    Xg = torch.from_numpy(X).to(env.dev)
+    ug = torch.from_numpy(u).to(env.dev)
+    ctx = env.ctx
+    xn = torch.empty(n, dtype=torch.float32, device=env.dev)
+    idx = torch.empty(k, dtype=torch.int64, device=env.dev)
+    Ca, Cb = torch.empty((k, d), dtype=torch.float32, device=env.dev), torch.empty((k, d), dtype=torch.float32, device=env.dev)
+    labels = torch.empty(n, dtype=torch.int32, device=env.dev)
+    tr = torch.zeros((iters, 2), dtype=torch.float64, device=env.dev)
+    flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=env.dev)   # 256 MB > L2
+
+    def run(i):
+        B.kmeans_row_norms(Xg, xnorm=xn, ctx=ctx)
+        B.kmeans_seed_pp(Xg, k, ug, idx_out=idx, C_out=Ca, ctx=ctx)
+        cur, nxt = Ca, Cb
+        for t in range(iters):
+            B.kmeans_assign(Xg, cur, xnorm=xn, compute="f32", engine=args.engine, labels=labels, ctx=ctx)
+            B.kmeans_update(Xg, labels, cur, C_new=nxt, cost_old=tr[t, 0:1], cost_new=tr[t, 1:2], ctx=ctx)
+            cur, nxt = nxt, cur
+
+    R = env.timed(run, args.steps, args.warmup, clocks=True, flush=lambda: flush_buf.fill_(1.0))
+    ms, prof = R["ms"], R["prof"]
+    value = env.world * F / (ms * 1e-3) / 1e9
+    kname = max((nm for nm in prof), key=lambda nm: prof[nm][1])
+    bytes_per = {"assign_tc": n * d * 4 + k * d * 4 + n * 4, "assign_simt": n * d * 4 + k * d * 4 + n * 4,
+                 "update": n * d * 4 + n * 4 + k * (d + 2) * 8, "seed": (k - 1) * n * d * 4,
+                 "recheck": n * 4, "center_prep": k * d * 4, "row_norms": n * d * 4}
+    roof = roofline(env.peaks, kname, kernel_avg_s(prof, kname), bytes_per.get(kname, n * d * 4), 0.0,
+                    FFMA_PEAK_TFLOPS, R["total_s"], bound="hbm",
+                    note="latency-bound: X (2.56 MB) is in L2 after its first read within a run and every "
+                         "kernel is a few microseconds; the fraction is not meaningful")
+    us_iter = sum(prof[nm][1] for nm in prof if nm in ("assign_tc", "assign_simt", "recheck", "center_prep",
+                                                         "update")) / max(args.steps, 1) / iters * 1e3
+
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Ch = torch.empty((k, d), dtype=torch.float32).pin_memory()
+        Lh = torch.empty(n, dtype=torch.int32).pin_memory()
+        Xd = torch.empty_like(Xg)
+
+        def e2e_step(i):
+            Xd.copy_(Xh, non_blocking=True)
+            B.kmeans_row_norms(Xd, xnorm=xn, ctx=ctx)
+            B.kmeans_seed_pp(Xd, k, ug, idx_out=idx, C_out=Ca, ctx=ctx)
+            cur, nxt = Ca, Cb
+            for t in range(iters):
+                B.kmeans_assign(Xd, cur, xnorm=xn, compute="f32", engine=args.engine, labels=labels, ctx=ctx)
+                B.kmeans_update(Xd, labels, cur, C_new=nxt, cost_old=tr[t, 0:1], cost_new=tr[t, 1:2], ctx=ctx)
+                cur, nxt = nxt, cur
+            Ch.copy_(cur, non_blocking=True)
+            Lh.copy_(labels, non_blocking=True)
+
+        E = env.timed(e2e_step, args.e2e_steps or 10, 2, flush=lambda: flush_buf.fill_(1.0))
+        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+               "d2h_bytes_per_step": int(k * d * 4 + n * 4), "ms_per_step": E["ms"]}
+
+    cpu = None
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        reps = [(X, k, u)] * 1000
+        cpu = oracle_lloyd_rate(reps, iters, min(args.cpu_seconds, 5.0))
+
+    line = base_line(env, "small", value, ms, args.steps, args.warmup, "f32", {
+        "workload": f"gaussian mixture n={n} d={d} k={k} (10 components, seed = rank); a step is row norms + "
+                    f"k-means++ + {iters} Lloyd iterations, FP32", "form": "f32", "engine": args.engine,
+        "l2": "L2 flushed (256 MB written) before every timed step",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["launches"],
+                 "clocks": R["clocks"], "kernels_ms": kernels_ms(prof), "us_per_iteration": us_iter,
+                 "run_ms": ms, "points_per_s": env.world * n * iters / (ms * 1e-3),
+                 "cost_last": float(tr[-1, 1].item())})
+    return line
+
+
+def _stream_chunk(job):
+    d, r, seed, row0, rows, comps = job
+    from paper_1502_04265_gb300 import synth
+
+    Q = synth.orthonormal_basis(d, r, seed)
+    X, _ = synth.subspace_mixture_chunk(Q, row0, rows, comps, seed)
+    return X
+
+
+def run_stream(env_args):
+    env, args = env_args
+    import numpy as np
+
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import synth
+
+    n, d, r, k, comps, iters, chunk = 2_000_000, 2048, 64, 1000, 500, 20, 65536
+    seed = env.rank
+    chunks = [(r0, min(n, r0 + chunk)) for r0 in range(0, n, chunk)]
+    ex, futs = env.pool
+    ctx = env.ctx
+    Xg = torch.empty((n, d), dtype=torch.float32, device=env.dev)
+    Xb = torch.empty((n, d), dtype=torch.bfloat16, device=env.dev)
+    pinned = []
+    for (r0, r1), f in zip(chunks, futs):
+        Xc = torch.from_numpy(f.result()).pin_memory()
+        pinned.append(Xc)
+        Xg[r0:r1].copy_(Xc, non_blocking=True)
+        B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], ctx=ctx)
+    ex.shutdown()
+    Q = synth.orthonormal_basis(d, r, seed)
+    V = torch.from_numpy(Q.astype(np.float32)).to(env.dev)
+    u = synth.seed_uniforms(k, seed=seed)
+    ug = torch.from_numpy(u).to(env.dev)
+    Y = torch.empty((n, r), dtype=torch.float32, device=env.dev)
+    ctx.sync()
+
+    def project(src):
+        for r0, r1 in chunks:
+            B.kmeans_project_block(src[r0:r1], V, Y=Y[r0:r1], ctx=ctx)
+
+    P32 = env.once(lambda: project(Xg))
+    P16 = env.once(lambda: project(Xb))          # Y from the BF16 projection feeds the rest
+    yn = B.kmeans_row_norms(Y, ctx=ctx)
+    Yb, _ = B.kmeans_quantize(Y, "bf16", ctx=ctx)
+    Y8, s8 = B.kmeans_quantize(Y, "fp8", ctx=ctx)
+    idx = torch.empty(k, dtype=torch.int64, device=env.dev)
+    C0 = torch.empty((k, r), dtype=torch.float32, device=env.dev)
+    S = env.once(lambda: B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=C0, ctx=ctx))
+    ctx.sync()
+
+    F = 2.0 * n * k * r + n * r
+    R = lloyd_timed(env, Y, Yb, None, yn, C0, "bf16", args.engine, args.steps, args.warmup, clocks=True)
+    ms, prof = R["ms"], R["prof"]
+    value = env.world * F / (ms * 1e-3) / 1e9
+    peaks = env.peaks
+    roof = roofline(peaks, "assign_tc", kernel_avg_s(prof, "assign_tc"), n * r * 2 + k * r * 2 + n * 4,
+                    2.0 * n * k * r, unit_peak(peaks, "bf16", True, R["total_s"]), R["total_s"],
+                    traffic=stored_traffic(f"assign_tc/bf16/{n}x{r}_k{k}"))
+
+    def proj_roof(P, es):
+        nl = len(chunks)
+        avg = kernel_avg_s(P["prof"], "project")
+        bytes_ = (n * d * es + n * r * 4) / nl + d * r * es
+        return {"ms_all_chunks": P["ms"], "launches": nl, "kernel_ms": avg * 1e3,
+                "achieved_gbs": bytes_ / avg / 1e9, "frac_hbm": bytes_ / avg / 1e9 / peaks["hbm_gbs"],
+                "tflops": 2.0 * n * d * r / nl / avg / 1e12}
+
+    forms = None
+    if not args.no_compare:
+        s2 = max(3, args.steps // 2)
+        R8 = lloyd_timed(env, Y, Y8, s8, yn, C0, "fp8", args.engine, s2, args.warmup)
+        R32 = lloyd_timed(env, Y, None, None, yn, C0, "f32", "tcgen05", s2, args.warmup)
+        it = args.warmup + s2 - 1
+        c16, c8, c32 = (float(x["costs"][it, 1]) for x in (R, R8, R32))
+        v8, v32 = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (R8, R32))
+        forms = {"bf16": {"value": value, "ms_per_step": ms,
+                          "rechecked_per_step": float(np.mean(R["rechecked"][args.warmup:]))},
+                 "fp8": {"value": v8, "ms_per_step": R8["ms"], "assign_ms": kernel_avg_s(R8["prof"], "assign_tc") * 1e3,
+                         "rechecked_per_step": float(np.mean(R8["rechecked"][args.warmup:])),
+                         "final_cost_rel_gap_vs_f32": abs(c8 - c32) / c32},
+                 "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms"],
+                                "assign_ms": kernel_avg_s(R32["prof"], "assign_tc") * 1e3},
+                 "speedup_bf16_vs_f32": value / v32, "speedup_fp8_vs_f32": v8 / v32,
+                 "final_cost_rel_gap_bf16_vs_f32": abs(c16 - c32) / c32,
+                 "note": "the three forms run the same Lloyd iterations from the same k-means++ centers"}
+
+    # whole run from the device-resident BF16 points: projection, norms, operand copy, k-means++, iterations
+    labels = torch.empty(n, dtype=torch.int32, device=env.dev)
+    Ca, Cb = torch.empty_like(C0), torch.empty_like(C0)
+    tr = torch.zeros((iters, 2), dtype=torch.float64, device=env.dev)
+
+    def whole(src_chunks=None):
+        if src_chunks is None:
+            project(Xb)
+        else:
+            for (r0, r1), Xc in zip(chunks, src_chunks):
+                Xg[r0:r1].copy_(Xc, non_blocking=True)
+                B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], ctx=ctx)
+                B.kmeans_project_block(Xb[r0:r1], V, Y=Y[r0:r1], ctx=ctx)
+        B.kmeans_row_norms(Y, xnorm=yn, ctx=ctx)
+        B.kmeans_quantize(Y, "bf16", Xq=Yb, ctx=ctx)
+        B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=Ca, ctx=ctx)
+        cur, nxt = Ca, Cb
+        for t in range(iters):
+            B.kmeans_assign(Y, cur, Xop=Yb, xnorm=yn, compute="bf16", engine=args.engine, labels=labels, ctx=ctx)
+            B.kmeans_update(Y, labels, cur, C_new=nxt, cost_old=tr[t, 0:1], cost_new=tr[t, 1:2], ctx=ctx)
+            cur, nxt = nxt, cur
+        return cur
+
+    W = env.once(whole)
+    Fw = iters * F
+    pipeline = {"projection_bf16": proj_roof(P16, 2), "projection_tf32": proj_roof(P32, 4),
+                "seed_ms": S["ms"], "iterations": iters, "total_ms": W["ms"],
+                "gflops_whole_run": Fw / (W["ms"] * 1e-3) / 1e9,
+                "note": "whole run from device-resident BF16 points: 31 projections, norms, BF16 copy of Y, "
+                        "k-means++ (k=1000 rounds over Y), 20 Lloyd iterations; seeding time counted, its flops not"}
+
+    e2e = None
+    if not args.no_e2e:
+        Ch = torch.empty((k, r), dtype=torch.float32).pin_memory()
+        Lh = torch.empty(n, dtype=torch.int32).pin_memory()
+
+        def e2e_step(i):
+            C = whole(pinned)
+            Ch.copy_(C, non_blocking=True)
+            Lh.copy_(labels, non_blocking=True)
+
+        E = env.timed(e2e_step, args.e2e_steps or 2, 1)
+        e2e = {"value": env.world * Fw / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+               "d2h_bytes_per_step": int(k * r * 4 + n * 4), "ms_per_step": E["ms"],
+               "note": "a step is the whole job from FP32 chunks in pinned host memory: H2D, BF16 copy, "
+                       "projection, norms, k-means++, 20 iterations, D2H of centers and labels"}
+
+    cpu = None
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        Xs = pinned[0].numpy()[:16384]
+        Ys = oracle.project(Xs, Q).astype(np.float32)
+        Cs = Ys[(u * Ys.shape[0]).astype(np.int64) % Ys.shape[0]]
+        cpu = oracle_assign_update_rate(Ys, Cs, args.cpu_seconds,
+                                        label="coordinates of chunk 0 projected by the oracle; ")
+
+    line = base_line(env, "stream", value, ms, args.steps, args.warmup, "bf16", {
+        "workload": f"{n} points, d={d}, {comps}-component mixture in a random rank-{r} subspace + N(0, 0.1^2) "
+                    f"noise, {len(chunks)} chunks of {chunk}; k={k} on the r={r} coordinates, one BF16 Lloyd "
+                    f"iteration per step", "form": "bf16", "engine": args.engine,
+        "l2": "inputs larger than L2 (Y BF16 256 MB; X 16.4 GB FP32 / 8.2 GB BF16)",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "pipeline": pipeline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e,
+                 "gpu_launches": R["launches"], "clocks": R["clocks"], "kernels_ms": kernels_ms(prof),
+                 "points_per_s": env.world * n / (ms * 1e-3), "cost_last": float(R["costs"][-1, 1])})
+    return line
+
+
+def _batch_problem(job):
+    n, d, k, seed = job
+    from paper_1502_04265_gb300 import synth
+
+    X, _ = synth.gaussian_mixture(n, d, k, seed=seed)
+    return X
+
+
+def batch_jobs(count, rank):
+    from paper_1502_04265_gb300 import synth
+
+    shapes = synth.batch_problem_list(count, seed=rank)
+    return shapes, [(s["n"], s["d"], s["k"], 1_000_000 * rank + s["seed"]) for s in shapes]
+
+
+def run_batch(env_args):
+    env, args = env_args
+    import numpy as np
+
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import synth
+
+    S, iters = 4, 20
+    shapes, jobs = env.batch_shapes
+    ex, futs = env.pool
+    ctx = env.ctx
+    hostX, probs = [], []
+    for s, f in zip(shapes, futs):
+        Xh = torch.from_numpy(f.result()).pin_memory()
+        hostX.append(Xh)
+        U = np.stack([synth.seed_uniforms(s["k"], seed=s["seed"] * S + j) for j in range(S)])
+        probs.append({"X": Xh.to(env.dev, non_blocking=True), "k": s["k"], "u": torch.from_numpy(U).to(env.dev)})
+    ex.shutdown()
+    ctx.sync()
+    F = sum(S * iters * (2.0 * s["n"] * s["k"] * s["d"] + s["n"] * s["d"]) for s in shapes)
+    n_tot = sum(s["n"] for s in shapes)
+    xbytes = sum(s["n"] * s["d"] * 4 for s in shapes)
+
+    def record(compute):
+        t0 = time.perf_counter()
+        B.kmeans_batch_run(probs, S, iters, compute=compute, graph=True, autotune=True, ctx=ctx)
+        ctx.sync()
+        return time.perf_counter() - t0
+
+    first_s = record("bf16")
+    costs16 = [p["cost_out"].clone() for p in probs]
+    R = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), args.steps, args.warmup - 1, clocks=True)
+    ms = R["ms"]
+    value = env.world * F / (ms * 1e-3) / 1e9
+    ok = all(torch.equal(p["cost_out"], c) for p, c in zip(probs, costs16))
+
+    # per-kernel times from one run that is not recorded into a graph
+    Pn = env.once(lambda: B.kmeans_batch_run(probs, S, iters, compute="bf16", graph=False, ctx=ctx), warmup=0)
+    prof = Pn["prof"]
+    peaks = env.peaks
+    a_bytes = sum(s["n"] * s["d"] * 2 + S * s["k"] * s["d"] * 2 + S * s["n"] * 4 for s in shapes)
+    a_flops = sum(2.0 * s["n"] * S * s["k"] * s["d"] for s in shapes)
+    roof = roofline(peaks, "assign_batched", kernel_avg_s(prof, "assign_batched"), a_bytes, a_flops,
+                    unit_peak(peaks, "bf16", True, R["total_s"]), R["total_s"],
+                    traffic=stored_traffic(f"assign_batched/bf16/c{len(shapes)}"),
+                    note="per-launch time from a run outside the graph (the graph itself is timed as a whole)")
+    per_iter = {nm: prof[nm][1] / max(prof[nm][0], 1) for nm in prof}
+
+    forms = None
+    if not args.no_compare:
+        first32 = record("f32")
+        R32 = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), max(2, args.steps // 2), 1)
+        gaps = []
+        for p, c16 in zip(probs, costs16):
+            a, b = c16[:, 1].cpu().numpy(), p["cost_out"][:, 1].cpu().numpy()
+            gaps.append(float(np.max(np.abs(a - b) / b)))
+        v32 = env.world * F / (R32["ms"] * 1e-3) / 1e9
+        forms = {"bf16": {"value": value, "ms_per_step": ms, "first_call_s": first_s},
+                 "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms"], "first_call_s": first32},
+                 "speedup_vs_f32": value / v32, "max_final_cost_rel_gap": max(gaps),
+                 "note": "same seeds in both forms; k-means++ is exact in both, so the runs agree up to "
+                         "rounding of the FP32/FP64 sums"}
+
+    e2e = None
+    if not args.no_e2e:
+        outs = [(torch.empty_like(p["C_out"], device="cpu").pin_memory(),
+                 torch.empty_like(p["cost_out"], device="cpu").pin_memory()) for p in probs]
+
+        def e2e_step(i):
+            for p, Xh in zip(probs, hostX):
+                p["X"].copy_(Xh, non_blocking=True)
+            B.kmeans_batch_run(probs, S, iters, compute="bf16", graph=True, autotune=True, ctx=ctx)
+            for p, (Co, co) in zip(probs, outs):
+                Co.copy_(p["C_out"], non_blocking=True)
+                co.copy_(p["cost_out"], non_blocking=True)
+
+        E = env.timed(e2e_step, args.e2e_steps or 2, 1)
+        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(xbytes),
+               "d2h_bytes_per_step": int(sum(p["C_out"].numel() * 4 + p["cost_out"].numel() * 8 for p in probs)),
+               "ms_per_step": E["ms"], "note": "H2D of every problem's X, planning + recording + launch of "
+                                               "the graph (tile widths cached), D2H of centers and costs"}
+
+    cpu = None
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        runs = []
+        for s, Xh in zip(shapes, hostX):
+            for j in range(S):
+                runs.append((Xh.numpy(), s["k"], synth.seed_uniforms(s["k"], seed=s["seed"] * S + j)))
+        cpu = oracle_lloyd_rate(runs, iters, args.cpu_seconds, label="problems in list order; ")
+
+    line = base_line(env, "batch", value, ms, args.steps, args.warmup, "bf16", {
+        "workload": f"{len(shapes)} gaussian-mixture problems (n log-uniform [1e3, 1e5], d in {{32, 128, 512}}, "
+                    f"k log-uniform [4, 256]; sum n = {n_tot}), {S} k-means++ seeds each, {iters} Lloyd "
+                    f"iterations; a step is one replay of the recorded graph", "form": "bf16",
+        "l2": f"inputs larger than L2 ({xbytes / 1e9:.1f} GB FP32 points)",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["launches"],
+                 "gpu_launches_note": "one graph launch per step; the graph holds the run's kernels",
+                 "clocks": R["clocks"], "kernels_ms_outside_graph": per_iter, "first_call_s": first_s,
+                 "replay_deterministic": bool(ok), "points_per_s": env.world * n_tot * S * iters / (ms * 1e-3)})
+    return line
+
+
+def run_learned(env, args):
+    import numpy as np
+
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import driver, synth
+    from paper_1502_04265_gb300.learned import ProposalNet
+
+    n, d, k, h, ntrain, nsub, topm = args.n or 4_000_000, 256, 16384, 256, 200_000, 200_000, 32
+    ctx = env.ctx
+    Xall = mixture(n + ntrain, d, k, seed=env.rank)
+    Xg = torch.from_numpy(Xall[:n]).to(env.dev)
+    Xtg = torch.from_numpy(Xall[n:]).to(env.dev)
+    Xh, _ = B.kmeans_quantize(Xg, "bf16", ctx=ctx)
+    u = synth.seed_uniforms(k, seed=env.rank)
+    ug = torch.from_numpy(u).to(env.dev)
+    t0 = time.perf_counter()
+    fit = driver.lloyd(Xg[:nsub], k, 5, ug, compute="f32", ctx=ctx)
+    C = fit["C"].contiguous()
+    ctx.sync()
+    centers_s = time.perf_counter() - t0
+    lt = B.kmeans_assign(Xtg, C, compute="f32", ctx=ctx)
+    net = ProposalNet(d, h, k, seed=env.rank, device=env.dev)
+    Xtb, _ = B.kmeans_quantize(Xtg, "bf16", ctx=ctx)
+    ctx.sync()
+    t0 = time.perf_counter()
+    losses = net.train(Xtb, lt, epochs=10, batch=4096, lr=3e-3, ctx=ctx)
+    ctx.sync()
+    train_s = time.perf_counter() - t0
+    s2 = B.kmeans_center_separation(C, ctx=ctx)
+    xnorm = B.kmeans_row_norms(Xg, ctx=ctx)
+    exact = B.kmeans_assign(Xg, C, xnorm=xnorm, compute="f32", engine="tcgen05", ctx=ctx)
+    ctx.sync()
+
+    F = 2.0 * n * k * d + n * d
+    K = args.steps
+    lab = torch.empty(n, dtype=torch.int32, device=env.dev)
+    nf = torch.zeros(K + args.warmup, dtype=torch.int64, device=env.dev)
+    cost = torch.zeros((K + args.warmup, 2), dtype=torch.float64, device=env.dev)
+    Cn = torch.empty_like(C)
+
+    def step_learned(i):
+        B.kmeans_learned_assign(net, Xg, Xh, C, s2, topm=topm, labels=lab, n_fallback=nf[i:i + 1], ctx=ctx)
+        B.kmeans_update(Xg, lab, C, C_new=Cn, cost_old=cost[i, 0:1], cost_new=cost[i, 1:2], ctx=ctx)
+
+    R = env.timed(step_learned, K, args.warmup, clocks=True)
+    ms, prof = R["ms"], R["prof"]
+    value = env.world * F / (ms * 1e-3) / 1e9
+    mis = int((lab != exact).sum().item())
+    nfb = nf.cpu().numpy()[args.warmup:]
+    c_learn = float(cost[-1, 0].item())
+    peaks = env.peaks
+    fl_top = 2.0 * n * h * k
+    roof = roofline(peaks, "mlp_topm", kernel_avg_s(prof, "mlp_topm"), n * h * 2 + k * h * 2 + n * topm * 4, fl_top,
+                    bf16_peak(peaks, R["total_s"]), R["total_s"],
+                    traffic=stored_traffic(f"mlp_topm/bf16/{n}x{h}_k{k}"),
+                    note="the output layer (h=256 -> k logits) with the fused top-32 epilogue; the logits are "
+                         "never stored")
+
+    def full_scan(compute, Xop, steps):
+        lab2 = torch.empty(n, dtype=torch.int32, device=env.dev)
+        c2 = torch.zeros((steps + 1, 2), dtype=torch.float64, device=env.dev)
+        Cn2 = torch.empty_like(C)
+
+        def st(i):
+            B.kmeans_assign(Xg, C, Xop=Xop, xnorm=xnorm, compute=compute, engine="tcgen05", labels=lab2, ctx=ctx)
+            B.kmeans_update(Xg, lab2, C, C_new=Cn2, cost_old=c2[i, 0:1], cost_new=c2[i, 1:2], ctx=ctx)
+
+        Rf = env.timed(st, steps, 1)
+        Rf["cost"] = float(c2[steps, 0].item())
+        Rf["mis"] = int((lab2 != exact).sum().item())
+        return Rf
+
+    forms = None
+    if not args.no_compare:
+        Rb = full_scan("bf16", Xh, max(2, min(K, 3)))
+        Rf = full_scan("f32", None, 2)
+        vb, vf = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (Rb, Rf))
+        forms = {"learned": {"value": value, "ms_per_step": ms, "misassigned": mis, "cost": c_learn},
+                 "bf16_full_scan": {"value": vb, "ms_per_step": Rb["ms"], "misassigned": Rb["mis"], "cost": Rb["cost"],
+                                    "assign_ms": kernel_avg_s(Rb["prof"], "assign_tc") * 1e3},
+                 "f32_full_scan_3xtf32": {"value": vf, "ms_per_step": Rf["ms"], "misassigned": Rf["mis"],
+                                          "cost": Rf["cost"], "assign_ms": kernel_avg_s(Rf["prof"], "assign_tc") * 1e3},
+                 "speedup_learned_vs_f32": Rf["ms"] / ms, "speedup_bf16_vs_f32": Rf["ms"] / Rb["ms"],
+                 "cost_ratio_learned_vs_f32": c_learn / Rf["cost"],
+                 "note": "misassigned = labels differing from the FP32 full scan's (exact) labels; costs are "
+                         "cost(C, labels) from the FP64 CF sums with the frozen centers"}
+
+    e2e = None
+    if not args.no_e2e:
+        Xhost = torch.from_numpy(Xall[:n]).pin_memory()
+        Lh = torch.empty(n, dtype=torch.int32).pin_memory()
+        ch = torch.empty(1, dtype=torch.float64).pin_memory()
+        Xd = torch.empty_like(Xg)
+        Xhd = torch.empty_like(Xh)
+
+        def e2e_step(i):
+            Xd.copy_(Xhost, non_blocking=True)
+            B.kmeans_quantize(Xd, "bf16", Xq=Xhd, ctx=ctx)
+            B.kmeans_learned_assign(net, Xd, Xhd, C, s2, topm=topm, labels=lab, ctx=ctx)
+            B.kmeans_update(Xd, lab, C, C_new=Cn, cost_old=cost[0, 0:1], cost_new=cost[0, 1:2], ctx=ctx)
+            Lh.copy_(lab, non_blocking=True)
+            ch.copy_(cost[0, 0:1], non_blocking=True)
+
+        E = env.timed(e2e_step, args.e2e_steps or 2, 1)
+        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+               "d2h_bytes_per_step": int(n * 4 + 8), "ms_per_step": E["ms"]}
+
+    cpu = None
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        Cs = Xall[(u * n).astype(np.int64) % n]
+        cpu = oracle_assign_update_rate(Xall[:n], Cs, args.cpu_seconds)
+
+    line = base_line(env, "learned", value, ms, K, args.warmup, "bf16", {
+        "workload": f"gaussian mixture n={n} d={d} k={k} ({k} components, seed = rank) + {ntrain} held-out "
+                    f"training points; centers: k-means++ on the first {nsub} points + 5 FP32 Lloyd iterations; "
+                    f"MLP {d}-{h}-{h}-{k} GELU, top-{topm}; a step is the learned assignment + CF update",
+        "form": "learned (BF16 MLP, FP32 exact candidates)", "l2": "inputs larger than L2 (X 4.1 GB FP32)",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["launches"],
+                 "clocks": R["clocks"], "kernels_ms": kernels_ms(prof),
+                 "fallback_rate": float(np.mean(nfb)) / n, "misassignment_rate": mis / n,
+                 "training": {"epochs": 10, "batch": 4096, "train_s": train_s, "loss_first": losses[0],
+                              "loss_last": losses[-1]},
+                 "centers_s": centers_s, "points_per_s": env.world * n / (ms * 1e-3)})
+    return line
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle timed on the host cores, on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1502_04265_gb300 import synth
+
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    budget = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
+    wl = args.workload
+    if wl in ("small", "batch"):
+        if wl == "small":
+            X = mixture(10_000, 64, 10, 0)
+            runs = [(X, 10, synth.seed_uniforms(10, 0))]
+            desc = "the whole run (k-means++ + 20 Lloyd iterations) per step"
+        else:
+            shapes, jobs = batch_jobs(args.problems, 0)
+            runs = []
+            for s in shapes[:8]:
+                X = _batch_problem((s["n"], s["d"], s["k"], s["seed"]))
+                runs.append((X, s["k"], synth.seed_uniforms(s["k"], seed=s["seed"] * 4)))
+            desc = "whole runs of the first problems (one seed each), in list order, per step"
+        vals, dts = [], []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = oracle_lloyd_rate(runs * 1000, 20, budget)
+            if i >= args.warmup:
+                vals.append(r["value"])
+                dts.append(time.perf_counter() - t0)
+        val = statistics.median(vals)
+        sample = desc + "; " + r["sample"]
+    else:
+        if wl == "highdim":
+            n, d, k = args.n or 200_000, args.d or 1024, args.k or 100
+            X = mixture(n, d, k, 0)
+            u = synth.seed_uniforms(k, 0)
+            C = X[(u * n).astype(np.int64) % n]
+        elif wl == "stream":
+            Q = synth.orthonormal_basis(2048, 64, 0)
+            Xc, _ = synth.subspace_mixture_chunk(Q, 0, 16384, 500, 0)
+            X = oracle.project(Xc, Q).astype(np.float32)
+            u = synth.seed_uniforms(1000, 0)
+            C = X[(u * X.shape[0]).astype(np.int64) % X.shape[0]]
+        else:
+            X = mixture(65536, 256, 16384, 0)
+            u = synth.seed_uniforms(16384, 0)
+            C = X[(u * X.shape[0]).astype(np.int64) % X.shape[0]]
+        vals, dts = [], []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = oracle_assign_update_rate(X, C, budget)
+            if i >= args.warmup:
+                vals.append(r["value"])
+                dts.append(time.perf_counter() - t0)
+        val = statistics.median(vals)
+        sample = r["sample"]
+    ms = 1e3 * statistics.mean(dts)
+    line = {"impl": "reference", "metric": METRICS[wl], "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{wl}: the FP64 oracle on a bounded sample per step ({sample})"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    # the seeded generators of the large workloads run in spawned processes, started before CUDA
+    pool, shapes = None, None
+    if args.workload == "stream":
+        n, d, r, chunk = 2_000_000, 2048, 64, 65536
+        jobs = [(d, r, rank, r0, min(n, r0 + chunk) - r0, 500) for r0 in range(0, n, chunk)]
+        pool = gen_pool(jobs, _stream_chunk)
+    elif args.workload == "batch":
+        shapes = batch_jobs(args.problems, rank)
+        pool = gen_pool(shapes[1], _batch_problem)
+    env = Env(args)
+    env.pool, env.batch_shapes = pool, shapes
+    if args.workload == "highdim":
+        line = run_highdim(env, args)
+    elif args.workload == "small":
+        line = run_small(env, args)
+    elif args.workload == "stream":
+        line = run_stream((env, args))
+    elif args.workload == "batch":
+        line = run_batch((env, args))
+    else:
+        line = run_learned(env, args)
+    if env.rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    if env.world > 1:
+        env.dist.destroy_process_group()
 
 
 if __name__ == "__main__":

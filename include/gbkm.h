@@ -255,6 +255,15 @@ typedef struct {
 int kmeans_batch_run(gbkm_ctx *ctx, const gbkm_problem *probs, int64_t count, int64_t seeds,
                      int64_t iters, int32_t compute, int32_t flags);
 
+/* Relaunch, on the context's stream, the CUDA graph that the last kmeans_batch_run
+ * with GBKM_BATCH_GRAPH recorded on this context (no paper counterpart): the same
+ * problems, seeds and iteration count, reading and writing the same buffers (X, u,
+ * C_out, labels_out, cost_out must still be allocated; their contents may have
+ * changed).  The graph keeps its tables in the context's workspace, so any other
+ * call on the context that uses the workspace in between invalidates it:
+ * GBKM_EINVAL if no graph was recorded or it has been invalidated. */
+int kmeans_batch_replay(gbkm_ctx *ctx);
+
 /* The project's tile autotuner (no paper counterpart): times the tcgen05
  * assignment of a synthetic 16,384-point problem of dimension d against ncols
  * centers with center-chunk widths of 64, 128 and 256 columns and returns the

@@ -17,7 +17,12 @@ extern "C" {
 struct gbkm_ctx;
 
 /* enable (1) or disable (0) event timing around the library's main kernels:
- * "assign_simt", "assign_tc", "recheck", "update", "seed", "project", "center_prep".
+ * "row_norms", "quantize", "assign_simt", "assign_tc", "recheck", "update", "seed", "project",
+ * "center_prep", "gemm", "mlp_forward", "mlp_hidden", "mlp_topm", "mlp_logits", "mlp_train_step",
+ * "learned_assign", "cand_check", "fallback", "batch_run" and, for a batched run
+ * that is not recorded into a graph, "seed_batched", "assign_batched",
+ * "recheck_batched", "update_batched".  Brackets nest: a composite call is timed as a
+ * whole and by its parts (so the parts' times also count in the whole's).
  * Enabling clears earlier records. */
 int gbkm_profile_enable(struct gbkm_ctx *ctx, int enable);
 

@@ -9,7 +9,7 @@ from __future__ import annotations
 __all__ = [
     "kmeans_row_norms", "kmeans_quantize", "kmeans_project_block", "kmeans_seed_pp",
     "kmeans_assign", "kmeans_update", "kmeans_cost", "gbkm_sync", "gbkm_version",
-    "Context", "default_context", "GbkmError", "lloyd", "kmeans_batch_run", "kmeans_autotune",
+    "Context", "default_context", "GbkmError", "lloyd", "kmeans_batch_run", "kmeans_batch_replay", "kmeans_autotune",
     "kmeans_update_noalloc",
 ]
 

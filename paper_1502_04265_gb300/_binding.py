@@ -70,6 +70,7 @@ _SIGS = {
     "kmeans_update_noalloc": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                          _vp, _vp]),
     "kmeans_batch_run": (ct.c_int, [_vp, ct.POINTER(Problem), _i64, _i64, _i64, _i32, _i32]),
+    "kmeans_batch_replay": (ct.c_int, [_vp]),
     "kmeans_autotune": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32)]),
     "kmeans_mlp_param_count": (ct.c_int64, [_i64, _i64, _i64]),
     "kmeans_gemm_bf16": (ct.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i32, _i32, _vp, _i64]),
@@ -406,6 +407,13 @@ def kmeans_batch_run(problems, seeds, iters, compute="bf16", graph=True, autotun
     c = _ctx(ctx, problems[0]["X"])
     c.check(load().kmeans_batch_run(c.handle, arr, len(problems), seeds, iters, DTYPES[compute], flags))
     return keep
+
+
+def kmeans_batch_replay(ctx=None):
+    """Relaunch the graph recorded by the last graph-mode kmeans_batch_run on this context."""
+    c = ctx or default_context()
+    c.bind_stream()
+    c.check(load().kmeans_batch_replay(c.handle))
 
 
 def kmeans_autotune(d, ncols, compute="bf16", ctx=None):

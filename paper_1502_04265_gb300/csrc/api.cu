@@ -26,6 +26,7 @@ int cuda_check(gbkm_ctx *c, cudaError_t e, const char *what) {
 }
 
 void *ws_reserve(gbkm_ctx *c, size_t bytes, int *rc) {
+    c->ws_epoch++;
     if (bytes <= c->ws_bytes) return c->ws;
     cudaError_t e = cudaStreamSynchronize(c->stream);  // the old block may still be in use
     if (e != cudaSuccess) {
@@ -52,6 +53,7 @@ void prof_begin(gbkm_ctx *c, const char *name) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
+            c->prof_open.push_back(SIZE_MAX);  // keeps begin/end pairs matched
             return;
         }
         c->pool.push_back(e);
@@ -60,11 +62,15 @@ void prof_begin(gbkm_ctx *c, const char *name) {
     c->pool_used += 2;
     cudaEventRecord(r.a, c->stream);
     c->recs.push_back(r);
+    c->prof_open.push_back(c->recs.size() - 1);
 }
 
+// closes the innermost open bracket (brackets nest: a composite call may time its parts)
 void prof_end(gbkm_ctx *c) {
-    if (!c->prof || c->recs.empty()) return;
-    cudaEventRecord(c->recs.back().b, c->stream);
+    if (!c->prof || c->prof_open.empty()) return;
+    const size_t i = c->prof_open.back();
+    c->prof_open.pop_back();
+    if (i != SIZE_MAX) cudaEventRecord(c->recs[i].b, c->stream);
 }
 
 namespace {
@@ -141,6 +147,7 @@ int gbkm_profile_enable(gbkm_ctx *c, int enable) {
     if (!c) return GBKM_EINVAL;
     c->prof = enable != 0;
     c->recs.clear();
+    c->prof_open.clear();
     c->pool_used = 0;
     return GBKM_OK;
 }
@@ -169,6 +176,7 @@ int gbkm_profile_read(gbkm_ctx *c, char *buf, int64_t len) {
         acc[q].ms += ms;
     }
     c->recs.clear();
+    c->prof_open.clear();
     c->pool_used = 0;
     int64_t off = 0;
     buf[0] = 0;
@@ -225,7 +233,10 @@ int kmeans_row_norms(gbkm_ctx *c, const float *X, int64_t n, int64_t d, float *x
     if (!c) return GBKM_EINVAL;
     if (n < 1 || d < 1 || !X || !xnorm) return set_error(c, GBKM_EINVAL, "row_norms: bad arguments");
     DeviceGuard g(c->device);
-    return gbkm::launch_row_norms(c, X, n, d, xnorm);
+    prof_begin(c, "row_norms");
+    const int rc = gbkm::launch_row_norms(c, X, n, d, xnorm);
+    prof_end(c);
+    return rc;
 }
 
 int kmeans_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int32_t dtype, void *Xq,
@@ -237,7 +248,10 @@ int kmeans_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int32_t d
     if (dtype == GBKM_FP8E4M3 && !scales) return set_error(c, GBKM_EINVAL, "quantize: FP8 needs scales");
     if (!aligned16(Xq)) return set_error(c, GBKM_EINVAL, "quantize: Xq must be 16-byte aligned");
     DeviceGuard g(c->device);
-    return gbkm::launch_quantize(c, X, n, d, dtype, Xq, scales);
+    prof_begin(c, "quantize");
+    const int rc = gbkm::launch_quantize(c, X, n, d, dtype, Xq, scales);
+    prof_end(c);
+    return rc;
 }
 
 int kmeans_project_block(gbkm_ctx *c, const void *X, int32_t xt, int64_t n, int64_t d,
@@ -307,12 +321,22 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     DeviceGuard g(c->device);
     const int64_t k_pad = use_tc ? ceil_div(k, 16) * 16 : k;
     const size_t esz = o.compute == GBKM_BF16 ? 2 : (o.compute == GBKM_FP8E4M3 ? 1 : 4);
+    // escalation: rows of a low-precision form whose near-tie band is too wide to list go through the
+    // 3xTF32 form (a far smaller error bound), then through the exact recheck
+    const bool esc = use_tc && o.recheck && o.compute != GBKM_F32 && gbkm::tc_assign_supported(GBKM_F32, d, k) &&
+                     aligned16(X) && (d % 4) == 0;
+    const int64_t ne = esc ? n : 0;
     WsPlan p;
     size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(1),
            o_cop = p.take<char>(use_tc ? k_pad * d * esz : 0),
            o_clo = p.take<float>(use_tc && o.compute == GBKM_F32 ? k_pad * d : 0),
            o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_cd = p.take<int32_t>(n * gbkm::CAND_STRIDE),
            o_fc = p.take<int32_t>(1);
+    size_t o_el = p.take<int32_t>(ne), o_ec = p.take<int32_t>(esc ? 2 : 0), o_xe = p.take<float>(ne * d),
+           o_xne = p.take<float>(ne), o_le = p.take<int32_t>(ne), o_mde = p.take<float>(min_d2 ? ne : 0),
+           o_cn2 = p.take<float>(esc ? k_pad : 0), o_cm2 = p.take<unsigned>(esc ? 1 : 0),
+           o_cop2 = p.take<float>(esc ? k_pad * d : 0), o_clo2 = p.take<float>(esc ? k_pad * d : 0),
+           o_fl2 = p.take<int32_t>(ne), o_cd2 = p.take<int32_t>(ne * gbkm::CAND_STRIDE);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
@@ -346,6 +370,40 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
         rc = gbkm::launch_assign_simt(c, X, xn, n, d, C, cp.cnorm, cp.cmax, k, err_rel, err_abs, out);
     prof_end(c);
     if (rc != GBKM_OK) return rc;
+    if (o.recheck && esc) {
+        int32_t *elist = ws_at<int32_t>(ws, o_el), *ecount = ws_at<int32_t>(ws, o_ec);
+        e = cudaMemsetAsync(ecount, 0, 2 * sizeof(int32_t), c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "memset escalation count");
+        prof_begin(c, "recheck");
+        rc = gbkm::launch_recheck(c, X, n, d, C, k, out, n_rechecked, elist, ecount);
+        prof_end(c);
+        if (rc != GBKM_OK) return rc;
+        prof_begin(c, "escalate");
+        gbkm::CenterPrep cp2;
+        cp2.cnorm = ws_at<float>(ws, o_cn2);
+        cp2.cmax = ws_at<unsigned>(ws, o_cm2);
+        cp2.cop = ws_at<void>(ws, o_cop2);
+        cp2.cop_lo = ws_at<void>(ws, o_clo2);
+        cp2.cscale = nullptr;
+        float *Xe = ws_at<float>(ws, o_xe), *xne = ws_at<float>(ws, o_xne), *mde = min_d2 ? ws_at<float>(ws, o_mde) : nullptr;
+        int32_t *le = ws_at<int32_t>(ws, o_le);
+        gbkm::AssignOut out2;
+        out2.labels = le;
+        out2.min_d2 = mde;
+        out2.flag_list = ws_at<int32_t>(ws, o_fl2);
+        out2.cand = ws_at<int32_t>(ws, o_cd2);
+        out2.flag_count = ecount + 1;
+        float er2, ea2;
+        gbkm::score_error_coeffs(GBKM_F32, 1, d, er2, ea2);
+        if ((rc = gbkm::launch_center_prep(c, C, k, d, GBKM_F32, k_pad, cp2)) == GBKM_OK &&
+            (rc = gbkm::launch_gather_rows(c, X, xn, n, d, elist, ecount, Xe, xne)) == GBKM_OK &&
+            (rc = gbkm::launch_assign_tc(c, GBKM_F32, Xe, nullptr, Xe, xne, n, d, cp2, k, k_pad, er2, ea2, out2,
+                                         ecount)) == GBKM_OK &&
+            (rc = gbkm::launch_recheck(c, Xe, n, d, C, k, out2, nullptr)) == GBKM_OK)
+            rc = gbkm::launch_scatter_rows(c, le, mde, elist, ecount, n, labels, min_d2);
+        prof_end(c);
+        return rc;
+    }
     if (o.recheck) {
         prof_begin(c, "recheck");
         rc = gbkm::launch_recheck(c, X, n, d, C, k, out, n_rechecked);
@@ -404,6 +462,17 @@ int kmeans_batch_run(gbkm_ctx *c, const gbkm_problem *probs, int64_t count, int6
     int rc = gbkm::batch_run(c, probs, count, seeds, iters, compute, flags, caps.data());
     prof_end(c);
     return rc;
+}
+
+int kmeans_batch_replay(gbkm_ctx *c) {
+    if (!c) return GBKM_EINVAL;
+    if (!c->graph_exec || c->graph_epoch != c->ws_epoch)
+        return set_error(c, GBKM_EINVAL, "batch_replay: no recorded batched graph, or the workspace was reused since");
+    DeviceGuard g(c->device);
+    prof_begin(c, "batch_run");
+    cudaError_t e = cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, c->stream);
+    prof_end(c);
+    return cuda_check(c, e, "graph launch");
 }
 
 int kmeans_autotune(gbkm_ctx *c, int32_t compute, int64_t d, int64_t ncols, int32_t *bn_out) {

@@ -30,6 +30,7 @@ struct gbkm_ctx {
     int device = 0;
     bool prof = false;              // per-kernel CUDA-event timing on the context's stream
     std::vector<ProfRec> recs;
+    std::vector<size_t> prof_open;  // indices of the open brackets in recs (innermost last)
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
     cudaStream_t stream = nullptr;
@@ -41,6 +42,8 @@ struct gbkm_ctx {
     int64_t launches = 0;
     void *tmap_scratch = nullptr;  // device copy of tensor maps (128 B aligned, 16 slots)
     void *graph_exec = nullptr;    // last instantiated batched-run graph (cudaGraphExec_t)
+    uint64_t ws_epoch = 0;         // bumped by every ws_reserve (any call that writes the workspace)
+    uint64_t graph_epoch = 0;      // ws_epoch when graph_exec was recorded (its tables live in ws)
     cudaStream_t cap_stream = nullptr;  // private stream the batched run is recorded on
     int bn_cap = 0;                // center-chunk width of the tcgen05 assignment (0: 256); autotuner knob
 };
@@ -222,8 +225,16 @@ int launch_assign_simt(gbkm_ctx *c, const float *X, const float *xnorm, int64_t 
 // Out[M x N] = A[M x K] B^T with B[nn * sbn + kk * sbk]
 int launch_gemm_simt_strided(gbkm_ctx *c, const float *A, const float *B, int64_t M, int64_t N,
                              int64_t K, int64_t sbn, int64_t sbk, float *Out);
+// exact re-resolution of the flagged rows; with esc_list, a row whose band is not listed (count
+// <= 0) is appended there (esc_count) for the next precision instead of being scanned over all k
 int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
-                   const AssignOut &o, int64_t *n_rechecked);
+                   const AssignOut &o, int64_t *n_rechecked, int32_t *esc_list = nullptr,
+                   int32_t *esc_count = nullptr);
+// rows of an escalation list gathered into a dense block (and their norms), labels scattered back
+int launch_gather_rows(gbkm_ctx *c, const float *X, const float *xnorm, int64_t n, int64_t d,
+                       const int32_t *list, const int32_t *count, float *Xe, float *xne);
+int launch_scatter_rows(gbkm_ctx *c, const int32_t *le, const float *mde, const int32_t *list, const int32_t *count,
+                        int64_t n, int32_t *labels, float *min_d2);
 
 // device-wide exclusive scan of L int32 (totals < 2^31); bsum holds ceil(L / 4096) ints
 void scan_excl(cudaStream_t st, const int32_t *in, int64_t L, int32_t *bsum, int32_t *out);
@@ -238,7 +249,7 @@ bool tc_assign_supported(int dtype, int64_t d, int64_t k);
 int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscales,
                      const float *X, const float *xnorm, int64_t n, int64_t d,
                      const CenterPrep &cp, int64_t k, int64_t k_pad, float err_rel,
-                     float err_abs, const AssignOut &o);
+                     float err_abs, const AssignOut &o, const int32_t *n_dev = nullptr);
 int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                         const float *bias, int act, int out_bf16, void *Y, int64_t ldy, float *Ypre, int64_t ldpre,
                         int32_t *top_idx, float *top_val, int topm);
@@ -276,7 +287,8 @@ struct BProb {
     int64_t crow0;           // first row of this problem among all centers rows (seeds x kps each)
     int64_t tile0;           // first global row tile
 };
-constexpr int BFLAG_STRIDE = 6;  // flag entry: problem, seed, row, candidate count (-1: all), c0, c1
+constexpr int BCAND_MAX = 4;     // candidates listed per flagged (problem, seed, point)
+constexpr int BFLAG_STRIDE = 4 + BCAND_MAX;  // flag entry: problem, seed, row, count (-1: all), candidates
 
 // batched tcgen05 distance GEMM over the (problem, row tile) work list; maps: 3 tensor maps per
 // problem (X operand, center operand, TF32 low part) in global memory, 64-byte aligned

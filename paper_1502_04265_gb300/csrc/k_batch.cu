@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(256) k_b_recheck(const BProb *__restrict__ pro
         const float *C = P.C[par] + (int64_t)s * P.k * P.d;
         float best = 0.f;
         int arg = -1;
-        if (e[3] == 2) {
-            for (int q = 0; q < 2; ++q) {
+        if (e[3] > 0 && e[3] <= BCAND_MAX) {
+            for (int q = 0; q < e[3]; ++q) {
                 const int j = e[4 + q];
                 const float v = warp_dd2(x, C + (int64_t)j * P.d, P.d);
                 if (arg < 0 || v < best || (v == best && j < arg)) {
@@ -816,7 +816,15 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
     }
     int64_t kmax_all = 0;
     for (auto &b : P) kmax_all = std::max(kmax_all, b.k);
+    // per-kernel timing brackets only outside a capture (a recorded graph is timed as a whole)
+    auto pb = [&](const char *name) {
+        if (!graph) prof_begin(c, name);
+    };
+    auto pe = [&]() {
+        if (!graph) prof_end(c);
+    };
     k_b_prep<<<(unsigned)blocks, 256, 0, st>>>(d_probs, d_blocks, bf ? 1 : 0);
+    pb("seed_batched");
     k_b_seed_first<<<(unsigned)npairs, 128, 0, st>>>(d_probs, d_pairs);
     c->launches += 2;
     for (int r = 1; r < kmax_all; ++r) {
@@ -824,6 +832,7 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         k_b_pick<<<(unsigned)npairs, PICKB_T, 0, st>>>(d_probs, d_pairs, r, c->status);
         c->launches += 2;
     }
+    pe();
     int par = 0;
     for (int64_t it = 0; it < iters; ++it) {
         e = cudaMemsetAsync(d_cmax, 0, 4 * count, st);
@@ -831,10 +840,15 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         if (e != cudaSuccess) break;
         k_b_cprep<<<(unsigned)crows, 128, 0, st>>>(d_probs, d_crow0, count, par, bf ? 1 : 0);
         c->launches += 1;
-        if ((rc = launch_assign_tc_batched(c, dtype, d_maps, d_probs, count, d_tile_prob, tiles, par, bn_max, d_flags,
-                                           d_fcount)) != GBKM_OK)
-            break;
+        pb("assign_batched");
+        rc = launch_assign_tc_batched(c, dtype, d_maps, d_probs, count, d_tile_prob, tiles, par, bn_max, d_flags,
+                                      d_fcount);
+        pe();
+        if (rc != GBKM_OK) break;
+        pb("recheck_batched");
         k_b_recheck<<<(unsigned)c->sm_count * 4, 256, 0, st>>>(d_probs, d_flags, d_fcount, par);
+        pe();
+        pb("update_batched");
         k_b_hist<<<(unsigned)ceil_div(nseg, 8), 256, hsm, st>>>(d_probs, d_pinfo, d_segs, nseg, kmax, d_hist);
         scan_excl(st, d_hist, hist_total, d_bsum, d_off);
         k_b_starts<<<(unsigned)ceil_div(G, 256), 256, 0, st>>>(d_pinfo, d_cpair, d_off, G, rows_total, d_start);
@@ -846,6 +860,7 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
                                                                           d_items, d_pbase, d_part, d_pnq, par, maxcb,
                                                                           d_nq, d_blk);
         k_b_final<<<(unsigned)npairs, 256, 0, st>>>(d_probs, d_pinfo, d_nq, d_blk, maxcb, d_costs);
+        pe();
         c->launches += 11;
         par ^= 1;
     }
@@ -868,6 +883,7 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
         if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
         c->graph_exec = ex;
+        c->graph_epoch = c->ws_epoch;
         e = cudaGraphLaunch(ex, st);
         if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
         c->launches += 0;

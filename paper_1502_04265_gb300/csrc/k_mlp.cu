@@ -240,15 +240,24 @@ int mlp_forward(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n, float
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
     __nv_bfloat16 *H1 = ws_at<__nv_bfloat16>(ws, oH1), *H2 = ws_at<__nv_bfloat16>(ws, oH2);
-    if ((rc = mlp_hidden(c, m, Xh, n, H1, H2, nullptr, nullptr)) != GBKM_OK) return rc;
+    prof_begin(c, "mlp_hidden");
+    rc = mlp_hidden(c, m, Xh, n, H1, H2, nullptr, nullptr);
+    prof_end(c);
+    if (rc != GBKM_OK) return rc;
     const __nv_bfloat16 *Wh = static_cast<const __nv_bfloat16 *>(m->params_bf16);
-    if (logits &&
-        (rc = launch_gemm_bf16_tc(c, H2, Wh + L.oW3, n, m->k, m->hidden, m->params + L.ob3, 0, 0, logits, m->k, nullptr,
-                                  0, nullptr, nullptr, 0)) != GBKM_OK)
-        return rc;
-    if (top_idx)
+    if (logits) {
+        prof_begin(c, "mlp_logits");
+        rc = launch_gemm_bf16_tc(c, H2, Wh + L.oW3, n, m->k, m->hidden, m->params + L.ob3, 0, 0, logits, m->k, nullptr,
+                                 0, nullptr, nullptr, 0);
+        prof_end(c);
+        if (rc != GBKM_OK) return rc;
+    }
+    if (top_idx) {
+        prof_begin(c, "mlp_topm");
         rc = launch_gemm_bf16_tc(c, H2, Wh + L.oW3, n, m->k, m->hidden, m->params + L.ob3, 0, 0, nullptr, 0, nullptr, 0,
                                  top_idx, nullptr, topm);
+        prof_end(c);
+    }
     return rc;
 }
 
@@ -363,7 +372,9 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
     int rc = mlp_forward(c, m, Xh, n, nullptr, cand, topm);
     if (rc == GBKM_OK) {
         e = cudaMemsetAsync(fc, 0, 8, c->stream);
+        prof_begin(c, "cand_check");
         k_cand_check<<<(unsigned)ceil_div(n * 32, 256), 256, 0, c->stream>>>(X, n, d, C, k, cand, topm, s2, labels, fl, fc);
+        prof_end(c);
         GBKM_LAUNCHED(c);
         // the rejected points get the full scan: their count is read back once
         int32_t nf = 0;
@@ -385,6 +396,7 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
                 cudaGetLastError();
                 rc = set_error(c, GBKM_ENOMEM, "learned_assign: fallback allocation failed");
             } else {
+                prof_begin(c, "fallback");
                 k_gather_rows<<<(unsigned)nf, 128, 0, c->stream>>>(X, d, fl, fc, sub);
                 GBKM_LAUNCHED(c);
                 gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 0};
@@ -393,6 +405,7 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
                     k_scatter_labels<<<(unsigned)ceil_div(nf, 256), 256, 0, c->stream>>>(subl, fl, fc, labels);
                     GBKM_LAUNCHED(c);
                 }
+                prof_end(c);
             }
             if (sub) cudaFreeAsync(sub, c->stream);
             if (subl) cudaFreeAsync(subl, c->stream);

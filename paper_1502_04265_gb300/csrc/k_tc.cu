@@ -26,14 +26,19 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int MAX_STAGES = 8;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
-constexpr int SMEM_BUDGET = 200 * 1024;
+constexpr int SMEM_BUDGET = 200 * 1024;      // stage ring of the batched kernel
+constexpr int MAX_DYN_SMEM = 227 * 1024;     // dynamic shared memory a CTA may use
 
 enum Form : int { F_BF16 = 0, F_TF32X3 = 1, F_FP8 = 2, F_TF32 = 3 };
 enum Epi : int { E_ARGMIN = 0, E_STORE = 1, E_TOPM = 2 };
 constexpr int TOPBUF = 64;  // per-row candidate buffer of the top-m epilogue (shared memory)
+constexpr int TROW = TOPBUF + 1;  // its row stride in floats
+// argmin epilogue shared memory: two groups' band lists, the hand-over slots and their barriers
+constexpr int ARGMIN_EXTRA_SMEM = 2 * 2 * CAND_MAX * 128 * 4 + 128 * 16 + 8 * 8;
 
 struct Args {
     int64_t n, d, k, k_pad;
+    const int32_t *n_dev;  // if set, the rows are the first min(n, *n_dev) (a count on the device)
     int n_chunks, bn, kb, stages, tmem_cols, m_tiles;
     uint32_t a_bytes, b_bytes, stage_bytes, tx_bytes;
     uint32_t idesc;
@@ -72,17 +77,125 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// the m-th largest key among a thread's cnt buffered candidates (stride 128 in shared memory):
-// the largest T with #{key >= T} >= m, found bit by bit from the top
-__device__ __forceinline__ uint32_t topm_threshold(const float *bv, int t, int cnt, int m) {
-    uint32_t T = 0;
-    for (int b = 31; b >= 0; --b) {
-        const uint32_t cand = T | (1u << b);
-        int c = 0;
-        for (int i = 0; i < cnt; ++i) c += fkey(bv[i * 128 + t]) >= cand;
-        if (c >= m) T = cand;
+// The certified band of one point, tracked by its thread over the score stream: the best score
+// v0 with its index i0 (the lowest index on equal scores: centers arrive in increasing order) in
+// registers, and every other center whose score was within E2 of the running best when it arrived
+// (a former best included, if still that close) in a per-thread list in shared memory (slot-major,
+// stride 128).  Entries that fall out of the band as v0 decreases are pruned when the list is full;
+// a candidate that finds it full of band members is dropped and only its score is kept (dmin, the
+// least dropped score), so the final band {j : s_j <= v0 + E2} is complete exactly when
+// dmin > v0 + E2.  A group of W scores costs a minimum tree unless its minimum can enter the band.
+template <int CAP>
+struct Band {
+    float v0, t, E2, dmin;
+    int i0, cnt;
+    float *lv;
+    int32_t *li;
+    __device__ __forceinline__ void reset(float e2) {
+        v0 = t = dmin = __int_as_float(0x7f800000);
+        E2 = e2;
+        i0 = 0;
+        cnt = 0;
     }
-    return T;
+    __device__ __forceinline__ void prune() {
+        int w = 0;
+        for (int q = 0; q < cnt; ++q) {
+            const float vv = lv[q * 128];
+            const int32_t jj = li[q * 128];
+            if (vv <= t) {
+                lv[w * 128] = vv;
+                li[w * 128] = jj;
+                ++w;
+            }
+        }
+        cnt = w;
+    }
+    __device__ __forceinline__ void list_push(float sc, int j) {
+        if (cnt == CAP) {
+            prune();
+            if (cnt == CAP) {
+                dmin = fminf(dmin, sc);
+                return;
+            }
+        }
+        lv[cnt * 128] = sc;
+        li[cnt * 128] = j;
+        ++cnt;
+    }
+    template <int W>
+    __device__ __forceinline__ static float select(const float (&sc)[W], int g) {
+        float r = sc[0];
+#pragma unroll
+        for (int h = 1; h < W; ++h) r = (h == g) ? sc[h] : r;
+        return r;
+    }
+    template <int W>
+    __device__ __forceinline__ static float min_tree(const float (&sc)[W]) {
+        float m[W / 2];
+#pragma unroll
+        for (int g = 0; g < W / 2; ++g) m[g] = fminf(sc[2 * g], sc[2 * g + 1]);
+#pragma unroll
+        for (int w = W / 4; w >= 1; w >>= 1)
+#pragma unroll
+            for (int g = 0; g < w; ++g) m[g] = fminf(m[2 * g], m[2 * g + 1]);
+        return m[0];
+    }
+    // W scores of centers j0 .. j0 + W - 1 (+inf where there is no center)
+    template <int W>
+    __device__ __forceinline__ void group(const float (&sc)[W], int j0) {
+        const float m = min_tree(sc);
+        if (m <= t) {
+            const float tn = fminf(t, m + E2);
+            uint32_t le = 0, eq = 0;
+#pragma unroll
+            for (int g = 0; g < W; ++g) {
+                le |= (sc[g] <= tn ? 1u : 0u) << g;
+                eq |= (sc[g] == m ? 1u : 0u) << g;
+            }
+            if (m < v0) {
+                if (v0 <= tn) list_push(v0, i0);
+                const int gb = __ffs(eq) - 1;
+                v0 = m;
+                i0 = j0 + gb;
+                t = tn;
+                le &= ~(1u << gb);
+            }
+            while (le) {
+                const int g = __ffs(le) - 1;
+                le &= le - 1;
+                list_push(select(sc, g), j0 + g);
+            }
+        }
+    }
+};
+
+// top-m order: larger value first, then lower index; the key is unique per center
+__device__ __forceinline__ unsigned long long topm_key(float v, int32_t j) {
+    return ((unsigned long long)fkey(v) << 32) | (uint32_t)(~j);
+}
+
+// Bitonic sort of 64 keys held two per lane (x at position lane, y at position lane + 32) into
+// ascending order across the warp; every lane takes part.
+__device__ __forceinline__ void warp_sort64(unsigned long long &x, unsigned long long &y) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                const unsigned long long lo = min(x, y), hi = max(x, y);
+                x = lo;
+                y = hi;
+            } else {
+                const unsigned long long ox = __shfl_xor_sync(0xffffffffu, x, j);
+                const unsigned long long oy = __shfl_xor_sync(0xffffffffu, y, j);
+                const bool lower = (lane & j) == 0;
+                const bool upx = (lane & k) == 0, upy = ((lane + 32) & k) == 0;
+                x = (lower == upx) ? min(x, ox) : max(x, ox);
+                y = (lower == upy) ? min(y, oy) : max(y, oy);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- PTX helpers
@@ -178,6 +291,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr)
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+// the first 16 columns of a 32-register buffer (the 16-column tail of a column range)
+__device__ __forceinline__ void tmem_ld16_into32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // wait for the thread's TMEM loads, with the loaded registers as operands so that no use of them
 // can be scheduled before the wait
@@ -208,11 +352,23 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // ---------------------------------------------------------------- the kernel
+// epilogue warpgroups of a k_tc instance: two (each takes half of every chunk's columns) except for
+// the top-m epilogue, whose per-row buffers leave room for one
+template <int EPI>
+constexpr int epi_groups() {
+    return EPI == E_TOPM ? 1 : 2;
+}
 template <int FORM, int EPI>
-__global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
+constexpr int tc_threads() {
+    return FORM == F_TF32X3 ? (epi_groups<EPI>() == 2 ? 512 : 384) : (epi_groups<EPI>() == 2 ? 384 : 256);
+}
+
+template <int FORM, int EPI>
+__global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
          const __grid_constant__ CUtensorMap tmB2, const Args a) {
     constexpr bool X3 = (FORM == F_TF32X3);
+    constexpr int NG = epi_groups<EPI>();
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned stage base, derived by pointer arithmetic on the shared array so that
     // accesses through it stay shared-memory accesses
@@ -232,7 +388,13 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 4);
+            mbar_init(&acce[b], 4 * NG);
+        }
+        if constexpr (EPI == E_ARGMIN && NG == 2) {
+            // hand-over of group 1's half of every point's band to group 0 (one pair per lane quarter)
+            uint64_t *xfull = reinterpret_cast<uint64_t *>(base + (size_t)a.stages * a.stage_bytes + 1024 +
+                                                           NG * 2 * CAND_MAX * 128 * 4 + 128 * 16);
+            for (int i = 0; i < 8; ++i) mbar_init(&xfull[i], 1);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -249,6 +411,9 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
     const uint32_t tmem_base = *tmem_slot;
     const int bn_alloc = a.tmem_cols / 2;
     const int units_per_tile = a.n_chunks;
+    // rows of this launch: n, or a count produced on the device by an earlier kernel
+    const int64_t n_rows = a.n_dev ? min(a.n, (int64_t)max(0, *a.n_dev)) : a.n;
+    const int m_tiles = (int)((n_rows + BM - 1) / BM);
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -256,7 +421,7 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
             int s = 0;
             uint32_t ph = 0;
             uint32_t issued = 0, last_par = 0;  // per-stage: issued bit, parity of the last issue
-            for (int tile = blockIdx.x; tile < a.m_tiles && !*abort_flag; tile += gridDim.x) {
+            for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
                 for (int nc = 0; nc < units_per_tile; ++nc) {
                     for (int kb = 0; kb < a.kb; ++kb) {
                         if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) goto producer_done;
@@ -291,7 +456,7 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
             bool committed = false;
             uint64_t *last_bar = nullptr;
             uint32_t last_parity = 0;
-            for (int tile = blockIdx.x; tile < a.m_tiles && !*abort_flag; tile += gridDim.x) {
+            for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
                 for (int nc = 0; nc < units_per_tile; ++nc) {
                     if (!mbar_wait(&acce[ab], aph ^ 1, abort_flag)) goto mma_done;
                     tc_fence_after();
@@ -337,12 +502,12 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
         mma_done:
             if (*abort_flag && committed && last_bar) mbar_drain(last_bar, last_parity, 500000000ull);
         }
-    } else if (X3 && warp >= 8) {
+    } else if (X3 && warp >= 8 && warp < 12) {
         // ------------------------------------------------ 3xTF32 split of the staged X tile
         const int t = threadIdx.x - 256;  // 0..127
         int s = 0;
         uint32_t ph = 0;
-        for (int tile = blockIdx.x; tile < a.m_tiles && !*abort_flag; tile += gridDim.x) {
+        for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
             for (int nc = 0; nc < units_per_tile; ++nc) {
                 for (int kb = 0; kb < a.kb; ++kb) {
                     if (!mbar_wait(&full[s], ph, abort_flag)) goto split_done;
@@ -374,244 +539,236 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
             }
         }
     split_done:;
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp >= 4 && (warp < 8 || (NG == 2 && warp >= (X3 ? 12 : 8)))) {
         // ------------------------------------------------ epilogue: one TMEM lane = one point
-        const int q = warp - 4;
+        const int q = warp & 3;             // TMEM lane quarter of this warp
+        const int eg = warp < 8 ? 0 : 1;    // epilogue group: which half of every chunk's columns
+        const int g16 = a.bn / 16, h16 = (g16 + NG - 1) / NG;
+        const int c_begin = eg * h16 * 16, c_end = min(a.bn, (eg + 1) * h16 * 16);
         int ab = 0;
-        uint32_t aph = 0;
+        uint32_t aph = 0, xph = 0;
         const float cm = (EPI == E_ARGMIN) ? __uint_as_float(*a.cmax) : 0.f;
-        for (int tile = blockIdx.x; tile < a.m_tiles && !*abort_flag; tile += gridDim.x) {
+        uint8_t *ex = base + (size_t)a.stages * a.stage_bytes + 1024;  // epilogue shared memory
+        for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
             const int64_t row = (int64_t)tile * BM + q * 32 + lane;
-            const bool valid = row < a.n;
-            float v0 = __int_as_float(0x7f800000), v1 = v0, v2 = v0;
-            int i0 = 0, i1 = 0;
+            const bool valid = row < n_rows;
             float sx = 1.f;
             if (EPI == E_ARGMIN && FORM == F_FP8 && valid) sx = a.xscale[row];
-            // top-m state: threshold and this thread's buffer (slot-major, stride 128)
+            // argmin state: the certified band of this point (error bound E2 on a score difference)
+            const float xn = (EPI == E_ARGMIN && valid) ? a.xnorm[row] : 0.f;
+            Band<CAND_MAX> band;
+            {
+                const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
+                band.reset(2.f * (a.err_rel * xr * cm + a.err_abs * cm * cm));
+                band.lv = reinterpret_cast<float *>(ex) + eg * (2 * CAND_MAX * 128) + q * 32 + lane;
+                band.li = reinterpret_cast<int32_t *>(band.lv + CAND_MAX * 128);
+            }
+            // top-m state: the value a candidate must beat and this row's buffer (row-major, TROW
+            // entries per row so that a warp reading one row's entries hits distinct banks)
             float tau = -__int_as_float(0x7f800000);
             int tcnt = 0;
-            const int et = q * 32 + lane;
-            float *tbv = reinterpret_cast<float *>(base + (size_t)a.stages * a.stage_bytes + 1024);
-            int32_t *tbi = reinterpret_cast<int32_t *>(tbv + TOPBUF * 128);
+            float *tbv_all = reinterpret_cast<float *>(ex);
+            int32_t *tbi_all = reinterpret_cast<int32_t *>(tbv_all + TROW * 128);
+            float *tbv = tbv_all + (q * 32 + lane) * TROW;
+            int32_t *tbi = tbi_all + (q * 32 + lane) * TROW;
+            // warp-cooperative: lane L's full buffer is cut to its topm best (rank order) and its
+            // threshold becomes the topm-th best value
+            auto compact = [&](int L) {
+                float *rv = tbv_all + (q * 32 + L) * TROW;
+                int32_t *ri = tbi_all + (q * 32 + L) * TROW;
+                const int lc = __shfl_sync(0xffffffffu, tcnt, L);
+                unsigned long long x = lane < lc ? topm_key(rv[lane], ri[lane]) : 0ull;
+                unsigned long long y = lane + 32 < lc ? topm_key(rv[lane + 32], ri[lane + 32]) : 0ull;
+                warp_sort64(x, y);
+                const int rk = 31 - lane;  // the rank of y (0 = best)
+                if (rk < a.topm) {
+                    rv[rk] = fkey_inv((uint32_t)(y >> 32));
+                    ri[rk] = ~(int32_t)(uint32_t)y;
+                }
+                const unsigned long long tk = __shfl_sync(0xffffffffu, y, 32 - a.topm);
+                __syncwarp();
+                if (lane == L) {
+                    tcnt = a.topm;
+                    tau = fkey_inv((uint32_t)(tk >> 32));
+                }
+            };
+            if constexpr (EPI == E_ARGMIN && NG == 2) {
+                // group 1 reuses its band list only after group 0 has merged the previous point's
+                if (eg == 1) {
+                    uint64_t *xempty = reinterpret_cast<uint64_t *>(ex + NG * 2 * CAND_MAX * 128 * 4 + 128 * 16) + 4;
+                    if (!mbar_wait(&xempty[q], xph ^ 1, abort_flag)) goto epi_done;
+                }
+            }
             for (int nc = 0; nc < units_per_tile; ++nc) {
                 if (!mbar_wait(&accf[ab], aph, abort_flag)) goto epi_done;
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * bn_alloc);
-                // 16 accumulator columns per tcgen05.ld; the load of the next group is in flight
-                // while the current group is processed
-                auto process = [&](const uint32_t (&r)[16], int c) {
+                // W accumulator columns starting at chunk column c
+                auto process = [&](const auto &r, int c) {
+                    constexpr int W = sizeof(r) / sizeof(uint32_t);
                     const int64_t j0 = (int64_t)nc * a.bn + c;
                     if constexpr (EPI == E_ARGMIN) {
                         if (j0 >= a.k) return;
-                        float cn[16], ms[16];
-                        if (j0 + 16 <= a.k_pad) {
+                        float cn[W], sc[W];
+                        if (j0 + W <= a.k_pad) {
 #pragma unroll
-                            for (int g = 0; g < 4; ++g) {
+                            for (int g = 0; g < W / 4; ++g) {
                                 const float4 t4 = __ldg(reinterpret_cast<const float4 *>(a.cnorm + j0) + g);
                                 cn[4 * g] = t4.x, cn[4 * g + 1] = t4.y, cn[4 * g + 2] = t4.z, cn[4 * g + 3] = t4.w;
                             }
                         } else {
 #pragma unroll
-                            for (int g = 0; g < 16; ++g)
+                            for (int g = 0; g < W; ++g)
                                 cn[g] = (j0 + g < a.k_pad) ? a.cnorm[j0 + g] : __int_as_float(0x7f800000);
                         }
+                        float ms[W];
 #pragma unroll
-                        for (int g = 0; g < 16; ++g) {
-                            if constexpr (FORM == F_FP8)
-                                ms[g] = (j0 + g < a.k) ? -2.f * sx * a.cscale[j0 + g] : -2.f;
-                            else
-                                ms[g] = -2.f;
-                        }
+                        for (int g = 0; g < W; ++g) ms[g] = -2.f;
+                        if constexpr (FORM == F_FP8) {
+                            // E4M3 scores carry the point's and the center's scales
+                            if (j0 + W <= a.k_pad) {
 #pragma unroll
-                        for (int g = 0; g < 16; ++g) {
-                            const int j = (int)(j0 + g);
-                            const float s = (j < a.k) ? fmaf(ms[g], __uint_as_float(r[g]), cn[g])
-                                                      : __int_as_float(0x7f800000);
-                            const bool lt0 = s < v0, lt1 = s < v1;
-                            const float m0 = fmaxf(v0, s), m1 = fmaxf(v1, s);
-                            v2 = fminf(v2, m1);
-                            v1 = fminf(v1, m0);
-                            v0 = fminf(v0, s);
-                            i1 = lt0 ? i0 : (lt1 ? j : i1);
-                            i0 = lt0 ? j : i0;
-                        }
-                    } else if constexpr (EPI == E_STORE) {
-                        const int64_t col0 = (int64_t)nc * a.bn + c;
-                        if (valid && col0 < a.k) {
-                            float v[16];
-#pragma unroll
-                            for (int g = 0; g < 16; ++g) v[g] = __uint_as_float(r[g]);
-                            if (a.bias) {
-#pragma unroll
-                                for (int g = 0; g < 4; ++g) {
-                                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g);
-                                    v[4 * g] += b4.x, v[4 * g + 1] += b4.y, v[4 * g + 2] += b4.z, v[4 * g + 3] += b4.w;
+                                for (int g = 0; g < W / 4; ++g) {
+                                    const float4 t4 = __ldg(reinterpret_cast<const float4 *>(a.cscale + j0) + g);
+                                    ms[4 * g] = -2.f * sx * t4.x, ms[4 * g + 1] = -2.f * sx * t4.y;
+                                    ms[4 * g + 2] = -2.f * sx * t4.z, ms[4 * g + 3] = -2.f * sx * t4.w;
                                 }
-                            }
-                            if (a.Ypre) {
-                                float4 *pr = reinterpret_cast<float4 *>(a.Ypre + row * a.ldpre + col0);
-#pragma unroll
-                                for (int g = 0; g < 4; ++g) pr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
-                            }
-                            if (a.act == 1) {
-#pragma unroll
-                                for (int g = 0; g < 16; ++g) v[g] = gelu_erf(v[g]);
-                            }
-                            if (a.out_bf16) {
-                                uint32_t w[8];
-#pragma unroll
-                                for (int g = 0; g < 8; ++g) {
-                                    __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * g], v[2 * g + 1]);
-                                    w[g] = *reinterpret_cast<uint32_t *>(&h);
-                                }
-                                uint4 *yr = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.Y) + row * a.ldy + col0);
-                                yr[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                                yr[1] = make_uint4(w[4], w[5], w[6], w[7]);
                             } else {
-                                float4 *yr = reinterpret_cast<float4 *>(a.Y + row * a.ldy + col0);
 #pragma unroll
-                                for (int g = 0; g < 4; ++g) yr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                                for (int g = 0; g < W; ++g) ms[g] = (j0 + g < a.k_pad) ? -2.f * sx * a.cscale[j0 + g] : -2.f;
+                            }
+                        }
+#pragma unroll
+                        for (int g = 0; g < W; ++g)
+                            sc[g] = (j0 + g < a.k) ? fmaf(ms[g], __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
+                        band.group(sc, (int)j0);
+                    } else if constexpr (EPI == E_STORE) {
+                        if (valid && j0 < a.k) {
+#pragma unroll
+                            for (int h = 0; h < W / 16; ++h) {
+                                const int64_t col0 = j0 + 16 * h;
+                                if (col0 >= a.k) break;
+                                float v[16];
+#pragma unroll
+                                for (int g = 0; g < 16; ++g) v[g] = __uint_as_float(r[16 * h + g]);
+                                if (a.bias) {
+#pragma unroll
+                                    for (int g = 0; g < 4; ++g) {
+                                        const float4 b4 = __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g);
+                                        v[4 * g] += b4.x, v[4 * g + 1] += b4.y, v[4 * g + 2] += b4.z, v[4 * g + 3] += b4.w;
+                                    }
+                                }
+                                if (a.Ypre) {
+                                    float4 *pr = reinterpret_cast<float4 *>(a.Ypre + row * a.ldpre + col0);
+#pragma unroll
+                                    for (int g = 0; g < 4; ++g)
+                                        pr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                                }
+                                if (a.act == 1) {
+#pragma unroll
+                                    for (int g = 0; g < 16; ++g) v[g] = gelu_erf(v[g]);
+                                }
+                                if (a.out_bf16) {
+                                    uint32_t w[8];
+#pragma unroll
+                                    for (int g = 0; g < 8; ++g) {
+                                        __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * g], v[2 * g + 1]);
+                                        w[g] = *reinterpret_cast<uint32_t *>(&hh);
+                                    }
+                                    uint4 *yr = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.Y) +
+                                                                          row * a.ldy + col0);
+                                    yr[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                                    yr[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                                } else {
+                                    float4 *yr = reinterpret_cast<float4 *>(a.Y + row * a.ldy + col0);
+#pragma unroll
+                                    for (int g = 0; g < 4; ++g)
+                                        yr[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                                }
                             }
                         }
                     } else {
-                        // top-m: candidates above the running threshold go to this row's buffer
-                        const int64_t col0 = (int64_t)nc * a.bn + c;
-                        if (col0 >= a.k) return;
-                        float sv[16];
+                        // top-m: candidates above the row's threshold go to its buffer; a group of 16
+                        // costs 16 compares unless some lane of the warp has a candidate in it
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) {
-                            const float4 b4 = a.bias ? __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g)
-                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-                            sv[4 * g] = __uint_as_float(r[4 * g]) + b4.x;
-                            sv[4 * g + 1] = __uint_as_float(r[4 * g + 1]) + b4.y;
-                            sv[4 * g + 2] = __uint_as_float(r[4 * g + 2]) + b4.z;
-                            sv[4 * g + 3] = __uint_as_float(r[4 * g + 3]) + b4.w;
-                        }
-                        uint32_t m = 0;
+                        for (int h = 0; h < W / 16; ++h) {
+                            const int64_t col0 = j0 + 16 * h;
+                            if (col0 >= a.k) break;
+                            float sv[16];
 #pragma unroll
-                        for (int g = 0; g < 16; ++g)
-                            if (sv[g] > tau && col0 + g < a.k) m |= 1u << g;
-                        while (m) {
-                            const int g = __ffs(m) - 1;
-                            m &= m - 1;
-                            float sg = 0.f;
-#pragma unroll
-                            for (int h = 0; h < 16; ++h)
-                                if (h == g) sg = sv[h];
-                            if (tcnt == TOPBUF) {
-                                const uint32_t T = topm_threshold(tbv, et, tcnt, a.topm);
-                                int nw = 0;
-                                for (int i = 0; i < tcnt; ++i) {
-                                    const float bvv = tbv[i * 128 + et];
-                                    if (fkey(bvv) >= T) {
-                                        tbv[nw * 128 + et] = bvv;
-                                        tbi[nw * 128 + et] = tbi[i * 128 + et];
-                                        ++nw;
-                                    }
-                                }
-                                tcnt = nw;
-                                tau = fkey_inv(T);
-                                if (!(sg > tau) || tcnt == TOPBUF) continue;
+                            for (int g = 0; g < 4; ++g) {
+                                const float4 b4 = a.bias ? __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                                sv[4 * g] = __uint_as_float(r[16 * h + 4 * g]) + b4.x;
+                                sv[4 * g + 1] = __uint_as_float(r[16 * h + 4 * g + 1]) + b4.y;
+                                sv[4 * g + 2] = __uint_as_float(r[16 * h + 4 * g + 2]) + b4.z;
+                                sv[4 * g + 3] = __uint_as_float(r[16 * h + 4 * g + 3]) + b4.w;
                             }
-                            tbv[tcnt * 128 + et] = sg;
-                            tbi[tcnt * 128 + et] = (int32_t)(col0 + g);
-                            ++tcnt;
+                            uint32_t msk = 0;
+#pragma unroll
+                            for (int g = 0; g < 16; ++g)
+                                if (sv[g] > tau && col0 + g < a.k) msk |= 1u << g;
+                            uint32_t any = __reduce_or_sync(0xffffffffu, msk);
+                            while (any) {
+                                const int g = __ffs(any) - 1;
+                                any &= any - 1;
+                                const float sg = Band<1>::select(sv, g);
+                                const bool want = (msk >> g) & 1u;
+                                uint32_t fullm = __ballot_sync(0xffffffffu, want && sg > tau && tcnt == TOPBUF);
+                                while (fullm) {
+                                    const int L = __ffs(fullm) - 1;
+                                    fullm &= fullm - 1;
+                                    compact(L);
+                                }
+                                if (want && sg > tau) {
+                                    tbv[tcnt] = sg;
+                                    tbi[tcnt] = (int32_t)(col0 + g);
+                                    ++tcnt;
+                                }
+                            }
                         }
                     }
                 };
-                uint32_t ra[16], rb[16];
-                tmem_ld16(tbase, ra);
-                tmem_wait_ld(ra);
-                for (int c = 0; c < a.bn; c += 32) {
-                    const bool has_b = c + 16 < a.bn;
-                    if (has_b) tmem_ld16(tbase + (uint32_t)(c + 16), rb);
-                    process(ra, c);
-                    if (has_b) {
+                // this group's columns in units of 32 (a 16-column tail), the next unit's TMEM load
+                // in flight while the current one is processed
+                {
+                    uint32_t ra[32], rb[32];
+                    int c = c_begin;
+                    // 32-column units, except 16 for 3xTF32 (its 512-thread CTA leaves 128 registers)
+                    constexpr int UW = X3 ? 16 : 32;
+                    auto load = [&](uint32_t (&r)[32], int cc) {
+                        if (UW == 32 && c_end - cc >= 32)
+                            tmem_ld32(tbase + (uint32_t)cc, r);
+                        else
+                            tmem_ld16_into32(tbase + (uint32_t)cc, r);
+                    };
+                    auto run = [&](const uint32_t (&r)[32], int cc) {
+                        if (UW == 32 && c_end - cc >= 32) {
+                            process(r, cc);
+                        } else {
+                            const uint32_t(&r16)[16] = *reinterpret_cast<const uint32_t(*)[16]>(&r[0]);
+                            process(r16, cc);
+                        }
+                    };
+                    if (c < c_end) {
+                        load(ra, c);
+                        tmem_wait_ld(ra);
+                    }
+                    while (c < c_end) {
+                        const int c1 = c + min(UW, c_end - c);
+                        if (c1 < c_end) load(rb, c1);
+                        run(ra, c);
+                        if (c1 >= c_end) break;
                         tmem_wait_ld(rb);
-                        if (c + 32 < a.bn) tmem_ld16(tbase + (uint32_t)(c + 32), ra);
-                        process(rb, c + 16);
-                        if (c + 32 < a.bn) tmem_wait_ld(ra);
+                        const int c2 = c1 + min(UW, c_end - c1);
+                        if (c2 < c_end) load(ra, c2);
+                        run(rb, c1);
+                        if (c2 >= c_end) break;
+                        tmem_wait_ld(ra);
+                        c = c2;
                     }
                 }
-                if constexpr (EPI == E_ARGMIN) {
-                    if (nc == units_per_tile - 1) {
-                        // the point's final top-2: label, expanded min distance, certified near-tie flag
-                        const float xn = valid ? a.xnorm[row] : 0.f;
-                        const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
-                        const float E2 = 2.f * (a.err_rel * xr * cm + a.err_abs * cm * cm);
-                        const bool flag = valid && !((v1 - v0) > E2);
-                        if (valid) {
-                            a.labels[row] = i0;
-                            if (a.min_d2) a.min_d2[row] = fmaxf(0.f, xn + v0);
-                        }
-                        if (a.flag_list) {
-                            const unsigned m = __ballot_sync(0xffffffffu, flag);
-                            if (m) {
-                                const int leader = __ffs(m) - 1;
-                                int b0 = 0;
-                                if (lane == leader) b0 = atomicAdd(a.flag_count, __popc(m));
-                                b0 = __shfl_sync(0xffffffffu, b0, leader);
-                                const int slot = b0 + __popc(m & lanemask_lt());
-                                int32_t *cf = a.cand + (int64_t)slot * CAND_STRIDE;
-                                if (flag) a.flag_list[slot] = (int32_t)row;
-                                // two candidates when every other center is certified worse (v2 is
-                                // the third best score); otherwise the band must be listed
-                                const bool pair = flag && (v2 - v0) > E2;
-                                const bool need_band = flag && !pair;
-                                if (pair) {
-                                    cf[0] = 2;
-                                    cf[1] = min(i0, i1);
-                                    cf[2] = max(i0, i1);
-                                }
-                                if (units_per_tile == 1 && __any_sync(0xffffffffu, need_band)) {
-                                    // a second pass over the accumulator, still resident in TMEM: every
-                                    // center whose score lies inside the band is a candidate
-                                    int cnt = 0;
-                                    auto band = [&](const uint32_t (&r)[16], int c) {
-                                        if (!need_band || c >= a.k) return;
-                                        float cn[16];
-#pragma unroll
-                                        for (int g = 0; g < 4; ++g) {
-                                            const float4 t4 = __ldg(reinterpret_cast<const float4 *>(a.cnorm + c) + g);
-                                            cn[4 * g] = t4.x, cn[4 * g + 1] = t4.y, cn[4 * g + 2] = t4.z, cn[4 * g + 3] = t4.w;
-                                        }
-                                        uint32_t inband = 0;
-#pragma unroll
-                                        for (int g = 0; g < 16; ++g) {
-                                            float ms = -2.f;
-                                            if constexpr (FORM == F_FP8) ms = (c + g < a.k) ? -2.f * sx * a.cscale[c + g] : 0.f;
-                                            const float sc = fmaf(ms, __uint_as_float(r[g]), cn[g]);
-                                            if (c + g < a.k && sc - v0 <= E2) inband |= 1u << g;
-                                        }
-                                        while (inband) {
-                                            const int g = __ffs(inband) - 1;
-                                            inband &= inband - 1;
-                                            if (cnt < CAND_MAX) cf[1 + cnt] = c + g;
-                                            ++cnt;
-                                        }
-                                    };
-                                    uint32_t ra[16], rb[16];
-                                    tmem_ld16(tbase, ra);
-                                    tmem_wait_ld(ra);
-                                    for (int c = 0; c < a.bn; c += 32) {
-                                        const bool has_b = c + 16 < a.bn;
-                                        if (has_b) tmem_ld16(tbase + (uint32_t)(c + 16), rb);
-                                        band(ra, c);
-                                        if (has_b) {
-                                            tmem_wait_ld(rb);
-                                            if (c + 32 < a.bn) tmem_ld16(tbase + (uint32_t)(c + 32), ra);
-                                            band(rb, c + 16);
-                                            if (c + 32 < a.bn) tmem_wait_ld(ra);
-                                        }
-                                    }
-                                    if (need_band) cf[0] = cnt <= CAND_MAX ? cnt : -1;
-                                } else if (need_band) {
-                                    cf[0] = -1;
-                                }
-                            }
-                        }
-                    }
-                }
+                // the accumulator is free once both groups have read their columns
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce[ab]);
@@ -619,27 +776,96 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                     ab = 0;
                     aph ^= 1;
                 }
-            }
-            if constexpr (EPI == E_TOPM) {
-                // exactly m outputs: keys above the m-th largest, then ties at it, -1 padding
-                if (valid) {
-                    const int m = a.topm;
-                    const uint32_t T = tcnt >= m ? topm_threshold(tbv, et, tcnt, m) : 0u;
-                    int w = 0;
-                    for (int pass = 0; pass < 2; ++pass)
-                        for (int i = 0; i < tcnt && w < m; ++i) {
-                            const float bvv = tbv[i * 128 + et];
-                            const uint32_t kk = fkey(bvv);
-                            if ((pass == 0 && kk > T) || (pass == 1 && kk == T)) {
-                                a.top_idx[row * m + w] = tbi[i * 128 + et];
-                                if (a.top_val) a.top_val[row * m + w] = bvv;
-                                ++w;
+                if constexpr (EPI == E_ARGMIN) {
+                    if (nc == units_per_tile - 1) {
+                        // group 1 hands its half of the point's band to group 0 through shared memory
+                        float4 *xch = reinterpret_cast<float4 *>(ex + NG * 2 * CAND_MAX * 128 * 4);
+                        uint64_t *xfull = reinterpret_cast<uint64_t *>(xch + 128), *xempty = xfull + 4;
+                        band.prune();
+                        if (NG == 2 && eg == 1) {
+                            xch[q * 32 + lane] = make_float4(band.v0, __int_as_float(band.i0), __int_as_float(band.cnt),
+                                                             band.dmin);
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&xfull[q]);
+                            xph ^= 1;
+                        } else {
+                            float vA = band.v0, vB = __int_as_float(0x7f800000), dB = vB;
+                            int iA = band.i0, iB = 0, cB = 0;
+                            const float *lvB = band.lv + 2 * CAND_MAX * 128;
+                            const int32_t *liB = band.li + 2 * CAND_MAX * 128;
+                            if (NG == 2) {
+                                if (!mbar_wait(&xfull[q], xph, abort_flag)) goto epi_done;
+                                const float4 o = xch[q * 32 + lane];
+                                vB = o.x, iB = __float_as_int(o.y), cB = __float_as_int(o.z), dB = o.w;
+                            }
+                            const bool takeB = vB < vA || (vB == vA && iB < iA);
+                            const float v = takeB ? vB : vA, vl = takeB ? vA : vB;
+                            const int ib = takeB ? iB : iA, il = takeB ? iA : iB;
+                            const float t = v + band.E2;
+                            // the band: the best, every listed center within E2 of it, the other
+                            // group's best if within E2; complete unless something was dropped
+                            int cnt = 1 + (vl <= t ? 1 : 0);
+                            for (int e = 0; e < band.cnt; ++e) cnt += band.lv[e * 128] <= t ? 1 : 0;
+                            for (int e = 0; e < cB; ++e) cnt += lvB[e * 128] <= t ? 1 : 0;
+                            const bool over = !(v < __int_as_float(0x7f800000)) || band.dmin <= t || dB <= t ||
+                                              cnt > CAND_MAX;
+                            const int bc = over ? -1 : cnt;
+                            const bool flag = valid && bc != 1;
+                            if (valid) {
+                                a.labels[row] = ib;
+                                if (a.min_d2) a.min_d2[row] = fmaxf(0.f, xn + v);
+                            }
+                            if (a.flag_list) {
+                                const unsigned m = __ballot_sync(0xffffffffu, flag);
+                                if (m) {
+                                    const int leader = __ffs(m) - 1;
+                                    int b0 = 0;
+                                    if (lane == leader) b0 = atomicAdd(a.flag_count, __popc(m));
+                                    b0 = __shfl_sync(0xffffffffu, b0, leader);
+                                    if (flag) {
+                                        const int slot = b0 + __popc(m & lanemask_lt());
+                                        a.flag_list[slot] = (int32_t)row;
+                                        // the band's centers (the best first), or -1: scan all centers
+                                        int32_t *cf = a.cand + (int64_t)slot * CAND_STRIDE;
+                                        cf[0] = bc;
+                                        if (bc > 0) {
+                                            int w = 1;
+                                            cf[w++] = ib;
+                                            if (vl <= t) cf[w++] = il;
+                                            for (int e = 0; e < band.cnt; ++e)
+                                                if (band.lv[e * 128] <= t) cf[w++] = band.li[e * 128];
+                                            for (int e = 0; e < cB; ++e)
+                                                if (lvB[e * 128] <= t) cf[w++] = liB[e * 128];
+                                        }
+                                    }
+                                }
+                            }
+                            if (NG == 2) {
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(&xempty[q]);
+                                xph ^= 1;
                             }
                         }
-                    for (; w < m; ++w) {
-                        a.top_idx[row * m + w] = -1;
-                        if (a.top_val) a.top_val[row * m + w] = -__int_as_float(0x7f800000);
                     }
+                }
+            }
+            if constexpr (EPI == E_TOPM) {
+                // every row of the warp in turn: its m best in rank order, -1 padding
+                for (int L = 0; L < 32; ++L) {
+                    const int64_t rowL = (int64_t)tile * BM + q * 32 + L;
+                    const float *rv = tbv_all + (q * 32 + L) * TROW;
+                    const int32_t *ri = tbi_all + (q * 32 + L) * TROW;
+                    const int lc = __shfl_sync(0xffffffffu, tcnt, L);
+                    unsigned long long x = lane < lc ? topm_key(rv[lane], ri[lane]) : 0ull;
+                    unsigned long long y = lane + 32 < lc ? topm_key(rv[lane + 32], ri[lane + 32]) : 0ull;
+                    warp_sort64(x, y);
+                    const int rk = 31 - lane;
+                    if (rowL < n_rows && rk < a.topm) {
+                        a.top_idx[rowL * a.topm + rk] = y ? ~(int32_t)(uint32_t)y : -1;
+                        if (a.top_val)
+                            a.top_val[rowL * a.topm + rk] = y ? fkey_inv((uint32_t)(y >> 32)) : -__int_as_float(0x7f800000);
+                    }
+                    __syncwarp();
                 }
             }
         }
@@ -838,12 +1064,19 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
             const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
             const float E2 = 2.f * (P.err_rel * xr * cm + P.err_abs * cm * cm);
             const int64_t ncols = (int64_t)P.seeds * P.kps;
-            float v0 = __int_as_float(0x7f800000), v1 = v0, v2 = v0;
-            int i0 = 0, i1 = 0, cur = 0;
+            Band<BCAND_MAX> band;
+            band.lv = reinterpret_cast<float *>(base + (size_t)stages * stage_bytes + 1024) + q * 32 + lane;
+            band.li = reinterpret_cast<int32_t *>(band.lv + BCAND_MAX * 128);
+            band.reset(E2);
+            int cur = 0;
             // emit the finished seed s of this point: label, certified near-tie flag, candidates
             auto finish = [&](int s) {
-                const bool flag = valid && !((v1 - v0) > E2);
-                if (valid) P.labels[(int64_t)s * P.n + row] = i0;
+                band.prune();
+                const bool over = !(band.v0 < __int_as_float(0x7f800000)) || band.dmin <= band.t ||
+                                  1 + band.cnt > BCAND_MAX;
+                const int bc = over ? -1 : 1 + band.cnt;
+                const bool flag = valid && bc != 1;
+                if (valid) P.labels[(int64_t)s * P.n + row] = band.i0;
                 const unsigned m = __ballot_sync(0xffffffffu, flag);
                 if (m) {
                     const int leader = __ffs(m) - 1;
@@ -855,14 +1088,14 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                         f[0] = p;
                         f[1] = s;
                         f[2] = (int32_t)row;
-                        const bool pair = (v2 - v0) > E2;
-                        f[3] = pair ? 2 : -1;
-                        f[4] = min(i0, i1);
-                        f[5] = max(i0, i1);
+                        f[3] = bc;
+                        if (bc > 0) {
+                            f[4] = band.i0;
+                            for (int q2 = 0; q2 < band.cnt; ++q2) f[5 + q2] = band.li[q2 * 128];
+                        }
                     }
                 }
-                v0 = v1 = v2 = __int_as_float(0x7f800000);
-                i0 = i1 = 0;
+                band.reset(E2);
             };
             for (int nc = 0; nc < P.n_chunks; ++nc) {
                 if (!mbar_wait(&accf[ab], aph, abort_flag)) goto epi_done;
@@ -878,24 +1111,16 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                         cur = s;
                     }
                     if (jl0 >= P.k) return;
-                    float cn[16];
+                    float cn[16], sc[16];
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         const float4 t4 = __ldg(reinterpret_cast<const float4 *>(P.cnorm + j0) + g);
                         cn[4 * g] = t4.x, cn[4 * g + 1] = t4.y, cn[4 * g + 2] = t4.z, cn[4 * g + 3] = t4.w;
                     }
 #pragma unroll
-                    for (int g = 0; g < 16; ++g) {
-                        const int j = jl0 + g;
-                        const float sc = (j < P.k) ? fmaf(-2.f, __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
-                        const bool lt0 = sc < v0, lt1 = sc < v1;
-                        const float m0 = fmaxf(v0, sc), m1 = fmaxf(v1, sc);
-                        v2 = fminf(v2, m1);
-                        v1 = fminf(v1, m0);
-                        v0 = fminf(v0, sc);
-                        i1 = lt0 ? i0 : (lt1 ? j : i1);
-                        i0 = lt0 ? j : i0;
-                    }
+                    for (int g = 0; g < 16; ++g)
+                        sc[g] = (jl0 + g < P.k) ? fmaf(-2.f, __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
+                    band.group(sc, jl0);
                 };
                 uint32_t ra[16], rb[16];
                 tmem_ld16(tbase, ra);
@@ -997,7 +1222,7 @@ static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra
     p.b_bytes = (uint32_t)p.bn * 128;
     p.stage_bytes = (x3 ? 2 : 1) * p.a_bytes + (x3 ? 2 : 1) * p.b_bytes;
     p.tx_bytes = p.a_bytes + (x3 ? 2 : 1) * p.b_bytes;
-    p.stages = (int)std::min<int64_t>(MAX_STAGES, (SMEM_BUDGET - extra_smem) / p.stage_bytes);
+    p.stages = (int)std::min<int64_t>(MAX_STAGES, (MAX_DYN_SMEM - 2048 - extra_smem) / p.stage_bytes);
     p.tmem_cols = (2 * p.bn <= 256) ? 256 : 512;
     p.smem = (size_t)p.stages * p.stage_bytes + 1024 + 1024 + extra_smem;
     return p;
@@ -1009,7 +1234,7 @@ static int launch(gbkm_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const
     auto kern = k_tc<FORM, EPI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 smem attribute");
-    const int threads = (FORM == F_TF32X3) ? 384 : 256;
+    const int threads = tc_threads<FORM, EPI>();
     const int grid = (int)std::min<int64_t>(c->sm_count, args.m_tiles);
     kern<<<grid, threads, p.smem, c->stream>>>(A, B, B2, args);
     GBKM_LAUNCHED(c);
@@ -1029,10 +1254,10 @@ bool tc_assign_supported(int dtype, int64_t d, int64_t k) {
 
 int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscales, const float *X,
                      const float *xnorm, int64_t n, int64_t d, const CenterPrep &cp, int64_t k, int64_t k_pad,
-                     float err_rel, float err_abs, const AssignOut &o) {
+                     float err_rel, float err_abs, const AssignOut &o, const int32_t *n_dev) {
     using namespace tc;
     const int form = (dtype == GBKM_BF16) ? F_BF16 : (dtype == GBKM_FP8E4M3 ? F_FP8 : F_TF32X3);
-    const Plan p = plan(form, d, k_pad, c->bn_cap > 0 ? c->bn_cap : 256);
+    const Plan p = plan(form, d, k_pad, c->bn_cap > 0 ? c->bn_cap : 256, ARGMIN_EXTRA_SMEM);
     const CUtensorMapDataType dt = (form == F_BF16)  ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                    : (form == F_FP8) ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -1050,6 +1275,7 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
     a.m_tiles = (int)ceil_div(n, BM);
     a.a_bytes = p.a_bytes, a.b_bytes = p.b_bytes, a.stage_bytes = p.stage_bytes, a.tx_bytes = p.tx_bytes;
     a.idesc = make_idesc(form, BM, p.bn);
+    a.n_dev = n_dev;
     a.cnorm = cp.cnorm, a.cscale = cp.cscale, a.xscale = Xscales, a.xnorm = xnorm, a.cmax = cp.cmax;
     a.err_rel = err_rel, a.err_abs = err_abs;
     a.labels = o.labels, a.min_d2 = o.min_d2, a.flag_list = o.flag_list, a.cand = o.cand, a.flag_count = o.flag_count;
@@ -1141,7 +1367,7 @@ int launch_assign_tc_batched(gbkm_ctx *c, int dtype, const void *maps, const BPr
     const uint32_t a_bytes = BM * 128, b_bytes = (uint32_t)bn_max * 128;
     const uint32_t stage_bytes = (x3 ? 2 : 1) * a_bytes + (x3 ? 2 : 1) * b_bytes;
     const int stages = (int)std::min<int64_t>(MAX_STAGES, SMEM_BUDGET / stage_bytes);
-    const size_t smem = (size_t)stages * stage_bytes + 2048;
+    const size_t smem = (size_t)stages * stage_bytes + 2048 + BCAND_MAX * 128 * 8;
     const int threads = x3 ? 384 : 256;
     const int grid = (int)std::min<int64_t>(c->sm_count, ntiles);
     cudaError_t e;
@@ -1175,7 +1401,7 @@ int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, in
         return set_error(c, GBKM_EUNSUPPORTED, "gemm: shape unsupported by the tcgen05 GEMM");
     const bool topk = top_idx != nullptr;
     if (topk && (topm < 1 || topm > TOPBUF / 2)) return set_error(c, GBKM_EINVAL, "gemm: topm must be in [1, 32]");
-    const int extra = topk ? TOPBUF * 128 * 8 : 0;
+    const int extra = topk ? TROW * 128 * 8 : 0;
     const Plan p = plan(F_BF16, K, N, 256, extra);
     CUtensorMap tA, tB;
     if (!make_tmap(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, (uint64_t)K, (uint64_t)M, 2, BM) ||

@@ -90,3 +90,28 @@ def test_autotune_returns_a_candidate(gb):
     bn = gb.kmeans_autotune(256, 400, "bf16")
     assert bn in (64, 128, 256)
     assert gb.kmeans_autotune(256, 400, "bf16") == bn  # cached
+
+
+def test_batch_replay_reproduces_the_run_and_is_invalidated_by_other_calls(gb):
+    """Replaying the recorded graph gives bit-identical outputs (the run is deterministic); a call
+    that reuses the context's workspace invalidates the graph (clean error, nothing launched)."""
+    seeds, iters = 2, 3
+    ctx = gb.Context(0)
+    probs, _ = _problems(seeds, salt=11)
+    gb.kmeans_batch_run(probs, seeds, iters, compute="bf16", graph=True, ctx=ctx)
+    ctx.sync()
+    first = [(p["C_out"].clone(), p["labels_out"].clone(), p["cost_out"].clone()) for p in probs]
+    for p in probs:
+        p["C_out"].zero_()
+        p["labels_out"].fill_(-1)
+        p["cost_out"].zero_()
+    gb.kmeans_batch_replay(ctx=ctx)
+    ctx.sync()
+    for p, (C, L, c) in zip(probs, first):
+        assert torch.equal(p["C_out"], C) and torch.equal(p["labels_out"], L) and torch.equal(p["cost_out"], c)
+    X = probs[0]["X"]
+    gb.kmeans_assign(X, probs[0]["C_out"][0].contiguous(), compute="f32", ctx=ctx)
+    with pytest.raises(gb.GbkmError):
+        gb.kmeans_batch_replay(ctx=ctx)
+    ctx.sync()
+    ctx.close()

@@ -118,3 +118,23 @@ def test_tc_project(gb, orc, xt, n, d, r):
     # per element |sum x_t v_t| error <= (2u + d 2^-22) sum |x_t v_t| <= (2u + d 2^-22) ||x|| (||v_q|| = 1)
     u = 2.0 ** -8 if xt == "bf16" else 2.0 ** -10
     assert np.all(np.abs(Y - Yr) <= (2 * u + d * 2.0 ** -22) * xn + 1e-5)
+
+
+@pytest.mark.parametrize("form", ["bf16", "f32", "fp8"])
+def test_tc_band_across_chunks_and_overflow(gb, orc, form):
+    """Near-tie bands whose members sit in different 256-center chunks, and a band larger than the
+    candidate list (12 identical centers, so the recheck scans every center): exact labels."""
+    rng = np.random.default_rng(11)
+    d, k = 64, 1000
+    C = rng.uniform(-10, 10, size=(k, d)).astype(np.float32)
+    C[700] = C[3] + np.float32(1e-3)
+    C[999] = C[3] - np.float32(1e-3)
+    C[900:912] = C[500]
+    X = np.concatenate([C[3] + rng.normal(size=(200, d)).astype(np.float32) * 0.5,
+                        C[500] + rng.normal(size=(200, d)).astype(np.float32) * 0.5,
+                        rng.uniform(-10, 10, size=(300, d)).astype(np.float32)]).astype(np.float32)
+    lab, _, nre = _assign(gb, X, C, form)
+    assert nre >= 400
+    assert_labels_match(orc, X, C.astype(np.float64), lab)
+    # the 12 identical centers tie exactly: the lowest index wins
+    assert np.all(lab[200:400] == 500)
