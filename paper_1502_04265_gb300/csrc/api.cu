@@ -333,10 +333,9 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
            o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_cd = p.take<int32_t>(n * gbkm::CAND_STRIDE),
            o_fc = p.take<int32_t>(1);
     size_t o_el = p.take<int32_t>(ne), o_ec = p.take<int32_t>(esc ? 2 : 0), o_xe = p.take<float>(ne * d),
-           o_xne = p.take<float>(ne), o_le = p.take<int32_t>(ne), o_mde = p.take<float>(min_d2 ? ne : 0),
-           o_cn2 = p.take<float>(esc ? k_pad : 0), o_cm2 = p.take<unsigned>(esc ? 1 : 0),
-           o_cop2 = p.take<float>(esc ? k_pad * d : 0), o_clo2 = p.take<float>(esc ? k_pad * d : 0),
-           o_fl2 = p.take<int32_t>(ne), o_cd2 = p.take<int32_t>(ne * gbkm::CAND_STRIDE);
+           o_xne = p.take<float>(ne), o_ehi = p.take<float>(esc ? k_pad * d : 0),
+           o_elo = p.take<float>(esc ? k_pad * d : 0), o_fl2 = p.take<int32_t>(ne),
+           o_cd2 = p.take<int32_t>(ne * gbkm::CAND_STRIDE);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
@@ -348,6 +347,8 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     cp.cop = use_tc ? ws_at<void>(ws, o_cop) : nullptr;
     cp.cop_lo = (use_tc && o.compute == GBKM_F32) ? ws_at<void>(ws, o_clo) : nullptr;
     cp.cscale = ws_at<float>(ws, o_cs);
+    cp.esc_hi = esc ? ws_at<float>(ws, o_ehi) : nullptr;
+    cp.esc_lo = esc ? ws_at<float>(ws, o_elo) : nullptr;
     prof_begin(c, "center_prep");
     rc = gbkm::launch_center_prep(c, C, k, d, o.compute, k_pad, cp);
     prof_end(c);
@@ -371,36 +372,36 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     prof_end(c);
     if (rc != GBKM_OK) return rc;
     if (o.recheck && esc) {
-        int32_t *elist = ws_at<int32_t>(ws, o_el), *ecount = ws_at<int32_t>(ws, o_ec);
-        e = cudaMemsetAsync(ecount, 0, 2 * sizeof(int32_t), c->stream);
+        gbkm::Escalation es;
+        es.list = ws_at<int32_t>(ws, o_el);
+        es.count = ws_at<int32_t>(ws, o_ec);
+        es.Xe = ws_at<float>(ws, o_xe);
+        es.xne = ws_at<float>(ws, o_xne);
+        es.xnorm = xn;
+        e = cudaMemsetAsync(es.count, 0, 2 * sizeof(int32_t), c->stream);
         if (e != cudaSuccess) return cuda_check(c, e, "memset escalation count");
         prof_begin(c, "recheck");
-        rc = gbkm::launch_recheck(c, X, n, d, C, k, out, n_rechecked, elist, ecount);
+        rc = gbkm::launch_recheck(c, X, n, d, C, k, out, n_rechecked, &es);
         prof_end(c);
         if (rc != GBKM_OK) return rc;
+        // the escalated rows: 3xTF32 assignment of the gathered block (row count on the device),
+        // then the exact recheck of its own near-ties; results go straight to the rows' slots
         prof_begin(c, "escalate");
-        gbkm::CenterPrep cp2;
-        cp2.cnorm = ws_at<float>(ws, o_cn2);
-        cp2.cmax = ws_at<unsigned>(ws, o_cm2);
-        cp2.cop = ws_at<void>(ws, o_cop2);
-        cp2.cop_lo = ws_at<void>(ws, o_clo2);
+        gbkm::CenterPrep cp2 = cp;
+        cp2.cop = cp.esc_hi;
+        cp2.cop_lo = cp.esc_lo;
         cp2.cscale = nullptr;
-        float *Xe = ws_at<float>(ws, o_xe), *xne = ws_at<float>(ws, o_xne), *mde = min_d2 ? ws_at<float>(ws, o_mde) : nullptr;
-        int32_t *le = ws_at<int32_t>(ws, o_le);
         gbkm::AssignOut out2;
-        out2.labels = le;
-        out2.min_d2 = mde;
+        out2.labels = labels;
+        out2.min_d2 = min_d2;
         out2.flag_list = ws_at<int32_t>(ws, o_fl2);
         out2.cand = ws_at<int32_t>(ws, o_cd2);
-        out2.flag_count = ecount + 1;
+        out2.flag_count = es.count + 1;
         float er2, ea2;
         gbkm::score_error_coeffs(GBKM_F32, 1, d, er2, ea2);
-        if ((rc = gbkm::launch_center_prep(c, C, k, d, GBKM_F32, k_pad, cp2)) == GBKM_OK &&
-            (rc = gbkm::launch_gather_rows(c, X, xn, n, d, elist, ecount, Xe, xne)) == GBKM_OK &&
-            (rc = gbkm::launch_assign_tc(c, GBKM_F32, Xe, nullptr, Xe, xne, n, d, cp2, k, k_pad, er2, ea2, out2,
-                                         ecount)) == GBKM_OK &&
-            (rc = gbkm::launch_recheck(c, Xe, n, d, C, k, out2, nullptr)) == GBKM_OK)
-            rc = gbkm::launch_scatter_rows(c, le, mde, elist, ecount, n, labels, min_d2);
+        if ((rc = gbkm::launch_assign_tc(c, GBKM_F32, es.Xe, nullptr, es.Xe, es.xne, n, d, cp2, k, k_pad, er2, ea2,
+                                         out2, es.count, es.list)) == GBKM_OK)
+            rc = gbkm::launch_recheck(c, es.Xe, n, d, C, k, out2, nullptr, nullptr, es.list);
         prof_end(c);
         return rc;
     }

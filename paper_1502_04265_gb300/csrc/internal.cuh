@@ -205,6 +205,8 @@ struct CenterPrep {
     void *cop;          // operand copy (k_pad x d) or null
     void *cop_lo;       // tf32 low part or null
     float *cscale;      // fp8 per-row scales or null
+    float *esc_hi;      // 3xTF32 split of the centers for the escalation pass (k_pad x d), or null
+    float *esc_lo;
 };
 int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dtype,
                        int64_t k_pad, const CenterPrep &cp);
@@ -225,16 +227,21 @@ int launch_assign_simt(gbkm_ctx *c, const float *X, const float *xnorm, int64_t 
 // Out[M x N] = A[M x K] B^T with B[nn * sbn + kk * sbk]
 int launch_gemm_simt_strided(gbkm_ctx *c, const float *A, const float *B, int64_t M, int64_t N,
                              int64_t K, int64_t sbn, int64_t sbk, float *Out);
-// exact re-resolution of the flagged rows; with esc_list, a row whose band is not listed (count
-// <= 0) is appended there (esc_count) for the next precision instead of being scanned over all k
+// Escalation of flagged rows whose band is not listed (count <= 0): the recheck appends each to
+// list (count) and copies the row and its norm into the dense block Xe / xne, for the next
+// precision's pass over that block, instead of scanning all k centers.
+struct Escalation {
+    int32_t *list;
+    int32_t *count;
+    float *Xe;
+    float *xne;
+    const float *xnorm;
+};
+// exact re-resolution of the flagged rows (X rows; labels / min_d2 of row i go to index
+// row_map[i] when row_map is set)
 int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
-                   const AssignOut &o, int64_t *n_rechecked, int32_t *esc_list = nullptr,
-                   int32_t *esc_count = nullptr);
-// rows of an escalation list gathered into a dense block (and their norms), labels scattered back
-int launch_gather_rows(gbkm_ctx *c, const float *X, const float *xnorm, int64_t n, int64_t d,
-                       const int32_t *list, const int32_t *count, float *Xe, float *xne);
-int launch_scatter_rows(gbkm_ctx *c, const int32_t *le, const float *mde, const int32_t *list, const int32_t *count,
-                        int64_t n, int32_t *labels, float *min_d2);
+                   const AssignOut &o, int64_t *n_rechecked, const Escalation *esc = nullptr,
+                   const int32_t *row_map = nullptr);
 
 // device-wide exclusive scan of L int32 (totals < 2^31); bsum holds ceil(L / 4096) ints
 void scan_excl(cudaStream_t st, const int32_t *in, int64_t L, int32_t *bsum, int32_t *out);
@@ -249,7 +256,8 @@ bool tc_assign_supported(int dtype, int64_t d, int64_t k);
 int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscales,
                      const float *X, const float *xnorm, int64_t n, int64_t d,
                      const CenterPrep &cp, int64_t k, int64_t k_pad, float err_rel,
-                     float err_abs, const AssignOut &o, const int32_t *n_dev = nullptr);
+                     float err_abs, const AssignOut &o, const int32_t *n_dev = nullptr,
+                     const int32_t *row_map = nullptr);
 int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                         const float *bias, int act, int out_bf16, void *Y, int64_t ldy, float *Ypre, int64_t ldpre,
                         int32_t *top_idx, float *top_val, int topm);

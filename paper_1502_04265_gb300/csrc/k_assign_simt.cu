@@ -312,8 +312,8 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
                                                  const int32_t *__restrict__ cand,
                                                  const int32_t *__restrict__ count, int64_t n,
                                                  int32_t *__restrict__ labels, float *__restrict__ min_d2,
-                                                 int64_t *n_rechecked, int *status, int32_t *__restrict__ esc_list,
-                                                 int32_t *__restrict__ esc_count) {
+                                                 int64_t *n_rechecked, int *status, Escalation esc,
+                                                 const int32_t *__restrict__ row_map) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
@@ -332,9 +332,17 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
         int arg = -1;
         const int32_t *cf = cand + f * CAND_STRIDE;
         const int nc = cf[0];
-        if (esc_list && !(nc > 0 && nc <= CAND_MAX)) {
+        if (esc.list && !(nc > 0 && nc <= CAND_MAX)) {
             // the band is not listed: the row goes to the next precision's pass
-            if (lane == 0) esc_list[atomicAdd(esc_count, 1)] = (int32_t)row;
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(esc.count, 1);
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (lane == 0) {
+                esc.list[slot] = (int32_t)row;
+                esc.xne[slot] = esc.xnorm[row];
+            }
+            float *y = esc.Xe + (int64_t)slot * d;
+            for (int64_t t = lane; t < d; t += 32) y[t] = x[t];
             continue;
         }
         const bool cached = vec && d <= 1024;
@@ -372,67 +380,22 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
             }
         }
         if (lane == 0) {
-            labels[row] = arg;
-            if (min_d2) min_d2[row] = best;
+            const int64_t dst = row_map ? (int64_t)row_map[row] : row;
+            labels[dst] = arg;
+            if (min_d2) min_d2[dst] = best;
         }
     }
 }
 
 int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
-                   const AssignOut &o, int64_t *n_rechecked, int32_t *esc_list, int32_t *esc_count) {
+                   const AssignOut &o, int64_t *n_rechecked, const Escalation *esc, const int32_t *row_map) {
     unsigned blocks = (unsigned)c->sm_count * 4;
+    Escalation e{};
+    if (esc) e = *esc;
     k_recheck<<<blocks, 256, 0, c->stream>>>(X, d, C, k, o.flag_list, o.cand, o.flag_count, n, o.labels,
-                                             o.min_d2, n_rechecked, c->status, esc_list, esc_count);
+                                             o.min_d2, n_rechecked, c->status, e, row_map);
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "recheck launch");
-}
-
-// one warp per listed row (grid-stride over the device count): row and norm into the dense block
-__global__ void __launch_bounds__(256) k_gather_esc(const float *__restrict__ X, const float *__restrict__ xnorm,
-                                                    int64_t n, int64_t d, const int32_t *__restrict__ list,
-                                                    const int32_t *__restrict__ count, float *__restrict__ Xe,
-                                                    float *__restrict__ xne, int *status) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
-    const int64_t cnt = min((int64_t)*count, n);
-    for (int64_t e = warp; e < cnt; e += nwarps) {
-        const int64_t row = list[e];
-        if (row < 0 || row >= n) {
-            if (lane == 0) status_raise(status, ST_BOUNDS);
-            continue;
-        }
-        const float *x = X + row * d;
-        float *y = Xe + e * d;
-        for (int64_t t = lane; t < d; t += 32) y[t] = x[t];
-        if (lane == 0) xne[e] = xnorm[row];
-    }
-}
-
-__global__ void k_scatter_esc(const int32_t *__restrict__ le, const float *__restrict__ mde,
-                              const int32_t *__restrict__ list, const int32_t *__restrict__ count, int64_t n,
-                              int32_t *__restrict__ labels, float *__restrict__ min_d2) {
-    const int64_t cnt = min((int64_t)*count, n);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = list[e];
-        if (row < 0 || row >= n) continue;
-        labels[row] = le[e];
-        if (min_d2) min_d2[row] = mde[e];
-    }
-}
-
-int launch_gather_rows(gbkm_ctx *c, const float *X, const float *xnorm, int64_t n, int64_t d, const int32_t *list,
-                       const int32_t *count, float *Xe, float *xne) {
-    k_gather_esc<<<(unsigned)c->sm_count * 8, 256, 0, c->stream>>>(X, xnorm, n, d, list, count, Xe, xne, c->status);
-    GBKM_LAUNCHED(c);
-    return cuda_check(c, cudaGetLastError(), "gather launch");
-}
-
-int launch_scatter_rows(gbkm_ctx *c, const int32_t *le, const float *mde, const int32_t *list, const int32_t *count,
-                        int64_t n, int32_t *labels, float *min_d2) {
-    k_scatter_esc<<<(unsigned)c->sm_count * 2, 256, 0, c->stream>>>(le, mde, list, count, n, labels, min_d2);
-    GBKM_LAUNCHED(c);
-    return cuda_check(c, cudaGetLastError(), "scatter launch");
 }
 
 }  // namespace gbkm

@@ -141,6 +141,10 @@ __global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C
                 ((float *)cp.cop)[j * d + t] = 0.f;
                 ((float *)cp.cop_lo)[j * d + t] = 0.f;
             }
+            if (cp.esc_hi) {
+                cp.esc_hi[j * d + t] = 0.f;
+                cp.esc_lo[j * d + t] = 0.f;
+            }
         }
         if (threadIdx.x == 0) {
             cp.cnorm[j] = __int_as_float(0x7f800000);
@@ -177,6 +181,15 @@ __global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C
         amax_s[0] = am;
     }
     __syncthreads();
+    if (cp.esc_hi) {
+        // the 3xTF32 split as well, for rows escalated from a low-precision form
+        for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+            const float v = c[t];
+            const float hi = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+            cp.esc_hi[j * d + t] = hi;
+            cp.esc_lo[j * d + t] = __uint_as_float(__float_as_uint(__fsub_rn(v, hi)) & 0xffffe000u);
+        }
+    }
     if (!cp.cop) return;
     if (dtype == GBKM_BF16) {
         for (int64_t t = threadIdx.x; t < d; t += blockDim.x)

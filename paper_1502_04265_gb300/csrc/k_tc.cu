@@ -39,6 +39,7 @@ constexpr int ARGMIN_EXTRA_SMEM = 2 * 2 * CAND_MAX * 128 * 4 + 128 * 16 + 8 * 8;
 struct Args {
     int64_t n, d, k, k_pad;
     const int32_t *n_dev;  // if set, the rows are the first min(n, *n_dev) (a count on the device)
+    const int32_t *row_map;  // if set, outputs of row i go to index row_map[i] (argmin epilogue)
     int n_chunks, bn, kb, stages, tmem_cols, m_tiles;
     uint32_t a_bytes, b_bytes, stage_bytes, tx_bytes;
     uint32_t idesc;
@@ -87,17 +88,19 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 // dmin > v0 + E2.  A group of W scores costs a minimum tree unless its minimum can enter the band.
 template <int CAP>
 struct Band {
-    float v0, t, E2, dmin;
+    float v0, t, E2, dmin, pt;  // pt: the threshold at the last prune (a full list is pruned again
+                                // only after the threshold has come down)
     int i0, cnt;
     float *lv;
     int32_t *li;
     __device__ __forceinline__ void reset(float e2) {
-        v0 = t = dmin = __int_as_float(0x7f800000);
+        v0 = t = dmin = pt = __int_as_float(0x7f800000);
         E2 = e2;
         i0 = 0;
         cnt = 0;
     }
     __device__ __forceinline__ void prune() {
+        pt = t;
         int w = 0;
         for (int q = 0; q < cnt; ++q) {
             const float vv = lv[q * 128];
@@ -112,7 +115,7 @@ struct Band {
     }
     __device__ __forceinline__ void list_push(float sc, int j) {
         if (cnt == CAP) {
-            prune();
+            if (t < pt) prune();
             if (cnt == CAP) {
                 dmin = fminf(dmin, sc);
                 return;
@@ -379,6 +382,11 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
+    {
+        // a CTA with no tile (the row count may come from the device) leaves before allocating
+        const int64_t nr = a.n_dev ? min(a.n, (int64_t)max(0, *a.n_dev)) : a.n;
+        if ((int64_t)blockIdx.x * BM >= nr) return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
@@ -812,8 +820,9 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                             const int bc = over ? -1 : cnt;
                             const bool flag = valid && bc != 1;
                             if (valid) {
-                                a.labels[row] = ib;
-                                if (a.min_d2) a.min_d2[row] = fmaxf(0.f, xn + v);
+                                const int64_t dst = a.row_map ? (int64_t)a.row_map[row] : row;
+                                a.labels[dst] = ib;
+                                if (a.min_d2) a.min_d2[dst] = fmaxf(0.f, xn + v);
                             }
                             if (a.flag_list) {
                                 const unsigned m = __ballot_sync(0xffffffffu, flag);
@@ -1254,7 +1263,7 @@ bool tc_assign_supported(int dtype, int64_t d, int64_t k) {
 
 int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscales, const float *X,
                      const float *xnorm, int64_t n, int64_t d, const CenterPrep &cp, int64_t k, int64_t k_pad,
-                     float err_rel, float err_abs, const AssignOut &o, const int32_t *n_dev) {
+                     float err_rel, float err_abs, const AssignOut &o, const int32_t *n_dev, const int32_t *row_map) {
     using namespace tc;
     const int form = (dtype == GBKM_BF16) ? F_BF16 : (dtype == GBKM_FP8E4M3 ? F_FP8 : F_TF32X3);
     const Plan p = plan(form, d, k_pad, c->bn_cap > 0 ? c->bn_cap : 256, ARGMIN_EXTRA_SMEM);
@@ -1276,6 +1285,7 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
     a.a_bytes = p.a_bytes, a.b_bytes = p.b_bytes, a.stage_bytes = p.stage_bytes, a.tx_bytes = p.tx_bytes;
     a.idesc = make_idesc(form, BM, p.bn);
     a.n_dev = n_dev;
+    a.row_map = row_map;
     a.cnorm = cp.cnorm, a.cscale = cp.cscale, a.xscale = Xscales, a.xnorm = xnorm, a.cmax = cp.cmax;
     a.err_rel = err_rel, a.err_abs = err_abs;
     a.labels = o.labels, a.min_d2 = o.min_d2, a.flag_list = o.flag_list, a.cand = o.cand, a.flag_count = o.flag_count;
