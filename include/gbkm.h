@@ -67,7 +67,9 @@ typedef struct {
     int32_t compute;    /* gbkm_dtype of the distance-GEMM operands */
     int32_t engine;     /* gbkm_engine */
     int32_t recheck;    /* 1 (default): re-resolve certified near-ties exactly from FP32 data */
-    int32_t reserved;
+    int32_t center_terms; /* GBKM_BF16 only: 2 = centers as two BF16 terms (hi + lo, a second MMA),
+                             which shrinks the near-tie bound where x's own rounding is small next
+                             to the distances; 0 or 1 (default) = one term */
 } gbkm_assign_opts;
 
 /* ------------------------------------------------------------------ context */
@@ -145,21 +147,28 @@ int kmeans_seed_pp(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const fl
  * ||x_i - c_j||^2, ties to the lowest j.  Scores ||c_j||^2 - 2 x_i . c_j come
  * from a distance GEMM in the operand format opts->compute:
  *   GBKM_F32:     Xop == X (FP32); SIMT FFMA or tcgen05 3xTF32 (split hi/lo);
- *   GBKM_BF16:    Xop is the bfloat16 copy of X; tcgen05 kind::f16;
+ *   GBKM_BF16:    Xop is the bfloat16 copy of X; tcgen05 kind::f16; with
+ *                 opts->center_terms == 2 the centers enter as two BF16 terms (hi +
+ *                 lo, two MMAs): the rounding of x is then the main error, and the
+ *                 bound on a score difference grows with the two centers' distances
+ *                 to x instead of with max ||c||;
  *   GBKM_FP8E4M3: Xop is the E4M3 copy with per-row scales (d <= 128 only);
  *                 tcgen05 kind::f8f6f4, scales applied in the epilogue.
- * The fused epilogue keeps the best and second-best score per row.  A row is a
- * certified near-tie when the computed gap is within the worst-case error
- * bound of the operand format; such rows (opts->recheck != 0) are re-resolved
- * over all k centers from the FP32 data with error-free transformations, so
- * every label equals the exact nearest center except where two centers lie
- * within ~1e-12 relative of each other.
+ * The fused epilogue keeps, per point, the best score and every center whose score
+ * lies within the worst-case error bound of a score difference from it (the
+ * certified band).  A point whose band holds more than its best center is a
+ * near-tie; with opts->recheck != 0 it is re-resolved from the FP32 data: the band's
+ * centers (up to 8) by direct FP32 differences, or, when the band cannot be listed,
+ * by a 3xTF32 pass over the gathered points (BF16 / FP8 forms; its own near-ties
+ * then take the direct recheck, scanning all k if needed).  Every label equals the
+ * exact nearest center except where two centers' distances agree to within the
+ * direct recheck's error ((ceil(d/128) + 10) 2^-24 relative).
  *   Xop_scales: per-row scales of an FP8 Xop (n x ceil(d/128)), else NULL.
  *   X: n x d FP32 (always required: recheck and bounds).
  *   xnorm: ||x_i||^2 FP32 from kmeans_row_norms, or NULL (then computed here).
  *   C: k x d FP32.  labels: n int32.  min_d2: n FP32 or NULL, the squared
- *   distance to the chosen center (expanded form, clamped at 0; exact form on
- *   rechecked rows).  n_rechecked: 1 int64 or NULL (device), rows rechecked.
+ *   distance to the chosen center (expanded form, clamped at 0; direct form on
+ *   rechecked rows).  n_rechecked: 1 int64 or NULL (device), near-tie rows.
  *   opts: host pointer or NULL (F32, AUTO, recheck on). */
 int kmeans_assign(gbkm_ctx *ctx, const void *Xop, const float *Xop_scales, const float *X,
                   const float *xnorm, int64_t n, int64_t d, const float *C, int64_t k,

@@ -45,7 +45,7 @@ class MLP(ct.Structure):
 
 class AssignOpts(ct.Structure):
     _fields_ = [("compute", ct.c_int32), ("engine", ct.c_int32), ("recheck", ct.c_int32),
-                ("reserved", ct.c_int32)]
+                ("center_terms", ct.c_int32)]
 
 
 _vp, _i64, _i32 = ct.c_void_p, ct.c_int64, ct.c_int32
@@ -288,7 +288,7 @@ def kmeans_seed_pp(X, k, u, w=None, idx_out=None, C_out=None, ctx=None):
 
 # ------------------------------------------------------------------ A4 + A5
 def kmeans_assign(X, C, Xop=None, Xop_scales=None, xnorm=None, compute="f32", engine="auto",
-                  recheck=True, labels=None, min_d2=None, n_rechecked=None, ctx=None):
+                  recheck=True, labels=None, min_d2=None, n_rechecked=None, center_terms=1, ctx=None):
     _req(X, torch.float32, name="X")
     n, d = X.shape
     _req(C, torch.float32, name="C")
@@ -302,7 +302,7 @@ def kmeans_assign(X, C, Xop=None, Xop_scales=None, xnorm=None, compute="f32", en
     if xnorm is not None:
         _req(xnorm, torch.float32, (n,), "xnorm")
     labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=X.device)
-    opts = AssignOpts(DTYPES[compute], ENGINES[engine], 1 if recheck else 0, 0)
+    opts = AssignOpts(DTYPES[compute], ENGINES[engine], 1 if recheck else 0, int(center_terms))
     c = _ctx(ctx, X)
     c.check(load().kmeans_assign(c.handle, _ptr(Xop), _ptr(Xop_scales), _ptr(X), _ptr(xnorm), n, d,
                                  _ptr(C), k, ct.byref(opts), _ptr(labels), _ptr(min_d2),

@@ -295,7 +295,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
                   const float *xnorm, int64_t n, int64_t d, const float *C, int64_t k,
                   const gbkm_assign_opts *opts, int32_t *labels, float *min_d2, int64_t *n_rechecked) {
     if (!c) return GBKM_EINVAL;
-    gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 0};
+    gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 1};
     if (opts) o = *opts;
     if (n < 1 || d < 1 || k < 1 || k > 65536 || !X || !C || !labels)
         return set_error(c, GBKM_EINVAL, "assign: bad arguments");
@@ -320,6 +320,9 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     }
     DeviceGuard g(c->device);
     const int64_t k_pad = use_tc ? ceil_div(k, 16) * 16 : k;
+    // BF16 centers as two BF16 terms (hi + lo) on request: the near-tie bound then grows with the
+    // point's distances to the two centers instead of with max ||c||
+    const bool split = use_tc && o.compute == GBKM_BF16 && o.center_terms == 2;
     const size_t esz = o.compute == GBKM_BF16 ? 2 : (o.compute == GBKM_FP8E4M3 ? 1 : 4);
     // escalation: rows of a low-precision form whose near-tie band is too wide to list go through the
     // 3xTF32 form (a far smaller error bound), then through the exact recheck
@@ -329,7 +332,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     WsPlan p;
     size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(1),
            o_cop = p.take<char>(use_tc ? k_pad * d * esz : 0),
-           o_clo = p.take<float>(use_tc && o.compute == GBKM_F32 ? k_pad * d : 0),
+           o_clo = p.take<float>(use_tc && (o.compute == GBKM_F32 || split) ? k_pad * d : 0),
            o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_cd = p.take<int32_t>(n * gbkm::CAND_STRIDE),
            o_fc = p.take<int32_t>(1);
     size_t o_el = p.take<int32_t>(ne), o_ec = p.take<int32_t>(esc ? 2 : 0), o_xe = p.take<float>(ne * d),
@@ -345,7 +348,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     cp.cnorm = ws_at<float>(ws, o_cn);
     cp.cmax = ws_at<unsigned>(ws, o_cm);
     cp.cop = use_tc ? ws_at<void>(ws, o_cop) : nullptr;
-    cp.cop_lo = (use_tc && o.compute == GBKM_F32) ? ws_at<void>(ws, o_clo) : nullptr;
+    cp.cop_lo = (use_tc && (o.compute == GBKM_F32 || split)) ? ws_at<void>(ws, o_clo) : nullptr;
     cp.cscale = ws_at<float>(ws, o_cs);
     cp.esc_hi = esc ? ws_at<float>(ws, o_ehi) : nullptr;
     cp.esc_lo = esc ? ws_at<float>(ws, o_elo) : nullptr;
@@ -560,7 +563,7 @@ int kmeans_cost(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *
         if (labels) cudaFreeAsync(labels, c->stream);
         return set_error(c, GBKM_ENOMEM, "cost: scratch allocation failed");
     }
-    gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 0};
+    gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 1};
     int rc = kmeans_assign(c, X, nullptr, X, nullptr, n, d, C, k, &o, labels, nullptr, nullptr);
     if (rc == GBKM_OK) rc = kmeans_update(c, X, n, d, w, labels, k, C, Cn, nullptr, cost, nullptr, nullptr);
     cudaFreeAsync(labels, c->stream);

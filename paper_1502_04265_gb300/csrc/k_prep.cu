@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C
     if (j >= k) {
         for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
             if (dtype == GBKM_BF16 && cp.cop) ((__nv_bfloat16 *)cp.cop)[j * d + t] = __float2bfloat16_rn(0.f);
+            if (dtype == GBKM_BF16 && cp.cop_lo) ((__nv_bfloat16 *)cp.cop_lo)[j * d + t] = __float2bfloat16_rn(0.f);
             if (dtype == GBKM_FP8E4M3 && cp.cop) ((uint8_t *)cp.cop)[j * d + t] = 0;
             if (dtype == GBKM_F32 && cp.cop) {
                 ((float *)cp.cop)[j * d + t] = 0.f;
@@ -192,8 +193,13 @@ __global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C
     }
     if (!cp.cop) return;
     if (dtype == GBKM_BF16) {
-        for (int64_t t = threadIdx.x; t < d; t += blockDim.x)
-            ((__nv_bfloat16 *)cp.cop)[j * d + t] = __float2bfloat16_rn(c[t]);
+        // with a low part: c = hi + lo + O(2^-16 |c|), hi = bf16(c), lo = bf16(c - hi)
+        for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(c[t]);
+            ((__nv_bfloat16 *)cp.cop)[j * d + t] = hi;
+            if (cp.cop_lo)
+                ((__nv_bfloat16 *)cp.cop_lo)[j * d + t] = __float2bfloat16_rn(__fsub_rn(c[t], __bfloat162float(hi)));
+        }
     } else if (dtype == GBKM_FP8E4M3) {
         const int e = e4m3_scale_exp(amax_s[0]);
         if (threadIdx.x == 0) cp.cscale[j] = ldexpf(1.f, e);

@@ -29,7 +29,8 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
 constexpr int SMEM_BUDGET = 200 * 1024;      // stage ring of the batched kernel
 constexpr int MAX_DYN_SMEM = 227 * 1024;     // dynamic shared memory a CTA may use
 
-enum Form : int { F_BF16 = 0, F_TF32X3 = 1, F_FP8 = 2, F_TF32 = 3 };
+// F_BF16X2: BF16 points against centers split into two BF16 terms (hi + lo), two MMAs per step
+enum Form : int { F_BF16 = 0, F_TF32X3 = 1, F_FP8 = 2, F_TF32 = 3, F_BF16X2 = 4 };
 enum Epi : int { E_ARGMIN = 0, E_STORE = 1, E_TOPM = 2 };
 constexpr int TOPBUF = 64;  // per-row candidate buffer of the top-m epilogue (shared memory)
 constexpr int TROW = TOPBUF + 1;  // its row stride in floats
@@ -47,6 +48,10 @@ struct Args {
     const float *cnorm, *cscale, *xscale, *xnorm;
     const unsigned *cmax;
     float err_rel, err_abs;
+    // two-term BF16 centers: band width A (D_j + D_0) + Bc with A = pair_a ||x||,
+    // Bc = pair_rel ||x|| cmax + pair_abs cmax^2, D = sqrt(XE + s), XE = ||x||^2 + single_rel ||x||
+    // cmax + single_abs cmax^2 (pair_a == 0: the constant width 2 (err_rel ||x|| cmax + err_abs cmax^2))
+    float pair_a, pair_rel, pair_abs, single_rel, single_abs;
     int32_t *labels;
     float *min_d2;
     int32_t *flag_list;
@@ -80,24 +85,40 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 
 // The certified band of one point, tracked by its thread over the score stream: the best score
 // v0 with its index i0 (the lowest index on equal scores: centers arrive in increasing order) in
-// registers, and every other center whose score was within E2 of the running best when it arrived
-// (a former best included, if still that close) in a per-thread list in shared memory (slot-major,
-// stride 128).  Entries that fall out of the band as v0 decreases are pruned when the list is full;
-// a candidate that finds it full of band members is dropped and only its score is kept (dmin, the
-// least dropped score), so the final band {j : s_j <= v0 + E2} is complete exactly when
-// dmin > v0 + E2.  A group of W scores costs a minimum tree unless its minimum can enter the band.
+// registers, and every other center whose score was within the band width of the running best when
+// it arrived (a former best included, if still that close) in a per-thread list in shared memory
+// (slot-major, stride 128).  Entries that fall out of the band as v0 decreases are pruned when the
+// list is full; a candidate that finds it full of band members is dropped and only its score is
+// kept (dmin, the least dropped score), so the final band {j : s_j <= t(v0)} is complete exactly
+// when dmin > t(v0).  A group of W scores costs a minimum tree unless its minimum can enter.
+// Band width: a constant Bc (a bound on the error of any score difference), or, for the two-term
+// BF16 centers, a bound that grows with the distances, |err(s_j - s_0)| <= A (D_j + D_0) + Bc with
+// D the distance bounds sqrt(XE + s); t(v) is the largest s_j that can satisfy it.
 template <int CAP>
 struct Band {
-    float v0, t, E2, dmin, pt;  // pt: the threshold at the last prune (a full list is pruned again
-                                // only after the threshold has come down)
+    float v0, t, dmin, pt;  // pt: the threshold at the last prune (a full list is pruned again
+                            // only after the threshold has come down)
+    float A, Bc, XE;        // band width parameters (A == 0: constant width Bc)
     int i0, cnt;
     float *lv;
     int32_t *li;
-    __device__ __forceinline__ void reset(float e2) {
+    __device__ __forceinline__ void reset(float bc, float a = 0.f, float xe = 0.f) {
         v0 = t = dmin = pt = __int_as_float(0x7f800000);
-        E2 = e2;
+        A = a;
+        Bc = bc;
+        XE = xe;
         i0 = 0;
         cnt = 0;
+    }
+    // the largest score that can still belong to the band of a best score v
+    __device__ __forceinline__ float t_of(float v) const {
+        if (A == 0.f) return v + Bc;
+        const float d0sq = fmaxf(XE + v, 0.f), d0 = sqrtf(d0sq);
+        const float K = d0sq + A * d0 + Bc;
+        const float y = 0.5f * (A + sqrtf(fmaf(A, A, 4.f * K)));
+        const float w = fmaxf(fmaf(y, y, -d0sq), 0.f);
+        // margins for the FP32 evaluation of the bound itself
+        return v + w * 1.001f + 1.0e-6f * (d0sq + fabsf(v));
     }
     __device__ __forceinline__ void prune() {
         pt = t;
@@ -148,7 +169,7 @@ struct Band {
     __device__ __forceinline__ void group(const float (&sc)[W], int j0) {
         const float m = min_tree(sc);
         if (m <= t) {
-            const float tn = fminf(t, m + E2);
+            const float tn = fminf(t, t_of(m));
             uint32_t le = 0, eq = 0;
 #pragma unroll
             for (int g = 0; g < W; ++g) {
@@ -265,7 +286,7 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
 template <int FORM>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
-    if constexpr (FORM == F_BF16) {
+    if constexpr (FORM == F_BF16 || FORM == F_BF16X2) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -371,6 +392,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
          const __grid_constant__ CUtensorMap tmB2, const Args a) {
     constexpr bool X3 = (FORM == F_TF32X3);
+    constexpr bool TWO_B = X3 || FORM == F_BF16X2;  // a second center operand (lo part)
     constexpr int NG = epi_groups<EPI>();
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned stage base, derived by pointer arithmetic on the shared array so that
@@ -435,11 +457,12 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                         if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) goto producer_done;
                         uint8_t *st = base + (size_t)s * a.stage_bytes;
                         mbar_expect_tx(&full[s], a.tx_bytes);
-                        const int32_t kx = kb * (int32_t)(128 / (FORM == F_BF16 ? 2 : (FORM == F_FP8 ? 1 : 4)));
+                        const int32_t kx =
+                            kb * (int32_t)(128 / ((FORM == F_BF16 || FORM == F_BF16X2) ? 2 : (FORM == F_FP8 ? 1 : 4)));
                         tma_load_2d(st, &tmA, &full[s], kx, tile * BM);
                         uint8_t *bdst = st + (X3 ? 2 : 1) * a.a_bytes;
                         tma_load_2d(bdst, &tmB, &full[s], kx, nc * a.bn);
-                        if constexpr (X3) tma_load_2d(bdst + a.b_bytes, &tmB2, &full[s], kx, nc * a.bn);
+                        if constexpr (TWO_B) tma_load_2d(bdst + a.b_bytes, &tmB2, &full[s], kx, nc * a.bn);
                         issued |= 1u << s;
                         last_par = (last_par & ~(1u << s)) | (ph << s);
                         if (++s == a.stages) {
@@ -485,6 +508,10 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                                 tc_mma<FORM>(d_tmem, alo + off, bdesc + off, a.idesc, acc);
                                 tc_mma<FORM>(d_tmem, adesc + off, blo + off, a.idesc, 1u);
                                 tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, 1u);
+                            } else if constexpr (FORM == F_BF16X2) {
+                                const uint64_t blo = sw128_desc(st + a.a_bytes + a.b_bytes);
+                                tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, acc);
+                                tc_mma<FORM>(d_tmem, adesc + off, blo + off, a.idesc, 1u);
                             } else {
                                 tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, acc);
                             }
@@ -562,12 +589,17 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
             const bool valid = row < n_rows;
             float sx = 1.f;
             if (EPI == E_ARGMIN && FORM == F_FP8 && valid) sx = a.xscale[row];
-            // argmin state: the certified band of this point (error bound E2 on a score difference)
+            // argmin state: the certified band of this point (its width bounds the error of a score
+            // difference)
             const float xn = (EPI == E_ARGMIN && valid) ? a.xnorm[row] : 0.f;
             Band<CAND_MAX> band;
             {
                 const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
-                band.reset(2.f * (a.err_rel * xr * cm + a.err_abs * cm * cm));
+                if (a.pair_a > 0.f)
+                    band.reset(a.pair_rel * xr * cm + a.pair_abs * cm * cm, a.pair_a * xr,
+                               xn * (1.f + 2.4e-7f) + a.single_rel * xr * cm + a.single_abs * cm * cm);
+                else
+                    band.reset(2.f * (a.err_rel * xr * cm + a.err_abs * cm * cm));
                 band.lv = reinterpret_cast<float *>(ex) + eg * (2 * CAND_MAX * 128) + q * 32 + lane;
                 band.li = reinterpret_cast<int32_t *>(band.lv + CAND_MAX * 128);
             }
@@ -809,9 +841,9 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                             const bool takeB = vB < vA || (vB == vA && iB < iA);
                             const float v = takeB ? vB : vA, vl = takeB ? vA : vB;
                             const int ib = takeB ? iB : iA, il = takeB ? iA : iB;
-                            const float t = v + band.E2;
-                            // the band: the best, every listed center within E2 of it, the other
-                            // group's best if within E2; complete unless something was dropped
+                            const float t = band.t_of(v);
+                            // the band: the best, every listed center within the band width of it,
+                            // the other group's best if that close; complete unless something was dropped
                             int cnt = 1 + (vl <= t ? 1 : 0);
                             for (int e = 0; e < band.cnt; ++e) cnt += band.lv[e * 128] <= t ? 1 : 0;
                             for (int e = 0; e < cB; ++e) cnt += lvB[e * 128] <= t ? 1 : 0;
@@ -1204,7 +1236,7 @@ static bool make_tmap(CUtensorMap *m, CUtensorMapDataType dt, const void *ptr, u
 }
 
 static uint32_t make_idesc(int form, int M, int N) {
-    uint32_t ab = (form == F_BF16) ? 1u : (form == F_FP8 ? 0u : 2u);
+    uint32_t ab = (form == F_BF16 || form == F_BF16X2) ? 1u : (form == F_FP8 ? 0u : 2u);
     uint32_t d = 0;
     d |= 1u << 4;           // D = FP32
     d |= ab << 7;           // A format
@@ -1222,15 +1254,15 @@ struct Plan {
 
 static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra_smem = 0) {
     Plan p;
-    const int esize = (form == F_BF16) ? 2 : (form == F_FP8 ? 1 : 4);
+    const int esize = (form == F_BF16 || form == F_BF16X2) ? 2 : (form == F_FP8 ? 1 : 4);
     p.n_chunks = (int)ceil_div(k_pad, bn_cap);
     p.bn = (int)(ceil_div(ceil_div(k_pad, p.n_chunks), 16) * 16);
     p.kb = (int)ceil_div(d * esize, 128);
-    const bool x3 = form == F_TF32X3;
+    const bool x3 = form == F_TF32X3, two_b = x3 || form == F_BF16X2;
     p.a_bytes = BM * 128;
     p.b_bytes = (uint32_t)p.bn * 128;
-    p.stage_bytes = (x3 ? 2 : 1) * p.a_bytes + (x3 ? 2 : 1) * p.b_bytes;
-    p.tx_bytes = p.a_bytes + (x3 ? 2 : 1) * p.b_bytes;
+    p.stage_bytes = (x3 ? 2 : 1) * p.a_bytes + (two_b ? 2 : 1) * p.b_bytes;
+    p.tx_bytes = p.a_bytes + (two_b ? 2 : 1) * p.b_bytes;
     p.stages = (int)std::min<int64_t>(MAX_STAGES, (MAX_DYN_SMEM - 2048 - extra_smem) / p.stage_bytes);
     p.tmem_cols = (2 * p.bn <= 256) ? 256 : 512;
     p.smem = (size_t)p.stages * p.stage_bytes + 1024 + 1024 + extra_smem;
@@ -1265,19 +1297,23 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
                      const float *xnorm, int64_t n, int64_t d, const CenterPrep &cp, int64_t k, int64_t k_pad,
                      float err_rel, float err_abs, const AssignOut &o, const int32_t *n_dev, const int32_t *row_map) {
     using namespace tc;
-    const int form = (dtype == GBKM_BF16) ? F_BF16 : (dtype == GBKM_FP8E4M3 ? F_FP8 : F_TF32X3);
+    // BF16 with a low part of the centers: the two-term form
+    const int form = (dtype == GBKM_BF16) ? (cp.cop_lo ? F_BF16X2 : F_BF16)
+                                          : (dtype == GBKM_FP8E4M3 ? F_FP8 : F_TF32X3);
+    const bool bf = form == F_BF16 || form == F_BF16X2;
     const Plan p = plan(form, d, k_pad, c->bn_cap > 0 ? c->bn_cap : 256, ARGMIN_EXTRA_SMEM);
-    const CUtensorMapDataType dt = (form == F_BF16)  ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+    const CUtensorMapDataType dt = bf                ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                    : (form == F_FP8) ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const uint32_t es = (form == F_BF16) ? 2 : (form == F_FP8 ? 1 : 4);
+    const uint32_t es = bf ? 2 : (form == F_FP8 ? 1 : 4);
     CUtensorMap tA, tB, tB2;
     if (!make_tmap(&tA, dt, Xop, (uint64_t)d, (uint64_t)n, es, BM) ||
         !make_tmap(&tB, dt, cp.cop, (uint64_t)d, (uint64_t)k_pad, es, (uint32_t)p.bn))
         return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the assign operands");
     tB2 = tB;
-    if (form == F_TF32X3 && !make_tmap(&tB2, dt, cp.cop_lo, (uint64_t)d, (uint64_t)k_pad, es, (uint32_t)p.bn))
-        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the TF32 low part");
+    if ((form == F_TF32X3 || form == F_BF16X2) &&
+        !make_tmap(&tB2, dt, cp.cop_lo, (uint64_t)d, (uint64_t)k_pad, es, (uint32_t)p.bn))
+        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the centers' low part");
     Args a{};
     a.n = n, a.d = d, a.k = k, a.k_pad = k_pad;
     a.n_chunks = p.n_chunks, a.bn = p.bn, a.kb = p.kb, a.stages = p.stages, a.tmem_cols = p.tmem_cols;
@@ -1288,8 +1324,19 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
     a.row_map = row_map;
     a.cnorm = cp.cnorm, a.cscale = cp.cscale, a.xscale = Xscales, a.xnorm = xnorm, a.cmax = cp.cmax;
     a.err_rel = err_rel, a.err_abs = err_abs;
+    if (form == F_BF16X2) {
+        // |x~ - x| <= u |x| with u = 2^-8 (BF16, nearest even), |c^ - c| <= u^2 |c| for hi + lo, FP32
+        // accumulation of 2d products bounded by 2d 2^-22 relative (4x the textbook 2d 2^-24)
+        const double u = ldexp(1.0, -8), g = 2.0 * (double)d * ldexp(1.0, -22) * (1 + u) * (1 + u);
+        a.pair_a = (float)(2 * u * (1 + 1e-6));
+        a.pair_rel = (float)((4 * g + 2 * u * 2 * u * u + 4 * u * u) * (1 + 1e-6));
+        a.pair_abs = (float)(ldexp(1.0, -23) * (1 + 1e-6));
+        a.single_rel = (float)((2 * g + 2 * u * (1 + u * u) + 2 * u * u) * (1 + 1e-6));
+        a.single_abs = (float)(ldexp(1.0, -24) * (1 + 1e-6));
+    }
     a.labels = o.labels, a.min_d2 = o.min_d2, a.flag_list = o.flag_list, a.cand = o.cand, a.flag_count = o.flag_count;
     a.status = c->status;
+    if (form == F_BF16X2) return launch<F_BF16X2, E_ARGMIN>(c, tA, tB, tB2, a, p);
     if (form == F_BF16) return launch<F_BF16, E_ARGMIN>(c, tA, tB, tB2, a, p);
     if (form == F_FP8) return launch<F_FP8, E_ARGMIN>(c, tA, tB, tB2, a, p);
     return launch<F_TF32X3, E_ARGMIN>(c, tA, tB, tB2, a, p);

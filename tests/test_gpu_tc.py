@@ -60,15 +60,18 @@ TC_CASES = [
 ]
 
 
-@pytest.mark.parametrize("form", ["bf16", "f32"])
+@pytest.mark.parametrize("form", ["bf16", "f32", "bf16x2"])
 @pytest.mark.parametrize("n,d,k", TC_CASES)
 def test_tc_assign_exact_labels(gb, orc, form, n, d, k):
     X, C = _data(n, d, k, seed=n + d + k)
-    lab, md, nre = _assign(gb, X, C, form)
+    if form == "bf16x2":
+        lab, md, nre = _assign(gb, X, C, "bf16", center_terms=2)
+    else:
+        lab, md, nre = _assign(gb, X, C, form)
     ref, d1, d2, _ = assert_labels_match(orc, X, C.astype(np.float64), lab)
     xn = orc.row_norms(X)
     cn = (C.astype(np.float64) ** 2).sum(1).max()
-    rel = 2.0 ** -6 if form == "bf16" else 1e-4
+    rel = 1e-4 if form == "f32" else 2.0 ** -6
     assert np.all(np.abs(md - d1) <= rel * np.sqrt(xn * cn) * 2 + 1e-3)
 
 
@@ -138,3 +141,22 @@ def test_tc_band_across_chunks_and_overflow(gb, orc, form):
     assert_labels_match(orc, X, C.astype(np.float64), lab)
     # the 12 identical centers tie exactly: the lowest index wins
     assert np.all(lab[200:400] == 500)
+
+
+@pytest.mark.parametrize("terms", [1, 2])
+@pytest.mark.parametrize("scale", [3.0, 10.0])
+def test_tc_bf16_pairs_near_bisectors(gb, orc, scale, terms):
+    """Pairs of close centers far from the origin and points scattered around each pair's
+    midpoint: many points sit near a bisector, where the BF16 rounding decides, and both BF16
+    forms' bounds (the two-term centers' one grows with the distances) must flag every point
+    they cannot certify."""
+    rng = np.random.default_rng(int(scale))
+    d, pairs, n = 256, 32, 20000
+    mu = rng.uniform(-scale, scale, size=(pairs, d))
+    delta = rng.normal(size=(pairs, d)) * (5.0 / np.sqrt(d))
+    C = np.concatenate([mu + delta, mu - delta]).astype(np.float32)
+    z = rng.integers(0, pairs, size=n)
+    X = (mu[z] + rng.normal(size=(n, d)) * 0.3).astype(np.float32)
+    lab, _, nre = _assign(gb, X, C, "bf16", center_terms=terms)
+    assert_labels_match(orc, X, C.astype(np.float64), lab)
+    assert nre > 0 and (scale > 5 or terms == 1 or nre < n)
