@@ -288,6 +288,8 @@ struct BProb {
     void *cop, *cop_lo;      // (seeds x kps) x d operand copies of the centers
     int32_t *labels;         // seeds x n
     double *D2;              // seeds x n
+    int32_t *A;              // seeds x n: nearest chosen center so far (k-means++ skip test)
+    double *cc;              // seeds x k: squared distances of the newest center to the earlier ones
     double *bsum;            // seeds x nb
     int32_t *stop;           // seeds
     const double *u;         // seeds x k uniforms

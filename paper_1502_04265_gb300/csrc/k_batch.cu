@@ -91,38 +91,83 @@ __global__ void k_b_seed_first(const BProb *__restrict__ probs, const int2 *__re
 }
 
 // round r >= 1: D^2 of every seed of the block's problem against that seed's center r-1, and the
-// block sum of D^2 per seed (rows in order within a warp, warps in order)
+// block sum of D^2 per seed (a fixed tree over the rows).  A row whose nearest center a satisfies
+// ||c_{r-1} - c_a||^2 > 4 D^2 keeps D^2 without reading the row (k-means++ skip test, exact: the
+// new center cannot come closer); the block's threads test the rows in parallel and the 8 warps
+// work through the list of rows that need a distance (one warp per row).
 __global__ void __launch_bounds__(256) k_b_d2(const BProb *__restrict__ probs, const int2 *__restrict__ blocks,
                                               int r) {
     const int2 b = blocks[blockIdx.x];
     const BProb &P = probs[b.x];
     if (r >= P.k) return;
-    __shared__ double wsum[8];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ double nd_s[256];
+    __shared__ int list[RB];
+    __shared__ int nlist;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t blk = b.y / RB;
+    const int64_t jc = r - 1;
+    const int64_t r0 = b.y, r1 = min(P.n, (int64_t)b.y + RB);
     for (int s = 0; s < P.seeds; ++s) {
         if (P.stop[s]) continue;  // uniform over the block
-        const float *c = P.C[0] + ((int64_t)s * P.k + (r - 1)) * P.d;
+        const float *c = P.C[0] + ((int64_t)s * P.k + jc) * P.d;
         double *D2 = P.D2 + (int64_t)s * P.n;
-        double run = 0.0;
-        for (int64_t i = b.y + w; i < min(P.n, (int64_t)b.y + RB); i += 8) {
+        int32_t *A = P.A + (int64_t)s * P.n;
+        const double *cc = P.cc + (int64_t)s * P.k;
+        if (tid == 0) nlist = 0;
+        __syncthreads();
+        if (tid < RB) {
+            const int64_t i = r0 + tid;
+            double od = 0.0;
+            if (i < r1) {
+                bool skip = false;
+                if (jc > 0) {
+                    od = D2[i];
+                    skip = cc[A[i]] > 4.0 * od * (1.0 + 1e-6);
+                }
+                if (!skip) list[atomicAdd(&nlist, 1)] = tid;
+            }
+            nd_s[tid] = od;
+        } else {
+            nd_s[tid] = 0.0;
+        }
+        __syncthreads();
+        const int m = nlist;
+        for (int e = w; e < m; e += 8) {
+            const int t = list[e];
+            const int64_t i = r0 + t;
             const float *x = P.X + i * P.d;
             DF acc;
-            for (int64_t t = lane; t < P.d; t += 32) acc.add_sqdiff(x[t], c[t]);
+            for (int64_t q = lane; q < P.d; q += 32) acc.add_sqdiff(x[q], c[q]);
             const double dist = warp_sum_df(acc);
-            const double nd = (r == 1) ? dist : fmin(D2[i], dist);
-            if (lane == 0) D2[i] = nd;
-            run += nd;
+            if (lane == 0 && (jc == 0 || dist < nd_s[t])) {
+                nd_s[t] = dist;
+                D2[i] = dist;
+                A[i] = (int32_t)jc;
+            }
         }
-        if (lane == 0) wsum[w] = run;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < 8; ++q) t += wsum[q];
-            P.bsum[(int64_t)s * P.nb + blk] = t;
-        }
+        const double v = (tid < RB && r0 + tid < r1) ? nd_s[tid] : 0.0;
+        const double tot = block_tree_sum_d(v, nd_s);
+        if (tid == 0) P.bsum[(int64_t)s * P.nb + blk] = tot;
         __syncthreads();
     }
+}
+
+// round r >= 2: cc[s][a] = ||c_{r-1} - c_a||^2 (double-float) for a < r - 1, one warp per
+// (pair, earlier center); grid.y = pair
+__global__ void __launch_bounds__(256) k_b_cc(const BProb *__restrict__ probs, const int2 *__restrict__ pairs, int r) {
+    const int2 ps = pairs[blockIdx.y];
+    const BProb &P = probs[ps.x];
+    if (r >= P.k || P.stop[ps.y]) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t jc = r - 1;
+    const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (a >= jc) return;
+    const float *C = P.C[0] + (int64_t)ps.y * P.k * P.d;
+    DF acc;
+    for (int64_t t = lane; t < P.d; t += 32) acc.add_sqdiff(C[jc * P.d + t], C[a * P.d + t]);
+    const double v = warp_sum_df(acc);
+    if (lane == 0) P.cc[(int64_t)ps.y * P.k + a] = v;
 }
 
 __device__ double block_incl_scan_db(double v, double *sh) {
@@ -687,7 +732,8 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         bn_max = std::max(bn_max, b.bn);
         // per-problem device buffers (sizes; carved below)
         wbytes += 256 * 12 + b.n * 4 + (bf ? b.n * b.d * 2 : 0) + 2 * S * b.k * b.d * 4 + S * b.kps * 4 + 4 +
-                  S * b.kps * b.d * (bf ? 2 : 8) + S * b.n * 4 + S * b.n * 8 + S * b.nb * 8 + S * 4;
+                  S * b.kps * b.d * (bf ? 2 : 8) + S * b.n * 4 + S * b.n * 8 + S * b.n * 4 + S * b.k * 8 + 2 * 256 +
+                  S * b.nb * 8 + S * 4;
     }
     maxcb = std::max<int64_t>(1, ceil_div(dmax, 256));
     const int64_t npairs = count * S;
@@ -712,6 +758,8 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         b.cop_lo = bf ? nullptr : static_cast<void *>(carve<float>(cur, S * b.kps * b.d));
         b.labels = carve<int32_t>(cur, S * b.n);
         b.D2 = carve<double>(cur, S * b.n);
+        b.A = carve<int32_t>(cur, S * b.n);
+        b.cc = carve<double>(cur, S * b.k);
         b.bsum = carve<double>(cur, S * b.nb);
         b.stop = carve<int32_t>(cur, S);
     }
@@ -828,6 +876,11 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
     k_b_seed_first<<<(unsigned)npairs, 128, 0, st>>>(d_probs, d_pairs);
     c->launches += 2;
     for (int r = 1; r < kmax_all; ++r) {
+        if (r >= 2) {
+            k_b_cc<<<dim3((unsigned)ceil_div((int64_t)(r - 1) * 32, 256), (unsigned)npairs), 256, 0, st>>>(d_probs,
+                                                                                                        d_pairs, r);
+            c->launches += 1;
+        }
         k_b_d2<<<(unsigned)blocks, 256, 0, st>>>(d_probs, d_blocks, r);
         k_b_pick<<<(unsigned)npairs, PICKB_T, 0, st>>>(d_probs, d_pairs, r, c->status);
         c->launches += 2;

@@ -1,6 +1,12 @@
 // k_seed.cu -- A3 k-means++ D^2 seeding (Section 1): for each round, a fused D^2 update
 // with per-block FP64 sums, then a one-CTA two-level prefix-sum sampler that writes the chosen
-// row into the centers on the device.  2 launches per round, no host synchronisation.
+// row into the centers on the device.  No host synchronisation.
+//
+// The D^2 update skips, exactly, every point the new center cannot reach: with a the point's
+// nearest chosen center and D its distance, ||x - c_new|| >= ||c_new - c_a|| - D, so when
+// ||c_new - c_a||^2 > 4 D^2 (with a margin far above the rounding of both double-float values) the
+// new distance exceeds D and min(D^2, ||x - c_new||^2) = D^2: the point's row is not read and D^2
+// keeps its bits.  The center-to-center distances of a round take one small kernel.
 #include "internal.cuh"
 
 namespace gbkm {
@@ -10,50 +16,88 @@ constexpr int SB = 128;    // rows per sampling block (one CTA of 8 warps, 16 ro
 constexpr int PICK_T = 1024;
 }  // namespace
 
-// p_i = w_i * D2_i (or w_i when mode_w) summed per block of SB rows; D2 refreshed against the
-// newest center c (init: D2 = distance to c).  One warp per row, rows interleaved across the
-// 8 warps; the block sum runs over warps in order, each warp over its rows in order.
+// p_i = w_i * D2_i summed per block of SB rows; D2 refreshed against the newest center c (round
+// j = index of c; init: D2 = distance to c), A = index of the nearest center so far, cc[a] =
+// ||c - c_a||^2 for the earlier centers (skip test above).  The block's threads test its rows in
+// parallel; the rows that need a distance go to a list that the 8 warps work through (one warp per
+// row); the block sum is a fixed tree over the rows.
 template <int VW>
 __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, int64_t n, int64_t d,
                                                    const float *__restrict__ w,
-                                                   const float *__restrict__ c, int init,
-                                                   double *__restrict__ D2, double *__restrict__ bsum,
+                                                   const float *__restrict__ c, int64_t j,
+                                                   double *__restrict__ D2, int32_t *__restrict__ A,
+                                                   const double *__restrict__ cc, double *__restrict__ bsum,
                                                    const int *__restrict__ stop) {
     if (*stop) return;
-    __shared__ double wsum[8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ double nd_s[256];
+    __shared__ int list[SB];
+    __shared__ int nlist;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
-    double run = 0.0;
-    for (int64_t i = r0 + wid; i < r1; i += 8) {
+    if (tid == 0) nlist = 0;
+    __syncthreads();
+    if (tid < SB) {
+        const int64_t i = r0 + tid;
+        double od = 0.0;
+        if (i < r1) {
+            bool skip = false;
+            if (j > 0) {
+                od = D2[i];
+                skip = cc[A[i]] > 4.0 * od * (1.0 + 1e-6);
+            }
+            if (!skip) list[atomicAdd(&nlist, 1)] = tid;
+        }
+        nd_s[tid] = od;
+    } else {
+        nd_s[tid] = 0.0;
+    }
+    __syncthreads();
+    const int m = nlist;
+    for (int e = wid; e < m; e += 8) {
+        const int t = list[e];
+        const int64_t i = r0 + t;
         const float *x = X + i * d;
         DF acc;
         if constexpr (VW == 4) {
             const float4 *x4 = reinterpret_cast<const float4 *>(x);
             const float4 *c4 = reinterpret_cast<const float4 *>(c);
 #pragma unroll 4
-            for (int64_t t = lane; t < d / 4; t += 32) {
-                float4 a = __ldg(x4 + t), b = __ldg(c4 + t);
+            for (int64_t q = lane; q < d / 4; q += 32) {
+                float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
                 acc.add_sqdiff(a.x, b.x);
                 acc.add_sqdiff(a.y, b.y);
                 acc.add_sqdiff(a.z, b.z);
                 acc.add_sqdiff(a.w, b.w);
             }
         } else {
-            for (int64_t t = lane; t < d; t += 32) acc.add_sqdiff(x[t], c[t]);
+            for (int64_t q = lane; q < d; q += 32) acc.add_sqdiff(x[q], c[q]);
         }
         const double dist = warp_sum_df(acc);
-        double nd = dist;
-        if (!init) nd = fmin(D2[i], dist);
-        if (lane == 0) D2[i] = nd;
-        run += (w ? (double)w[i] : 1.0) * nd;
+        if (lane == 0 && (j == 0 || dist < nd_s[t])) {
+            nd_s[t] = dist;
+            D2[i] = dist;
+            A[i] = (int32_t)j;
+        }
     }
-    if (lane == 0) wsum[wid] = run;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < 8; ++q) s += wsum[q];
-        bsum[blockIdx.x] = s;
-    }
+    double p = 0.0;
+    if (tid < SB && r0 + tid < r1) p = (w ? (double)w[r0 + tid] : 1.0) * nd_s[tid];
+    const double s = block_tree_sum_d(p, nd_s);
+    if (tid == 0) bsum[blockIdx.x] = s;
+}
+
+// cc[a] = ||C[j] - C[a]||^2 (double-float) for a < j: one warp per earlier center
+__global__ void __launch_bounds__(256) k_center_dist(const float *__restrict__ C, int64_t d, int64_t j,
+                                                     double *__restrict__ cc, const int *__restrict__ stop) {
+    if (*stop) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (a >= j) return;
+    const float *cj = C + j * d, *ca = C + a * d;
+    DF acc;
+    for (int64_t t = lane; t < d; t += 32) acc.add_sqdiff(cj[t], ca[t]);
+    const double v = warp_sum_df(acc);
+    if (lane == 0) cc[a] = v;
 }
 
 // block sums of w (first center of a weighted run)
@@ -219,11 +263,13 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
               const double *u, int64_t *idx_out, float *C_out) {
     const int64_t nb = ceil_div(n, SB);
     WsPlan p;
-    size_t o_d2 = p.take<double>(n), o_b = p.take<double>(nb), o_stop = p.take<int>(1);
+    size_t o_d2 = p.take<double>(n), o_a = p.take<int32_t>(n), o_cc = p.take<double>(k), o_b = p.take<double>(nb),
+           o_stop = p.take<int>(1);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
-    double *D2 = ws_at<double>(ws, o_d2), *bsum = ws_at<double>(ws, o_b);
+    double *D2 = ws_at<double>(ws, o_d2), *bsum = ws_at<double>(ws, o_b), *cc = ws_at<double>(ws, o_cc);
+    int32_t *A = ws_at<int32_t>(ws, o_a);
     int *stop = ws_at<int>(ws, o_stop);
     cudaError_t e = cudaMemsetAsync(stop, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(idx_out, 0xff, sizeof(int64_t) * k, c->stream);
@@ -239,15 +285,26 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
         c->launches += 1;
     }
     c->launches += 1;
-    for (int64_t j = 1; j <= k; ++j) {
-        const float *cprev = C_out + (j - 1) * d;
-        if (j == k) break;  // D2 against the last center is not needed
+    for (int64_t j = 1; j < k; ++j) {
+        // refresh D2 against center j - 1 (chosen in the previous round), then pick center j
+        const int64_t jc = j - 1;
+        const float *cprev = C_out + jc * d;
+        if (jc > 0) {
+            prof_begin(c, "seed_cc");
+            k_center_dist<<<(unsigned)ceil_div(jc * 32, 256), 256, 0, c->stream>>>(C_out, d, jc, cc, stop);
+            prof_end(c);
+            c->launches += 1;
+        }
+        prof_begin(c, "seed_d2");
         if (vec)
-            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, j == 1, D2, bsum, stop);
+            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop);
         else
-            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, j == 1, D2, bsum, stop);
+            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop);
+        prof_end(c);
+        prof_begin(c, "seed_pick");
         k_pick<<<1, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, 0, idx_out, C_out, stop,
                                             c->status);
+        prof_end(c);
         c->launches += 2;
     }
     return cuda_check(c, cudaGetLastError(), "seed launch");
