@@ -309,8 +309,9 @@ int kmeans_gemm_bf16(gbkm_ctx *ctx, const void *A, const void *B, int64_t M, int
                      const float *bias, int32_t act, int32_t out_bf16, void *Y, int64_t ldy);
 
 /* Forward pass on Xh (n x d_in BF16): logits (n x k FP32) and/or the indices of the topm
- * (1..32) largest logits of every point (n x topm int32, order unspecified, -1 padding), the
- * latter selected inside the logits GEMM's epilogue so that the logits are never stored. */
+ * (1..32) largest logits of every point (n x topm int32, in decreasing logit order, equal logits
+ * by increasing index, -1 padding), the latter selected inside the logits GEMM's epilogue so that
+ * the logits are never stored. */
 int kmeans_mlp_forward(gbkm_ctx *ctx, const gbkm_mlp *mlp, const void *Xh, int64_t n, float *logits,
                        int32_t *top_idx, int32_t topm);
 
@@ -326,11 +327,11 @@ int kmeans_mlp_train_step(gbkm_ctx *ctx, gbkm_mlp *mlp, const void *Xh, const in
  * the squared acceptance radius of kmeans_learned_assign's certificate. */
 int kmeans_center_separation(gbkm_ctx *ctx, const float *C, int64_t k, int64_t d, float *s2);
 
-/* Assignment step (Section 1) with learned candidates: the MLP proposes topm centers per point,
- * their exact FP32 distances give the best candidate b, and b is accepted when the point lies
- * certifiably inside the ball of radius s(c_b) (then every other center is strictly farther);
- * the remaining points get the full scan of kmeans_assign (FP32).  The labels are therefore those
- * of the exact method.  X: n x d FP32, Xh: its BF16 copy, C: k x d, s2 from
+/* Assignment step (Section 1) with learned candidates: the MLP proposes topm centers per point
+ * (in decreasing logit order); their exact FP32 distances are taken in that order until a candidate
+ * b has the point certifiably inside the ball of radius s(c_b) (then every other center is strictly
+ * farther, so b is the exact label); the points without such a candidate get the full scan of
+ * kmeans_assign (FP32).  The labels are therefore those of the exact method.  X: n x d FP32, Xh: its BF16 copy, C: k x d, s2 from
  * kmeans_center_separation; labels: n int32; n_fallback: 1 int64 (device) or NULL; cand_out:
  * n x topm int32 or NULL.  Synchronises once (to size the fallback scan). */
 int kmeans_learned_assign(gbkm_ctx *ctx, const gbkm_mlp *mlp, const float *X, const void *Xh, int64_t n,

@@ -139,9 +139,11 @@ __global__ void __launch_bounds__(256) k_center_sep(const float *__restrict__ C,
     if (lane == 0) s2[j] = 0.25f * best;
 }
 
-// one warp per point: exact FP32 distances to its m candidates, best candidate b (ties: lower
-// index); accepted when d(x, c_b) is certifiably below s2[b] (relative margin 1e-5 covers the FP32
-// rounding of both sides), else appended to the fallback list
+// one warp per point: exact FP32 distances to its candidates in rank order until one, b, satisfies
+// d(x, c_b) < s2[b] = min_c ||c_b - c||^2 / 4 certifiably (relative margins of 1e-5 cover the FP32
+// rounding of both sides): then c_b is the unique nearest center of all k (Elkan's bound), so the
+// first such candidate is the label and the rest need no distance; a point without one goes to the
+// fallback list
 __global__ void __launch_bounds__(256) k_cand_check(const float *__restrict__ X, int64_t n, int64_t d,
                                                     const float *__restrict__ C, int64_t k,
                                                     const int32_t *__restrict__ cand, int m,
@@ -151,9 +153,8 @@ __global__ void __launch_bounds__(256) k_cand_check(const float *__restrict__ X,
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const float *x = X + i * d;
-    float best = __int_as_float(0x7f800000);
     int arg = -1;
-    for (int q = 0; q < m; ++q) {
+    for (int q = 0; q < m && arg < 0; ++q) {
         const int j = cand[i * m + q];
         if (j < 0 || j >= k) continue;
         const float *c = C + (int64_t)j * d;
@@ -163,14 +164,10 @@ __global__ void __launch_bounds__(256) k_cand_check(const float *__restrict__ X,
             a = fmaf(e, e, a);
         }
         a = warp_sum_f(a);
-        if (a < best || (a == best && j < arg)) {
-            best = a;
-            arg = j;
-        }
+        if (a * (1.f + 1e-5f) < s2[j] * (1.f - 1e-5f)) arg = j;
     }
     if (lane == 0) {
-        const bool ok = arg >= 0 && best * (1.f + 1e-5f) < s2[arg] * (1.f - 1e-5f);
-        if (ok) {
+        if (arg >= 0) {
             labels[i] = arg;
         } else {
             const int slot = atomicAdd(fb_count, 1);

@@ -133,3 +133,17 @@ def test_learned_assign_labels_are_exact(gb):
     gb.gbkm_sync()
     assert torch.equal(labels, exact)
     assert int(nf.item()) < 20000 // 10
+
+
+def test_topm_order_is_rank_order(gb):
+    """The top-m indices come in decreasing logit order (equal logits by increasing index)."""
+    d, h, k, n, m = 64, 64, 1024, 257, 32
+    net = _net(gb, d, h, k, seed=7)
+    Xh = bf(np.random.default_rng(8).normal(size=(n, d)))
+    logits = torch.empty((n, k), dtype=torch.float32, device=DEV)
+    top = torch.empty((n, m), dtype=torch.int32, device=DEV)
+    gb.kmeans_mlp_forward(net, Xh, logits=logits, top_idx=top, topm=m)
+    Z, T = logits.cpu().numpy(), top.cpu().numpy()
+    for i in range(n):
+        ref = np.lexsort((np.arange(k), -Z[i]))[:m]
+        assert np.array_equal(T[i], ref)
