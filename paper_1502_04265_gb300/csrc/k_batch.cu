@@ -508,14 +508,18 @@ __device__ __forceinline__ DF df_add_b(DF a, DF b) {
 }
 
 // one CTA per item (<= BIG rows of one cluster): sums of the rows shifted by the cluster's first
-// row (as the single-problem k_segsum), 128 rows at a time, one float per thread and column
+// row (as the single-problem k_segsum).  The 256 threads form rp row slots of dp columns (dp = d
+// rounded up to a power of two in [32, 256], rp = 256 / dp): thread (slot, column) sums its column
+// over the rows slot, slot + rp, ... four at a time (loads in flight together) into double-float
+// accumulators; the slots are then combined in a fixed order.  Wider rows take several 256-column
+// passes.
 __global__ void __launch_bounds__(256) k_b_segsum(const BProb *__restrict__ probs, const PairInfo *__restrict__ pinfo,
                                                   const int32_t *__restrict__ cpair, const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ start,
                                                   const int32_t *__restrict__ item_start,
                                                   const int64_t *__restrict__ pbase, int64_t G,
                                                   float2 *__restrict__ part_s, double *__restrict__ part_nq) {
-    __shared__ int32_t rows_s[128];
+    __shared__ float2 red2[256];
     __shared__ double qred[256];
     const int64_t item = blockIdx.x;
     if (item >= item_start[G]) return;
@@ -525,37 +529,56 @@ __global__ void __launch_bounds__(256) k_b_segsum(const BProb *__restrict__ prob
     const int64_t d = P.d;
     const int64_t it = item - item_start[g];
     const int64_t r0 = start[g] + it * BIG;
-    const int64_t rows = min((int64_t)start[g + 1] - r0, BIG);
+    const int rows = (int)min((int64_t)start[g + 1] - r0, BIG);
     const float *ref = P.X + (int64_t)perm[start[g]] * d;
     float2 *out = part_s + pbase[g] + it * d;
     const int tid = threadIdx.x;
+    int dp = 32;
+    while (dp < d && dp < 256) dp <<= 1;
+    const int rp = 256 / dp, slot = tid / dp, cl = tid % dp;
+    const int32_t *pr = perm + r0;
     DF qacc;
-    // columns in passes of 256 threads; rows staged 128 at a time
-    for (int64_t cb = 0; cb < d; cb += 256) {
-        const int64_t col = cb + tid;
+    for (int64_t cb = 0; cb < d; cb += dp) {
+        const int64_t col = cb + cl;
         const bool act = col < d;
         const float c = act ? ref[col] : 0.f;
         DF sacc;
-        for (int64_t rb = 0; rb < rows; rb += 128) {
-            __syncthreads();
-            if (tid < 128 && rb + tid < rows) rows_s[tid] = perm[r0 + rb + tid];
-            __syncthreads();
-            const int nr = (int)min((int64_t)128, rows - rb);
-            for (int r = 0; r < nr; r += 4) {
-                float sb = 0.f, qb = 0.f;
+        int r = slot;
+        for (; r + 3 * rp < rows; r += 4 * rp) {
+            float v[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (r + u < nr && act) {
-                        const float t = __fsub_rn(__ldg(P.X + (int64_t)rows_s[r + u] * d + col), c);
-                        sb = __fadd_rn(sb, t);
-                        qb = __fmaf_rn(t, t, qb);
-                    }
-                }
-                sacc.add(sb);
-                qacc.add(qb);
+            for (int u = 0; u < 4; ++u) v[u] = act ? __ldg(P.X + (int64_t)pr[r + u * rp] * d + col) : c;
+            float sb = 0.f, qb = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float t = __fsub_rn(v[u], c);
+                sb = __fadd_rn(sb, t);
+                qb = __fmaf_rn(t, t, qb);
             }
+            sacc.add(sb);
+            qacc.add(qb);
         }
-        if (act) out[col] = make_float2(sacc.hi, sacc.lo);
+        for (; r < rows; r += rp) {
+            const float t = act ? __fsub_rn(__ldg(P.X + (int64_t)pr[r] * d + col), c) : 0.f;
+            sacc.add(t);
+            qacc.add(__fmul_rn(t, t));
+        }
+        // combine the row slots of each column in slot order
+        red2[tid] = make_float2(sacc.hi, sacc.lo);
+        __syncthreads();
+        if (slot == 0 && act) {
+            DF tot;
+            tot.hi = red2[cl].x, tot.lo = red2[cl].y;
+            for (int q = 1; q < rp; ++q) {
+                const float2 o = red2[q * dp + cl];
+                float hs, he;
+                two_sum(tot.hi, o.x, hs, he);
+                tot.hi = hs;
+                tot.lo = __fadd_rn(__fadd_rn(tot.lo, o.y), he);
+            }
+            out[col] = make_float2(tot.hi, tot.lo);
+        }
+        __syncthreads();
     }
     const double q = block_tree_sum_d(qacc.value(), qred);
     if (tid == 0) {
