@@ -100,29 +100,29 @@ def load_peaks():
             "source": "fallback"}
 
 
-def kernel_source_hash():
-    """Hash of the kernel sources, to tell whether stored ncu counters still apply."""
+def source_hash(files):
+    """Hash of the given kernel source files (relative to csrc/), to tell whether stored ncu
+    counters still apply."""
     import hashlib
 
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1502_04265_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in sorted(files):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
 def stored_traffic(key):
     """DRAM bytes per launch of `key` from a committed ncu capture (profiles/traffic.json), or
-    None when the kernels changed since the capture."""
+    None when its kernel sources changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         table = json.load(f)
     e = table.get(key)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != source_hash(e.get("sources", [])):
         return None
     return e["dram_bytes_per_launch"]
 

@@ -306,7 +306,8 @@ __device__ __forceinline__ float warp_direct_d2_rx(const float4 (&xr)[8], const 
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, int64_t d,
+// (3 CTAs per SM: 24 warps, each with one flagged row's loads in flight)
+__global__ void __launch_bounds__(256, 3) k_recheck(const float *__restrict__ X, int64_t d,
                                                  const float *__restrict__ C, int64_t k,
                                                  const int32_t *__restrict__ list,
                                                  const int32_t *__restrict__ cand,
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(256) k_recheck(const float *__restrict__ X, in
 
 int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
                    const AssignOut &o, int64_t *n_rechecked, const Escalation *esc, const int32_t *row_map) {
-    unsigned blocks = (unsigned)c->sm_count * 4;
+    unsigned blocks = (unsigned)c->sm_count * 3;
     Escalation e{};
     if (esc) e = *esc;
     k_recheck<<<blocks, 256, 0, c->stream>>>(X, d, C, k, o.flag_list, o.cand, o.flag_count, n, o.labels,
