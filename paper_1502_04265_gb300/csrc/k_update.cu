@@ -9,7 +9,7 @@
 //   5. k_items     chunks of R rows per cluster, exclusive scan -> work-item table
 //   6. k_segsum    one CTA per chunk of 128 rows: sums of w (x - s), w, w ||x - s||^2 with s the
 //                  cluster's first row -> FP64 partials
-//   7. k_finalize  one CTA per (cluster, 256 columns): double-float sums of the partials in chunk order,
+//   7. k_finalize  one CTA per (cluster, 256 columns): FP64 sums of the partials in chunk order,
 //                  centroid and CF cost terms
 //   8. k_final     one CTA: FP64 totals in cluster order
 #include <mutex>
@@ -256,27 +256,6 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return a;
 }
 
-// double-float product (TwoProd of the high parts by fma, cross terms in FP32): about 2^-44 relative,
-// on the FP32 pipe (GB300's FP64 rate is a small fraction of its FP32 rate)
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float pe = __fmaf_rn(a.hi, b.hi, -p);
-    pe = __fmaf_rn(a.hi, b.lo, pe);
-    pe = __fmaf_rn(a.lo, b.hi, pe);
-    float s, e;
-    two_sum(p, pe, s, e);
-    DF r;
-    r.hi = s;
-    r.lo = e;
-    return r;
-}
-__device__ __forceinline__ DF df_from(double v) {
-    DF r;
-    r.hi = (float)v;
-    r.lo = (float)(v - (double)r.hi);
-    return r;
-}
-
 template <int VW, bool WEIGHTED>
 __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int64_t d,
                                                 const float *__restrict__ w,
@@ -430,25 +409,16 @@ __global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ par
                                                   const float *__restrict__ C_old, float *__restrict__ C_new,
                                                   double *__restrict__ counts, double *__restrict__ nq,
                                                   double *__restrict__ blk) {
-    __shared__ double wred[2][8];
-    __shared__ double s_N, s_Q;
+    __shared__ double sh[256];
     const int64_t j = blockIdx.x, cb = blockIdx.y;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int32_t i0 = item_start[j], i1 = item_start[j + 1];
-    if (wid == 0) {
-        // N_j and Q'_j: the cluster's items summed by one warp in FP64
-        double n_part = 0.0, q_part = 0.0;
-        for (int32_t it = i0 + lane; it < i1; it += 32) {
-            n_part += part_nq[(int64_t)it * 2];
-            q_part += part_nq[(int64_t)it * 2 + 1];
-        }
-        n_part = warp_sum_d(n_part);
-        q_part = warp_sum_d(q_part);
-        if (lane == 0) s_N = n_part, s_Q = q_part;
+    double n_part = 0.0, q_part = 0.0;
+    for (int32_t it = i0 + (int32_t)threadIdx.x; it < i1; it += (int32_t)blockDim.x) {
+        n_part += part_nq[(int64_t)it * 2];
+        if (cb == 0) q_part += part_nq[(int64_t)it * 2 + 1];
     }
-    __syncthreads();
-    const double N = s_N;
-    DF a_old, b_sq;  // per column: 2 e S' + N e^2 and S'^2 / N, in double-float
+    const double N = block_tree_sum_d(n_part, sh);
+    double a_old = 0.0, b_sq = 0.0;
     const int64_t t = cb * 256 + threadIdx.x;
     if (t < d) {
         // 8 independent double-float accumulators keep 8 partial loads in flight; combined in order
@@ -471,36 +441,31 @@ __global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ par
         }
 #pragma unroll
         for (int q = 1; q < 8; ++q) acc[0] = df_add(acc[0], acc[q]);
-        const DF Sp = acc[0];
+        const double Sp = acc[0].value();
         const float co = C_old[j * d + t];
         if (N > 0.0) {
-            const float sref = X[(int64_t)perm[start[j]] * d + t];
-            DF e;  // s - c_old, exactly
-            two_sum(sref, -co, e.hi, e.lo);
-            const DF Nd = df_from(N), rN = df_from(1.0 / N);
-            DF eS = df_mul(e, Sp);
-            eS.hi *= 2.f, eS.lo *= 2.f;
-            a_old = df_add(eS, df_mul(Nd, df_mul(e, e)));
-            b_sq = df_mul(df_mul(Sp, Sp), rN);
-            const DF mu = df_mul(Sp, rN);
-            C_new[j * d + t] = __fadd_rn(sref, __fadd_rn(mu.hi, mu.lo));
+            const double sref = (double)X[(int64_t)perm[start[j]] * d + t];
+            const double e = sref - (double)co;
+            a_old = 2.0 * e * Sp + N * e * e;
+            b_sq = Sp * Sp;
+            C_new[j * d + t] = (float)(sref + Sp / N);
         } else {
             C_new[j * d + t] = co;
         }
     }
-    const double at = warp_sum_df(a_old), bt = warp_sum_df(b_sq);
-    if (lane == 0) wred[0][wid] = at, wred[1][wid] = bt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double A = 0.0, Bt = 0.0;
-        for (int q = 0; q < 8; ++q) A += wred[0][q], Bt += wred[1][q];
-        if (cb == 0) {
+    const double at = block_tree_sum_d(a_old, sh);
+    const double bt = block_tree_sum_d(b_sq, sh);
+    if (cb == 0) {
+        const double Q = block_tree_sum_d(q_part, sh);
+        if (threadIdx.x == 0) {
             if (counts) counts[j] = N;
             nq[j * 2] = N;
-            nq[j * 2 + 1] = s_Q;
+            nq[j * 2 + 1] = Q;
         }
-        blk[(j * gridDim.y + cb) * 2] = A;
-        blk[(j * gridDim.y + cb) * 2 + 1] = Bt;
+    }
+    if (threadIdx.x == 0) {
+        blk[(j * gridDim.y + cb) * 2] = at;
+        blk[(j * gridDim.y + cb) * 2 + 1] = bt;
     }
 }
 
@@ -519,7 +484,7 @@ __global__ void __launch_bounds__(256) k_final(const double *__restrict__ nq, co
         }
         if (N > 0.0) {
             x += Q + a;
-            y += Q - b;  // b = ||S'_j||^2 / N_j
+            y += Q - b / N;
         } else {
             z += 1.0;
         }
