@@ -970,8 +970,8 @@ def run_learned(env, args):
     roof = roofline(peaks, "mlp_topm", kernel_avg_s(prof, "mlp_topm"), n * h * 2 + k * h * 2 + n * topm * 4, fl_top,
                     bf16_peak(peaks, R["total_s"]), R["total_s"],
                     traffic=stored_traffic(f"mlp_topm/bf16/{n}x{h}_k{k}"),
-                    note="the output layer (h=256 -> k logits) with the fused top-32 epilogue; the logits are "
-                         "never stored")
+                    note="the output layer (h=256 -> k logits) with the fused grouped top-32 proposal (the best "
+                         "center of each 16-center group competes); the logits are never stored")
 
     def full_scan(compute, Xop, steps):
         lab2 = torch.empty(n, dtype=torch.int32, device=env.dev)

@@ -308,12 +308,14 @@ int64_t kmeans_mlp_param_count(int64_t d_in, int64_t hidden, int64_t k);
 int kmeans_gemm_bf16(gbkm_ctx *ctx, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                      const float *bias, int32_t act, int32_t out_bf16, void *Y, int64_t ldy);
 
-/* Forward pass on Xh (n x d_in BF16): logits (n x k FP32) and/or the indices of the topm
- * (1..32) largest logits of every point (n x topm int32, in decreasing logit order, equal logits
- * by increasing index, -1 padding), the latter selected inside the logits GEMM's epilogue so that
- * the logits are never stored. */
+/* Forward pass on Xh (n x d_in BF16): logits (n x k FP32) and/or topm (1..32) proposed centers
+ * per point (n x topm int32, in decreasing logit order, equal logits by increasing index, -1
+ * padding), selected inside the logits GEMM's epilogue so that the logits are never stored.
+ * group 0 or 1: the topm largest logits; group 16: every aligned group of 16 centers offers only
+ * its best center (lowest index on equal logits) and the topm best offers are returned, which
+ * keeps the selection to one comparison per group in the epilogue. */
 int kmeans_mlp_forward(gbkm_ctx *ctx, const gbkm_mlp *mlp, const void *Xh, int64_t n, float *logits,
-                       int32_t *top_idx, int32_t topm);
+                       int32_t *top_idx, int32_t topm, int32_t group);
 
 /* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8, decoupled decay wd on wd_mask) on the mean
  * softmax cross-entropy of the batch Xh (B x d_in BF16, B % 8 == 0) against labels (B int32 in
@@ -328,7 +330,7 @@ int kmeans_mlp_train_step(gbkm_ctx *ctx, gbkm_mlp *mlp, const void *Xh, const in
 int kmeans_center_separation(gbkm_ctx *ctx, const float *C, int64_t k, int64_t d, float *s2);
 
 /* Assignment step (Section 1) with learned candidates: the MLP proposes topm centers per point
- * (in decreasing logit order); their exact FP32 distances are taken in that order until a candidate
+ * (group 16 of kmeans_mlp_forward, in decreasing logit order); their exact FP32 distances are taken in that order until a candidate
  * b has the point certifiably inside the ball of radius s(c_b) (then every other center is strictly
  * farther, so b is the exact label); the points without such a candidate get the full scan of
  * kmeans_assign (FP32).  The labels are therefore those of the exact method.  X: n x d FP32, Xh: its BF16 copy, C: k x d, s2 from

@@ -74,7 +74,7 @@ _SIGS = {
     "kmeans_autotune": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32)]),
     "kmeans_mlp_param_count": (ct.c_int64, [_i64, _i64, _i64]),
     "kmeans_gemm_bf16": (ct.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i32, _i32, _vp, _i64]),
-    "kmeans_mlp_forward": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _i64, _vp, _vp, _i32]),
+    "kmeans_mlp_forward": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _i64, _vp, _vp, _i32, _i32]),
     "kmeans_mlp_train_step": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _vp, _i64, ct.c_float, ct.c_float, _vp, _vp]),
     "kmeans_center_separation": (ct.c_int, [_vp, _vp, _i64, _i64, _vp]),
     "kmeans_learned_assign": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i32, _vp,
@@ -453,12 +453,12 @@ def _mlp_struct(net):
                _ptr(net.wd_mask).value if net.wd_mask is not None else None, net.step)
 
 
-def kmeans_mlp_forward(net, Xh, logits=None, top_idx=None, topm=32, ctx=None):
+def kmeans_mlp_forward(net, Xh, logits=None, top_idx=None, topm=32, group=1, ctx=None):
     _req(Xh, torch.bfloat16, name="Xh")
     n = Xh.shape[0]
     m = _mlp_struct(net)
     c = _ctx(ctx, Xh)
-    c.check(load().kmeans_mlp_forward(c.handle, ct.byref(m), _ptr(Xh), n, _ptr(logits), _ptr(top_idx), topm))
+    c.check(load().kmeans_mlp_forward(c.handle, ct.byref(m), _ptr(Xh), n, _ptr(logits), _ptr(top_idx), topm, int(group)))
     return logits, top_idx
 
 

@@ -508,11 +508,11 @@ int kmeans_gemm_bf16(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64
 }
 
 int kmeans_mlp_forward(gbkm_ctx *c, const gbkm_mlp *mlp, const void *Xh, int64_t n, float *logits, int32_t *top_idx,
-                       int32_t topm) {
+                       int32_t topm, int32_t group) {
     if (!c) return GBKM_EINVAL;
     DeviceGuard g(c->device);
     prof_begin(c, "mlp_forward");
-    int rc = gbkm::mlp_forward(c, mlp, Xh, n, logits, top_idx, topm);
+    int rc = gbkm::mlp_forward(c, mlp, Xh, n, logits, top_idx, topm, group);
     prof_end(c);
     return rc;
 }

@@ -260,9 +260,10 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
                      const int32_t *row_map = nullptr);
 int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                         const float *bias, int act, int out_bf16, void *Y, int64_t ldy, float *Ypre, int64_t ldpre,
-                        int32_t *top_idx, float *top_val, int topm);
+                        int32_t *top_idx, float *top_val, int topm, int group = 1);
 int64_t mlp_param_count(const gbkm_mlp *m);
-int mlp_forward(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n, float *logits, int32_t *top_idx, int topm);
+int mlp_forward(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n, float *logits, int32_t *top_idx, int topm,
+                int group = 1);
 int mlp_train_step(gbkm_ctx *c, gbkm_mlp *m, const void *Xh, const int32_t *labels, int64_t B, float lr, float wd,
                    float *loss_rows, float *grad_out);
 int center_separation(gbkm_ctx *c, const float *C, int64_t k, int64_t d, float *s2);

@@ -228,7 +228,8 @@ static int mlp_hidden(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n,
                                H2pre, m->hidden, nullptr, nullptr, 0);
 }
 
-int mlp_forward(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n, float *logits, int32_t *top_idx, int topm) {
+int mlp_forward(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n, float *logits, int32_t *top_idx, int topm,
+                int group) {
     if (!mlp_ok(m) || n < 1 || !Xh || (!logits && !top_idx)) return set_error(c, GBKM_EINVAL, "mlp_forward: bad arguments");
     const MlpLayout L = mlp_layout(*m);
     WsPlan p;
@@ -252,7 +253,7 @@ int mlp_forward(gbkm_ctx *c, const gbkm_mlp *m, const void *Xh, int64_t n, float
     if (top_idx) {
         prof_begin(c, "mlp_topm");
         rc = launch_gemm_bf16_tc(c, H2, Wh + L.oW3, n, m->k, m->hidden, m->params + L.ob3, 0, 0, nullptr, 0, nullptr, 0,
-                                 top_idx, nullptr, topm);
+                                 top_idx, nullptr, topm, group);
         prof_end(c);
     }
     return rc;
@@ -366,7 +367,7 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
         cudaGetLastError();
         return set_error(c, GBKM_ENOMEM, "learned_assign: buffer allocation failed");
     }
-    int rc = mlp_forward(c, m, Xh, n, nullptr, cand, topm);
+    int rc = mlp_forward(c, m, Xh, n, nullptr, cand, topm, 16);
     if (rc == GBKM_OK) {
         e = cudaMemsetAsync(fc, 0, 8, c->stream);
         prof_begin(c, "cand_check");

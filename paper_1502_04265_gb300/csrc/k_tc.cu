@@ -69,6 +69,7 @@ struct Args {
     int32_t *top_idx;
     float *top_val;
     int topm;
+    int topm_group;  // 16: the best center of each 16-center group competes (one per group), else every center
     int *status;
 };
 
@@ -728,6 +729,48 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                             }
                         }
                     } else {
+                        if (a.topm_group == 16) {
+                            // grouped proposal: each aligned group of 16 centers offers its best one
+                            // (lowest index on equal logits), at most one append per lane and group
+#pragma unroll
+                            for (int h = 0; h < W / 16; ++h) {
+                                const int64_t col0 = j0 + 16 * h;
+                                if (col0 >= a.k) break;
+                                float sv[16];
+#pragma unroll
+                                for (int g = 0; g < 4; ++g) {
+                                    const float4 b4 = a.bias ? __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g)
+                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                                    sv[4 * g] = __uint_as_float(r[16 * h + 4 * g]) + b4.x;
+                                    sv[4 * g + 1] = __uint_as_float(r[16 * h + 4 * g + 1]) + b4.y;
+                                    sv[4 * g + 2] = __uint_as_float(r[16 * h + 4 * g + 2]) + b4.z;
+                                    sv[4 * g + 3] = __uint_as_float(r[16 * h + 4 * g + 3]) + b4.w;
+                                }
+#pragma unroll
+                                for (int g = 0; g < 16; ++g)
+                                    if (col0 + g >= a.k) sv[g] = -__int_as_float(0x7f800000);
+                                float m8[8];
+#pragma unroll
+                                for (int g = 0; g < 8; ++g) m8[g] = fmaxf(sv[2 * g], sv[2 * g + 1]);
+                                const float gm = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
+                                                       fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+                                if (gm > tau) {
+                                    uint32_t eq = 0;
+#pragma unroll
+                                    for (int g = 0; g < 16; ++g) eq |= (sv[g] == gm ? 1u : 0u) << g;
+                                    tbv[tcnt] = gm;
+                                    tbi[tcnt] = (int32_t)(col0 + __ffs(eq) - 1);
+                                    ++tcnt;
+                                }
+                                uint32_t fullm = __ballot_sync(0xffffffffu, tcnt == TOPBUF);
+                                while (fullm) {
+                                    const int L = __ffs(fullm) - 1;
+                                    fullm &= fullm - 1;
+                                    compact(L);
+                                }
+                            }
+                            return;
+                        }
                         // top-m: candidates above the row's threshold go to its buffer; a group of 16
                         // costs 16 compares unless some lane of the warp has a candidate in it
 #pragma unroll
@@ -1452,7 +1495,7 @@ int launch_assign_tc_batched(gbkm_ctx *c, int dtype, const void *maps, const BPr
 // A: M x K, B: N x K, row-major BF16, K % 8 == 0, N % 16 == 0, 16-byte aligned.
 int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                         const float *bias, int act, int out_bf16, void *Y, int64_t ldy, float *Ypre, int64_t ldpre,
-                        int32_t *top_idx, float *top_val, int topm) {
+                        int32_t *top_idx, float *top_val, int topm, int group) {
     using namespace tc;
     if (M < 1 || N < 16 || N % 16 || K < 8 || K % 8 || !tc::encode_fn())
         return set_error(c, GBKM_EUNSUPPORTED, "gemm: shape unsupported by the tcgen05 GEMM");
@@ -1472,7 +1515,7 @@ int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, in
     a.idesc = make_idesc(F_BF16, BM, p.bn);
     a.Y = static_cast<float *>(Y), a.ldy = ldy;
     a.bias = bias, a.act = act, a.out_bf16 = out_bf16, a.Ypre = Ypre, a.ldpre = ldpre;
-    a.top_idx = top_idx, a.top_val = top_val, a.topm = topm;
+    a.top_idx = top_idx, a.top_val = top_val, a.topm = topm, a.topm_group = group == 16 ? 16 : 1;
     a.status = c->status;
     if (topk) return launch<F_BF16, E_TOPM>(c, tA, tB, tB, a, p);
     return launch<F_BF16, E_STORE>(c, tA, tB, tB, a, p);

@@ -147,3 +147,21 @@ def test_topm_order_is_rank_order(gb):
     for i in range(n):
         ref = np.lexsort((np.arange(k), -Z[i]))[:m]
         assert np.array_equal(T[i], ref)
+
+
+def test_grouped_proposal_is_best_of_top_groups(gb):
+    """group 16: the best center of each aligned 16-center group competes; the m best offers come
+    back in decreasing logit order (ties by lower index), checked against the GPU's own logits."""
+    d, h, k, n, m = 64, 64, 2048 + 48, 300, 32
+    net = _net(gb, d, h, k, seed=9)
+    Xh = bf(np.random.default_rng(10).normal(size=(n, d)))
+    logits = torch.empty((n, k), dtype=torch.float32, device=DEV)
+    top = torch.empty((n, m), dtype=torch.int32, device=DEV)
+    gb.kmeans_mlp_forward(net, Xh, logits=logits, top_idx=top, topm=m, group=16)
+    Z, T = logits.cpu().numpy(), top.cpu().numpy()
+    for i in range(n):
+        G = Z[i].reshape(-1, 16)
+        best = G.argmax(1) + 16 * np.arange(G.shape[0])   # argmax: first index of the maximum
+        vals = Z[i][best]
+        ref = best[np.lexsort((best, -vals))][:m]
+        assert np.array_equal(T[i], ref)
