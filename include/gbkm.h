@@ -330,12 +330,14 @@ int kmeans_mlp_train_step(gbkm_ctx *ctx, gbkm_mlp *mlp, const void *Xh, const in
 int kmeans_center_separation(gbkm_ctx *ctx, const float *C, int64_t k, int64_t d, float *s2);
 
 /* Assignment step (Section 1) with learned candidates: the MLP proposes topm centers per point
- * (group 16 of kmeans_mlp_forward, in decreasing logit order); their exact FP32 distances are taken in that order until a candidate
- * b has the point certifiably inside the ball of radius s(c_b) (then every other center is strictly
- * farther, so b is the exact label); the points without such a candidate get the full scan of
- * kmeans_assign (FP32).  The labels are therefore those of the exact method.  X: n x d FP32, Xh: its BF16 copy, C: k x d, s2 from
- * kmeans_center_separation; labels: n int32; n_fallback: 1 int64 (device) or NULL; cand_out:
- * n x topm int32 or NULL.  Synchronises once (to size the fallback scan). */
+ * (group 16 of kmeans_mlp_forward, in decreasing logit order); their exact FP32 distances are taken
+ * in that order until a candidate b has the point certifiably inside the ball of radius s(c_b) (then
+ * every other center is strictly farther, so b is the exact label); the points without such a
+ * candidate are gathered and get the full scan of kmeans_assign in its BF16 form, whose certified
+ * near-tie recheck makes its labels exact too.  The labels are therefore those of the exact method.
+ * X: n x d FP32, Xh: its BF16 copy (n x d), C: k x d, s2 from kmeans_center_separation; labels:
+ * n int32; n_fallback: 1 int64 (device) or NULL; cand_out: n x topm int32 or NULL.  Synchronises
+ * once (to size the fallback scan). */
 int kmeans_learned_assign(gbkm_ctx *ctx, const gbkm_mlp *mlp, const float *X, const void *Xh, int64_t n,
                           int64_t d, const float *C, int64_t k, const float *s2, int32_t topm,
                           int32_t *labels, int64_t *n_fallback, int32_t *cand_out);

@@ -178,12 +178,17 @@ __global__ void __launch_bounds__(256) k_cand_check(const float *__restrict__ X,
 
 // gather the fallback rows (list, count on the device) into a contiguous block; rows past the
 // count are left untouched
-__global__ void k_gather_rows(const float *__restrict__ X, int64_t d, const int32_t *__restrict__ list,
-                              const int32_t *__restrict__ count, float *__restrict__ out) {
+// gathers the listed rows of X (FP32) and of its BF16 copy Xh into compact row-major blocks
+__global__ void k_gather_rows(const float *__restrict__ X, const __nv_bfloat16 *__restrict__ Xh, int64_t d,
+                              const int32_t *__restrict__ list, const int32_t *__restrict__ count,
+                              float *__restrict__ out, __nv_bfloat16 *__restrict__ outh) {
     const int64_t r = blockIdx.x;
     if (r >= *count) return;
     const int64_t src = list[r];
-    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) out[r * d + t] = X[src * d + t];
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+        out[r * d + t] = X[src * d + t];
+        outh[r * d + t] = Xh[src * d + t];
+    }
 }
 
 __global__ void k_scatter_labels(const int32_t *__restrict__ sub, const int32_t *__restrict__ list,
@@ -387,18 +392,23 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
         }
         if (rc == GBKM_OK && nf > 0) {
             float *sub = nullptr;
+            __nv_bfloat16 *subh = nullptr;
             int32_t *subl = nullptr;
             e = cudaMallocAsync(&sub, sizeof(float) * (size_t)nf * d, c->stream);
+            if (e == cudaSuccess) e = cudaMallocAsync(&subh, sizeof(__nv_bfloat16) * (size_t)nf * d, c->stream);
             if (e == cudaSuccess) e = cudaMallocAsync(&subl, sizeof(int32_t) * (size_t)nf, c->stream);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 rc = set_error(c, GBKM_ENOMEM, "learned_assign: fallback allocation failed");
             } else {
                 prof_begin(c, "fallback");
-                k_gather_rows<<<(unsigned)nf, 128, 0, c->stream>>>(X, d, fl, fc, sub);
+                k_gather_rows<<<(unsigned)nf, 128, 0, c->stream>>>(X, static_cast<const __nv_bfloat16 *>(Xh), d, fl,
+                                                                   fc, sub, subh);
                 GBKM_LAUNCHED(c);
-                gbkm_assign_opts o = {GBKM_F32, GBKM_ENGINE_AUTO, 1, 0};
-                rc = kmeans_assign(c, sub, nullptr, sub, nullptr, nf, d, C, k, &o, subl, nullptr, nullptr);
+                // BF16 distance GEMM with the certified near-tie recheck: the same exact labels as the
+                // FP32 scan at a fraction of its tensor time
+                gbkm_assign_opts o = {GBKM_BF16, GBKM_ENGINE_AUTO, 1, 0};
+                rc = kmeans_assign(c, subh, nullptr, sub, nullptr, nf, d, C, k, &o, subl, nullptr, nullptr);
                 if (rc == GBKM_OK) {
                     k_scatter_labels<<<(unsigned)ceil_div(nf, 256), 256, 0, c->stream>>>(subl, fl, fc, labels);
                     GBKM_LAUNCHED(c);
@@ -406,6 +416,7 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
                 prof_end(c);
             }
             if (sub) cudaFreeAsync(sub, c->stream);
+            if (subh) cudaFreeAsync(subh, c->stream);
             if (subl) cudaFreeAsync(subl, c->stream);
         }
     }

@@ -31,7 +31,7 @@ constexpr int MAX_DYN_SMEM = 227 * 1024;     // dynamic shared memory a CTA may 
 
 // F_BF16X2: BF16 points against centers split into two BF16 terms (hi + lo), two MMAs per step
 enum Form : int { F_BF16 = 0, F_TF32X3 = 1, F_FP8 = 2, F_TF32 = 3, F_BF16X2 = 4 };
-enum Epi : int { E_ARGMIN = 0, E_STORE = 1, E_TOPM = 2 };
+enum Epi : int { E_ARGMIN = 0, E_STORE = 1, E_TOPM = 2, E_TOPG = 3 };
 constexpr int TOPBUF = 64;  // per-row candidate buffer of the top-m epilogue (shared memory)
 constexpr int TROW = TOPBUF + 1;  // its row stride in floats
 // argmin epilogue shared memory: two groups' band lists, the hand-over slots and their barriers
@@ -69,7 +69,6 @@ struct Args {
     int32_t *top_idx;
     float *top_val;
     int topm;
-    int topm_group;  // 16: the best center of each 16-center group competes (one per group), else every center
     int *status;
 };
 
@@ -378,10 +377,10 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // ---------------------------------------------------------------- the kernel
 // epilogue warpgroups of a k_tc instance: two (each takes half of every chunk's columns) except for
-// the top-m epilogue, whose per-row buffers leave room for one
+// the top-m epilogues, whose per-row buffers leave room for one
 template <int EPI>
 constexpr int epi_groups() {
-    return EPI == E_TOPM ? 1 : 2;
+    return (EPI == E_TOPM || EPI == E_TOPG) ? 1 : 2;
 }
 template <int FORM, int EPI>
 constexpr int tc_threads() {
@@ -728,69 +727,86 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                                 }
                             }
                         }
-                    } else {
-                        if (a.topm_group == 16) {
-                            // grouped proposal: each aligned group of 16 centers offers its best one
-                            // (lowest index on equal logits), at most one append per lane and group
+                    } else if constexpr (EPI == E_TOPG) {
+                        // grouped proposal: each aligned group of 16 centers offers its best one (lowest
+                        // index on equal logits); at most one append per row and group
+                        if (j0 >= a.k) return;
+                        const int jc = (int)j0;
+                        float sv[W];
 #pragma unroll
-                            for (int h = 0; h < W / 16; ++h) {
-                                const int64_t col0 = j0 + 16 * h;
-                                if (col0 >= a.k) break;
-                                float sv[16];
+                        for (int g = 0; g < W; ++g) sv[g] = __uint_as_float(r[g]);
+                        if (a.bias) {
 #pragma unroll
-                                for (int g = 0; g < 4; ++g) {
-                                    const float4 b4 = a.bias ? __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g)
-                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
-                                    sv[4 * g] = __uint_as_float(r[16 * h + 4 * g]) + b4.x;
-                                    sv[4 * g + 1] = __uint_as_float(r[16 * h + 4 * g + 1]) + b4.y;
-                                    sv[4 * g + 2] = __uint_as_float(r[16 * h + 4 * g + 2]) + b4.z;
-                                    sv[4 * g + 3] = __uint_as_float(r[16 * h + 4 * g + 3]) + b4.w;
-                                }
-#pragma unroll
-                                for (int g = 0; g < 16; ++g)
-                                    if (col0 + g >= a.k) sv[g] = -__int_as_float(0x7f800000);
-                                float m8[8];
-#pragma unroll
-                                for (int g = 0; g < 8; ++g) m8[g] = fmaxf(sv[2 * g], sv[2 * g + 1]);
-                                const float gm = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
-                                                       fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
-                                if (gm > tau) {
-                                    uint32_t eq = 0;
-#pragma unroll
-                                    for (int g = 0; g < 16; ++g) eq |= (sv[g] == gm ? 1u : 0u) << g;
-                                    tbv[tcnt] = gm;
-                                    tbi[tcnt] = (int32_t)(col0 + __ffs(eq) - 1);
-                                    ++tcnt;
-                                }
-                                uint32_t fullm = __ballot_sync(0xffffffffu, tcnt == TOPBUF);
-                                while (fullm) {
-                                    const int L = __ffs(fullm) - 1;
-                                    fullm &= fullm - 1;
-                                    compact(L);
-                                }
+                            for (int g = 0; g < W / 4; ++g) {
+                                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(a.bias + jc) + g);
+                                sv[4 * g] += b4.x, sv[4 * g + 1] += b4.y, sv[4 * g + 2] += b4.z, sv[4 * g + 3] += b4.w;
                             }
-                            return;
                         }
-                        // top-m: candidates above the row's threshold go to its buffer; a group of 16
-                        // costs 16 compares unless some lane of the warp has a candidate in it
+                        if (j0 + W > a.k) {
+#pragma unroll
+                            for (int g = 0; g < W; ++g)
+                                if (jc + g >= (int)a.k) sv[g] = -__int_as_float(0x7f800000);
+                        }
+                        // a row whose buffer lacks room for this unit's offers is cut first
+                        uint32_t fullm = __ballot_sync(0xffffffffu, tcnt > TOPBUF - W / 16);
+                        while (fullm) {
+                            const int L = __ffs(fullm) - 1;
+                            fullm &= fullm - 1;
+                            compact(L);
+                        }
+                        float gm[W / 16];
 #pragma unroll
                         for (int h = 0; h < W / 16; ++h) {
-                            const int64_t col0 = j0 + 16 * h;
-                            if (col0 >= a.k) break;
+                            const float *u = sv + 16 * h;
+                            const float m0 = fmaxf(fmaxf(u[0], u[1]), fmaxf(u[2], u[3]));
+                            const float m1 = fmaxf(fmaxf(u[4], u[5]), fmaxf(u[6], u[7]));
+                            const float m2 = fmaxf(fmaxf(u[8], u[9]), fmaxf(u[10], u[11]));
+                            const float m3 = fmaxf(fmaxf(u[12], u[13]), fmaxf(u[14], u[15]));
+                            gm[h] = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+                        }
+                        float gx = gm[0];
+#pragma unroll
+                        for (int h = 1; h < W / 16; ++h) gx = fmaxf(gx, gm[h]);
+                        if (gx > tau) {
+#pragma unroll
+                            for (int h = 0; h < W / 16; ++h) {
+                                if (gm[h] > tau) {
+                                    uint32_t eq = 0;
+#pragma unroll
+                                    for (int g = 0; g < 16; ++g) eq |= (sv[16 * h + g] == gm[h] ? 1u : 0u) << g;
+                                    tbv[tcnt] = gm[h];
+                                    tbi[tcnt] = jc + 16 * h + __ffs(eq) - 1;
+                                    ++tcnt;
+                                }
+                            }
+                        }
+                    } else {
+                        // exact top-m: candidates above the row's threshold go to its buffer; a group of
+                        // 16 costs 16 compares unless some lane of the warp has a candidate in it
+                        if (j0 >= a.k) return;
+                        const int jc = (int)j0;
+#pragma unroll
+                        for (int h = 0; h < W / 16; ++h) {
+                            const int col0 = jc + 16 * h;
+                            if (col0 >= (int)a.k) break;
                             float sv[16];
 #pragma unroll
-                            for (int g = 0; g < 4; ++g) {
-                                const float4 b4 = a.bias ? __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g)
-                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-                                sv[4 * g] = __uint_as_float(r[16 * h + 4 * g]) + b4.x;
-                                sv[4 * g + 1] = __uint_as_float(r[16 * h + 4 * g + 1]) + b4.y;
-                                sv[4 * g + 2] = __uint_as_float(r[16 * h + 4 * g + 2]) + b4.z;
-                                sv[4 * g + 3] = __uint_as_float(r[16 * h + 4 * g + 3]) + b4.w;
+                            for (int g = 0; g < 16; ++g) sv[g] = __uint_as_float(r[16 * h + g]);
+                            if (a.bias) {
+#pragma unroll
+                                for (int g = 0; g < 4; ++g) {
+                                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(a.bias + col0) + g);
+                                    sv[4 * g] += b4.x, sv[4 * g + 1] += b4.y, sv[4 * g + 2] += b4.z, sv[4 * g + 3] += b4.w;
+                                }
+                            }
+                            if (col0 + 16 > (int)a.k) {
+#pragma unroll
+                                for (int g = 0; g < 16; ++g)
+                                    if (col0 + g >= (int)a.k) sv[g] = -__int_as_float(0x7f800000);
                             }
                             uint32_t msk = 0;
 #pragma unroll
-                            for (int g = 0; g < 16; ++g)
-                                if (sv[g] > tau && col0 + g < a.k) msk |= 1u << g;
+                            for (int g = 0; g < 16; ++g) msk |= (sv[g] > tau ? 1u : 0u) << g;
                             uint32_t any = __reduce_or_sync(0xffffffffu, msk);
                             while (any) {
                                 const int g = __ffs(any) - 1;
@@ -805,7 +821,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                                 }
                                 if (want && sg > tau) {
                                     tbv[tcnt] = sg;
-                                    tbi[tcnt] = (int32_t)(col0 + g);
+                                    tbi[tcnt] = col0 + g;
                                     ++tcnt;
                                 }
                             }
@@ -819,18 +835,24 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                     int c = c_begin;
                     // 32-column units, except 16 for 3xTF32 (its 512-thread CTA leaves 128 registers)
                     constexpr int UW = X3 ? 16 : 32;
+                    // (the grouped top-m epilogue runs on chunk widths that are multiples of 32)
+                    constexpr bool ONLY32 = EPI == E_TOPG;
                     auto load = [&](uint32_t (&r)[32], int cc) {
-                        if (UW == 32 && c_end - cc >= 32)
+                        if (ONLY32 || (UW == 32 && c_end - cc >= 32))
                             tmem_ld32(tbase + (uint32_t)cc, r);
                         else
                             tmem_ld16_into32(tbase + (uint32_t)cc, r);
                     };
                     auto run = [&](const uint32_t (&r)[32], int cc) {
-                        if (UW == 32 && c_end - cc >= 32) {
+                        if constexpr (ONLY32) {
                             process(r, cc);
                         } else {
-                            const uint32_t(&r16)[16] = *reinterpret_cast<const uint32_t(*)[16]>(&r[0]);
-                            process(r16, cc);
+                            if (UW == 32 && c_end - cc >= 32) {
+                                process(r, cc);
+                            } else {
+                                const uint32_t(&r16)[16] = *reinterpret_cast<const uint32_t(*)[16]>(&r[0]);
+                                process(r16, cc);
+                            }
                         }
                     };
                     if (c < c_end) {
@@ -933,7 +955,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                     }
                 }
             }
-            if constexpr (EPI == E_TOPM) {
+            if constexpr (EPI == E_TOPM || EPI == E_TOPG) {
                 // every row of the warp in turn: its m best in rank order, -1 padding
                 for (int L = 0; L < 32; ++L) {
                     const int64_t rowL = (int64_t)tile * BM + q * 32 + L;
@@ -1295,11 +1317,11 @@ struct Plan {
     size_t smem;
 };
 
-static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra_smem = 0) {
+static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra_smem = 0, int bn_align = 16) {
     Plan p;
     const int esize = (form == F_BF16 || form == F_BF16X2) ? 2 : (form == F_FP8 ? 1 : 4);
     p.n_chunks = (int)ceil_div(k_pad, bn_cap);
-    p.bn = (int)(ceil_div(ceil_div(k_pad, p.n_chunks), 16) * 16);
+    p.bn = (int)(ceil_div(ceil_div(k_pad, p.n_chunks), bn_align) * bn_align);
     p.kb = (int)ceil_div(d * esize, 128);
     const bool x3 = form == F_TF32X3, two_b = x3 || form == F_BF16X2;
     p.a_bytes = BM * 128;
@@ -1502,7 +1524,8 @@ int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, in
     const bool topk = top_idx != nullptr;
     if (topk && (topm < 1 || topm > TOPBUF / 2)) return set_error(c, GBKM_EINVAL, "gemm: topm must be in [1, 32]");
     const int extra = topk ? TROW * 128 * 8 : 0;
-    const Plan p = plan(F_BF16, K, N, 256, extra);
+    const bool grouped = topk && group == 16;
+    const Plan p = plan(F_BF16, K, N, 256, extra, grouped ? 32 : 16);
     CUtensorMap tA, tB;
     if (!make_tmap(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, (uint64_t)K, (uint64_t)M, 2, BM) ||
         !make_tmap(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, (uint64_t)K, (uint64_t)N, 2, (uint32_t)p.bn))
@@ -1515,8 +1538,9 @@ int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, in
     a.idesc = make_idesc(F_BF16, BM, p.bn);
     a.Y = static_cast<float *>(Y), a.ldy = ldy;
     a.bias = bias, a.act = act, a.out_bf16 = out_bf16, a.Ypre = Ypre, a.ldpre = ldpre;
-    a.top_idx = top_idx, a.top_val = top_val, a.topm = topm, a.topm_group = group == 16 ? 16 : 1;
+    a.top_idx = top_idx, a.top_val = top_val, a.topm = topm;
     a.status = c->status;
+    if (grouped) return launch<F_BF16, E_TOPG>(c, tA, tB, tB, a, p);
     if (topk) return launch<F_BF16, E_TOPM>(c, tA, tB, tB, a, p);
     return launch<F_BF16, E_STORE>(c, tA, tB, tB, a, p);
 }
