@@ -754,31 +754,26 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                             fullm &= fullm - 1;
                             compact(L);
                         }
-                        float gm[W / 16];
+                        // per group: its maximum and the lowest index holding it (the first quad whose
+                        // maximum equals it, then the first entry of that quad), then a branch-free
+                        // append: the entry is written at the buffer's end and kept if it beats tau
 #pragma unroll
                         for (int h = 0; h < W / 16; ++h) {
                             const float *u = sv + 16 * h;
-                            const float m0 = fmaxf(fmaxf(u[0], u[1]), fmaxf(u[2], u[3]));
-                            const float m1 = fmaxf(fmaxf(u[4], u[5]), fmaxf(u[6], u[7]));
-                            const float m2 = fmaxf(fmaxf(u[8], u[9]), fmaxf(u[10], u[11]));
-                            const float m3 = fmaxf(fmaxf(u[12], u[13]), fmaxf(u[14], u[15]));
-                            gm[h] = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
-                        }
-                        float gx = gm[0];
+                            float mq[4];
 #pragma unroll
-                        for (int h = 1; h < W / 16; ++h) gx = fmaxf(gx, gm[h]);
-                        if (gx > tau) {
+                            for (int t = 0; t < 4; ++t)
+                                mq[t] = fmaxf(fmaxf(u[4 * t], u[4 * t + 1]), fmaxf(u[4 * t + 2], u[4 * t + 3]));
+                            const float gm = fmaxf(fmaxf(mq[0], mq[1]), fmaxf(mq[2], mq[3]));
+                            const int qt = mq[0] == gm ? 0 : (mq[1] == gm ? 1 : (mq[2] == gm ? 2 : 3));
+                            float e0 = u[0], e1 = u[1], e2 = u[2];
 #pragma unroll
-                            for (int h = 0; h < W / 16; ++h) {
-                                if (gm[h] > tau) {
-                                    uint32_t eq = 0;
-#pragma unroll
-                                    for (int g = 0; g < 16; ++g) eq |= (sv[16 * h + g] == gm[h] ? 1u : 0u) << g;
-                                    tbv[tcnt] = gm[h];
-                                    tbi[tcnt] = jc + 16 * h + __ffs(eq) - 1;
-                                    ++tcnt;
-                                }
-                            }
+                            for (int t = 1; t < 4; ++t)
+                                if (qt == t) e0 = u[4 * t], e1 = u[4 * t + 1], e2 = u[4 * t + 2];
+                            const int et = e0 == gm ? 0 : (e1 == gm ? 1 : (e2 == gm ? 2 : 3));
+                            tbv[tcnt] = gm;
+                            tbi[tcnt] = jc + 16 * h + 4 * qt + et;
+                            tcnt += gm > tau ? 1 : 0;
                         }
                     } else {
                         // exact top-m: candidates above the row's threshold go to its buffer; a group of
