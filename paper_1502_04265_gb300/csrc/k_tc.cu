@@ -678,9 +678,15 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                                 for (int g = 0; g < W; ++g) ms[g] = (j0 + g < a.k_pad) ? -2.f * sx * a.cscale[j0 + g] : -2.f;
                             }
                         }
+                        if (j0 + W <= a.k) {
 #pragma unroll
-                        for (int g = 0; g < W; ++g)
-                            sc[g] = (j0 + g < a.k) ? fmaf(ms[g], __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
+                            for (int g = 0; g < W; ++g) sc[g] = fmaf(ms[g], __uint_as_float(r[g]), cn[g]);
+                        } else {
+                            const int kr = (int)(a.k - j0);  // real centers in this unit (< W)
+#pragma unroll
+                            for (int g = 0; g < W; ++g)
+                                sc[g] = g < kr ? fmaf(ms[g], __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
+                        }
                         band.group(sc, (int)j0);
                     } else if constexpr (EPI == E_STORE) {
                         if (valid && j0 < a.k) {
@@ -1205,8 +1211,9 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                 auto process = [&](const uint32_t (&r)[16], int c) {
                     const int64_t j0 = (int64_t)nc * P.bn + c;  // column among all seeds' centers
                     if (j0 >= ncols) return;
-                    const int s = (int)(j0 / P.kps);
-                    const int jl0 = (int)(j0 - (int64_t)s * P.kps);
+                    const int kps = (int)P.kps;
+                    const int s = (int)j0 / kps;
+                    const int jl0 = (int)j0 - s * kps;
                     if (s != cur) {
                         finish(cur);
                         cur = s;
@@ -1218,9 +1225,14 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                         const float4 t4 = __ldg(reinterpret_cast<const float4 *>(P.cnorm + j0) + g);
                         cn[4 * g] = t4.x, cn[4 * g + 1] = t4.y, cn[4 * g + 2] = t4.z, cn[4 * g + 3] = t4.w;
                     }
+                    if (jl0 + 16 <= P.k) {
 #pragma unroll
-                    for (int g = 0; g < 16; ++g)
-                        sc[g] = (jl0 + g < P.k) ? fmaf(-2.f, __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
+                        for (int g = 0; g < 16; ++g) sc[g] = fmaf(-2.f, __uint_as_float(r[g]), cn[g]);
+                    } else {
+#pragma unroll
+                        for (int g = 0; g < 16; ++g)
+                            sc[g] = (jl0 + g < P.k) ? fmaf(-2.f, __uint_as_float(r[g]), cn[g]) : __int_as_float(0x7f800000);
+                    }
                     band.group(sc, jl0);
                 };
                 uint32_t ra[16], rb[16];
