@@ -240,13 +240,13 @@ __global__ void __launch_bounds__(SCAN_T) k_items(const int32_t *__restrict__ st
 // point of the same cluster, so the shifted values are of the size of the cluster's spread):
 // S'_c = sum w (x - s_j), Q'_c = sum w ||x - s_j||^2, N_c = sum w.  Every FP32 cancellation is
 // therefore bounded by the cluster's own scatter; k_finalize moves the cluster's sums to other
-// references exactly.  Each thread keeps 8 row loads in flight (row offsets staged in shared
-// memory, the tail padded with the reference row at weight 0), sums S over 8-row blocks and Q
+// references exactly.  Each thread keeps 16 row loads in flight (row offsets staged in shared
+// memory, the tail padded with the reference row at weight 0), sums S over 16-row blocks and Q
 // over 4-row blocks in FP32 and adds every block into a double-float accumulator (error-free
 // TwoSum); the G = 256 / tpr row groups are combined in double-float in group order.  The item's
 // S' is stored as (hi, lo) float pairs, its N and Q' in FP64.  Small items (R = 128 rows) keep
 // every SM busy to the end.
-constexpr int SEG_UNROLL = 8;
+constexpr int SEG_UNROLL = 16;
 
 __device__ __forceinline__ DF df_add(DF a, DF b) {
     float s, e;
@@ -533,8 +533,9 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
 }
 
 // the update pipeline on a workspace block of P.bytes bytes; returns the number of launches
-// (or -1 on a CUDA error, left in cudaGetLastError)
-static int update_run(cudaStream_t st, int *status, void *ws, const UpdatePlan &P, const float *X,
+// (or -1 on a CUDA error, left in cudaGetLastError).  With a context, the segmented sums are
+// timed as the part "segsum" of the caller's "update" bracket.
+static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const UpdatePlan &P, const float *X,
                       int64_t n, int64_t d, const float *w, const int32_t *labels, int64_t k,
                       const float *C_old, float *C_new, double *counts, double *cost_old,
                       double *cost_new, int64_t *n_empty) {
@@ -564,6 +565,7 @@ static int update_run(cudaStream_t st, int *status, void *ws, const UpdatePlan &
     k_items<<<1, SCAN_T, 0, st>>>(start, k, CHUNK_R, item_start);
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const unsigned items = (unsigned)P.items_max;
+    if (c) prof_begin(c, "segsum");
     if (vec && w)
         k_segsum<4, true><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
     else if (vec)
@@ -572,6 +574,7 @@ static int update_run(cudaStream_t st, int *status, void *ws, const UpdatePlan &
         k_segsum<1, true><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
     else
         k_segsum<1, false><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+    if (c) prof_end(c);
     k_finalize<<<dim3((unsigned)k, (unsigned)P.ncb), 256, 0, st>>>(part, part_nq, X, perm, start, d, k,
                                                                   item_start, C_old, C_new, counts, terms,
                                                                   terms + 2 * k);
@@ -586,7 +589,7 @@ int update_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, P.bytes, &rc);
     if (!ws) return rc;
-    const int nl = update_run(c->stream, c->status, ws, P, X, n, d, w, labels, k, C_old, C_new, counts,
+    const int nl = update_run(c, c->stream, c->status, ws, P, X, n, d, w, labels, k, C_old, C_new, counts,
                               cost_old, cost_new, n_empty);
     if (nl < 0) return cuda_check(c, cudaGetLastError(), "update launch");
     c->launches += nl;
@@ -638,7 +641,7 @@ extern "C" int kmeans_update_noalloc(void *cuda_stream, const float *X, int64_t 
     }
     int *label_check = static_cast<int *>(base);
     void *ws = static_cast<char *>(base) + 256;
-    const int nl = gbkm::update_run((cudaStream_t)cuda_stream, label_check, ws, P, X, n, d, w, labels,
+    const int nl = gbkm::update_run(nullptr, (cudaStream_t)cuda_stream, label_check, ws, P, X, n, d, w, labels,
                                     k, C_old, C_new, counts, cost_old, cost_new, n_empty);
     if (nl < 0) {
         cudaGetLastError();
