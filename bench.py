@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--workload", default="highdim", choices=list(METRICS))
     ap.add_argument("--form", default="auto", choices=["auto", "f32", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tcgen05"])
+    ap.add_argument("--center-terms", type=int, default=1, choices=[1, 2],
+                    help="BF16 form: centers as one BF16 term, or two (head + tail, a narrower certified band)")
     ap.add_argument("--n", type=int, default=None, help="override n (highdim / learned)")
     ap.add_argument("--d", type=int, default=None, help="override d (highdim)")
     ap.add_argument("--k", type=int, default=None, help="override k (highdim)")
@@ -322,7 +324,7 @@ def gen_pool(jobs, fn, workers=None):
     return ex, [ex.submit(fn, j) for j in jobs]
 
 
-def lloyd_timed(env, X, Xop, scales, xnorm, C0, compute, engine, steps, warmup, clocks=False):
+def lloyd_timed(env, X, Xop, scales, xnorm, C0, compute, engine, steps, warmup, clocks=False, center_terms=1):
     """`warmup` + `steps` Lloyd iterations from C0 (assign + update per step); the timed steps'
     ms, launches, profile, the FP64 cost trace and recheck counts."""
     torch, B = env.torch, env.B
@@ -334,7 +336,7 @@ def lloyd_timed(env, X, Xop, scales, xnorm, C0, compute, engine, steps, warmup, 
 
     def step(i):
         B.kmeans_assign(X, Cs[0], Xop=Xop, Xop_scales=scales, xnorm=xnorm, compute=compute, engine=engine,
-                        labels=labels, n_rechecked=nre[i:i + 1], ctx=env.ctx)
+                        labels=labels, n_rechecked=nre[i:i + 1], center_terms=center_terms, ctx=env.ctx)
         B.kmeans_update(X, labels, Cs[0], C_new=Cs[1], cost_old=cost[i, 0:1], cost_new=cost[i, 1:2], ctx=env.ctx)
         Cs.reverse()
 
@@ -452,7 +454,8 @@ def run_highdim(env, args):
         form = "f32"
     ctx.sync()
 
-    R = lloyd_timed(env, Xg, Xop, None, xnorm, C0, form, engine, args.steps, args.warmup, clocks=True)
+    R = lloyd_timed(env, Xg, Xop, None, xnorm, C0, form, engine, args.steps, args.warmup, clocks=True,
+                    center_terms=args.center_terms if form == "bf16" else 1)
     ms, prof = R["ms"], R["prof"]
     value = env.world * F / (ms * 1e-3) / 1e9
     peaks = env.peaks
@@ -561,7 +564,8 @@ def run_highdim(env, args):
 
     line = base_line(env, "highdim", value, ms, args.steps, args.warmup, form, {
         "workload": f"gaussian mixture n={n} d={d} k={k} ({k} components, seed = rank), one Lloyd iteration "
-                    f"per step", "form": form, "engine": engine,
+                    f"per step", "form": form + ("x2 (two-term centers)" if form == "bf16" and args.center_terms == 2 else ""),
+        "engine": engine,
         "l2": "inputs larger than L2 (X is 819 MB FP32 / 410 MB BF16)",
         "parallelism": "replicas" if env.world > 1 else "single GPU"})
     line.update({"roofline": roof, "rooflines": rooflines, "step_roofline": step_roof, "pipeline": pipeline,
@@ -708,7 +712,8 @@ def run_stream(env_args):
     ctx.sync()
 
     F = 2.0 * n * k * r + n * r
-    R = lloyd_timed(env, Y, Yb, None, yn, C0, "bf16", args.engine, args.steps, args.warmup, clocks=True)
+    R = lloyd_timed(env, Y, Yb, None, yn, C0, "bf16", args.engine, args.steps, args.warmup, clocks=True,
+                    center_terms=args.center_terms)
     ms, prof = R["ms"], R["prof"]
     value = env.world * F / (ms * 1e-3) / 1e9
     peaks = env.peaks

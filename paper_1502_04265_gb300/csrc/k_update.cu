@@ -240,13 +240,13 @@ __global__ void __launch_bounds__(SCAN_T) k_items(const int32_t *__restrict__ st
 // point of the same cluster, so the shifted values are of the size of the cluster's spread):
 // S'_c = sum w (x - s_j), Q'_c = sum w ||x - s_j||^2, N_c = sum w.  Every FP32 cancellation is
 // therefore bounded by the cluster's own scatter; k_finalize moves the cluster's sums to other
-// references exactly.  Each thread keeps 16 row loads in flight (row offsets staged in shared
-// memory, the tail padded with the reference row at weight 0), sums S over 16-row blocks and Q
-// over 4-row blocks in FP32 and adds every block into a double-float accumulator (error-free
+// references exactly.  Each thread keeps UNR row loads in flight (16 when the G row groups times 16
+// rows do not exceed an item, else 8; row offsets staged in shared memory, the tail padded with the
+// reference row at weight 0), sums S over UNR-row blocks and Q over 4-row blocks in FP32 and adds
+// every block into a double-float accumulator (error-free
 // TwoSum); the G = 256 / tpr row groups are combined in double-float in group order.  The item's
 // S' is stored as (hi, lo) float pairs, its N and Q' in FP64.  Small items (R = 128 rows) keep
 // every SM busy to the end.
-constexpr int SEG_UNROLL = 16;
 
 __device__ __forceinline__ DF df_add(DF a, DF b) {
     float s, e;
@@ -256,7 +256,7 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return a;
 }
 
-template <int VW, bool WEIGHTED>
+template <int VW, bool WEIGHTED, int SEG_UNROLL>
 __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int64_t d,
                                                 const float *__restrict__ w,
                                                 const int32_t *__restrict__ perm,
@@ -532,6 +532,16 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     return P;
 }
 
+template <int VW, bool WEIGHTED>
+static void launch_segsum(bool u16, unsigned items, cudaStream_t st, const float *X, int64_t d, const float *w,
+                          const int32_t *perm, const int32_t *start, const int32_t *item_start, int64_t k,
+                          float2 *part, double *part_nq) {
+    if (u16)
+        k_segsum<VW, WEIGHTED, 16><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+    else
+        k_segsum<VW, WEIGHTED, 8><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+}
+
 // the update pipeline on a workspace block of P.bytes bytes; returns the number of launches
 // (or -1 on a CUDA error, left in cudaGetLastError).  With a context, the segmented sums are
 // timed as the part "segsum" of the caller's "update" bracket.
@@ -565,15 +575,21 @@ static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const
     k_items<<<1, SCAN_T, 0, st>>>(start, k, CHUNK_R, item_start);
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const unsigned items = (unsigned)P.items_max;
+    // 16 loads in flight per thread unless the row groups of the narrowest column pass would then
+    // pad an item beyond its 128 rows
+    const int64_t ncv = vec ? d / 4 : d, last_pass = ncv - ((ncv - 1) / 256) * 256;
+    int64_t tpr = 1;
+    while (tpr < last_pass) tpr <<= 1;
+    const bool u16 = (256 / tpr) * 16 <= CHUNK_R;
     if (c) prof_begin(c, "segsum");
     if (vec && w)
-        k_segsum<4, true><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+        launch_segsum<4, true>(u16, items, st, X, d, w, perm, start, item_start, k, part, part_nq);
     else if (vec)
-        k_segsum<4, false><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+        launch_segsum<4, false>(u16, items, st, X, d, w, perm, start, item_start, k, part, part_nq);
     else if (w)
-        k_segsum<1, true><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+        launch_segsum<1, true>(u16, items, st, X, d, w, perm, start, item_start, k, part, part_nq);
     else
-        k_segsum<1, false><<<items, 256, 0, st>>>(X, d, w, perm, start, item_start, k, CHUNK_R, part, part_nq);
+        launch_segsum<1, false>(u16, items, st, X, d, w, perm, start, item_start, k, part, part_nq);
     if (c) prof_end(c);
     k_finalize<<<dim3((unsigned)k, (unsigned)P.ncb), 256, 0, st>>>(part, part_nq, X, perm, start, d, k,
                                                                   item_start, C_old, C_new, counts, terms,
