@@ -3,15 +3,16 @@
 // Pipeline (all on the context's stream, no host synchronisation, no float atomics):
 //   1. k_hist      one warp per label segment: warp-aggregated (match_any) label histogram,
 //                  column s of the cluster-major table hist[j * S + s]
-//   2. scan        exclusive scan of the table -> stable output slot of every (cluster, segment)
-//   3. k_starts    first slot of every cluster
-//   4. k_scatter   one warp per segment: stable rank inside the warp + running slot -> perm
-//   5. k_items     chunks of R rows per cluster, exclusive scan -> work-item table
-//   6. k_segsum    one CTA per chunk of 128 rows: sums of w (x - s), w, w ||x - s||^2 with s the
+//   2. offsets     k <= 2048 (per-warp tables in shared memory): k_row_scan, one warp per cluster
+//                  scanning its row, the last CTA deriving the cluster starts and the work items;
+//                  otherwise a device-wide exclusive scan of the table, k_starts and k_items
+//   3. k_scatter   one warp per segment: stable rank inside the warp + running slot -> perm
+//                  (work items: chunks of R rows per cluster, item_start = their exclusive scan)
+//   4. k_segsum    one CTA per chunk of 128 rows: sums of w (x - s), w, w ||x - s||^2 with s the
 //                  cluster's first row -> FP64 partials
-//   7. k_finalize  one CTA per (cluster, 256 columns): FP64 sums of the partials in chunk order,
+//   5. k_finalize  one CTA per (cluster, 256 columns): FP64 sums of the partials in chunk order,
 //                  centroid and CF cost terms
-//   8. k_final     one CTA: FP64 totals in cluster order
+//   6. k_final     one CTA: FP64 totals in cluster order
 #include <mutex>
 
 #include "internal.cuh"
@@ -83,9 +84,10 @@ __global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ lab
 // (no clearing pass needed).
 __global__ void __launch_bounds__(256) k_hist_sm(const int32_t *__restrict__ labels, int64_t n, int64_t k,
                                                  int64_t R, int64_t S, int32_t *__restrict__ hist,
-                                                 int *status) {
+                                                 int *status, int32_t *__restrict__ ticket) {
     extern __shared__ int32_t hsm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;  // for k_row_scan, which runs next
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (s >= S) return;
     volatile int32_t *mine = hsm + (int64_t)wib * k;
@@ -117,13 +119,13 @@ __global__ void __launch_bounds__(256) k_hist_sm(const int32_t *__restrict__ lab
 
 __global__ void __launch_bounds__(256) k_scatter_sm(const int32_t *__restrict__ labels, int64_t n, int64_t k,
                                                     int64_t R, int64_t S, const int32_t *__restrict__ off,
-                                                    int32_t *__restrict__ perm) {
+                                                    const int32_t *__restrict__ start, int32_t *__restrict__ perm) {
     extern __shared__ int32_t hsm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (s >= S) return;
     volatile int32_t *mine = hsm + (int64_t)wib * k;
-    for (int64_t j = lane; j < k; j += 32) mine[j] = off[j * S + s];
+    for (int64_t j = lane; j < k; j += 32) mine[j] = start[j] + off[j * S + s];
     __syncwarp();
     const int64_t r0 = s * R, r1 = min(n, r0 + R);
     for (int64_t base = r0; base < r1; base += 32 * HIST_PF) {
@@ -232,6 +234,77 @@ __global__ void __launch_bounds__(SCAN_T) k_items(const int32_t *__restrict__ st
         run += (int32_t)((start[j + 1] - start[j] + R - 1) / R);
     }
     if (threadIdx.x == 0) item_start[k] = total;
+}
+
+// Offsets of the shared-memory path in one launch: one warp per cluster j scans its row of the
+// table, off[j, s] = sum_{s' < s} hist[j, s'] (relative to the cluster's first slot), and stores
+// the row total cnt[j]; the last CTA to finish (atomic ticket, zeroed by k_hist_sm) turns the
+// totals into start[] (exclusive scan over clusters, start[k] = valid rows) and item_start[]
+// (work items of R rows per cluster, item_start[k] = total).  No CTA waits for another.
+constexpr int ROWSCAN_U = 8;  // table entries per lane loaded together
+__global__ void __launch_bounds__(256) k_row_scan(const int32_t *__restrict__ hist, int64_t k, int64_t S,
+                                                  int64_t R, int32_t *__restrict__ off, int32_t *cnt,
+                                                  int32_t *__restrict__ start, int32_t *__restrict__ item_start,
+                                                  int32_t *ticket) {
+    __shared__ int32_t sh[32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (j < k) {
+        const int32_t *h = hist + j * S;
+        int32_t *o = off + j * S;
+        int32_t run = 0;
+        for (int64_t s0 = 0; s0 < S; s0 += 32 * ROWSCAN_U) {
+            int32_t v[ROWSCAN_U];
+#pragma unroll
+            for (int u = 0; u < ROWSCAN_U; ++u) {
+                const int64_t sx = s0 + u * 32 + lane;
+                v[u] = sx < S ? h[sx] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < ROWSCAN_U; ++u) {
+                int32_t x = v[u];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                    if (lane >= d) x += y;
+                }
+                const int64_t sx = s0 + u * 32 + lane;
+                if (sx < S) o[sx] = run + x - v[u];
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        if (lane == 0) cnt[j] = run;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const volatile int32_t *vc = cnt;
+    const int64_t per = (k + blockDim.x - 1) / blockDim.x;
+    const int64_t j0 = (int64_t)threadIdx.x * per, j1 = min(k, j0 + per);
+    int32_t rows = 0, items = 0;
+    for (int64_t q = j0; q < j1; ++q) {
+        const int32_t c = vc[q];
+        rows += c;
+        items += (int32_t)((c + R - 1) / R);
+    }
+    int32_t total_rows, total_items;
+    int32_t r0 = block_excl_scan(rows, sh, total_rows);
+    int32_t i0 = block_excl_scan(items, sh, total_items);
+    for (int64_t q = j0; q < j1; ++q) {
+        const int32_t c = vc[q];
+        start[q] = r0;
+        item_start[q] = i0;
+        r0 += c;
+        i0 += (int32_t)((c + R - 1) / R);
+    }
+    if (threadIdx.x == 0) {
+        start[k] = total_rows;
+        item_start[k] = total_items;
+    }
 }
 
 // ---------------------------------------------------------------- segmented CF sums
@@ -409,7 +482,8 @@ __global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ par
                                                   const float *__restrict__ C_old, float *__restrict__ C_new,
                                                   double *__restrict__ counts, double *__restrict__ nq,
                                                   double *__restrict__ blk) {
-    __shared__ double sh[256];
+    __shared__ double sh[3 * 256];
+    __shared__ double inv_s;
     const int64_t j = blockIdx.x, cb = blockIdx.y;
     const int32_t i0 = item_start[j], i1 = item_start[j + 1];
     double n_part = 0.0, q_part = 0.0;
@@ -418,6 +492,10 @@ __global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ par
         if (cb == 0) q_part += part_nq[(int64_t)it * 2 + 1];
     }
     const double N = block_tree_sum_d(n_part, sh);
+    // one FP64 reciprocal per CTA (FP64 division is a long sequence on the slow FP64 pipe)
+    if (threadIdx.x == 0) inv_s = N > 0.0 ? 1.0 / N : 0.0;
+    __syncthreads();
+    const double invN = inv_s;
     double a_old = 0.0, b_sq = 0.0;
     const int64_t t = cb * 256 + threadIdx.x;
     if (t < d) {
@@ -448,15 +526,27 @@ __global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ par
             const double e = sref - (double)co;
             a_old = 2.0 * e * Sp + N * e * e;
             b_sq = Sp * Sp;
-            C_new[j * d + t] = (float)(sref + Sp / N);
+            C_new[j * d + t] = (float)(sref + Sp * invN);
         } else {
             C_new[j * d + t] = co;
         }
     }
-    const double at = block_tree_sum_d(a_old, sh);
-    const double bt = block_tree_sum_d(b_sq, sh);
+    // the three block sums in one tree (fixed order)
+    sh[threadIdx.x] = a_old;
+    sh[256 + threadIdx.x] = b_sq;
+    sh[512 + threadIdx.x] = q_part;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+            sh[256 + threadIdx.x] += sh[256 + threadIdx.x + o];
+            if (cb == 0) sh[512 + threadIdx.x] += sh[512 + threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const double at = sh[0], bt = sh[256];
     if (cb == 0) {
-        const double Q = block_tree_sum_d(q_part, sh);
+        const double Q = sh[512];
         if (threadIdx.x == 0) {
             if (counts) counts[j] = N;
             nq[j * 2] = N;
@@ -503,7 +593,7 @@ __global__ void __launch_bounds__(256) k_final(const double *__restrict__ nq, co
 struct UpdatePlan {
     int64_t R, S, L, nbs, items_max, ncb;
     bool smem_hist;
-    size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_nq, o_terms, bytes;
+    size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_nq, o_terms, o_cnt, o_ticket, bytes;
 };
 
 static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
@@ -528,6 +618,8 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     P.o_part = p.take<float2>(P.items_max * d);
     P.o_nq = p.take<double>(P.items_max * 2);
     P.o_terms = p.take<double>(k * (2 + 2 * P.ncb));
+    P.o_cnt = p.take<int32_t>(k);
+    P.o_ticket = p.take<int32_t>(1);
     P.bytes = p.off;
     return P;
 }
@@ -551,7 +643,8 @@ static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const
                       double *cost_new, int64_t *n_empty) {
     int32_t *hist = ws_at<int32_t>(ws, P.o_hist), *off = ws_at<int32_t>(ws, P.o_off),
             *bsum = ws_at<int32_t>(ws, P.o_bsum), *start = ws_at<int32_t>(ws, P.o_start),
-            *item_start = ws_at<int32_t>(ws, P.o_items), *perm = ws_at<int32_t>(ws, P.o_perm);
+            *item_start = ws_at<int32_t>(ws, P.o_items), *perm = ws_at<int32_t>(ws, P.o_perm),
+            *cnt = ws_at<int32_t>(ws, P.o_cnt), *ticket = ws_at<int32_t>(ws, P.o_ticket);
     float2 *part = ws_at<float2>(ws, P.o_part);
     double *part_nq = ws_at<double>(ws, P.o_nq), *terms = ws_at<double>(ws, P.o_terms);
     const unsigned seg_blocks = (unsigned)ceil_div(P.S, 8);
@@ -561,18 +654,18 @@ static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const
             cudaFuncSetAttribute(k_hist_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
             cudaFuncSetAttribute(k_scatter_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
         }
-        k_hist_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, hist, status);
+        k_hist_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, hist, status, ticket);
+        k_row_scan<<<(unsigned)ceil_div(k, 8), 256, 0, st>>>(hist, k, P.S, CHUNK_R, off, cnt, start, item_start,
+                                                            ticket);
+        k_scatter_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, off, start, perm);
     } else {
         if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * P.L, st) != cudaSuccess) return -1;
         k_hist<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, hist, status);
-    }
-    scan_excl(st, hist, P.L, bsum, off);
-    k_starts<<<(unsigned)ceil_div(k, 256), 256, 0, st>>>(off, hist, k, P.S, start);
-    if (P.smem_hist)
-        k_scatter_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, off, perm);
-    else
+        scan_excl(st, hist, P.L, bsum, off);
+        k_starts<<<(unsigned)ceil_div(k, 256), 256, 0, st>>>(off, hist, k, P.S, start);
         k_scatter<<<seg_blocks, 256, 0, st>>>(labels, n, k, P.R, P.S, off, perm);
-    k_items<<<1, SCAN_T, 0, st>>>(start, k, CHUNK_R, item_start);
+        k_items<<<1, SCAN_T, 0, st>>>(start, k, CHUNK_R, item_start);
+    }
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const unsigned items = (unsigned)P.items_max;
     // 16 loads in flight per thread unless the row groups of the narrowest column pass would then
@@ -595,7 +688,7 @@ static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const
                                                                   item_start, C_old, C_new, counts, terms,
                                                                   terms + 2 * k);
     k_final<<<1, 256, 0, st>>>(terms, terms + 2 * k, k, P.ncb, cost_old, cost_new, n_empty);
-    return cudaPeekAtLastError() == cudaSuccess ? 10 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? (P.smem_hist ? 6 : 10) : -1;
 }
 
 int update_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
