@@ -169,25 +169,27 @@ struct Band {
     __device__ __forceinline__ void group(const float (&sc)[W], int j0) {
         const float m = min_tree(sc);
         if (m <= t) {
+            // t_of is monotone, so tn < t only when m is a new best
             const float tn = fminf(t, t_of(m));
-            uint32_t le = 0, eq = 0;
+            uint32_t le = 0;
 #pragma unroll
-            for (int g = 0; g < W; ++g) {
-                le |= (sc[g] <= tn ? 1u : 0u) << g;
-                eq |= (sc[g] == m ? 1u : 0u) << g;
-            }
-            if (m < v0) {
-                if (v0 <= tn) list_push(v0, i0);
-                const int gb = __ffs(eq) - 1;
-                v0 = m;
-                i0 = j0 + gb;
-                t = tn;
-                le &= ~(1u << gb);
-            }
+            for (int g = 0; g < W; ++g) le |= (sc[g] <= tn ? 1u : 0u) << g;
+            bool found = !(m < v0);
+            if (!found && v0 <= tn) list_push(v0, i0);
+            t = tn;
+            // the members in index order: the first one equal to a new best m becomes the best
+            // (lowest index on ties), the others enter the list
             while (le) {
                 const int g = __ffs(le) - 1;
                 le &= le - 1;
-                list_push(select(sc, g), j0 + g);
+                const float sg = select(sc, g);
+                if (!found && sg == m) {
+                    v0 = m;
+                    i0 = j0 + g;
+                    found = true;
+                } else {
+                    list_push(sg, j0 + g);
+                }
             }
         }
     }
