@@ -324,6 +324,17 @@ def gen_pool(jobs, fn, workers=None):
     return ex, [ex.submit(fn, j) for j in jobs]
 
 
+def primary_form(requested, d):
+    """The form of a workload's primary line: the one requested, or the faster exact form at the
+    shape (driver.exact_form: FP32 3xTF32 below 256 dimensions, BF16 with the certified recheck
+    from 256 up)."""
+    if requested in ("bf16", "f32"):
+        return requested
+    from paper_1502_04265_gb300 import driver
+
+    return driver.exact_form(d)
+
+
 def lloyd_timed(env, X, Xop, scales, xnorm, C0, compute, engine, steps, warmup, clocks=False, center_terms=1):
     """`warmup` + `steps` Lloyd iterations from C0 (assign + update per step); the timed steps'
     ms, launches, profile, the FP64 cost trace and recheck counts."""
@@ -712,14 +723,20 @@ def run_stream(env_args):
     ctx.sync()
 
     F = 2.0 * n * k * r + n * r
-    R = lloyd_timed(env, Y, Yb, None, yn, C0, "bf16", args.engine, args.steps, args.warmup, clocks=True,
-                    center_terms=args.center_terms)
+    # the primary form: the faster exact one at this shape (FP32 3xTF32 below 256 dimensions, where
+    # BF16's certified band holds most points and their recheck costs more than the halved read)
+    pf = primary_form(args.form, r)
+    R = lloyd_timed(env, Y, Yb if pf == "bf16" else None, None, yn, C0, pf, args.engine if pf == "bf16" else "tcgen05",
+                    args.steps, args.warmup, clocks=True, center_terms=args.center_terms if pf == "bf16" else 1)
     ms, prof = R["ms"], R["prof"]
     value = env.world * F / (ms * 1e-3) / 1e9
     peaks = env.peaks
-    roof = roofline(peaks, "assign_tc", kernel_avg_s(prof, "assign_tc"), n * r * 2 + k * r * 2 + n * 4,
-                    2.0 * n * k * r, unit_peak(peaks, "bf16", True, R["total_s"]), R["total_s"],
-                    traffic=stored_traffic(f"assign_tc/bf16/{n}x{r}_k{k}"))
+    es = 2 if pf == "bf16" else 4
+    roof = roofline(peaks, "assign_tc", kernel_avg_s(prof, "assign_tc"), n * r * es + k * r * es + n * 4,
+                    2.0 * n * k * r, unit_peak(peaks, pf, True, R["total_s"]), R["total_s"],
+                    bound=None if pf == "bf16" else "tensor",
+                    note=None if pf == "bf16" else "3xTF32: measured BF16 peak x nominal TF32/BF16 ratio / 3",
+                    traffic=stored_traffic(f"assign_tc/{pf}/{n}x{r}_k{k}"))
 
     def proj_roof(P, es):
         nl = len(chunks)
@@ -733,18 +750,21 @@ def run_stream(env_args):
     if not args.no_compare:
         s2 = max(3, args.steps // 2)
         R8 = lloyd_timed(env, Y, Y8, s8, yn, C0, "fp8", args.engine, s2, args.warmup)
-        R32 = lloyd_timed(env, Y, None, None, yn, C0, "f32", "tcgen05", s2, args.warmup)
+        if pf == "bf16":
+            R16, R32 = R, lloyd_timed(env, Y, None, None, yn, C0, "f32", "tcgen05", s2, args.warmup)
+        else:
+            R16, R32 = lloyd_timed(env, Y, Yb, None, yn, C0, "bf16", args.engine, s2, args.warmup), R
         it = args.warmup + s2 - 1
-        c16, c8, c32 = (float(x["costs"][it, 1]) for x in (R, R8, R32))
-        v8, v32 = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (R8, R32))
-        forms = {"bf16": {"value": value, "ms_per_step": ms,
-                          "rechecked_per_step": float(np.mean(R["rechecked"][args.warmup:]))},
+        c16, c8, c32 = (float(x["costs"][it, 1]) for x in (R16, R8, R32))
+        v16, v8, v32 = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (R16, R8, R32))
+        forms = {"bf16": {"value": v16, "ms_per_step": R16["ms"], "assign_ms": kernel_avg_s(R16["prof"], "assign_tc") * 1e3,
+                          "rechecked_per_step": float(np.mean(R16["rechecked"][args.warmup:]))},
                  "fp8": {"value": v8, "ms_per_step": R8["ms"], "assign_ms": kernel_avg_s(R8["prof"], "assign_tc") * 1e3,
                          "rechecked_per_step": float(np.mean(R8["rechecked"][args.warmup:])),
                          "final_cost_rel_gap_vs_f32": abs(c8 - c32) / c32},
                  "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms"],
                                 "assign_ms": kernel_avg_s(R32["prof"], "assign_tc") * 1e3},
-                 "speedup_bf16_vs_f32": value / v32, "speedup_fp8_vs_f32": v8 / v32,
+                 "primary": pf, "speedup_bf16_vs_f32": v16 / v32, "speedup_fp8_vs_f32": v8 / v32,
                  "final_cost_rel_gap_bf16_vs_f32": abs(c16 - c32) / c32,
                  "note": "the three forms run the same Lloyd iterations from the same k-means++ centers"}
 
@@ -762,11 +782,13 @@ def run_stream(env_args):
                 B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], ctx=ctx)
                 B.kmeans_project_block(Xb[r0:r1], V, Y=Y[r0:r1], ctx=ctx)
         B.kmeans_row_norms(Y, xnorm=yn, ctx=ctx)
-        B.kmeans_quantize(Y, "bf16", Xq=Yb, ctx=ctx)
+        if pf == "bf16":
+            B.kmeans_quantize(Y, "bf16", Xq=Yb, ctx=ctx)
         B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=Ca, ctx=ctx)
         cur, nxt = Ca, Cb
         for t in range(iters):
-            B.kmeans_assign(Y, cur, Xop=Yb, xnorm=yn, compute="bf16", engine=args.engine, labels=labels, ctx=ctx)
+            B.kmeans_assign(Y, cur, Xop=Yb if pf == "bf16" else None, xnorm=yn, compute=pf,
+                            engine=args.engine if pf == "bf16" else "tcgen05", labels=labels, ctx=ctx)
             B.kmeans_update(Y, labels, cur, C_new=nxt, cost_old=tr[t, 0:1], cost_new=tr[t, 1:2], ctx=ctx)
             cur, nxt = nxt, cur
         return cur
@@ -776,8 +798,9 @@ def run_stream(env_args):
     pipeline = {"projection_bf16": proj_roof(P16, 2), "projection_tf32": proj_roof(P32, 4),
                 "seed_ms": S["ms"], "iterations": iters, "total_ms": W["ms"],
                 "gflops_whole_run": Fw / (W["ms"] * 1e-3) / 1e9,
-                "note": "whole run from device-resident BF16 points: 31 projections, norms, BF16 copy of Y, "
-                        "k-means++ (k=1000 rounds over Y), 20 Lloyd iterations; seeding time counted, its flops not"}
+                "note": "whole run from device-resident BF16 points: 31 projections, norms, (BF16 copy of Y for "
+                        "the BF16 form), k-means++ (k=1000 rounds over Y), 20 Lloyd iterations in the primary form; "
+                        "seeding time counted, its flops not"}
 
     e2e = None
     if not args.no_e2e:
@@ -806,10 +829,12 @@ def run_stream(env_args):
         cpu = oracle_assign_update_rate(Ys, Cs, args.cpu_seconds,
                                         label="coordinates of chunk 0 projected by the oracle; ")
 
-    line = base_line(env, "stream", value, ms, args.steps, args.warmup, "bf16", {
+    line = base_line(env, "stream", value, ms, args.steps, args.warmup, "bf16" if pf == "bf16" else "f32", {
         "workload": f"{n} points, d={d}, {comps}-component mixture in a random rank-{r} subspace + N(0, 0.1^2) "
-                    f"noise, {len(chunks)} chunks of {chunk}; k={k} on the r={r} coordinates, one BF16 Lloyd "
-                    f"iteration per step", "form": "bf16", "engine": args.engine,
+                    f"noise, {len(chunks)} chunks of {chunk} projected in BF16; k={k} on the r={r} coordinates, one "
+                    f"Lloyd iteration per step", "form": pf if pf == "bf16" else "f32_3xtf32",
+        "form_policy": "the faster exact form at the shape: FP32 (3xTF32) below d=256, BF16 + recheck above; "
+                       "every form is listed under forms", "engine": args.engine,
         "l2": "inputs larger than L2 (Y BF16 256 MB; X 16.4 GB FP32 / 8.2 GB BF16)",
         "parallelism": "replicas" if env.world > 1 else "single GPU"})
     line.update({"roofline": roof, "pipeline": pipeline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e,
@@ -862,37 +887,44 @@ def run_batch(env_args):
         ctx.sync()
         return time.perf_counter() - t0
 
-    first_s = record("bf16")
-    costs16 = [p["cost_out"].clone() for p in probs]
+    # one form for the whole batched launch: the faster exact form for its smallest dimension
+    pf = primary_form(args.form, min(s["d"] for s in shapes))
+    first_s = record(pf)
+    costs_p = [p["cost_out"].clone() for p in probs]
     R = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), args.steps, args.warmup - 1, clocks=True)
     ms = R["ms"]
     value = env.world * F / (ms * 1e-3) / 1e9
-    ok = all(torch.equal(p["cost_out"], c) for p, c in zip(probs, costs16))
+    ok = all(torch.equal(p["cost_out"], c) for p, c in zip(probs, costs_p))
 
     # per-kernel times from one run that is not recorded into a graph
-    Pn = env.once(lambda: B.kmeans_batch_run(probs, S, iters, compute="bf16", graph=False, ctx=ctx), warmup=0)
+    Pn = env.once(lambda: B.kmeans_batch_run(probs, S, iters, compute=pf, graph=False, ctx=ctx), warmup=0)
     prof = Pn["prof"]
     peaks = env.peaks
-    a_bytes = sum(s["n"] * s["d"] * 2 + S * s["k"] * s["d"] * 2 + S * s["n"] * 4 for s in shapes)
+    es = 2 if pf == "bf16" else 4
+    a_bytes = sum(s["n"] * s["d"] * es + S * s["k"] * s["d"] * es + S * s["n"] * 4 for s in shapes)
     a_flops = sum(2.0 * s["n"] * S * s["k"] * s["d"] for s in shapes)
     roof = roofline(peaks, "assign_batched", kernel_avg_s(prof, "assign_batched"), a_bytes, a_flops,
-                    unit_peak(peaks, "bf16", True, R["total_s"]), R["total_s"],
-                    traffic=stored_traffic(f"assign_batched/bf16/c{len(shapes)}"),
-                    note="per-launch time from a run outside the graph (the graph itself is timed as a whole)")
+                    unit_peak(peaks, pf, True, R["total_s"]), R["total_s"],
+                    traffic=stored_traffic(f"assign_batched/{pf}/c{len(shapes)}"),
+                    note="per-launch time from a run outside the graph (the graph itself is timed as a whole)"
+                         + ("" if pf == "bf16" else "; 3xTF32: measured BF16 peak x nominal TF32/BF16 ratio / 3"))
     per_iter = {nm: prof[nm][1] / max(prof[nm][0], 1) for nm in prof}
 
     forms = None
     if not args.no_compare:
-        first32 = record("f32")
-        R32 = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), max(2, args.steps // 2), 1)
+        other = "bf16" if pf == "f32" else "f32"
+        first_o = record(other)
+        Ro = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), max(2, args.steps // 2), 1)
         gaps = []
-        for p, c16 in zip(probs, costs16):
-            a, b = c16[:, 1].cpu().numpy(), p["cost_out"][:, 1].cpu().numpy()
+        for p, cp in zip(probs, costs_p):
+            a, b = cp[:, 1].cpu().numpy(), p["cost_out"][:, 1].cpu().numpy()
             gaps.append(float(np.max(np.abs(a - b) / b)))
-        v32 = env.world * F / (R32["ms"] * 1e-3) / 1e9
-        forms = {"bf16": {"value": value, "ms_per_step": ms, "first_call_s": first_s},
-                 "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms"], "first_call_s": first32},
-                 "speedup_vs_f32": value / v32, "max_final_cost_rel_gap": max(gaps),
+        vo = env.world * F / (Ro["ms"] * 1e-3) / 1e9
+        v16, ms16, f16 = (value, ms, first_s) if pf == "bf16" else (vo, Ro["ms"], first_o)
+        v32, ms32, f32_ = (vo, Ro["ms"], first_o) if pf == "bf16" else (value, ms, first_s)
+        forms = {"bf16": {"value": v16, "ms_per_step": ms16, "first_call_s": f16},
+                 "f32_3xtf32": {"value": v32, "ms_per_step": ms32, "first_call_s": f32_},
+                 "primary": pf, "speedup_bf16_vs_f32": v16 / v32, "max_final_cost_rel_gap": max(gaps),
                  "note": "same seeds in both forms; k-means++ is exact in both, so the runs agree up to "
                          "rounding of the FP32/FP64 sums"}
 
@@ -904,7 +936,7 @@ def run_batch(env_args):
         def e2e_step(i):
             for p, Xh in zip(probs, hostX):
                 p["X"].copy_(Xh, non_blocking=True)
-            B.kmeans_batch_run(probs, S, iters, compute="bf16", graph=True, autotune=True, ctx=ctx)
+            B.kmeans_batch_run(probs, S, iters, compute=pf, graph=True, autotune=True, ctx=ctx)
             for p, (Co, co) in zip(probs, outs):
                 Co.copy_(p["C_out"], non_blocking=True)
                 co.copy_(p["cost_out"], non_blocking=True)
@@ -923,10 +955,13 @@ def run_batch(env_args):
                 runs.append((Xh.numpy(), s["k"], synth.seed_uniforms(s["k"], seed=s["seed"] * S + j)))
         cpu = oracle_lloyd_rate(runs, iters, args.cpu_seconds, label="problems in list order; ")
 
-    line = base_line(env, "batch", value, ms, args.steps, args.warmup, "bf16", {
+    line = base_line(env, "batch", value, ms, args.steps, args.warmup, "bf16" if pf == "bf16" else "f32", {
         "workload": f"{len(shapes)} gaussian-mixture problems (n log-uniform [1e3, 1e5], d in {{32, 128, 512}}, "
                     f"k log-uniform [4, 256]; sum n = {n_tot}), {S} k-means++ seeds each, {iters} Lloyd "
-                    f"iterations; a step is one replay of the recorded graph", "form": "bf16",
+                    f"iterations; a step is one replay of the recorded graph",
+        "form": pf if pf == "bf16" else "f32_3xtf32",
+        "form_policy": "one form per batched launch, the faster exact form for the smallest dimension in the "
+                       "batch (FP32 3xTF32 below d=256); both forms are listed under forms",
         "l2": f"inputs larger than L2 ({xbytes / 1e9:.1f} GB FP32 points)",
         "parallelism": "replicas" if env.world > 1 else "single GPU"})
     line.update({"roofline": roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["launches"],

@@ -12,15 +12,30 @@ import torch
 from . import _binding as B
 
 
+# below this dimension BF16's certified band holds most points of typical data, and their FP32
+# recheck costs more than the halved read of X saves
+BF16_MIN_D = 256
+
+
+def exact_form(d):
+    """The faster of the two exact assignment forms for points of dimension d: "f32" (3xTF32)
+    below BF16_MIN_D, "bf16" (with the certified recheck) from there up."""
+    return "f32" if d < BF16_MIN_D else "bf16"
+
+
 def lloyd(X, k, iters, u, w=None, compute="f32", engine="auto", C0=None, ctx=None,
           return_trace=False):
     """Seed with k-means++ (unless C0 is given), then run `iters` Lloyd iterations.
+
+    compute: "f32", "bf16", "fp8", or "auto" (exact_form of the dimension).
 
     Returns a dict with C (k x d), labels, the device cost trace
     [cost(C_t, L_t), cost(C_{t+1}, L_t)] per iteration and the seeding indices.
     """
     n, d = X.shape
     dev = X.device
+    if compute == "auto":
+        compute = exact_form(d)
     idx = None
     if C0 is None:
         idx, C = B.kmeans_seed_pp(X, k, u, w=w, ctx=ctx)
