@@ -222,7 +222,7 @@ class Env:
     def event(self):
         return self.torch.cuda.Event(enable_timing=True)
 
-    def timed(self, step, steps, warmup, clocks=False, flush=None):
+    def timed(self, step, steps, warmup, clocks=False, flush=None, profile=True):
         """`warmup` untimed and `steps` timed calls of step(i), CUDA events on the launching
         stream, barrier + synchronize on both sides; with `flush`, L2 is overwritten before
         every step and only the steps are timed.  Returns ms per step (max over ranks), our
@@ -237,35 +237,43 @@ class Env:
         if sampler:
             sampler.start()
             time.sleep(0.5)
-        self.ctx.profile(True)
+        def run_steps(first):
+            pairs = []
+            if flush is None:
+                a, b = self.event(), self.event()
+                a.record(self.stream)
+                for i in range(steps):
+                    step(first + i)
+                b.record(self.stream)
+                pairs.append((a, b))
+            else:
+                for i in range(steps):
+                    flush()
+                    a, b = self.event(), self.event()
+                    a.record(self.stream)
+                    step(first + i)
+                    b.record(self.stream)
+                    pairs.append((a, b))
+            torch.cuda.synchronize(self.dev)
+            return sum(a.elapsed_time(b) for a, b in pairs)
+
+        # the timed pass runs without the library's per-kernel events (they add a few percent to a
+        # short step); a second pass of the same steps, with them, gives the per-kernel times
         l0 = self.ctx.launch_count()
         self.barrier()
         torch.cuda.synchronize(self.dev)
-        pairs = []
-        if flush is None:
-            a, b = self.event(), self.event()
-            a.record(self.stream)
-            for i in range(steps):
-                step(warmup + i)
-            b.record(self.stream)
-            pairs.append((a, b))
-        else:
-            for i in range(steps):
-                flush()
-                a, b = self.event(), self.event()
-                a.record(self.stream)
-                step(warmup + i)
-                b.record(self.stream)
-                pairs.append((a, b))
-        torch.cuda.synchronize(self.dev)
+        ms_total = run_steps(warmup)
         self.barrier()
-        ms_total = sum(a.elapsed_time(b) for a, b in pairs)
         launches = self.ctx.launch_count() - l0
-        prof = self.ctx.profile_read()
-        self.ctx.profile(False)
         clk = sampler.stop() if sampler else None
+        ms_prof, prof = None, {}
+        if profile:
+            self.ctx.profile(True)
+            ms_prof = run_steps(warmup + steps) / max(steps, 1)
+            prof = self.ctx.profile_read()
+            self.ctx.profile(False)
         return {"ms": self.max_over_ranks(ms_total / max(steps, 1)), "launches": int(launches), "prof": prof,
-                "clocks": clk, "total_s": ms_total * 1e-3}
+                "clocks": clk, "total_s": ms_total * 1e-3, "ms_profiled": ms_prof}
 
     def once(self, fn, warmup=1):
         """Device time of one call of fn() after `warmup` calls, with the per-kernel profile."""
@@ -342,8 +350,9 @@ def lloyd_timed(env, X, Xop, scales, xnorm, C0, compute, engine, steps, warmup, 
     n = X.shape[0]
     labels = torch.empty(n, dtype=torch.int32, device=env.dev)
     Cs = [C0.clone(), torch.empty_like(C0)]
-    cost = torch.zeros((steps + warmup, 2), dtype=torch.float64, device=env.dev)
-    nre = torch.zeros(steps + warmup, dtype=torch.int64, device=env.dev)
+    # indices: warm-up, the timed pass, then the profiled pass of the same number of steps
+    cost = torch.zeros((2 * steps + warmup, 2), dtype=torch.float64, device=env.dev)
+    nre = torch.zeros(2 * steps + warmup, dtype=torch.int64, device=env.dev)
 
     def step(i):
         B.kmeans_assign(X, Cs[0], Xop=Xop, Xop_scales=scales, xnorm=xnorm, compute=compute, engine=engine,
@@ -364,7 +373,10 @@ def assign_kernel(prof):
 def base_line(env, workload, value, ms, steps, warmup, dtype, config):
     return {"metric": METRICS[workload], "value": value, "unit": UNIT, "n_gpus": env.world, "steps": steps,
             "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config,
+            "kernel_timing": "per-kernel CUDA events on the launching stream, recorded by the library around "
+                             "each kernel during a second pass of the same steps right after the timed one (the "
+                             "timed pass runs without them: they add a few percent to a short step)"}
 
 
 def kernels_ms(prof):
@@ -549,7 +561,7 @@ def run_highdim(env, args):
             cost_h.copy_(co2[1:2], non_blocking=True)
             st["C"], st["Cn"] = st["Cn"], st["C"]
 
-        E = env.timed(e2e_step, args.e2e_steps or 5, 1)
+        E = env.timed(e2e_step, args.e2e_steps or 5, 1, profile=False)
         e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * d * 4 + 8),
                "ms_per_step": E["ms"], "note": "H2D of X from pinned memory, norms, operand copy, assign, "
@@ -650,7 +662,7 @@ def run_small(env, args):
             Ch.copy_(cur, non_blocking=True)
             Lh.copy_(labels, non_blocking=True)
 
-        E = env.timed(e2e_step, args.e2e_steps or 10, 2, flush=lambda: flush_buf.fill_(1.0))
+        E = env.timed(e2e_step, args.e2e_steps or 10, 2, flush=lambda: flush_buf.fill_(1.0), profile=False)
         e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(k * d * 4 + n * 4), "ms_per_step": E["ms"]}
 
@@ -812,7 +824,7 @@ def run_stream(env_args):
             Ch.copy_(C, non_blocking=True)
             Lh.copy_(labels, non_blocking=True)
 
-        E = env.timed(e2e_step, args.e2e_steps or 2, 1)
+        E = env.timed(e2e_step, args.e2e_steps or 2, 1, profile=False)
         e2e = {"value": env.world * Fw / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(k * r * 4 + n * 4), "ms_per_step": E["ms"],
                "note": "a step is the whole job from FP32 chunks in pinned host memory: H2D, BF16 copy, "
@@ -891,7 +903,7 @@ def run_batch(env_args):
     pf = primary_form(args.form, min(s["d"] for s in shapes))
     first_s = record(pf)
     costs_p = [p["cost_out"].clone() for p in probs]
-    R = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), args.steps, args.warmup - 1, clocks=True)
+    R = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), args.steps, args.warmup - 1, clocks=True, profile=False)
     ms = R["ms"]
     value = env.world * F / (ms * 1e-3) / 1e9
     ok = all(torch.equal(p["cost_out"], c) for p, c in zip(probs, costs_p))
@@ -914,7 +926,7 @@ def run_batch(env_args):
     if not args.no_compare:
         other = "bf16" if pf == "f32" else "f32"
         first_o = record(other)
-        Ro = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), max(2, args.steps // 2), 1)
+        Ro = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), max(2, args.steps // 2), 1, profile=False)
         gaps = []
         for p, cp in zip(probs, costs_p):
             a, b = cp[:, 1].cpu().numpy(), p["cost_out"][:, 1].cpu().numpy()
@@ -941,7 +953,7 @@ def run_batch(env_args):
                 Co.copy_(p["C_out"], non_blocking=True)
                 co.copy_(p["cost_out"], non_blocking=True)
 
-        E = env.timed(e2e_step, args.e2e_steps or 2, 1)
+        E = env.timed(e2e_step, args.e2e_steps or 2, 1, profile=False)
         e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(xbytes),
                "d2h_bytes_per_step": int(sum(p["C_out"].numel() * 4 + p["cost_out"].numel() * 8 for p in probs)),
                "ms_per_step": E["ms"], "note": "H2D of every problem's X, planning + recording + launch of "
@@ -1007,8 +1019,8 @@ def run_learned(env, args):
     F = 2.0 * n * k * d + n * d
     K = args.steps
     lab = torch.empty(n, dtype=torch.int32, device=env.dev)
-    nf = torch.zeros(K + args.warmup, dtype=torch.int64, device=env.dev)
-    cost = torch.zeros((K + args.warmup, 2), dtype=torch.float64, device=env.dev)
+    nf = torch.zeros(2 * K + args.warmup, dtype=torch.int64, device=env.dev)
+    cost = torch.zeros((2 * K + args.warmup, 2), dtype=torch.float64, device=env.dev)
     Cn = torch.empty_like(C)
 
     def step_learned(i):
@@ -1031,7 +1043,7 @@ def run_learned(env, args):
 
     def full_scan(compute, Xop, steps):
         lab2 = torch.empty(n, dtype=torch.int32, device=env.dev)
-        c2 = torch.zeros((steps + 1, 2), dtype=torch.float64, device=env.dev)
+        c2 = torch.zeros((2 * steps + 1, 2), dtype=torch.float64, device=env.dev)
         Cn2 = torch.empty_like(C)
 
         def st(i):
@@ -1074,7 +1086,7 @@ def run_learned(env, args):
             Lh.copy_(lab, non_blocking=True)
             ch.copy_(cost[0, 0:1], non_blocking=True)
 
-        E = env.timed(e2e_step, args.e2e_steps or 2, 1)
+        E = env.timed(e2e_step, args.e2e_steps or 2, 1, profile=False)
         e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(n * 4 + 8), "ms_per_step": E["ms"]}
 
