@@ -462,22 +462,23 @@ def run_highdim(env, args):
     ctx = env.ctx
     xnorm = B.kmeans_row_norms(Xg, ctx=ctx)
     _, C0 = B.kmeans_seed_pp(Xg, k, ug, ctx=ctx)
-    form, engine, Xop = args.form, args.engine, None
+    form, engine, Xop, Xr = args.form, args.engine, None, None
     if form in ("auto", "bf16"):
-        Xb, _ = B.kmeans_quantize(Xg, "bf16", ctx=ctx)
+        # the BF16 copy and the rows' rounding residuals (the certified band's side data)
+        Xb, Xrb = B.kmeans_quantize(Xg, "bf16", ctx=ctx)
         try:
-            B.kmeans_assign(Xg, C0, Xop=Xb, xnorm=xnorm, compute="bf16", engine=engine, ctx=ctx)
-            form, Xop = "bf16", Xb
+            B.kmeans_assign(Xg, C0, Xop=Xb, Xop_scales=Xrb, xnorm=xnorm, compute="bf16", engine=engine, ctx=ctx)
+            form, Xop, Xr = "bf16", Xb, Xrb
         except B.GbkmError:
             if form == "bf16":
                 raise
             form = "f32"
-            del Xb
+            del Xb, Xrb
     else:
         form = "f32"
     ctx.sync()
 
-    R = lloyd_timed(env, Xg, Xop, None, xnorm, C0, form, engine, args.steps, args.warmup, clocks=True,
+    R = lloyd_timed(env, Xg, Xop, Xr, xnorm, C0, form, engine, args.steps, args.warmup, clocks=True,
                     center_terms=args.center_terms if form == "bf16" else 1)
     ms, prof = R["ms"], R["prof"]
     value = env.world * F / (ms * 1e-3) / 1e9
@@ -523,11 +524,12 @@ def run_highdim(env, args):
     def whole():
         B.kmeans_row_norms(Xg, xnorm=xnorm, ctx=ctx)
         if form == "bf16":
-            B.kmeans_quantize(Xg, "bf16", Xq=Xop, ctx=ctx)
+            B.kmeans_quantize(Xg, "bf16", Xq=Xop, scales=Xr, ctx=ctx)
         B.kmeans_seed_pp(Xg, k, ug, C_out=Ca, ctx=ctx)
         cur, nxt = Ca, Cb
         for t in range(iters):
-            B.kmeans_assign(Xg, cur, Xop=Xop, xnorm=xnorm, compute=form, engine=engine, labels=labels, ctx=ctx)
+            B.kmeans_assign(Xg, cur, Xop=Xop, Xop_scales=Xr, xnorm=xnorm, compute=form, engine=engine,
+                            labels=labels, ctx=ctx)
             B.kmeans_update(Xg, labels, cur, C_new=nxt, cost_old=tr[t, 0:1], cost_new=tr[t, 1:2], ctx=ctx)
             cur, nxt = nxt, cur
 
@@ -545,6 +547,7 @@ def run_highdim(env, args):
         Xd = torch.empty_like(Xg)
         xn2 = torch.empty(n, dtype=torch.float32, device=env.dev)
         Xb2 = torch.empty((n, d), dtype=torch.bfloat16, device=env.dev) if form == "bf16" else None
+        Xr2 = torch.empty(n, dtype=torch.float32, device=env.dev) if form == "bf16" else None
         Ce, Cen = R["C"].clone(), torch.empty_like(C0)
         lab2 = torch.empty(n, dtype=torch.int32, device=env.dev)
         co2 = torch.empty(2, dtype=torch.float64, device=env.dev)
@@ -554,8 +557,9 @@ def run_highdim(env, args):
             Xd.copy_(Xh, non_blocking=True)
             B.kmeans_row_norms(Xd, xnorm=xn2, ctx=ctx)
             if Xb2 is not None:
-                B.kmeans_quantize(Xd, "bf16", Xq=Xb2, ctx=ctx)
-            B.kmeans_assign(Xd, st["C"], Xop=Xb2, xnorm=xn2, compute=form, engine=engine, labels=lab2, ctx=ctx)
+                B.kmeans_quantize(Xd, "bf16", Xq=Xb2, scales=Xr2, ctx=ctx)
+            B.kmeans_assign(Xd, st["C"], Xop=Xb2, Xop_scales=Xr2, xnorm=xn2, compute=form, engine=engine,
+                            labels=lab2, ctx=ctx)
             B.kmeans_update(Xd, lab2, st["C"], C_new=st["Cn"], cost_old=co2[0:1], cost_new=co2[1:2], ctx=ctx)
             Ch_out.copy_(st["Cn"], non_blocking=True)
             cost_h.copy_(co2[1:2], non_blocking=True)
@@ -711,7 +715,7 @@ def run_stream(env_args):
         Xc = torch.from_numpy(f.result()).pin_memory()
         pinned.append(Xc)
         Xg[r0:r1].copy_(Xc, non_blocking=True)
-        B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], ctx=ctx)
+        B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], residuals=False, ctx=ctx)
     ex.shutdown()
     Q = synth.orthonormal_basis(d, r, seed)
     V = torch.from_numpy(Q.astype(np.float32)).to(env.dev)
@@ -727,7 +731,7 @@ def run_stream(env_args):
     P32 = env.once(lambda: project(Xg))
     P16 = env.once(lambda: project(Xb))          # Y from the BF16 projection feeds the rest
     yn = B.kmeans_row_norms(Y, ctx=ctx)
-    Yb, _ = B.kmeans_quantize(Y, "bf16", ctx=ctx)
+    Yb, Yr = B.kmeans_quantize(Y, "bf16", ctx=ctx)
     Y8, s8 = B.kmeans_quantize(Y, "fp8", ctx=ctx)
     idx = torch.empty(k, dtype=torch.int64, device=env.dev)
     C0 = torch.empty((k, r), dtype=torch.float32, device=env.dev)
@@ -738,7 +742,8 @@ def run_stream(env_args):
     # the primary form: the faster exact one at this shape (FP32 3xTF32 below 256 dimensions, where
     # BF16's certified band holds most points and their recheck costs more than the halved read)
     pf = primary_form(args.form, r)
-    R = lloyd_timed(env, Y, Yb if pf == "bf16" else None, None, yn, C0, pf, args.engine if pf == "bf16" else "tcgen05",
+    R = lloyd_timed(env, Y, Yb if pf == "bf16" else None, Yr if pf == "bf16" else None, yn, C0, pf,
+                    args.engine if pf == "bf16" else "tcgen05",
                     args.steps, args.warmup, clocks=True, center_terms=args.center_terms if pf == "bf16" else 1)
     ms, prof = R["ms"], R["prof"]
     value = env.world * F / (ms * 1e-3) / 1e9
@@ -765,7 +770,7 @@ def run_stream(env_args):
         if pf == "bf16":
             R16, R32 = R, lloyd_timed(env, Y, None, None, yn, C0, "f32", "tcgen05", s2, args.warmup)
         else:
-            R16, R32 = lloyd_timed(env, Y, Yb, None, yn, C0, "bf16", args.engine, s2, args.warmup), R
+            R16, R32 = lloyd_timed(env, Y, Yb, Yr, yn, C0, "bf16", args.engine, s2, args.warmup), R
         it = args.warmup + s2 - 1
         c16, c8, c32 = (float(x["costs"][it, 1]) for x in (R16, R8, R32))
         v16, v8, v32 = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (R16, R8, R32))
@@ -791,15 +796,16 @@ def run_stream(env_args):
         else:
             for (r0, r1), Xc in zip(chunks, src_chunks):
                 Xg[r0:r1].copy_(Xc, non_blocking=True)
-                B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], ctx=ctx)
+                B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], residuals=False, ctx=ctx)
                 B.kmeans_project_block(Xb[r0:r1], V, Y=Y[r0:r1], ctx=ctx)
         B.kmeans_row_norms(Y, xnorm=yn, ctx=ctx)
         if pf == "bf16":
-            B.kmeans_quantize(Y, "bf16", Xq=Yb, ctx=ctx)
+            B.kmeans_quantize(Y, "bf16", Xq=Yb, scales=Yr, ctx=ctx)
         B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=Ca, ctx=ctx)
         cur, nxt = Ca, Cb
         for t in range(iters):
-            B.kmeans_assign(Y, cur, Xop=Yb if pf == "bf16" else None, xnorm=yn, compute=pf,
+            B.kmeans_assign(Y, cur, Xop=Yb if pf == "bf16" else None, Xop_scales=Yr if pf == "bf16" else None,
+                            xnorm=yn, compute=pf,
                             engine=args.engine if pf == "bf16" else "tcgen05", labels=labels, ctx=ctx)
             B.kmeans_update(Y, labels, cur, C_new=nxt, cost_old=tr[t, 0:1], cost_new=tr[t, 1:2], ctx=ctx)
             cur, nxt = nxt, cur
@@ -995,7 +1001,7 @@ def run_learned(env, args):
     Xall = mixture(n + ntrain, d, k, seed=env.rank)
     Xg = torch.from_numpy(Xall[:n]).to(env.dev)
     Xtg = torch.from_numpy(Xall[n:]).to(env.dev)
-    Xh, _ = B.kmeans_quantize(Xg, "bf16", ctx=ctx)
+    Xh, Xhr = B.kmeans_quantize(Xg, "bf16", ctx=ctx)
     u = synth.seed_uniforms(k, seed=env.rank)
     ug = torch.from_numpy(u).to(env.dev)
     t0 = time.perf_counter()
@@ -1005,7 +1011,7 @@ def run_learned(env, args):
     centers_s = time.perf_counter() - t0
     lt = B.kmeans_assign(Xtg, C, compute="f32", ctx=ctx)
     net = ProposalNet(d, h, k, seed=env.rank, device=env.dev)
-    Xtb, _ = B.kmeans_quantize(Xtg, "bf16", ctx=ctx)
+    Xtb, _ = B.kmeans_quantize(Xtg, "bf16", residuals=False, ctx=ctx)
     ctx.sync()
     t0 = time.perf_counter()
     losses = net.train(Xtb, lt, epochs=10, batch=4096, lr=3e-3, ctx=ctx)
@@ -1041,13 +1047,14 @@ def run_learned(env, args):
                     note="the output layer (h=256 -> k logits) with the fused grouped top-32 proposal (the best "
                          "center of each 16-center group competes); the logits are never stored")
 
-    def full_scan(compute, Xop, steps):
+    def full_scan(compute, Xop, Xres, steps):
         lab2 = torch.empty(n, dtype=torch.int32, device=env.dev)
         c2 = torch.zeros((2 * steps + 1, 2), dtype=torch.float64, device=env.dev)
         Cn2 = torch.empty_like(C)
 
         def st(i):
-            B.kmeans_assign(Xg, C, Xop=Xop, xnorm=xnorm, compute=compute, engine="tcgen05", labels=lab2, ctx=ctx)
+            B.kmeans_assign(Xg, C, Xop=Xop, Xop_scales=Xres, xnorm=xnorm, compute=compute, engine="tcgen05",
+                            labels=lab2, ctx=ctx)
             B.kmeans_update(Xg, lab2, C, C_new=Cn2, cost_old=c2[i, 0:1], cost_new=c2[i, 1:2], ctx=ctx)
 
         Rf = env.timed(st, steps, 1)
@@ -1057,8 +1064,8 @@ def run_learned(env, args):
 
     forms = None
     if not args.no_compare:
-        Rb = full_scan("bf16", Xh, max(2, min(K, 3)))
-        Rf = full_scan("f32", None, 2)
+        Rb = full_scan("bf16", Xh, Xhr, max(2, min(K, 3)))
+        Rf = full_scan("f32", None, None, 2)
         vb, vf = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (Rb, Rf))
         forms = {"learned": {"value": value, "ms_per_step": ms, "misassigned": mis, "cost": c_learn},
                  "bf16_full_scan": {"value": vb, "ms_per_step": Rb["ms"], "misassigned": Rb["mis"], "cost": Rb["cost"],
@@ -1080,7 +1087,7 @@ def run_learned(env, args):
 
         def e2e_step(i):
             Xd.copy_(Xhost, non_blocking=True)
-            B.kmeans_quantize(Xd, "bf16", Xq=Xhd, ctx=ctx)
+            B.kmeans_quantize(Xd, "bf16", Xq=Xhd, residuals=False, ctx=ctx)
             B.kmeans_learned_assign(net, Xd, Xhd, C, s2, topm=topm, labels=lab, ctx=ctx)
             B.kmeans_update(Xd, lab, C, C_new=Cn, cost_old=cost[0, 0:1], cost_new=cost[0, 1:2], ctx=ctx)
             Lh.copy_(lab, non_blocking=True)

@@ -101,7 +101,9 @@ int kmeans_row_norms(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, float 
 
 /* Copy of X in a lower-precision operand format (precision form of the
  * distance and projection GEMMs; no paper counterpart).
- *   dtype == GBKM_BF16:    Xq is n x d bfloat16 (round to nearest even); scales unused.
+ *   dtype == GBKM_BF16:    Xq is n x d bfloat16 (round to nearest even); scales, when not
+ *     NULL, is n FP32 and receives each row's rounding residual ||x_i - Xq_i|| rounded
+ *     up, which kmeans_assign uses for a narrower certified band.
  *   dtype == GBKM_FP8E4M3: Xq is n x d E4M3 bytes; scales is n x ceil(d/128) FP32,
  *     scale = 2^e with e the smallest integer such that the block's max |x| * 2^-e
  *     <= 448 (1 for an all-zero block); x ~= scale * e4m3(q), round to nearest even.
@@ -163,7 +165,10 @@ int kmeans_seed_pp(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const fl
  * then take the direct recheck, scanning all k if needed).  Every label equals the
  * exact nearest center except where two centers' distances agree to within the
  * direct recheck's error ((ceil(d/128) + 10) 2^-24 relative).
- *   Xop_scales: per-row scales of an FP8 Xop (n x ceil(d/128)), else NULL.
+ *   Xop_scales: per-row scales of an FP8 Xop (n x ceil(d/128)); for a BF16 Xop with
+ *     one-term centers, optionally the rows' rounding residuals from kmeans_quantize
+ *     (n FP32): the band then uses them and the centers' largest residual in place
+ *     of the worst case u ||x||, u ||c|| (the bound stays certified); else NULL.
  *   X: n x d FP32 (always required: recheck and bounds).
  *   xnorm: ||x_i||^2 FP32 from kmeans_row_norms, or NULL (then computed here).
  *   C: k x d FP32.  labels: n int32.  min_d2: n FP32 or NULL, the squared

@@ -232,11 +232,15 @@ def kmeans_row_norms(X, xnorm=None, ctx=None):
 
 
 # ------------------------------------------------------------------ A0
-def kmeans_quantize(X, dtype="bf16", Xq=None, scales=None, ctx=None):
+def kmeans_quantize(X, dtype="bf16", Xq=None, scales=None, residuals=True, ctx=None):
+    """(Xq, scales): for "fp8" the per-block scales; for "bf16" the rows' rounding residuals
+    (n FP32, the side data kmeans_assign takes as Xop_scales), or None with residuals=False."""
     _req(X, torch.float32, name="X")
     n, d = X.shape
     if dtype == "bf16":
         Xq = Xq if Xq is not None else torch.empty((n, d), dtype=torch.bfloat16, device=X.device)
+        if scales is None and residuals:
+            scales = torch.empty(n, dtype=torch.float32, device=X.device)
     elif dtype == "fp8":
         Xq = Xq if Xq is not None else torch.empty((n, d), dtype=torch.uint8, device=X.device)
         nb = (d + 127) // 128

@@ -330,7 +330,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
                      aligned16(X) && (d % 4) == 0;
     const int64_t ne = esc ? n : 0;
     WsPlan p;
-    size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(1),
+    size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(2),
            o_cop = p.take<char>(use_tc ? k_pad * d * esz : 0),
            o_clo = p.take<float>(use_tc && (o.compute == GBKM_F32 || split) ? k_pad * d : 0),
            o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_cd = p.take<int32_t>(n * gbkm::CAND_STRIDE),
@@ -347,6 +347,8 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     gbkm::CenterPrep cp;
     cp.cnorm = ws_at<float>(ws, o_cn);
     cp.cmax = ws_at<unsigned>(ws, o_cm);
+    // one-term BF16 with the rows' rounding residuals: the centers' largest residual as well
+    cp.emax = (use_tc && o.compute == GBKM_BF16 && !split && Xop_scales) ? cp.cmax + 1 : nullptr;
     cp.cop = use_tc ? ws_at<void>(ws, o_cop) : nullptr;
     cp.cop_lo = (use_tc && (o.compute == GBKM_F32 || split)) ? ws_at<void>(ws, o_clo) : nullptr;
     cp.cscale = ws_at<float>(ws, o_cs);

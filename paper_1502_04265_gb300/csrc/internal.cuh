@@ -202,6 +202,7 @@ int launch_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int dtype
 struct CenterPrep {
     float *cnorm;       // k
     unsigned *cmax;     // 1: max ||c_j|| as float bits
+    unsigned *emax;     // 1: max ||c_j - bf16(c_j)|| as float bits (one-term BF16 operand), or null
     void *cop;          // operand copy (k_pad x d) or null
     void *cop_lo;       // tf32 low part or null
     float *cscale;      // fp8 per-row scales or null

@@ -178,17 +178,33 @@ __global__ void __launch_bounds__(256) k_cand_check(const float *__restrict__ X,
 
 // gather the fallback rows (list, count on the device) into a contiguous block; rows past the
 // count are left untouched
-// gathers the listed rows of X (FP32) and of its BF16 copy Xh into compact row-major blocks
-__global__ void k_gather_rows(const float *__restrict__ X, const __nv_bfloat16 *__restrict__ Xh, int64_t d,
-                              const int32_t *__restrict__ list, const int32_t *__restrict__ count,
-                              float *__restrict__ out, __nv_bfloat16 *__restrict__ outh) {
+// gathers the listed rows of X (FP32) and of its BF16 copy Xh into compact row-major blocks, with
+// each row's rounding residual ||x - xh|| rounded up (the assignment's narrower certified band;
+// the residuals are exact in FP32, their squares and sums round to (d + 4) 2^-23 relative at most)
+__global__ void __launch_bounds__(128) k_gather_rows(const float *__restrict__ X, const __nv_bfloat16 *__restrict__ Xh,
+                                                     int64_t d, const int32_t *__restrict__ list,
+                                                     const int32_t *__restrict__ count, float *__restrict__ out,
+                                                     __nv_bfloat16 *__restrict__ outh, float *__restrict__ resid) {
+    __shared__ float part[4];
     const int64_t r = blockIdx.x;
     if (r >= *count) return;
     const int64_t src = list[r];
+    float s = 0.f;
     for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
-        out[r * d + t] = X[src * d + t];
-        outh[r * d + t] = Xh[src * d + t];
+        const float v = X[src * d + t];
+        const __nv_bfloat16 h = Xh[src * d + t];
+        out[r * d + t] = v;
+        outh[r * d + t] = h;
+        const float e = v - __bfloat162float(h);
+        s = fmaf(e, e, s);
     }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        resid[r] = sqrtf((part[0] + part[1] + part[2] + part[3]) * (1.f + (float)(d + 4) * 1.1920929e-7f)) *
+                   (1.f + 2.4e-7f);
 }
 
 __global__ void k_scatter_labels(const int32_t *__restrict__ sub, const int32_t *__restrict__ list,
@@ -391,10 +407,11 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
             if (e != cudaSuccess) rc = cuda_check(c, e, "fallback count out");
         }
         if (rc == GBKM_OK && nf > 0) {
-            float *sub = nullptr;
+            float *sub = nullptr, *subr = nullptr;
             __nv_bfloat16 *subh = nullptr;
             int32_t *subl = nullptr;
             e = cudaMallocAsync(&sub, sizeof(float) * (size_t)nf * d, c->stream);
+            if (e == cudaSuccess) e = cudaMallocAsync(&subr, sizeof(float) * (size_t)nf, c->stream);
             if (e == cudaSuccess) e = cudaMallocAsync(&subh, sizeof(__nv_bfloat16) * (size_t)nf * d, c->stream);
             if (e == cudaSuccess) e = cudaMallocAsync(&subl, sizeof(int32_t) * (size_t)nf, c->stream);
             if (e != cudaSuccess) {
@@ -403,12 +420,12 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
             } else {
                 prof_begin(c, "fallback");
                 k_gather_rows<<<(unsigned)nf, 128, 0, c->stream>>>(X, static_cast<const __nv_bfloat16 *>(Xh), d, fl,
-                                                                   fc, sub, subh);
+                                                                   fc, sub, subh, subr);
                 GBKM_LAUNCHED(c);
                 // BF16 distance GEMM with the certified near-tie recheck: the same exact labels as the
                 // FP32 scan at a fraction of its tensor time
                 gbkm_assign_opts o = {GBKM_BF16, GBKM_ENGINE_AUTO, 1, 0};
-                rc = kmeans_assign(c, subh, nullptr, sub, nullptr, nf, d, C, k, &o, subl, nullptr, nullptr);
+                rc = kmeans_assign(c, subh, subr, sub, nullptr, nf, d, C, k, &o, subl, nullptr, nullptr);
                 if (rc == GBKM_OK) {
                     k_scatter_labels<<<(unsigned)ceil_div(nf, 256), 256, 0, c->stream>>>(subl, fl, fc, labels);
                     GBKM_LAUNCHED(c);
@@ -416,6 +433,7 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
                 prof_end(c);
             }
             if (sub) cudaFreeAsync(sub, c->stream);
+            if (subr) cudaFreeAsync(subr, c->stream);
             if (subh) cudaFreeAsync(subh, c->stream);
             if (subl) cudaFreeAsync(subl, c->stream);
         }

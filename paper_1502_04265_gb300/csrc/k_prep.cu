@@ -66,6 +66,48 @@ __global__ void __launch_bounds__(256) k_to_bf16(const float *__restrict__ X, in
     for (int64_t e = m8 * 8 + tid; e < m; e += nth) out[e] = __float2bfloat16_rn(X[e]);
 }
 
+// The same copy, one warp per row, with the row's rounding residual ||x - bf16(x)||: the residual
+// of each element is exact in FP32 (x and its rounding are within a factor of two), its square and
+// the row sum round up to (d + 4) 2^-23 relative at most, which the stored bound covers.
+__global__ void __launch_bounds__(256) k_to_bf16_rows(const float *__restrict__ X, int64_t n, int64_t d,
+                                                      __nv_bfloat16 *__restrict__ out, float *__restrict__ resid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const float *x = X + row * d;
+    __nv_bfloat16 *o = out + row * d;
+    float s = 0.f;
+    const bool vec = (d % 4) == 0 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+    if (vec) {
+        for (int64_t t = lane; t < d / 4; t += 32) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(x) + t);
+            const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+            uint2 w;
+            w.x = *reinterpret_cast<const uint32_t *>(&h0);
+            w.y = *reinterpret_cast<const uint32_t *>(&h1);
+            reinterpret_cast<uint2 *>(o)[t] = w;
+            const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+            const float e0 = v.x - f0.x, e1 = v.y - f0.y, e2 = v.z - f1.x, e3 = v.w - f1.y;
+            s = fmaf(e0, e0, s);
+            s = fmaf(e1, e1, s);
+            s = fmaf(e2, e2, s);
+            s = fmaf(e3, e3, s);
+        }
+    } else {
+        for (int64_t t = lane; t < d; t += 32) {
+            const float v = x[t];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            o[t] = h;
+            const float e = v - __bfloat162float(h);
+            s = fmaf(e, e, s);
+        }
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+    if (lane == 0) resid[row] = sqrtf(s * (1.f + (float)(d + 4) * 1.1920929e-7f)) * (1.f + 2.4e-7f);
+}
+
 // smallest e with amax * 2^-e <= 448 (e = 0 when amax == 0)
 __device__ __forceinline__ int e4m3_scale_exp(float amax) {
     if (!(amax > 0.f)) return 0;
@@ -110,7 +152,10 @@ int launch_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int dtype
                     float *scales) {
     if (n == 0) return GBKM_OK;
     int64_t cap = (int64_t)c->sm_count * 8;
-    if (dtype == GBKM_BF16) {
+    if (dtype == GBKM_BF16 && scales) {
+        // with the per-row rounding residuals (the assignment's tighter certified band)
+        k_to_bf16_rows<<<(unsigned)ceil_div(n, 8), 256, 0, c->stream>>>(X, n, d, (__nv_bfloat16 *)Xq, scales);
+    } else if (dtype == GBKM_BF16) {
         int64_t blocks = ceil_div(n * d, 256 * 8);
         if (blocks > cap) blocks = cap;
         k_to_bf16<<<(unsigned)blocks, 256, 0, c->stream>>>(X, n * d, (__nv_bfloat16 *)Xq);
@@ -155,30 +200,44 @@ __global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C
     }
     const float *c = C + j * d;
     DF acc;
-    float amax = 0.f;
+    float amax = 0.f, res = 0.f;  // res: sum of the squared BF16 rounding residuals (one-term BF16)
     for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
         float v = c[t];
         acc.add_prod(v, v);
         amax = fmaxf(amax, fabsf(v));
+        if (cp.emax) {
+            const float e = v - __bfloat162float(__float2bfloat16_rn(v));
+            res = fmaf(e, e, res);
+        }
     }
     double s = warp_sum_d(acc.value());
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        res += __shfl_xor_sync(0xffffffffu, res, o);
+    }
+    __shared__ float res_s[8];
     if (lane == 0) {
         red[wid] = s;
         amax_s[wid] = amax;
+        res_s[wid] = res;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        float am = 0.f;
+        float am = 0.f, rs = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             tot += red[w];
             am = fmaxf(am, amax_s[w]);
+            rs += res_s[w];
         }
         cp.cnorm[j] = (float)tot;
         float nrm = (float)sqrt(tot) * (1.f + 1.0e-6f);
         atomicMax(cp.cmax, __float_as_uint(nrm));
+        // ||c_j - bf16(c_j)|| rounded up: each residual is exact, its square and the sums round to
+        // (d + 4) 2^-23 relative at most
+        if (cp.emax)
+            atomicMax(cp.emax, __float_as_uint(sqrtf(rs * (1.f + (float)(d + 4) * 1.1920929e-7f)) * (1.f + 2.4e-7f)));
         amax_s[0] = am;
     }
     __syncthreads();
@@ -221,6 +280,7 @@ __global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C
 int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dtype,
                        int64_t k_pad, const CenterPrep &cp) {
     cudaError_t e = cudaMemsetAsync(cp.cmax, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess && cp.emax) e = cudaMemsetAsync(cp.emax, 0, sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "memset cmax");
     k_center_prep<<<(unsigned)k_pad, 256, 0, c->stream>>>(C, k, d, dtype, cp);
     GBKM_LAUNCHED(c);

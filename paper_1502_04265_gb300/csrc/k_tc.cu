@@ -48,6 +48,12 @@ struct Args {
     const float *cnorm, *cscale, *xscale, *xnorm;
     const unsigned *cmax;
     float err_rel, err_abs;
+    // one-term BF16 with the operands' actual rounding residuals: ||x_i - bf16(x_i)|| per row and
+    // max_j ||c_j - bf16(c_j)|| (null: the worst case u ||x||, u ||c|| in err_rel); acc_g = the FP32
+    // accumulation factor d 2^-22, err_u2 = 2u of the score's own FP32 rounding
+    const float *xresid;
+    const unsigned *emax;
+    float acc_g, err_u2;
     // two-term BF16 centers: band width A (D_j + D_0) + Bc with A = pair_a ||x||,
     // Bc = pair_rel ||x|| cmax + pair_abs cmax^2, D = sqrt(XE + s), XE = ||x||^2 + single_rel ||x||
     // cmax + single_abs cmax^2 (pair_a == 0: the constant width 2 (err_rel ||x|| cmax + err_abs cmax^2))
@@ -585,6 +591,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
         int ab = 0;
         uint32_t aph = 0, xph = 0;
         const float cm = (EPI == E_ARGMIN) ? __uint_as_float(*a.cmax) : 0.f;
+        const float em = (EPI == E_ARGMIN && FORM == F_BF16 && a.xresid) ? __uint_as_float(*a.emax) : 0.f;
         uint8_t *ex = base + (size_t)a.stages * a.stage_bytes + 1024;  // epilogue shared memory
         for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
             const int64_t row = (int64_t)tile * BM + q * 32 + lane;
@@ -597,11 +604,20 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
             Band<CAND_MAX> band;
             {
                 const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
-                if (a.pair_a > 0.f)
+                if (a.pair_a > 0.f) {
                     band.reset(a.pair_rel * xr * cm + a.pair_abs * cm * cm, a.pair_a * xr,
                                xn * (1.f + 2.4e-7f) + a.single_rel * xr * cm + a.single_abs * cm * cm);
-                else
+                } else if (FORM == F_BF16 && a.xresid) {
+                    // with dx = x~ - x and e_j = c~_j - c_j: |x~.c~_j - x.c_j| <= ||dx|| (cmax + emax) +
+                    // ||x|| emax (Cauchy-Schwarz), plus the FP32 accumulation of d products,
+                    // d 2^-22 (||x|| + ||dx||)(cmax + emax); a score difference takes two of these
+                    const float dr = valid ? a.xresid[row] : 0.f, ce = cm + em;
+                    const float e1 = 2.f * (dr * ce + xr * em + a.acc_g * (xr + dr) * ce) + a.err_u2 * xr * cm +
+                                     a.err_abs * cm * cm;
+                    band.reset(2.f * e1 * (1.f + 1.0e-3f));
+                } else {
                     band.reset(2.f * (a.err_rel * xr * cm + a.err_abs * cm * cm));
+                }
                 band.lv = reinterpret_cast<float *>(ex) + eg * (2 * CAND_MAX * 128) + q * 32 + lane;
                 band.li = reinterpret_cast<int32_t *>(band.lv + CAND_MAX * 128);
             }
@@ -1398,6 +1414,12 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
     a.row_map = row_map;
     a.cnorm = cp.cnorm, a.cscale = cp.cscale, a.xscale = Xscales, a.xnorm = xnorm, a.cmax = cp.cmax;
     a.err_rel = err_rel, a.err_abs = err_abs;
+    if (form == F_BF16 && Xscales && cp.emax) {
+        // BF16 scales are the rows' rounding residuals (kmeans_quantize)
+        a.xresid = Xscales, a.emax = cp.emax;
+        a.acc_g = (float)((double)d * ldexp(1.0, -22) * (1 + 1e-6));
+        a.err_u2 = (float)(2.0 * ldexp(1.0, -24) * (1 + 1e-6));
+    }
     if (form == F_BF16X2) {
         // |x~ - x| <= u |x| with u = 2^-8 (BF16, nearest even), |c^ - c| <= u^2 |c| for hi + lo, FP32
         // accumulation of 2d products bounded by 2d 2^-22 relative (4x the textbook 2d 2^-24)

@@ -18,9 +18,10 @@ BF16_MIN_D = 256
 
 
 def exact_form(d):
-    """The faster of the two exact assignment forms for points of dimension d: "f32" (3xTF32)
-    below BF16_MIN_D, "bf16" (with the certified recheck) from there up."""
-    return "f32" if d < BF16_MIN_D else "bf16"
+    """The faster of the two exact assignment forms for points of dimension d: "bf16" (with the
+    certified recheck) from BF16_MIN_D up when the tensor-core engine takes the shape (d a
+    multiple of 8), "f32" otherwise."""
+    return "bf16" if d >= BF16_MIN_D and d % 8 == 0 else "f32"
 
 
 def lloyd(X, k, iters, u, w=None, compute="f32", engine="auto", C0=None, ctx=None,

@@ -35,12 +35,29 @@ def test_row_norms(gb, orc, n, d):
 
 
 @pytest.mark.parametrize("n,d", [(513, 64), (77, 1030), (5, 3)])
-def test_quantize_bf16_bitexact(gb, orc, n, d):
+@pytest.mark.parametrize("residuals", [False, True])
+def test_quantize_bf16_bitexact(gb, orc, n, d, residuals):
     X, _ = synth.gaussian_mixture(n, d, 4, seed=7)
     X[0, 0] = 0.0
-    Xq, _ = gb.kmeans_quantize(T(X), "bf16")
+    Xq, _ = gb.kmeans_quantize(T(X), "bf16", residuals=residuals)
     got = H(Xq.view(torch.int16)).view(np.uint16)
     assert np.array_equal(got, orc.quant_bf16(X))
+
+
+@pytest.mark.parametrize("n,d", [(513, 64), (77, 1030), (300, 37), (5, 3)])
+def test_quantize_bf16_residuals_bound(gb, orc, n, d):
+    """The rows' rounding residuals ||x - bf16(x)|| are upper bounds, above the exact value by no
+    more than the FP32 summation margin the kernel adds, sqrt(1 + (d + 4) 2^-23) (1 + 2.4e-7)."""
+    X, _ = synth.gaussian_mixture(n, d, 4, seed=8)
+    X[1] = 0.0
+    _, r = gb.kmeans_quantize(T(X), "bf16")
+    xq = orc.bf16_to_f32(orc.quant_bf16(X)).astype(np.float64)
+    exact = np.sqrt(((X.astype(np.float64) - xq) ** 2).sum(axis=1))
+    got = H(r).astype(np.float64)
+    assert np.all(got >= exact)
+    margin = np.sqrt(1 + (d + 4) * 2.0 ** -23) * (1 + 2.4e-7) * (1 + 1e-6)
+    assert np.all(got <= exact * margin + 1e-30)
+    assert got[1] == 0.0
 
 
 @pytest.mark.parametrize("n,d", [(300, 64), (40, 128), (33, 200), (7, 5)])
@@ -112,9 +129,13 @@ def test_assign_recheck_off_still_valid(gb, orc):
 
 
 # ------------------------------------------------------------------ A6 + A7
+# k up to 2,048 takes the shared-memory label tables and the one-launch offsets; k above, the
+# device-wide scan; d = 1,024 / 1,100 take 16 row loads in flight per thread, d = 64 / 1,030 eight
 @pytest.mark.parametrize("n,d,k,weighted", [(3000, 64, 10, False), (2049, 37, 25, True),
                                             (600, 1030, 7, False), (5, 3, 9, True),
-                                            (1500, 1100, 5, True), (900, 4, 3, False)])
+                                            (1500, 1100, 5, True), (900, 4, 3, False),
+                                            (6000, 16, 2048, False), (7000, 24, 2049, True),
+                                            (30000, 16, 3000, False), (2000, 1024, 40, False)])
 def test_update_matches_oracle(gb, orc, n, d, k, weighted):
     X, z = synth.gaussian_mixture(n, d, k, seed=n + k)
     lab = (z % max(1, k - 2)).astype(np.int32)       # leaves empty clusters when k > 2
@@ -133,10 +154,11 @@ def test_update_matches_oracle(gb, orc, n, d, k, weighted):
     assert cn == pytest.approx(ref["cost_new"], rel=COST_REL_F32)
 
 
-def test_update_is_bit_reproducible(gb):
-    X, z = synth.gaussian_mixture(20000, 128, 30, seed=2)
+@pytest.mark.parametrize("k", [30, 3000])
+def test_update_is_bit_reproducible(gb, k):
+    X, z = synth.gaussian_mixture(20000, 128, k, seed=2)
     Xg, lg = T(X), T(z.astype(np.int32))
-    C0 = T(np.zeros((30, 128), np.float32))
+    C0 = T(np.zeros((k, 128), np.float32))
     a = gb.kmeans_update(Xg, lg, C0)
     A = (H(a["C_new"]).copy(), H(a["cost_new"]).copy())
     b = gb.kmeans_update(Xg, lg, C0)

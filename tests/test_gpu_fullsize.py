@@ -93,3 +93,23 @@ def test_small_workload_full_run(gb, orc, form, engine):
     # drift a near-tie flip causes (trajectories are compared on cost only)
     ref_C, ref_L, ref_trace, _ = orc.lloyd(X, C0, 20)
     assert trace[-1, 1] == pytest.approx(ref_trace[-1], rel=1e-4)
+
+
+@pytest.mark.parametrize("d", [64, 300, 320])
+def test_auto_form_matches_f32(gb, d):
+    """driver.lloyd(compute="auto") takes FP32 below 256 dimensions or where d % 8 != 0 (d = 300) and
+    BF16 (certified recheck) otherwise (d = 320); both are exact, so the run matches the FP32 run
+    from the same seeds."""
+    from paper_1502_04265_gb300 import driver
+
+    X, _ = synth.gaussian_mixture(20_000, d, 12, seed=d)
+    u = torch.from_numpy(synth.seed_uniforms(12, seed=1)).to(DEV)
+    Xg = torch.from_numpy(X).to(DEV)
+    a = driver.lloyd(Xg, 12, 8, u, compute="auto", return_trace=True)
+    b = driver.lloyd(Xg, 12, 8, u, compute="f32", return_trace=True)
+    gb.gbkm_sync()
+    assert torch.equal(a["seed_idx"], b["seed_idx"])
+    same = float((a["labels"] == b["labels"]).float().mean().item())
+    assert same >= 0.9999
+    ta, tb = a["trace"].cpu().numpy(), b["trace"].cpu().numpy()
+    assert abs(ta[-1, 1] - tb[-1, 1]) <= 1e-6 * tb[-1, 1]

@@ -160,3 +160,24 @@ def test_tc_bf16_pairs_near_bisectors(gb, orc, scale, terms):
     lab, _, nre = _assign(gb, X, C, "bf16", center_terms=terms)
     assert_labels_match(orc, X, C.astype(np.float64), lab)
     assert nre > 0 and (scale > 5 or terms == 1 or nre < n)
+
+
+def test_bf16_residual_band_exact_with_fewer_rechecks(gb, orc):
+    """The band built from the rows' and centers' actual BF16 residuals (side data of the quantised
+    copy) is narrower than the worst case u ||x|| ||c||: fewer rows are rechecked, and the labels
+    are still the exact nearest centers."""
+    X, _ = synth.gaussian_mixture(6000, 1024, 100, seed=21)
+    C = X[(synth.seed_uniforms(100, 3) * 6000).astype(np.int64)].copy()
+    Xg, Cg = T(X), T(C)
+    Xb, Xr = gb.kmeans_quantize(Xg, "bf16")
+    out = []
+    for sc in (None, Xr):
+        nre = torch.zeros(1, dtype=torch.int64, device=DEV)
+        lab = gb.kmeans_assign(Xg, Cg, Xop=Xb, Xop_scales=sc, compute="bf16", engine="tcgen05", n_rechecked=nre)
+        gb.gbkm_sync()
+        assert_labels_match(orc, X, C.astype(np.float64), H(lab))
+        out.append(int(H(nre)[0]))
+    worst, resid = out
+    assert resid <= worst
+    if worst >= 100:
+        assert resid < worst
