@@ -762,6 +762,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                         if (a.bias) {
 #pragma unroll
                             for (int g = 0; g < W / 4; ++g) {
+                                if (4 * g >= 16 && jc + 16 >= (int)a.k) break;
                                 const float4 b4 = __ldg(reinterpret_cast<const float4 *>(a.bias + jc) + g);
                                 sv[4 * g] += b4.x, sv[4 * g + 1] += b4.y, sv[4 * g + 2] += b4.z, sv[4 * g + 3] += b4.w;
                             }
