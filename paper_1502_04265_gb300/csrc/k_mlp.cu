@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(256) k_center_sep(const float *__restrict__ C,
     if (lane == 0) s2[j] = 0.25f * best;
 }
 
-// one warp per point: exact FP32 distances to its candidates in rank order until one, b, satisfies
+// one warp per point (four candidates at a time, the row held in registers, when d is a multiple of
+// 128 up to 1,024): exact FP32 distances to its candidates in rank order until one, b, satisfies
 // d(x, c_b) < s2[b] = min_c ||c_b - c||^2 / 4 certifiably (relative margins of 1e-5 cover the FP32
 // rounding of both sides): then c_b is the unique nearest center of all k (Elkan's bound), so the
 // first such candidate is the label and the rest need no distance; a point without one goes to the
@@ -154,17 +155,55 @@ __global__ void __launch_bounds__(256) k_cand_check(const float *__restrict__ X,
     if (i >= n) return;
     const float *x = X + i * d;
     int arg = -1;
-    for (int q = 0; q < m && arg < 0; ++q) {
-        const int j = cand[i * m + q];
-        if (j < 0 || j >= k) continue;
-        const float *c = C + (int64_t)j * d;
-        float a = 0.f;
-        for (int64_t t = lane; t < d; t += 32) {
-            const float e = x[t] - c[t];
-            a = fmaf(e, e, a);
+    const bool v4 = (d % 128) == 0 && d <= 1024 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+    if (v4) {
+        // the row in registers (d / 128 float4 per lane) and four candidates' rows in flight at a
+        // time; the first of them in rank order that certifies is taken
+        const int nv = (int)(d / 128);
+        float4 xr[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+            xr[v] = v < nv ? __ldg(reinterpret_cast<const float4 *>(x) + v * 32 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q0 = 0; q0 < m && arg < 0; q0 += 4) {
+            int js[4];
+            float acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = q0 + u < m ? cand[i * m + q0 + u] : -1;
+                js[u] = (j >= 0 && j < k) ? j : -1;
+                acc[u] = 0.f;
+            }
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                if (v >= nv) break;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (js[u] < 0) continue;
+                    const float4 c4 = __ldg(reinterpret_cast<const float4 *>(C + (int64_t)js[u] * d) + v * 32 + lane);
+                    const float e0 = xr[v].x - c4.x, e1 = xr[v].y - c4.y, e2 = xr[v].z - c4.z, e3 = xr[v].w - c4.w;
+                    acc[u] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, acc[u]))));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = warp_sum_f(acc[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (arg < 0 && js[u] >= 0 && acc[u] * (1.f + 1e-5f) < s2[js[u]] * (1.f - 1e-5f)) arg = js[u];
         }
-        a = warp_sum_f(a);
-        if (a * (1.f + 1e-5f) < s2[j] * (1.f - 1e-5f)) arg = j;
+    } else {
+        for (int q = 0; q < m && arg < 0; ++q) {
+            const int j = cand[i * m + q];
+            if (j < 0 || j >= k) continue;
+            const float *c = C + (int64_t)j * d;
+            float a = 0.f;
+            for (int64_t t = lane; t < d; t += 32) {
+                const float e = x[t] - c[t];
+                a = fmaf(e, e, a);
+            }
+            a = warp_sum_f(a);
+            if (a * (1.f + 1e-5f) < s2[j] * (1.f - 1e-5f)) arg = j;
+        }
     }
     if (lane == 0) {
         if (arg >= 0) {
