@@ -330,12 +330,13 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
                      aligned16(X) && (d % 4) == 0;
     const int64_t ne = esc ? n : 0;
     WsPlan p;
-    size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(2),
+    // o_cm: the call's counters, zeroed by one memset: cmax, emax, flag count, escalation count (2)
+    size_t o_xn = p.take<float>(xnorm ? 0 : n), o_cn = p.take<float>(k_pad), o_cm = p.take<unsigned>(8),
            o_cop = p.take<char>(use_tc ? k_pad * d * esz : 0),
            o_clo = p.take<float>(use_tc && (o.compute == GBKM_F32 || split) ? k_pad * d : 0),
            o_cs = p.take<float>(k_pad), o_fl = p.take<int32_t>(n), o_cd = p.take<int32_t>(n * gbkm::CAND_STRIDE),
-           o_fc = p.take<int32_t>(1);
-    size_t o_el = p.take<int32_t>(ne), o_ec = p.take<int32_t>(esc ? 2 : 0), o_xe = p.take<float>(ne * d),
+           o_fc = o_cm + 2 * sizeof(unsigned);
+    size_t o_el = p.take<int32_t>(ne), o_ec = o_cm + 3 * sizeof(unsigned), o_xe = p.take<float>(ne * d),
            o_xne = p.take<float>(ne), o_ehi = p.take<float>(esc ? k_pad * d : 0),
            o_elo = p.take<float>(esc ? k_pad * d : 0), o_fl2 = p.take<int32_t>(ne),
            o_cd2 = p.take<int32_t>(ne * gbkm::CAND_STRIDE);
@@ -347,6 +348,8 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     gbkm::CenterPrep cp;
     cp.cnorm = ws_at<float>(ws, o_cn);
     cp.cmax = ws_at<unsigned>(ws, o_cm);
+    if (cudaError_t e0 = cudaMemsetAsync(cp.cmax, 0, 8 * sizeof(unsigned), c->stream); e0 != cudaSuccess)
+        return cuda_check(c, e0, "memset counters");
     // one-term BF16 with the rows' rounding residuals: the centers' largest residual as well
     cp.emax = (use_tc && o.compute == GBKM_BF16 && !split && Xop_scales) ? cp.cmax + 1 : nullptr;
     cp.cop = use_tc ? ws_at<void>(ws, o_cop) : nullptr;
@@ -364,8 +367,7 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
     out.flag_list = o.recheck ? ws_at<int32_t>(ws, o_fl) : nullptr;
     out.cand = ws_at<int32_t>(ws, o_cd);
     out.flag_count = ws_at<int32_t>(ws, o_fc);
-    cudaError_t e = cudaMemsetAsync(out.flag_count, 0, sizeof(int32_t), c->stream);
-    if (e != cudaSuccess) return cuda_check(c, e, "memset flag count");
+    cudaError_t e = cudaSuccess;
     float err_rel, err_abs;
     gbkm::score_error_coeffs(o.compute, use_tc, d, err_rel, err_abs);
     prof_begin(c, use_tc ? "assign_tc" : "assign_simt");
@@ -383,8 +385,6 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
         es.Xe = ws_at<float>(ws, o_xe);
         es.xne = ws_at<float>(ws, o_xne);
         es.xnorm = xn;
-        e = cudaMemsetAsync(es.count, 0, 2 * sizeof(int32_t), c->stream);
-        if (e != cudaSuccess) return cuda_check(c, e, "memset escalation count");
         prof_begin(c, "recheck");
         rc = gbkm::launch_recheck(c, X, n, d, C, k, out, n_rechecked, &es);
         prof_end(c);

@@ -209,6 +209,7 @@ struct CenterPrep {
     float *esc_hi;      // 3xTF32 split of the centers for the escalation pass (k_pad x d), or null
     float *esc_lo;
 };
+// (cp.cmax and cp.emax are maxima by atomics: the caller zeroes them first)
 int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dtype,
                        int64_t k_pad, const CenterPrep &cp);
 

@@ -279,9 +279,6 @@ __global__ void __launch_bounds__(256) k_center_prep(const float *__restrict__ C
 
 int launch_center_prep(gbkm_ctx *c, const float *C, int64_t k, int64_t d, int dtype,
                        int64_t k_pad, const CenterPrep &cp) {
-    cudaError_t e = cudaMemsetAsync(cp.cmax, 0, sizeof(unsigned), c->stream);
-    if (e == cudaSuccess && cp.emax) e = cudaMemsetAsync(cp.emax, 0, sizeof(unsigned), c->stream);
-    if (e != cudaSuccess) return cuda_check(c, e, "memset cmax");
     k_center_prep<<<(unsigned)k_pad, 256, 0, c->stream>>>(C, k, d, dtype, cp);
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "center_prep launch");

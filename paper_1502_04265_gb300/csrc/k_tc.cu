@@ -71,6 +71,10 @@ struct Args {
     int out_bf16;
     float *Ypre;
     int64_t ldpre;
+    // bias_mma: the bias enters the accumulator through one more K block per unit (A: the ones
+    // operand, tmA2; B: the bias operand, tmB2, columns (bf16(b), bf16(b - bf16(b)), 0, ...)), so the
+    // epilogues add none (bias is then null)
+    int bias_mma;
     // top-m epilogue: the m largest (acc + bias) of every row, over all N chunks
     int32_t *top_idx;
     float *top_val;
@@ -398,7 +402,7 @@ constexpr int tc_threads() {
 template <int FORM, int EPI>
 __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-         const __grid_constant__ CUtensorMap tmB2, const Args a) {
+         const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ CUtensorMap tmA2, const Args a) {
     constexpr bool X3 = (FORM == F_TF32X3);
     constexpr bool TWO_B = X3 || FORM == F_BF16X2;  // a second center operand (lo part)
     constexpr int NG = epi_groups<EPI>();
@@ -478,6 +482,23 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                             ph ^= 1;
                         }
                     }
+                    if constexpr (FORM == F_BF16) {
+                        if (a.bias_mma) {
+                            // the bias block: the ones operand (the same tile for every row tile) and
+                            // this chunk's rows of the bias operand
+                            if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) goto producer_done;
+                            uint8_t *st = base + (size_t)s * a.stage_bytes;
+                            mbar_expect_tx(&full[s], a.tx_bytes);
+                            tma_load_2d(st, &tmA2, &full[s], 0, 0);
+                            tma_load_2d(st + a.a_bytes, &tmB2, &full[s], 0, nc * a.bn);
+                            issued |= 1u << s;
+                            last_par = (last_par & ~(1u << s)) | (ph << s);
+                            if (++s == a.stages) {
+                                s = 0;
+                                ph ^= 1;
+                            }
+                        }
+                    }
                 }
             }
         producer_done:
@@ -531,6 +552,22 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                         if (++s == a.stages) {
                             s = 0;
                             ph ^= 1;
+                        }
+                    }
+                    if constexpr (FORM == F_BF16) {
+                        if (a.bias_mma) {
+                            // one K = 16 step: ones x (bias head, bias tail, 0 ...) adds the bias
+                            if (!mbar_wait(&full[s], ph, abort_flag)) goto mma_done;
+                            tc_fence_after();
+                            uint8_t *st = base + (size_t)s * a.stage_bytes;
+                            tc_mma<FORM>(d_tmem, sw128_desc(st), sw128_desc(st + a.a_bytes), a.idesc, 1u);
+                            tc_commit(&empty[s]);
+                            last_bar = &empty[s];
+                            last_parity = ph;
+                            if (++s == a.stages) {
+                                s = 0;
+                                ph ^= 1;
+                            }
                         }
                     }
                     tc_commit(&accf[ab]);
@@ -1362,13 +1399,13 @@ static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra
 
 template <int FORM, int EPI>
 static int launch(gbkm_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &B2, Args &args,
-                  const Plan &p) {
+                  const Plan &p, const CUtensorMap *A2 = nullptr) {
     auto kern = k_tc<FORM, EPI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 smem attribute");
     const int threads = tc_threads<FORM, EPI>();
     const int grid = (int)std::min<int64_t>(c->sm_count, args.m_tiles);
-    kern<<<grid, threads, p.smem, c->stream>>>(A, B, B2, args);
+    kern<<<grid, threads, p.smem, c->stream>>>(A, B, B2, A2 ? *A2 : A, args);
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "tcgen05 kernel launch");
 }
@@ -1543,6 +1580,20 @@ int launch_assign_tc_batched(gbkm_ctx *c, int dtype, const void *maps, const BPr
 }
 
 
+// Operands of the bias K block: ones (BM x 64 BF16, columns 0 and 1 = 1) and, per output column j,
+// (bf16(b_j), bf16(b_j - bf16(b_j)), 0, ..., 0): the MMA adds b_j to within 2^-17 |b_j|.
+__global__ void k_bias_operands(const float *__restrict__ bias, int64_t N, __nv_bfloat16 *__restrict__ ones,
+                                __nv_bfloat16 *__restrict__ bb) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < (int64_t)tc::BM * 64) ones[i] = __float2bfloat16_rn((i % 64) < 2 ? 1.f : 0.f);
+    if (i < N * 64) {
+        const int64_t j = i / 64, col = i % 64;
+        const float b = bias[j];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        bb[i] = col == 0 ? hi : (col == 1 ? __float2bfloat16_rn(b - __bfloat162float(hi)) : __float2bfloat16_rn(0.f));
+    }
+}
+
 // D = A B^T on tcgen05 (BF16 operands, FP32 accumulation) with a fused epilogue: store
 // act(D + bias) in FP32 or BF16 (and optionally the FP32 pre-activation), or, when top_idx is
 // given, the indices of the topm largest entries of every row of D + bias (D never written).
@@ -1572,9 +1623,37 @@ int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, in
     a.bias = bias, a.act = act, a.out_bf16 = out_bf16, a.Ypre = Ypre, a.ldpre = ldpre;
     a.top_idx = top_idx, a.top_val = top_val, a.topm = topm;
     a.status = c->status;
-    if (grouped) return launch<F_BF16, E_TOPG>(c, tA, tB, tB, a, p);
-    if (topk) return launch<F_BF16, E_TOPM>(c, tA, tB, tB, a, p);
-    return launch<F_BF16, E_STORE>(c, tA, tB, tB, a, p);
+    // the bias through the MMA (one more K block per unit) instead of loads and adds in the epilogue
+    CUtensorMap tA2 = tA, tB2 = tB;
+    void *bops = nullptr;
+    if (bias) {
+        const size_t ones_n = (size_t)BM * 64, bb_n = (size_t)N * 64;
+        cudaError_t e = cudaMallocAsync(&bops, sizeof(__nv_bfloat16) * (ones_n + bb_n), c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(c, GBKM_ENOMEM, "gemm: bias operand allocation failed");
+        }
+        __nv_bfloat16 *ones = static_cast<__nv_bfloat16 *>(bops), *bb = ones + ones_n;
+        k_bias_operands<<<(unsigned)ceil_div((int64_t)std::max(ones_n, bb_n), 256), 256, 0, c->stream>>>(bias, N, ones,
+                                                                                                      bb);
+        GBKM_LAUNCHED(c);
+        if (!make_tmap(&tA2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, ones, 64, (uint64_t)BM, 2, BM) ||
+            !make_tmap(&tB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bb, 64, (uint64_t)N, 2, (uint32_t)p.bn)) {
+            cudaFreeAsync(bops, c->stream);
+            return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the bias operands");
+        }
+        a.bias = nullptr;
+        a.bias_mma = 1;
+    }
+    int rc;
+    if (grouped)
+        rc = launch<F_BF16, E_TOPG>(c, tA, tB, tB2, a, p, &tA2);
+    else if (topk)
+        rc = launch<F_BF16, E_TOPM>(c, tA, tB, tB2, a, p, &tA2);
+    else
+        rc = launch<F_BF16, E_STORE>(c, tA, tB, tB2, a, p, &tA2);
+    if (bops) cudaFreeAsync(bops, c->stream);
+    return rc;
 }
 
 }  // namespace gbkm
