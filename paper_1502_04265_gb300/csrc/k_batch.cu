@@ -764,7 +764,7 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
     wbytes += 4096 + count * (sizeof(BProb) + 3 * 128 + sizeof(gbkm_problem) + 8) + tiles * 4 + blocks * 8 +
               npairs * (8 + sizeof(PairInfo)) + nseg * 8 + G * (4 + 4 + 4 + 8 + 16 + 16 * maxcb) + 2 * hist_total * 4 +
               nbs * 4 + rows_total * 4 + items_max * 16 + pelems * 8 + npairs * 16 + (int64_t)count * 4 +
-              rows_total * BFLAG_STRIDE * 4 + 64 * 256;
+              rows_total * BFLAG_STRIDE * 4 + 64 * 256 + blocks * 8 + npairs * 8 + 2 * 256;
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, wbytes, &rc);
     if (!ws) return rc;
@@ -794,6 +794,10 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
     int32_t *d_tile_prob = carve<int32_t>(cur, tiles);
     int2 *d_blocks = carve<int2>(cur, blocks);
     int2 *d_pairs = carve<int2>(cur, npairs);
+    // the same tables with the problems in decreasing k: round r of the seeding launches only the
+    // prefix of problems with k > r
+    int2 *d_sblocks = carve<int2>(cur, blocks);
+    int2 *d_spairs = carve<int2>(cur, npairs);
     PairInfo *d_pinfo = carve<PairInfo>(cur, npairs);
     int2 *d_segs = carve<int2>(cur, nseg);
     int64_t *d_crow0 = carve<int64_t>(cur, count);
@@ -845,6 +849,19 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
             gb += b.k;
         }
     }
+    std::vector<int64_t> ord(count);
+    for (int64_t p = 0; p < count; ++p) ord[p] = p;
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return P[x].k > P[y].k; });
+    std::vector<int2> sblk_tab, spairs;
+    std::vector<int64_t> sblk_pre(count + 1, 0);  // blocks of the first i problems in that order
+    sblk_tab.reserve(blocks);
+    spairs.reserve(npairs);
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t p = ord[i];
+        for (int64_t r = 0; r < P[p].n; r += RB) sblk_tab.push_back(make_int2((int)p, (int)r));
+        for (int64_t s2 = 0; s2 < S; ++s2) spairs.push_back(make_int2((int)p, (int)s2));
+        sblk_pre[i + 1] = (int64_t)sblk_tab.size();
+    }
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
 #define CPY(dst, src, bytes) \
@@ -855,6 +872,8 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
     CPY(d_tile_prob, tile_prob.data(), 4 * tiles);
     CPY(d_blocks, blk_tab.data(), 8 * blocks);
     CPY(d_pairs, pairs.data(), 8 * npairs);
+    CPY(d_sblocks, sblk_tab.data(), 8 * blocks);
+    CPY(d_spairs, spairs.data(), 8 * npairs);
     CPY(d_pinfo, pinfo.data(), sizeof(PairInfo) * npairs);
     CPY(d_segs, segs.data(), 8 * nseg);
     CPY(d_crow0, crow0.data(), 8 * count);
@@ -898,14 +917,16 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
     pb("seed_batched");
     k_b_seed_first<<<(unsigned)npairs, 128, 0, st>>>(d_probs, d_pairs);
     c->launches += 2;
+    int64_t na = count;  // problems with k > r: a prefix of the decreasing-k order
     for (int r = 1; r < kmax_all; ++r) {
+        while (na > 0 && P[ord[na - 1]].k <= r) --na;
+        const unsigned nbl = (unsigned)sblk_pre[na], npr = (unsigned)(na * S);
         if (r >= 2) {
-            k_b_cc<<<dim3((unsigned)ceil_div((int64_t)(r - 1) * 32, 256), (unsigned)npairs), 256, 0, st>>>(d_probs,
-                                                                                                        d_pairs, r);
+            k_b_cc<<<dim3((unsigned)ceil_div((int64_t)(r - 1) * 32, 256), npr), 256, 0, st>>>(d_probs, d_spairs, r);
             c->launches += 1;
         }
-        k_b_d2<<<(unsigned)blocks, 256, 0, st>>>(d_probs, d_blocks, r);
-        k_b_pick<<<(unsigned)npairs, PICKB_T, 0, st>>>(d_probs, d_pairs, r, c->status);
+        k_b_d2<<<nbl, 256, 0, st>>>(d_probs, d_sblocks, r);
+        k_b_pick<<<npr, PICKB_T, 0, st>>>(d_probs, d_spairs, r, c->status);
         c->launches += 2;
     }
     pe();
