@@ -132,14 +132,34 @@ __global__ void __launch_bounds__(256) k_b_d2(const BProb *__restrict__ probs, c
         }
         __syncthreads();
         const int m = nlist;
-        for (int e = w; e < m; e += 8) {
-            const int t = list[e];
+        // lpr lanes per listed row (32 / lpr rows per warp at a time): short rows keep the lanes
+        // busy and their sums take fewer butterfly steps
+        const bool v4 = (P.d % 4) == 0 && ((reinterpret_cast<uintptr_t>(P.X) & 15) == 0) &&
+                        ((reinterpret_cast<uintptr_t>(c) & 15) == 0);
+        const int lpr = lanes_per_row(P.d, v4 ? 4 : 1), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
+        for (int e0 = w * rpw; e0 < m; e0 += 8 * rpw) {
+            const int e = e0 + sub;
+            const bool has = e < m;
+            const int t = has ? list[e] : 0;
             const int64_t i = r0 + t;
-            const float *x = P.X + i * P.d;
             DF acc;
-            for (int64_t q = lane; q < P.d; q += 32) acc.add_sqdiff(x[q], c[q]);
-            const double dist = warp_sum_df(acc);
-            if (lane == 0 && (jc == 0 || dist < nd_s[t])) {
+            if (has) {
+                const float *x = P.X + i * P.d;
+                if (v4) {
+                    for (int64_t q = sl; q < P.d / 4; q += lpr) {
+                        const float4 a4 = __ldg(reinterpret_cast<const float4 *>(x) + q);
+                        const float4 b4 = __ldg(reinterpret_cast<const float4 *>(c) + q);
+                        acc.add_sqdiff(a4.x, b4.x);
+                        acc.add_sqdiff(a4.y, b4.y);
+                        acc.add_sqdiff(a4.z, b4.z);
+                        acc.add_sqdiff(a4.w, b4.w);
+                    }
+                } else {
+                    for (int64_t q = sl; q < P.d; q += lpr) acc.add_sqdiff(x[q], c[q]);
+                }
+            }
+            const double dist = group_sum_df(acc, lpr);
+            if (has && sl == 0 && (jc == 0 || dist < nd_s[t])) {
                 nd_s[t] = dist;
                 D2[i] = dist;
                 A[i] = (int32_t)jc;

@@ -53,27 +53,34 @@ __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, 
     }
     __syncthreads();
     const int m = nlist;
-    for (int e = wid; e < m; e += 8) {
-        const int t = list[e];
+    // lpr lanes per listed row (32 / lpr rows per warp at a time), so that short rows keep the
+    // lanes busy and their sums take fewer butterfly steps
+    const int lpr = lanes_per_row(d, VW), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
+    for (int e0 = wid * rpw; e0 < m; e0 += 8 * rpw) {
+        const int e = e0 + sub;
+        const bool has = e < m;
+        const int t = has ? list[e] : 0;
         const int64_t i = r0 + t;
-        const float *x = X + i * d;
         DF acc;
-        if constexpr (VW == 4) {
-            const float4 *x4 = reinterpret_cast<const float4 *>(x);
-            const float4 *c4 = reinterpret_cast<const float4 *>(c);
+        if (has) {
+            const float *x = X + i * d;
+            if constexpr (VW == 4) {
+                const float4 *x4 = reinterpret_cast<const float4 *>(x);
+                const float4 *c4 = reinterpret_cast<const float4 *>(c);
 #pragma unroll 4
-            for (int64_t q = lane; q < d / 4; q += 32) {
-                float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
-                acc.add_sqdiff(a.x, b.x);
-                acc.add_sqdiff(a.y, b.y);
-                acc.add_sqdiff(a.z, b.z);
-                acc.add_sqdiff(a.w, b.w);
+                for (int64_t q = sl; q < d / 4; q += lpr) {
+                    float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
+                    acc.add_sqdiff(a.x, b.x);
+                    acc.add_sqdiff(a.y, b.y);
+                    acc.add_sqdiff(a.z, b.z);
+                    acc.add_sqdiff(a.w, b.w);
+                }
+            } else {
+                for (int64_t q = sl; q < d; q += lpr) acc.add_sqdiff(x[q], c[q]);
             }
-        } else {
-            for (int64_t q = lane; q < d; q += 32) acc.add_sqdiff(x[q], c[q]);
         }
-        const double dist = warp_sum_df(acc);
-        if (lane == 0 && (j == 0 || dist < nd_s[t])) {
+        const double dist = group_sum_df(acc, lpr);
+        if (has && sl == 0 && (j == 0 || dist < nd_s[t])) {
             nd_s[t] = dist;
             D2[i] = dist;
             A[i] = (int32_t)j;
