@@ -152,7 +152,7 @@ __device__ __forceinline__ double group_sum_df(DF a, int width) {
 
 // lanes per row for a row of d floats read as float4 (vw = 4) or singly: the smallest power of two
 // covering the row's vectors, at most 32
-__device__ __forceinline__ int lanes_per_row(int64_t d, int vw) {
+__host__ __device__ __forceinline__ int lanes_per_row(int64_t d, int vw) {
     const int64_t nv = vw == 4 ? d / 4 : d;
     int l = 1;
     while (l < 32 && l < nv) l <<= 1;

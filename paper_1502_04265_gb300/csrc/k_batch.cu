@@ -179,15 +179,20 @@ __global__ void __launch_bounds__(256) k_b_cc(const BProb *__restrict__ probs, c
     const int2 ps = pairs[blockIdx.y];
     const BProb &P = probs[ps.x];
     if (r >= P.k || P.stop[ps.y]) return;
-    const int lane = threadIdx.x & 31;
+    // lpr lanes per earlier center (the grid provides 32; the rest of a warp's lanes take further
+    // centers): short rows keep the lanes busy
+    const int lpr = lanes_per_row(P.d, 1), sl = (threadIdx.x & 31) % lpr;
     const int64_t jc = r - 1;
-    const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (a >= jc) return;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t a = g / lpr;
+    if ((g & ~(int64_t)31) / lpr >= jc) return;  // the whole warp is past the last center
+    const bool has = a < jc;
     const float *C = P.C[0] + (int64_t)ps.y * P.k * P.d;
     DF acc;
-    for (int64_t t = lane; t < P.d; t += 32) acc.add_sqdiff(C[jc * P.d + t], C[a * P.d + t]);
-    const double v = warp_sum_df(acc);
-    if (lane == 0) P.cc[(int64_t)ps.y * P.k + a] = v;
+    if (has)
+        for (int64_t t = sl; t < P.d; t += lpr) acc.add_sqdiff(C[jc * P.d + t], C[a * P.d + t]);
+    const double v = group_sum_df(acc, lpr);
+    if (has && sl == 0) P.cc[(int64_t)ps.y * P.k + a] = v;
 }
 
 __device__ double block_incl_scan_db(double v, double *sh) {

@@ -97,14 +97,18 @@ __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, 
 __global__ void __launch_bounds__(256) k_center_dist(const float *__restrict__ C, int64_t d, int64_t j,
                                                      double *__restrict__ cc, const int *__restrict__ stop) {
     if (*stop) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (a >= j) return;
+    // lpr lanes per earlier center (32 / lpr centers per warp)
+    const int lpr = lanes_per_row(d, 1), sl = (threadIdx.x & 31) % lpr;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t a = g / lpr;
+    if ((g & ~(int64_t)31) / lpr >= j) return;  // the whole warp is past the last center
+    const bool has = a < j;
     const float *cj = C + j * d, *ca = C + a * d;
     DF acc;
-    for (int64_t t = lane; t < d; t += 32) acc.add_sqdiff(cj[t], ca[t]);
-    const double v = warp_sum_df(acc);
-    if (lane == 0) cc[a] = v;
+    if (has)
+        for (int64_t t = sl; t < d; t += lpr) acc.add_sqdiff(cj[t], ca[t]);
+    const double v = group_sum_df(acc, lpr);
+    if (has && sl == 0) cc[a] = v;
 }
 
 // block sums of w (first center of a weighted run)
@@ -298,7 +302,8 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
         const float *cprev = C_out + jc * d;
         if (jc > 0) {
             prof_begin(c, "seed_cc");
-            k_center_dist<<<(unsigned)ceil_div(jc * 32, 256), 256, 0, c->stream>>>(C_out, d, jc, cc, stop);
+            k_center_dist<<<(unsigned)ceil_div(jc * lanes_per_row(d, 1), 256), 256, 0, c->stream>>>(C_out, d, jc, cc,
+                                                                                                     stop);
             prof_end(c);
             c->launches += 1;
         }
