@@ -136,29 +136,6 @@ __device__ __forceinline__ double warp_sum_df(DF a) {
     return a.value();
 }
 
-// the same within every aligned group of `width` lanes (a power of two <= 32; every lane of the
-// warp calls it): each group gets the sum of its own lanes
-__device__ __forceinline__ double group_sum_df(DF a, int width) {
-    for (int o = width >> 1; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, a.hi, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, a.lo, o);
-        float s, e;
-        two_sum(a.hi, h2, s, e);
-        a.hi = s;
-        a.lo = __fadd_rn(__fadd_rn(a.lo, l2), e);
-    }
-    return a.value();
-}
-
-// lanes per row for a row of d floats read as float4 (vw = 4) or singly: the smallest power of two
-// covering the row's vectors, at most 32
-__host__ __device__ __forceinline__ int lanes_per_row(int64_t d, int vw) {
-    const int64_t nv = vw == 4 ? d / 4 : d;
-    int l = 1;
-    while (l < 32 && l < nv) l <<= 1;
-    return l;
-}
-
 // deterministic tree sum of blockDim.x doubles in shared memory (blockDim.x a power of two);
 // every thread must call it; returns the total to every thread
 __device__ __forceinline__ double block_tree_sum_d(double v, double *sh) {

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "seed_util.cuh"
 
 namespace gbkm {
 

@@ -8,6 +8,7 @@
 // new distance exceeds D and min(D^2, ||x - c_new||^2) = D^2: the point's row is not read and D^2
 // keeps its bits.  The center-to-center distances of a round take one small kernel.
 #include "internal.cuh"
+#include "seed_util.cuh"
 
 namespace gbkm {
 
