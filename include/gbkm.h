@@ -309,7 +309,8 @@ int64_t kmeans_mlp_param_count(int64_t d_in, int64_t hidden, int64_t k);
 /* D = A B^T on the tensor cores with a fused epilogue (building block of the MLP):
  * A: M x K, B: N x K, BF16 row-major (K % 8 == 0, N % 16 == 0, 16-byte aligned);
  * Y[i, j] = act(D[i, j] + bias[j]) (act 0: none, 1: GELU), FP32 or BF16 (out_bf16), row stride ldy.
- * bias may be NULL. */
+ * bias may be NULL; it enters the FP32 accumulator through the tensor cores as the BF16 head and
+ * tail of each bias[j] (2^-17 relative), the same way in every GEMM of the MLP. */
 int kmeans_gemm_bf16(gbkm_ctx *ctx, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                      const float *bias, int32_t act, int32_t out_bf16, void *Y, int64_t ldy);
 
