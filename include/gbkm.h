@@ -187,10 +187,11 @@ int kmeans_assign(gbkm_ctx *ctx, const void *Xop, const float *Xop_scales, const
  * N_j = sum w_i, S_j = sum w_i x_i, Q_j = sum w_i ||x_i||^2 over rows labelled j;
  * C_new[j] = S_j / N_j, or C_old[j] when N_j == 0 (empty cluster keeps its center).
  * The rows are grouped by a stable counting sort of the labels (per-segment
- * histograms with warp-aggregated match_any counting, a device-wide scan, a
- * stable scatter), then each cluster's rows are summed in fixed-size chunks
- * with error-free FP32 transformations and the chunks combined in FP64 in
- * chunk order: no floating-point atomics, bit-reproducible.
+ * histograms with warp-aggregated match_any counting; for k <= 2048 one launch
+ * scans each cluster's row of the table, else a device-wide scan; a stable
+ * scatter), then each cluster's rows are summed in fixed-size chunks with
+ * error-free FP32 transformations and the chunks combined in FP64 in chunk
+ * order: no floating-point atomics, bit-reproducible.
  * Costs from the CF identity (Section 2.1), in FP64:
  *   cost_old = sum_j Q_j - 2 c_old_j . S_j + N_j ||c_old_j||^2 = cost(C_old, labels)
  *   cost_new = sum_j Q_j - ||S_j||^2 / N_j                      = cost(C_new, labels)
