@@ -3,7 +3,7 @@
 // Pipeline (all on the context's stream, no host synchronisation, no float atomics):
 //   1. k_hist      one warp per label segment: warp-aggregated (match_any) label histogram,
 //                  column s of the cluster-major table hist[j * S + s]
-//   2. offsets     k <= 2048 (per-warp tables in shared memory): k_row_scan, one warp per cluster
+//   2. offsets     k <= 2048 (per-warp tables in shared memory): k_row_scan, one CTA per cluster
 //                  scanning its row, the last CTA deriving the cluster starts and the work items;
 //                  otherwise a device-wide exclusive scan of the table, k_starts and k_items
 //   3. k_scatter   one warp per segment: stable rank inside the warp + running slot -> perm
@@ -236,45 +236,35 @@ __global__ void __launch_bounds__(SCAN_T) k_items(const int32_t *__restrict__ st
     if (threadIdx.x == 0) item_start[k] = total;
 }
 
-// Offsets of the shared-memory path in one launch: one warp per cluster j scans its row of the
+// Offsets of the shared-memory path in one launch: one CTA per cluster j scans its row of the
 // table, off[j, s] = sum_{s' < s} hist[j, s'] (relative to the cluster's first slot), and stores
 // the row total cnt[j]; the last CTA to finish (atomic ticket, zeroed by k_hist_sm) turns the
 // totals into start[] (exclusive scan over clusters, start[k] = valid rows) and item_start[]
 // (work items of R rows per cluster, item_start[k] = total).  No CTA waits for another.
-constexpr int ROWSCAN_U = 8;  // table entries per lane loaded together
 __global__ void __launch_bounds__(256) k_row_scan(const int32_t *__restrict__ hist, int64_t k, int64_t S,
                                                   int64_t R, int32_t *__restrict__ off, int32_t *cnt,
                                                   int32_t *__restrict__ start, int32_t *__restrict__ item_start,
                                                   int32_t *ticket) {
     __shared__ int32_t sh[32];
     __shared__ int last;
-    const int lane = threadIdx.x & 31;
-    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (j < k) {
+    // cluster j = blockIdx.x: every thread scans a contiguous range of the row, one block scan
+    // places the ranges
+    {
+        const int64_t j = blockIdx.x;
         const int32_t *h = hist + j * S;
         int32_t *o = off + j * S;
-        int32_t run = 0;
-        for (int64_t s0 = 0; s0 < S; s0 += 32 * ROWSCAN_U) {
-            int32_t v[ROWSCAN_U];
-#pragma unroll
-            for (int u = 0; u < ROWSCAN_U; ++u) {
-                const int64_t sx = s0 + u * 32 + lane;
-                v[u] = sx < S ? h[sx] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < ROWSCAN_U; ++u) {
-                int32_t x = v[u];
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
-                    if (lane >= d) x += y;
-                }
-                const int64_t sx = s0 + u * 32 + lane;
-                if (sx < S) o[sx] = run + x - v[u];
-                run += __shfl_sync(0xffffffffu, x, 31);
-            }
+        const int64_t per = (S + blockDim.x - 1) / blockDim.x;
+        const int64_t s0 = min(S, (int64_t)threadIdx.x * per), s1 = min(S, s0 + per);
+        int32_t v = 0;
+        for (int64_t sx = s0; sx < s1; ++sx) v += h[sx];
+        int32_t total;
+        int32_t run = block_excl_scan(v, sh, total);
+        for (int64_t sx = s0; sx < s1; ++sx) {
+            const int32_t c = h[sx];
+            o[sx] = run;
+            run += c;
         }
-        if (lane == 0) cnt[j] = run;
+        if (threadIdx.x == 0) cnt[j] = total;
     }
     __threadfence();
     __syncthreads();
@@ -655,7 +645,7 @@ static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const
             cudaFuncSetAttribute(k_scatter_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
         }
         k_hist_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, hist, status, ticket);
-        k_row_scan<<<(unsigned)ceil_div(k, 8), 256, 0, st>>>(hist, k, P.S, CHUNK_R, off, cnt, start, item_start,
+        k_row_scan<<<(unsigned)k, 256, 0, st>>>(hist, k, P.S, CHUNK_R, off, cnt, start, item_start,
                                                             ticket);
         k_scatter_sm<<<seg_blocks, 256, hsm, st>>>(labels, n, k, P.R, P.S, off, start, perm);
     } else {
