@@ -52,8 +52,10 @@ METRICS = {
     "stream": "assign+update GFLOP/s (Lloyd iteration on projected coordinates, 2M x 64, k=1000)",
     "batch": "assign+update GFLOP/s (512 problems x 4 seeds x 20 iterations per replay)",
     "learned": "assign+update GFLOP/s, exact-method flops (learned assignment, 4M x 256, k=16384)",
+    "swn": "assign+update GFLOP/s (Lloyd iteration, StructuredWithNoise 50 sets x 5000 points, d=1000, k=50)",
 }
-DEFAULT_STEPS = {"highdim": 30, "small": 20, "stream": 20, "batch": 5, "learned": 5}
+DEFAULT_STEPS = {"highdim": 30, "small": 20, "stream": 20, "batch": 5, "learned": 5, "swn": 30}
+SWN_X = 20   # signal dimensions per hidden set (Section 3 leaves the count open)
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense ratios, applied to the measured BF16 peak
@@ -71,9 +73,9 @@ def parse():
     ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tcgen05"])
     ap.add_argument("--center-terms", type=int, default=1, choices=[1, 2],
                     help="BF16 form: centers as one BF16 term, or two (head + tail, a narrower certified band)")
-    ap.add_argument("--n", type=int, default=None, help="override n (highdim / learned)")
-    ap.add_argument("--d", type=int, default=None, help="override d (highdim)")
-    ap.add_argument("--k", type=int, default=None, help="override k (highdim)")
+    ap.add_argument("--n", type=int, default=None, help="override n (highdim / learned / swn)")
+    ap.add_argument("--d", type=int, default=None, help="override d (highdim / swn)")
+    ap.add_argument("--k", type=int, default=None, help="override k (highdim; swn: the number of hidden sets)")
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -447,15 +449,33 @@ def mixture(n, d, comps, seed):
     return X
 
 
+def swn_shape(args):
+    """StructuredWithNoise: ell hidden sets of y points in d dimensions, k = ell."""
+    ell = args.k or 50
+    y = (args.n or 250_000) // ell
+    return ell, y, args.d or 1000
+
+
+def workload_data(args, seed):
+    """(X, hidden labels or None, n, d, k) of the highdim or swn workload."""
+    from paper_1502_04265_gb300 import synth
+
+    if args.workload == "swn":
+        ell, y, d = swn_shape(args)
+        X, z = synth.structured_with_noise(ell, y, d, SWN_X, seed=seed)
+        return X, z, ell * y, d, ell
+    n, d, k = args.n or 200_000, args.d or 1024, args.k or 100
+    return mixture(n, d, k, seed=seed), None, n, d, k
+
+
 def run_highdim(env, args):
     import numpy as np
 
     torch, B = env.torch, env.B
     from paper_1502_04265_gb300 import synth
 
-    n, d, k = args.n or 200_000, args.d or 1024, args.k or 100
+    X, hidden, n, d, k = workload_data(args, env.rank)
     F = 2.0 * n * k * d + n * d
-    X = mixture(n, d, k, seed=env.rank)
     u = synth.seed_uniforms(k, seed=env.rank)
     Xg = torch.from_numpy(X).to(env.dev)
     ug = torch.from_numpy(u).to(env.dev)
@@ -538,6 +558,21 @@ def run_highdim(env, args):
                 "gflops_whole_run": iters * F / (W["ms"] * 1e-3) / 1e9,
                 "stage_ms": {nm: W["prof"][nm][1] for nm in ("row_norms", "quantize", "seed") if nm in W["prof"]},
                 "note": "one whole run from raw X: the k-means++ time is included, its flops are not"}
+    if hidden is not None:
+        # the planted partition's cost (its own means, through the library's update) against the run's
+        zt = torch.from_numpy(hidden).to(env.dev)
+        hc = torch.zeros(2, dtype=torch.float64, device=env.dev)
+        B.kmeans_update(Xg, zt, Ca, C_new=torch.empty_like(C0), cost_old=hc[0:1], cost_new=hc[1:2], ctx=ctx)
+        ctx.sync()
+        lab = labels.cpu().numpy()
+        tab = np.zeros((k, k), dtype=np.int64)
+        np.add.at(tab, (lab, hidden), 1)
+        planted, final = float(hc[1]), float(tr[iters - 1, 1])
+        pipeline["hidden_sets"] = {"planted_cost": planted, "final_cost": final, "cost_ratio": final / planted,
+                                   "purity": float(tab.max(axis=1).sum()) / n,
+                                   "note": "purity = share of points whose cluster's most common hidden set is "
+                                           "their own, after the whole run's last assignment"}
+        del zt
 
     e2e = None
     if not args.no_e2e:
@@ -589,11 +624,16 @@ def run_highdim(env, args):
     if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
         cpu = oracle_assign_update_rate(X, R["C"].cpu().numpy(), args.cpu_seconds)
 
-    line = base_line(env, "highdim", value, ms, args.steps, args.warmup, form, {
-        "workload": f"gaussian mixture n={n} d={d} k={k} ({k} components, seed = rank), one Lloyd iteration "
-                    f"per step", "form": form + ("x2 (two-term centers)" if form == "bf16" and args.center_terms == 2 else ""),
+    if hidden is None:
+        wdesc = f"gaussian mixture n={n} d={d} k={k} ({k} components, seed = rank), one Lloyd iteration per step"
+    else:
+        wdesc = (f"StructuredWithNoise: {k} hidden sets x {n // k} points, d={d}, {SWN_X} signal dimensions per "
+                 f"set in [-10, 10], the rest in [-1/2, 1/2] (seed = rank), k={k}, one Lloyd iteration per step")
+    line = base_line(env, args.workload, value, ms, args.steps, args.warmup, form, {
+        "workload": wdesc,
+        "form": form + ("x2 (two-term centers)" if form == "bf16" and args.center_terms == 2 else ""),
         "engine": engine,
-        "l2": "inputs larger than L2 (X is 819 MB FP32 / 410 MB BF16)",
+        "l2": f"inputs larger than L2 (X is {n * d * 4 / 1e6:.0f} MB FP32 / {n * d * 2 / 1e6:.0f} MB BF16)",
         "parallelism": "replicas" if env.world > 1 else "single GPU"})
     line.update({"roofline": roof, "rooflines": rooflines, "step_roofline": step_roof, "pipeline": pipeline,
                  "forms": forms,
@@ -1153,9 +1193,8 @@ def run_reference(args, rank, world):
         val = statistics.median(vals)
         sample = desc + "; " + r["sample"]
     else:
-        if wl == "highdim":
-            n, d, k = args.n or 200_000, args.d or 1024, args.k or 100
-            X = mixture(n, d, k, 0)
+        if wl in ("highdim", "swn"):
+            X, _, n, d, k = workload_data(args, 0)
             u = synth.seed_uniforms(k, 0)
             C = X[(u * n).astype(np.int64) % n]
         elif wl == "stream":
@@ -1206,7 +1245,7 @@ def main():
         pool = gen_pool(shapes[1], _batch_problem)
     env = Env(args)
     env.pool, env.batch_shapes = pool, shapes
-    if args.workload == "highdim":
+    if args.workload in ("highdim", "swn"):
         line = run_highdim(env, args)
     elif args.workload == "small":
         line = run_small(env, args)

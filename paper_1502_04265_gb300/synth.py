@@ -59,6 +59,28 @@ def gaussian_mixture(n: int, d: int, n_comp: int, seed: int, *, chunk_rows: int 
     return X, z
 
 
+def structured_with_noise(ell: int, y: int, d: int, x: int, seed: int, *, big: float = 10.0,
+                          small: float = 0.5):
+    """The StructuredWithNoise instances of Section 3: ell hidden point sets of y points in R^d.
+
+    Cluster i draws x of the d dimensions uniformly without replacement; each of its points takes
+    those coordinates uniformly from [-big, big] and every other coordinate uniformly from
+    [-small, small] (the paper fixes big = 10, small = 1/2).  Returns X (ell * y x d, FP32, the
+    clusters one after another) and the cluster of every row.
+    """
+    rng = np.random.default_rng([seed, 0x5A7])
+    X = np.empty((ell * y, d), dtype=np.float32)
+    z = np.repeat(np.arange(ell, dtype=np.int32), y)
+    for i in range(ell):
+        dims = rng.choice(d, size=x, replace=False)
+        blk = X[i * y:(i + 1) * y]
+        blk[:] = rng.random((y, d), dtype=np.float32)
+        blk *= np.float32(2 * small)
+        blk -= np.float32(small)
+        blk[:, dims] = (rng.random((y, x), dtype=np.float32) * np.float32(2) - np.float32(1)) * np.float32(big)
+    return X, z
+
+
 def seed_uniforms(k: int, seed: int) -> np.ndarray:
     """The k uniforms in [0, 1) that drive one k-means++ run (FP64).
 
