@@ -190,8 +190,9 @@ int kmeans_assign(gbkm_ctx *ctx, const void *Xop, const float *Xop_scales, const
  * histograms with warp-aggregated match_any counting; for k <= 2048 one launch
  * scans each cluster's row of the table, else a device-wide scan; a stable
  * scatter), then each cluster's rows are summed in fixed-size chunks with
- * error-free FP32 transformations and the chunks combined in FP64 in chunk
- * order: no floating-point atomics, bit-reproducible.
+ * error-free FP32 transformations, the chunk sums folded in runs of 32 chunks and
+ * the runs combined in run order (double-float, then FP64): no floating-point
+ * atomics, bit-reproducible, and no cluster's sum a chain as long as its rows.
  * Costs from the CF identity (Section 2.1), in FP64:
  *   cost_old = sum_j Q_j - 2 c_old_j . S_j + N_j ||c_old_j||^2 = cost(C_old, labels)
  *   cost_new = sum_j Q_j - ||S_j||^2 / N_j                      = cost(C_new, labels)

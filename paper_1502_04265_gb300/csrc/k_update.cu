@@ -10,9 +10,11 @@
 //                  (work items: chunks of R rows per cluster, item_start = their exclusive scan)
 //   4. k_segsum    one CTA per chunk of 128 rows: sums of w (x - s), w, w ||x - s||^2 with s the
 //                  cluster's first row -> FP64 partials
-//   5. k_finalize  one CTA per (cluster, 256 columns): FP64 sums of the partials in chunk order,
+//   5. k_fold      one CTA per (run of 32 work items, 256 columns): double-float sums of each
+//                  cluster's partials inside the run, so no cluster's sum is one long chain
+//   6. k_finalize  one CTA per (cluster, 256 columns): the cluster's folded sums in run order,
 //                  centroid and CF cost terms
-//   6. k_final     one CTA: FP64 totals in cluster order
+//   7. k_final     one CTA: FP64 totals in cluster order
 #include <mutex>
 
 #include "internal.cuh"
@@ -22,6 +24,7 @@ namespace gbkm {
 namespace {
 constexpr int SCAN_T = 1024, SCAN_E = 4;           // scan block: 1024 threads x 4 elements
 constexpr int64_t CHUNK_R = 128;                    // rows per segmented-sum work item
+constexpr int32_t FOLD_I = 32;                      // work items per k_fold run
 constexpr int64_t SMEM_HIST_MAX_K = 2048;           // per-warp histograms in shared memory up to here
 constexpr int HIST_PF = 8;                          // label steps a warp loads ahead
 
@@ -457,14 +460,63 @@ __global__ void __launch_bounds__(256) k_segsum(const float *__restrict__ X, int
     }
 }
 
-// One CTA per (cluster j, block of 256 columns).  Sums of the cluster's items in item order (N_j,
-// Q'_j in FP64; S'_j in double-float) are its CF shifted by the reference row s_j.  Then, in
+// Work items are ordered by cluster, so the items of run g = [32 g, 32 g + 32) belong to a
+// contiguous range of clusters.  One CTA per (run g, block of 256 columns) sums, per column, the
+// items of each cluster j it touches and writes that sum to slot g + j: along the item order both
+// g and j only grow (and one of them grows between two consecutive (run, cluster) pairs), so no two
+// pairs share a slot, and there are fewer than runs + k slots.  Cluster j's slots are then
+// g + j for g from its first item's run to its last item's run.
+__global__ void __launch_bounds__(256) k_fold(const float2 *__restrict__ part_s,
+                                              const int32_t *__restrict__ item_start, int64_t k, int64_t d,
+                                              float2 *__restrict__ fold_s) {
+    const int32_t total = item_start[k];
+    const int32_t a = (int32_t)blockIdx.x * FOLD_I;
+    if (a >= total) return;
+    const int32_t b = min(a + FOLD_I, total);
+    const int64_t t = (int64_t)blockIdx.y * 256 + threadIdx.x;
+    if (t >= d) return;
+    // cluster of item a: largest j with item_start[j] <= a
+    int64_t lo = 0, hi = k - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (item_start[mid] <= a) lo = mid;
+        else hi = mid - 1;
+    }
+    for (int64_t j = lo; j < k && item_start[j] < b; ++j) {
+        const int32_t s0 = max(item_start[j], a), s1 = min(item_start[j + 1], b);
+        if (s0 >= s1) continue;
+        DF acc[8];
+        int32_t it = s0;
+        for (; it + 8 <= s1; it += 8) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 p = part_s[(int64_t)(it + q) * d + t];
+                DF o;
+                o.hi = p.x, o.lo = p.y;
+                acc[q] = df_add(acc[q], o);
+            }
+        }
+        for (int q = 0; it < s1; ++it, ++q) {
+            const float2 p = part_s[(int64_t)it * d + t];
+            DF o;
+            o.hi = p.x, o.lo = p.y;
+            acc[q] = df_add(acc[q], o);
+        }
+#pragma unroll
+        for (int q = 1; q < 8; ++q) acc[0] = df_add(acc[0], acc[q]);
+        fold_s[((int64_t)blockIdx.x + j) * d + t] = make_float2(acc[0].hi, acc[0].lo);
+    }
+}
+
+// One CTA per (cluster j, block of 256 columns).  Sums of the cluster's items (N_j, Q'_j in FP64,
+// in item order; S'_j in double-float, over the cluster's k_fold slots in run order) are its CF
+// shifted by the reference row s_j.  Then, in
 // FP64 (Section 2.1's CF identity: sum_x ||x - y||^2 = Q' + 2 (s - y) . S' + N ||s - y||^2):
 //   centroid         mu_j = s_j + S'_j / N_j
 //   cost of c_old    Q'_j + sum_t [2 (s_t - c_t) S'_t + N (s_t - c_t)^2]
 //   cost of mu_j     Q'_j - ||S'_j||^2 / N_j
 // The per-column terms are summed per block here and across blocks by k_final.
-__global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ part_s,
+__global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ fold_s,
                                                   const double *__restrict__ part_nq,
                                                   const float *__restrict__ X, const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ start, int64_t d, int64_t k,
@@ -489,23 +541,27 @@ __global__ void __launch_bounds__(256) k_finalize(const float2 *__restrict__ par
     double a_old = 0.0, b_sq = 0.0;
     const int64_t t = cb * 256 + threadIdx.x;
     if (t < d) {
-        // 8 independent double-float accumulators keep 8 partial loads in flight; combined in order
+        // the cluster's slots g + j, g = first run .. last run (none for an empty cluster); 8
+        // independent double-float accumulators keep 8 loads in flight, combined in order
         DF acc[8];
-        int32_t it = i0;
-        for (; it + 8 <= i1; it += 8) {
+        if (i1 > i0) {
+            const int64_t s0 = i0 / FOLD_I + j, s1 = (i1 - 1) / FOLD_I + j + 1;
+            int64_t sl = s0;
+            for (; sl + 8 <= s1; sl += 8) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float2 p = part_s[(int64_t)(it + q) * d + t];
+                for (int q = 0; q < 8; ++q) {
+                    const float2 p = fold_s[(sl + q) * d + t];
+                    DF o;
+                    o.hi = p.x, o.lo = p.y;
+                    acc[q] = df_add(acc[q], o);
+                }
+            }
+            for (int q = 0; sl < s1; ++sl, ++q) {
+                const float2 p = fold_s[sl * d + t];
                 DF o;
                 o.hi = p.x, o.lo = p.y;
                 acc[q] = df_add(acc[q], o);
             }
-        }
-        for (int q = 0; it < i1; ++it, ++q) {
-            const float2 p = part_s[(int64_t)it * d + t];
-            DF o;
-            o.hi = p.x, o.lo = p.y;
-            acc[q] = df_add(acc[q], o);
         }
 #pragma unroll
         for (int q = 1; q < 8; ++q) acc[0] = df_add(acc[0], acc[q]);
@@ -581,9 +637,10 @@ __global__ void __launch_bounds__(256) k_final(const double *__restrict__ nq, co
 
 // sizes and workspace layout of one update
 struct UpdatePlan {
-    int64_t R, S, L, nbs, items_max, ncb;
+    int64_t R, S, L, nbs, items_max, runs_max, ncb;
     bool smem_hist;
-    size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_nq, o_terms, o_cnt, o_ticket, bytes;
+    size_t o_hist, o_off, o_bsum, o_start, o_items, o_perm, o_part, o_fold, o_nq, o_terms, o_cnt, o_ticket,
+        bytes;
 };
 
 static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
@@ -598,6 +655,7 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     P.L = k * P.S;
     P.nbs = ceil_div(P.L, (int64_t)SCAN_T * SCAN_E);
     P.items_max = ceil_div(n, CHUNK_R) + k;
+    P.runs_max = ceil_div(P.items_max, (int64_t)FOLD_I);
     WsPlan p;
     P.o_hist = p.take<int32_t>(P.L);
     P.o_off = p.take<int32_t>(P.L);
@@ -606,6 +664,7 @@ static UpdatePlan update_plan(int64_t n, int64_t d, int64_t k) {
     P.o_items = p.take<int32_t>(k + 1);
     P.o_perm = p.take<int32_t>(n);
     P.o_part = p.take<float2>(P.items_max * d);
+    P.o_fold = p.take<float2>((P.runs_max + k) * d);
     P.o_nq = p.take<double>(P.items_max * 2);
     P.o_terms = p.take<double>(k * (2 + 2 * P.ncb));
     P.o_cnt = p.take<int32_t>(k);
@@ -635,7 +694,7 @@ static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const
             *bsum = ws_at<int32_t>(ws, P.o_bsum), *start = ws_at<int32_t>(ws, P.o_start),
             *item_start = ws_at<int32_t>(ws, P.o_items), *perm = ws_at<int32_t>(ws, P.o_perm),
             *cnt = ws_at<int32_t>(ws, P.o_cnt), *ticket = ws_at<int32_t>(ws, P.o_ticket);
-    float2 *part = ws_at<float2>(ws, P.o_part);
+    float2 *part = ws_at<float2>(ws, P.o_part), *fold = ws_at<float2>(ws, P.o_fold);
     double *part_nq = ws_at<double>(ws, P.o_nq), *terms = ws_at<double>(ws, P.o_terms);
     const unsigned seg_blocks = (unsigned)ceil_div(P.S, 8);
     const size_t hsm = P.smem_hist ? sizeof(int32_t) * 8 * (size_t)k : 0;
@@ -674,11 +733,12 @@ static int update_run(gbkm_ctx *c, cudaStream_t st, int *status, void *ws, const
     else
         launch_segsum<1, false>(u16, items, st, X, d, w, perm, start, item_start, k, part, part_nq);
     if (c) prof_end(c);
-    k_finalize<<<dim3((unsigned)k, (unsigned)P.ncb), 256, 0, st>>>(part, part_nq, X, perm, start, d, k,
+    k_fold<<<dim3((unsigned)P.runs_max, (unsigned)P.ncb), 256, 0, st>>>(part, item_start, k, d, fold);
+    k_finalize<<<dim3((unsigned)k, (unsigned)P.ncb), 256, 0, st>>>(fold, part_nq, X, perm, start, d, k,
                                                                   item_start, C_old, C_new, counts, terms,
                                                                   terms + 2 * k);
     k_final<<<1, 256, 0, st>>>(terms, terms + 2 * k, k, P.ncb, cost_old, cost_new, n_empty);
-    return cudaPeekAtLastError() == cudaSuccess ? (P.smem_hist ? 6 : 10) : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? (P.smem_hist ? 7 : 11) : -1;
 }
 
 int update_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,

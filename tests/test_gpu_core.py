@@ -154,6 +154,29 @@ def test_update_matches_oracle(gb, orc, n, d, k, weighted):
     assert cn == pytest.approx(ref["cost_new"], rel=COST_REL_F32)
 
 
+@pytest.mark.parametrize("n,d,k,share", [(60_000, 96, 20, 0.85), (200_000, 33, 3, 0.999),
+                                           (9_000, 1000, 4000, 0.6)])
+def test_update_skewed_clusters(gb, orc, n, d, k, share):
+    """One cluster holds most rows (its chunk sums span many 32-item runs of the fold), the rest are
+    spread over the other clusters with some empty: counts, centroids and costs match the oracle."""
+    rng = np.random.default_rng(n + k)
+    X, _ = synth.gaussian_mixture(n, d, 5, seed=k)
+    lab = rng.integers(0, max(1, k // 2), size=n).astype(np.int32)   # clusters >= k/2 stay empty
+    big = rng.random(n) < share
+    lab[big] = k // 3
+    C_old = synth.gaussian_mixture(k, d, 3, seed=n)[0]
+    out = gb.kmeans_update(T(X), T(lab), T(C_old))
+    gb.gbkm_sync()
+    ref = orc.update(X, lab, C_old.astype(np.float64))
+    assert np.array_equal(H(out["counts"]), ref["N"])
+    assert int(H(out["n_empty"])[0]) == ref["n_empty"]
+    assert centroid_err(H(out["C_new"]), ref["C_new"], X, lab) <= CENTROID_REL
+    empty = ref["N"] == 0
+    assert np.array_equal(H(out["C_new"])[empty], C_old[empty])
+    assert float(H(out["cost_old"])[0]) == pytest.approx(ref["cost_old"], rel=COST_REL_F32)
+    assert float(H(out["cost_new"])[0]) == pytest.approx(ref["cost_new"], rel=COST_REL_F32)
+
+
 @pytest.mark.parametrize("k", [30, 3000])
 def test_update_is_bit_reproducible(gb, k):
     X, z = synth.gaussian_mixture(20000, 128, k, seed=2)
