@@ -31,6 +31,7 @@
 #ifndef GBKM_H
 #define GBKM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -110,6 +111,31 @@ int kmeans_row_norms(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, float 
  * X: n x d FP32.  Xq must be 16-byte aligned. */
 int kmeans_quantize(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, int32_t dtype,
                     void *Xq, float *scales);
+
+/* ------------------------------------------------------------------ A0 + A1: ingest */
+
+/* Page-locked host memory mapped into every device's address space, for kmeans_ingest
+ * sources (the kernel reads it across the CPU-GPU link; no copy-engine transfer).
+ * gbkm_host_alloc: *out receives a block of `bytes` bytes, or NULL with GBKM_ENOMEM.
+ * gbkm_host_free: releases a block from gbkm_host_alloc (NULL is a no-op; any other
+ * pointer returns GBKM_EINVAL).  The caller owns the block and frees it after the
+ * last call that reads it has completed. */
+int gbkm_host_alloc(size_t bytes, void **out);
+int gbkm_host_free(void *p);
+
+/* One read of a block of points feeding the rest of the path (Section 2.1's
+ * sum-of-squares term and the BF16 operand copy, as kmeans_row_norms and
+ * kmeans_quantize(GBKM_BF16, with scales) compute them):
+ *   X_dev = X_src (NULL to skip), xnorm[i] = ||x_i||^2 (NULL to skip),
+ *   Xq = bf16(X_src) (NULL to skip), resid[i] = ||x_i - Xq_i|| rounded up (NULL to
+ *   skip; needs Xq).
+ * X_src: n x d FP32, either device memory or a range inside one gbkm_host_alloc block
+ * (checked exactly; any other host memory returns GBKM_EINVAL).  X_dev (16-byte
+ * aligned, not X_src): n x d FP32 device memory; Xq (16-byte aligned): n x d bfloat16.
+ * The sums run in the same order as those of kmeans_row_norms and kmeans_quantize on a
+ * 16-byte-aligned copy, so xnorm, Xq and resid equal theirs bitwise. */
+int kmeans_ingest(gbkm_ctx *ctx, const float *X_src, int64_t n, int64_t d, float *X_dev,
+                  float *xnorm, void *Xq, float *resid);
 
 /* ------------------------------------------------------------------ A2: block projection */
 

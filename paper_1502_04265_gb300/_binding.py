@@ -60,6 +60,9 @@ _SIGS = {
     "gbkm_profile_enable": (ct.c_int, [_vp, ct.c_int]),
     "gbkm_profile_read": (ct.c_int, [_vp, ct.c_char_p, _i64]),
     "kmeans_row_norms": (ct.c_int, [_vp, _vp, _i64, _i64, _vp]),
+    "gbkm_host_alloc": (ct.c_int, [ct.c_size_t, ct.POINTER(ct.c_void_p)]),
+    "gbkm_host_free": (ct.c_int, [_vp]),
+    "kmeans_ingest": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
     "kmeans_quantize": (ct.c_int, [_vp, _vp, _i64, _i64, _i32, _vp, _vp]),
     "kmeans_project_block": (ct.c_int, [_vp, _vp, _i32, _i64, _i64, _vp, _i64, _vp, _vp]),
     "kmeans_seed_pp": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp, _vp]),
@@ -250,6 +253,64 @@ def kmeans_quantize(X, dtype="bf16", Xq=None, scales=None, residuals=True, ctx=N
     c = _ctx(ctx, X)
     c.check(load().kmeans_quantize(c.handle, _ptr(X), n, d, DTYPES[dtype], _ptr(Xq), _ptr(scales)))
     return Xq, scales
+
+
+# ------------------------------------------------------------------ A0 + A1 from host memory
+class HostBlock:
+    """A page-locked, device-mapped host block from gbkm_host_alloc, viewed as a CPU tensor
+    (`.tensor`); kmeans_ingest reads such blocks directly.  Freed by close() or on collection."""
+
+    def __init__(self, shape, dtype=torch.float32):
+        import numpy as np
+
+        shape = tuple(int(s) for s in shape)
+        itemsize = torch.empty((), dtype=dtype).element_size()
+        nbytes = max(1, itemsize * int(np.prod(shape)))
+        p = ct.c_void_p()
+        rc = load().gbkm_host_alloc(nbytes, ct.byref(p))
+        if rc != GBKM_OK:
+            raise GbkmError(rc, f"gbkm_host_alloc of {nbytes} bytes failed")
+        self._p = p.value
+        raw = (ct.c_uint8 * nbytes).from_address(self._p)
+        flat = torch.frombuffer(raw, dtype=torch.uint8)
+        self.tensor = flat[:itemsize * int(np.prod(shape))].view(dtype).view(shape)
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self.tensor = None
+            load().gbkm_host_free(ct.c_void_p(self._p))
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kmeans_ingest(X_src, X_dev=None, xnorm=None, Xq=None, resid=None, copy=True, quantize=True, device=None,
+                  ctx=None):
+    """One read of X_src (a CUDA tensor, or a CPU tensor inside a HostBlock): returns (X_dev, xnorm,
+    Xq, resid) with X_dev the device copy (None with copy=False), xnorm the squared row norms, and
+    the BF16 copy with the rows' rounding residuals (None with quantize=False)."""
+    _req(X_src, torch.float32, name="X_src")
+    if not X_src.is_contiguous():
+        raise ValueError("X_src must be contiguous (row-major)")
+    n, d = X_src.shape
+    dev = X_src.device if X_src.is_cuda else torch.device(device if device is not None else "cuda")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    if copy and X_dev is None:
+        X_dev = torch.empty((n, d), dtype=torch.float32, device=dev)
+    if xnorm is None:
+        xnorm = torch.empty(n, dtype=torch.float32, device=dev)
+    if quantize:
+        Xq = Xq if Xq is not None else torch.empty((n, d), dtype=torch.bfloat16, device=dev)
+        resid = resid if resid is not None else torch.empty(n, dtype=torch.float32, device=dev)
+    c = _ctx(ctx, xnorm)
+    c.check(load().kmeans_ingest(c.handle, ct.c_void_p(X_src.data_ptr()), n, d, _ptr(X_dev) if copy else None,
+                                 _ptr(xnorm), _ptr(Xq) if quantize else None, _ptr(resid) if quantize else None))
+    return (X_dev if copy else None), xnorm, (Xq if quantize else None), (resid if quantize else None)
 
 
 # ------------------------------------------------------------------ A2

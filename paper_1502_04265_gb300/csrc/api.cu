@@ -3,6 +3,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -89,7 +91,29 @@ struct DeviceGuard {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// page-locked, device-mapped host blocks handed out by gbkm_host_alloc: base address -> bytes
+std::mutex g_host_mu;
+std::map<uintptr_t, size_t> g_host_blocks;
+
+// the gbkm_host_alloc block holding all of [p, p + bytes), or 0
+uintptr_t host_block_of(const void *p, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    const uintptr_t q = reinterpret_cast<uintptr_t>(p);
+    auto it = g_host_blocks.upper_bound(q);
+    if (it == g_host_blocks.begin()) return 0;
+    --it;
+    const uintptr_t b = it->first;
+    const size_t sz = it->second;
+    if (q - b >= sz || bytes > sz - (q - b)) return 0;
+    return b;
+}
+
 }  // namespace
+
+namespace gbkm {
+int launch_ingest(gbkm_ctx *c, const float *src, int64_t n, int64_t d, float *xdev, float *xnorm, void *xq,
+                  float *resid);
+}
 
 namespace gbkm {
 // worst-case relative error coefficients of the distance scores of each operand format:
@@ -250,6 +274,74 @@ int kmeans_quantize(gbkm_ctx *c, const float *X, int64_t n, int64_t d, int32_t d
     DeviceGuard g(c->device);
     prof_begin(c, "quantize");
     const int rc = gbkm::launch_quantize(c, X, n, d, dtype, Xq, scales);
+    prof_end(c);
+    return rc;
+}
+
+int gbkm_host_alloc(size_t bytes, void **out) {
+    if (!out || bytes == 0) return GBKM_EINVAL;
+    *out = nullptr;
+    void *p = nullptr;
+    const cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return GBKM_ENOMEM;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_host_mu);
+        g_host_blocks[reinterpret_cast<uintptr_t>(p)] = bytes;
+    }
+    *out = p;
+    return GBKM_OK;
+}
+
+int gbkm_host_free(void *p) {
+    if (!p) return GBKM_OK;
+    {
+        std::lock_guard<std::mutex> lock(g_host_mu);
+        auto it = g_host_blocks.find(reinterpret_cast<uintptr_t>(p));
+        if (it == g_host_blocks.end()) return GBKM_EINVAL;
+        g_host_blocks.erase(it);
+    }
+    if (cudaFreeHost(p) != cudaSuccess) {
+        cudaGetLastError();
+        return GBKM_ECUDA;
+    }
+    return GBKM_OK;
+}
+
+int kmeans_ingest(gbkm_ctx *c, const float *X_src, int64_t n, int64_t d, float *X_dev, float *xnorm,
+                  void *Xq, float *resid) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || !X_src) return set_error(c, GBKM_EINVAL, "ingest: bad arguments");
+    if (resid && !Xq) return set_error(c, GBKM_EINVAL, "ingest: resid needs Xq");
+    if (Xq && !aligned16(Xq)) return set_error(c, GBKM_EINVAL, "ingest: Xq must be 16-byte aligned");
+    if (X_dev && !aligned16(X_dev)) return set_error(c, GBKM_EINVAL, "ingest: X_dev must be 16-byte aligned");
+    if (X_dev == X_src) return set_error(c, GBKM_EINVAL, "ingest: X_dev may not be X_src");
+    if ((uint64_t)n > (uint64_t)INT64_MAX / 4 / (uint64_t)d)
+        return set_error(c, GBKM_EINVAL, "ingest: n x d overflows");
+    DeviceGuard g(c->device);
+    const size_t bytes = (size_t)n * (size_t)d * sizeof(float);
+    const float *src = nullptr;
+    if (const uintptr_t b = host_block_of(X_src, bytes)) {
+        // the block's address in this device's address space
+        void *dbase = nullptr;
+        const cudaError_t e = cudaHostGetDevicePointer(&dbase, reinterpret_cast<void *>(b), 0);
+        if (e != cudaSuccess || !dbase) return cuda_check(c, e != cudaSuccess ? e : cudaErrorInvalidValue, "ingest: mapped host block");
+        src = reinterpret_cast<const float *>(static_cast<char *>(dbase) + (reinterpret_cast<uintptr_t>(X_src) - b));
+    } else {
+        cudaPointerAttributes at;
+        const cudaError_t e = cudaPointerGetAttributes(&at, X_src);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(c, GBKM_EINVAL, "ingest: X_src is neither device memory nor a gbkm_host_alloc block");
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+            return set_error(c, GBKM_EINVAL, "ingest: X_src is neither device memory nor a gbkm_host_alloc block");
+        src = X_src;
+    }
+    prof_begin(c, "ingest");
+    const int rc = gbkm::launch_ingest(c, src, n, d, X_dev, xnorm, Xq, resid);
     prof_end(c);
     return rc;
 }

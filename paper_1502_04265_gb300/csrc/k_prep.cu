@@ -108,6 +108,102 @@ __global__ void __launch_bounds__(256) k_to_bf16_rows(const float *__restrict__ 
     if (lane == 0) resid[row] = sqrtf(s * (1.f + (float)(d + 4) * 1.1920929e-7f)) * (1.f + 2.4e-7f);
 }
 
+// ---------------------------------------------------------------- A0 + A1 in one pass
+// One warp per row of a source that may sit in page-locked host memory mapped into the device's
+// address space: the row is copied to HBM and its squared norm, BF16 copy and BF16 rounding
+// residual are formed from the same registers, so the source is read once.  Each lane issues up
+// to 8 four-float loads before it uses any, keeping a row's bytes in flight together across the
+// long-latency CPU-GPU link.  With d % 4 == 0 lane l takes the element groups 4t..4t+3 for
+// t = l, l + 32, ... (as k_row_norms and k_to_bf16_rows do on aligned rows), otherwise the
+// elements t = l, l + 32, ...: the sums are formed in the same order as those kernels', so the
+// results are bitwise theirs.
+__device__ __forceinline__ float4 ld_row4(const float *x, int64_t t, bool vload) {
+    if (vload) return __ldg(reinterpret_cast<const float4 *>(x) + t);
+    return make_float4(__ldg(x + 4 * t), __ldg(x + 4 * t + 1), __ldg(x + 4 * t + 2), __ldg(x + 4 * t + 3));
+}
+
+__global__ void __launch_bounds__(256) k_ingest(const float *__restrict__ src, int64_t n, int64_t d,
+                                                float *__restrict__ xdev, float *__restrict__ xnorm,
+                                                __nv_bfloat16 *__restrict__ xq, float *__restrict__ resid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const float *x = src + row * d;
+    float s = 0.f, r = 0.f;
+    if ((d & 3) == 0) {
+        const bool vload = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+        const bool vstore = (reinterpret_cast<uintptr_t>(xdev) & 15) == 0;
+        const int64_t q = d / 4;
+        float *xo = xdev ? xdev + row * d : nullptr;
+        __nv_bfloat16 *qo = xq ? xq + row * d : nullptr;
+        for (int64_t base = 0; base < q; base += 256) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t t = base + u * 32 + lane;
+                if (t < q) v[u] = ld_row4(x, t, vload);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t t = base + u * 32 + lane;
+                if (t >= q) break;
+                if (xo) {
+                    if (vstore) {
+                        reinterpret_cast<float4 *>(xo)[t] = v[u];
+                    } else {
+                        xo[4 * t] = v[u].x, xo[4 * t + 1] = v[u].y, xo[4 * t + 2] = v[u].z, xo[4 * t + 3] = v[u].w;
+                    }
+                }
+                s = fmaf(v[u].x, v[u].x, s);
+                s = fmaf(v[u].y, v[u].y, s);
+                s = fmaf(v[u].z, v[u].z, s);
+                s = fmaf(v[u].w, v[u].w, s);
+                if (qo) {
+                    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[u].x, v[u].y);
+                    const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[u].z, v[u].w);
+                    uint2 w;
+                    w.x = *reinterpret_cast<const uint32_t *>(&h0);
+                    w.y = *reinterpret_cast<const uint32_t *>(&h1);
+                    reinterpret_cast<uint2 *>(qo)[t] = w;
+                    const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+                    const float e0 = v[u].x - f0.x, e1 = v[u].y - f0.y, e2 = v[u].z - f1.x, e3 = v[u].w - f1.y;
+                    r = fmaf(e0, e0, r);
+                    r = fmaf(e1, e1, r);
+                    r = fmaf(e2, e2, r);
+                    r = fmaf(e3, e3, r);
+                }
+            }
+        }
+    } else {
+        for (int64_t t = lane; t < d; t += 32) {
+            const float v = __ldg(x + t);
+            if (xdev) xdev[row * d + t] = v;
+            s = fmaf(v, v, s);
+            if (xq) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                xq[row * d + t] = h;
+                const float e = v - __bfloat162float(h);
+                r = fmaf(e, e, r);
+            }
+        }
+    }
+    s = warp_sum_f(s);
+    r = warp_sum_f(r);
+    if (lane == 0) {
+        if (xnorm) xnorm[row] = s;
+        if (resid) resid[row] = sqrtf(r * (1.f + (float)(d + 4) * 1.1920929e-7f)) * (1.f + 2.4e-7f);
+    }
+}
+
+int launch_ingest(gbkm_ctx *c, const float *src, int64_t n, int64_t d, float *xdev, float *xnorm, void *xq,
+                  float *resid) {
+    if (n == 0) return GBKM_OK;
+    k_ingest<<<(unsigned)ceil_div(n, 8), 256, 0, c->stream>>>(src, n, d, xdev, xnorm, (__nv_bfloat16 *)xq,
+                                                              resid);
+    GBKM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "ingest launch");
+}
+
 // smallest e with amax * 2^-e <= 448 (e = 0 when amax == 0)
 __device__ __forceinline__ int e4m3_scale_exp(float amax) {
     if (!(amax > 0.f)) return 0;

@@ -60,6 +60,60 @@ def test_quantize_bf16_residuals_bound(gb, orc, n, d):
     assert got[1] == 0.0
 
 
+# one read of a block in a mapped host block (or on the device): the copy, norms, BF16 copy and
+# residuals equal those of the separate kernels bitwise, and the oracle's
+@pytest.mark.parametrize("n,d,offset", [(1037, 1024, 0), (999, 37, 0), (300, 1000, 0), (257, 64, 1),
+                                        (1, 1, 0)])
+def test_ingest_from_host_block(gb, orc, n, d, offset):
+    X, _ = synth.gaussian_mixture(n, d, 5, seed=n + d)
+    X[0, 0] = 0.0
+    blk = gb.HostBlock((n * d + offset,))
+    src = blk.tensor[offset:offset + n * d].view(n, d)   # offset 1: a source that is not 16-byte aligned
+    src.copy_(torch.from_numpy(X))
+    Xd, xn, Xq, r = gb.kmeans_ingest(src, device=DEV)
+    gb.gbkm_sync()
+    assert np.array_equal(H(Xd), X)
+    assert np.array_equal(H(xn), H(gb.kmeans_row_norms(Xd)))
+    Xq2, r2 = gb.kmeans_quantize(Xd, "bf16")
+    assert np.array_equal(H(Xq.view(torch.int16)), H(Xq2.view(torch.int16)))
+    assert np.array_equal(H(r), H(r2))
+    assert np.array_equal(H(Xq.view(torch.int16)).view(np.uint16), orc.quant_bf16(X))
+    np.testing.assert_allclose(H(xn), orc.row_norms(X), rtol=(d / 32 + 8) * 2.0 ** -24 * 2)
+    del src
+    blk.close()
+
+
+def test_ingest_from_device_without_copy(gb, orc):
+    X, _ = synth.gaussian_mixture(2000, 256, 5, seed=4)
+    Xg = T(X)
+    none, xn, Xq, r = gb.kmeans_ingest(Xg, copy=False)
+    gb.gbkm_sync()
+    assert none is None
+    assert np.array_equal(H(xn), H(gb.kmeans_row_norms(Xg)))
+    Xq2, r2 = gb.kmeans_quantize(Xg, "bf16")
+    assert np.array_equal(H(Xq.view(torch.int16)), H(Xq2.view(torch.int16))) and np.array_equal(H(r), H(r2))
+
+
+def test_ingest_rejects_other_host_memory(gb):
+    """Pageable memory, page-locked memory the library did not hand out, and a range that runs past
+    the end of a host block are refused before any launch."""
+    n, d = 64, 32
+    plain = torch.zeros((n, d), dtype=torch.float32)
+    pinned = torch.zeros((n, d), dtype=torch.float32).pin_memory()
+    blk = gb.HostBlock((n, d))
+    lib, ctx = gb.load(), gb.default_context(torch.device(DEV))
+    ctx.bind_stream()
+    xn = torch.empty(2 * n, dtype=torch.float32, device=DEV)
+    for ptr, rows in ((plain.data_ptr(), n), (pinned.data_ptr(), n), (blk.tensor.data_ptr(), n + 1),
+                      (blk.tensor.data_ptr() + 4 * d, n)):
+        rc = lib.kmeans_ingest(ctx.handle, ptr, rows, d, None, gb._ptr(xn), None, None)
+        assert rc == gb.GBKM_EINVAL
+    assert lib.kmeans_ingest(ctx.handle, blk.tensor.data_ptr(), n, d, None, gb._ptr(xn), None, None) == 0
+    gb.gbkm_sync()
+    assert lib.gbkm_host_free(plain.data_ptr()) == gb.GBKM_EINVAL
+    blk.close()
+
+
 @pytest.mark.parametrize("n,d", [(300, 64), (40, 128), (33, 200), (7, 5)])
 def test_quantize_fp8_bitexact(gb, orc, n, d):
     X, _ = synth.gaussian_mixture(n, d, 4, seed=8)
