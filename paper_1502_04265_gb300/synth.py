@@ -107,6 +107,23 @@ def orthonormal_basis(d: int, r: int, seed: int) -> np.ndarray:
     return Q
 
 
+def gaussian_sketch(d: int, s: int, seed: int) -> np.ndarray:
+    """A d x s matrix of independent N(0, 1) draws, FP32: the random matrix a randomised SVD
+    multiplies a piece by (drawn here and passed in, so every implementation uses the same one)."""
+    rng = np.random.default_rng([seed, 0x5C7])
+    return rng.standard_normal((d, s), dtype=np.float32)
+
+
+def planted_spectrum(n: int, d: int, sigmas, seed: int) -> np.ndarray:
+    """U diag(sigmas) W^T with random orthonormal U (n x r) and W (d x r), FP64: a matrix whose
+    singular values are exactly `sigmas` (r = len(sigmas)) and whose right singular vectors are W."""
+    sig = np.asarray(sigmas, dtype=np.float64)
+    r = sig.shape[0]
+    U = orthonormal_basis(n, r, seed * 2 + 1)
+    W = orthonormal_basis(d, r, seed * 2 + 2)
+    return (U * sig[None, :]) @ W.T
+
+
 def subspace_mixture_chunk(Q: np.ndarray, row0: int, rows: int, n_comp: int, seed: int,
                            noise: float = 0.1):
     """Rows [row0, row0+rows) of the rank-r-subspace workload, FP32.
