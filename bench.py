@@ -53,8 +53,9 @@ METRICS = {
     "batch": "assign+update GFLOP/s (512 problems x 4 seeds x 20 iterations per replay)",
     "learned": "assign+update GFLOP/s, exact-method flops (learned assignment, 4M x 256, k=16384)",
     "swn": "assign+update GFLOP/s (Lloyd iteration, StructuredWithNoise 50 sets x 5000 points, d=1000, k=50)",
+    "svd": "randomised truncated SVD GFLOP/s (one piece 65,536 x 2,048, l=64, s=80)",
 }
-DEFAULT_STEPS = {"highdim": 30, "small": 20, "stream": 20, "batch": 5, "learned": 5, "swn": 30}
+DEFAULT_STEPS = {"highdim": 30, "small": 20, "stream": 20, "batch": 5, "learned": 5, "swn": 30, "svd": 20}
 SWN_X = 20   # signal dimensions per hidden set (Section 3 leaves the count open)
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -1173,6 +1174,121 @@ def run_learned(env, args):
     return line
 
 
+# ---------------------------------------------------------------------------- randomised SVD of a piece
+def svd_shape(args):
+    return args.n or 65536, args.d or 2048, 64, 80
+
+
+def svd_flops(n, d, s, ell):
+    """Y = A Omega and Bt = A^T Q (2 n d s each), the two CholeskyQR passes (n s^2 for each Gram,
+    2 n s^2 for each Y R^-1), the Gram of Bt (d s^2) and V = Bt T (2 d s l)."""
+    return 4.0 * n * d * s + 6.0 * n * s * s + d * s * s + 2.0 * d * s * ell
+
+
+def svd_piece(n, d, seed):
+    from paper_1502_04265_gb300 import synth
+
+    Qp = synth.orthonormal_basis(d, 64, seed)
+    A, _ = synth.subspace_mixture_chunk(Qp, 0, n, 500, seed)
+    return A, Qp
+
+
+def oracle_svd_rate(A, Om, ell, cpu_seconds):
+    """The FP64 oracle's randomised SVD on the first rows of the piece, repeated for about
+    cpu_seconds; GFLOP/s by the same flop count."""
+    import numpy as np
+
+    from oracle import rsvd as orsvd
+
+    d, s = Om.shape
+    rows = min(A.shape[0], 8192)
+    Ad, Omd = A[:rows].astype(np.float64), Om.astype(np.float64)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        orsvd.rsvd(Ad, Omd, ell)
+        reps += 1
+        if time.perf_counter() - t0 >= cpu_seconds:
+            break
+    dt = time.perf_counter() - t0
+    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count() or 1)
+    return {"value": reps * svd_flops(rows, d, s, ell) / dt / 1e9, "unit": UNIT, "cores": int(threads),
+            "kind": "oracle",
+            "sample": f"first {rows} of {A.shape[0]} rows x {reps} runs: numpy FP64 (BLAS threads = {threads}), "
+                      f"{dt:.1f} s"}
+
+
+def run_svd(env, args):
+    import numpy as np
+
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import synth
+
+    n, d, ell, s = svd_shape(args)
+    A, Qp = svd_piece(n, d, env.rank)
+    Om = synth.gaussian_sketch(d, s, seed=env.rank)
+    Ag, Omg = torch.from_numpy(A).to(env.dev), torch.from_numpy(Om).to(env.dev)
+    ctx = env.ctx
+    V = torch.empty((d, ell), dtype=torch.float32, device=env.dev)
+    sig = torch.empty(ell, dtype=torch.float32, device=env.dev)
+    info = torch.zeros(1, dtype=torch.int32, device=env.dev)
+
+    def step(i):
+        B.kmeans_rsvd(Ag, Omg, ell, V=V, sigma=sig, info=info, ctx=ctx)
+
+    R = env.timed(step, args.steps, args.warmup, clocks=True)
+    ms, prof = R["ms"], R["prof"]
+    F = svd_flops(n, d, s, ell)
+    value = env.world * F / (ms * 1e-3) / 1e9
+    note = "FFMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    rooflines = {
+        "rsvd_sketch": roofline(env.peaks, "rsvd_sketch", kernel_avg_s(prof, "rsvd_sketch"), n * d * 4 + n * s * 4,
+                                2.0 * n * d * s, FFMA_PEAK_TFLOPS, R["total_s"], bound="alu", note=note),
+        "rsvd_rows": roofline(env.peaks, "rsvd_rows", kernel_avg_s(prof, "rsvd_rows"), n * d * 4 + n * s * 4,
+                              2.0 * n * d * s, FFMA_PEAK_TFLOPS, R["total_s"], bound="alu", note=note)}
+    roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
+    Vh = V.cpu().numpy().astype(np.float64)
+    quality = {"info": int(info.item()),
+               "orthonormality": float(np.max(np.abs(Vh.T @ Vh - np.eye(ell)))),
+               "planted_subspace_distance": float(np.linalg.norm(Vh @ Vh.T - Qp @ Qp.T, 2)),
+               "sigma_first_last": [float(sig[0]), float(sig[-1])]}
+
+    e2e = None
+    if not args.no_e2e:
+        hb = B.HostBlock((n, d))
+        hb.tensor.copy_(torch.from_numpy(A))
+        Ad = torch.empty_like(Ag)
+        xn = torch.empty(n, dtype=torch.float32, device=env.dev)
+        Vh_out = torch.empty((d, ell), dtype=torch.float32).pin_memory()
+        sh_out = torch.empty(ell, dtype=torch.float32).pin_memory()
+
+        def e2e_step(i):
+            B.kmeans_ingest(hb.tensor, X_dev=Ad, xnorm=xn, quantize=False, device=env.dev, ctx=ctx)
+            B.kmeans_rsvd(Ad, Omg, ell, V=V, sigma=sig, info=info, ctx=ctx)
+            Vh_out.copy_(V, non_blocking=True)
+            sh_out.copy_(sig, non_blocking=True)
+
+        E = env.timed(e2e_step, args.e2e_steps or 5, 1, profile=False)
+        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+               "d2h_bytes_per_step": int(d * ell * 4 + ell * 4), "ms_per_step": E["ms"],
+               "note": "every step: the piece read from a mapped host block (kmeans_ingest), the SVD, and D2H "
+                       "of V and the singular values"}
+        del hb
+
+    cpu = None
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_svd_rate(A, Om, ell, args.cpu_seconds)
+
+    line = base_line(env, "svd", value, ms, args.steps, args.warmup, "f32", {
+        "workload": f"one piece of the rank-64-subspace workload (n={n}, d={d}, 500-component mixture in a random "
+                    f"64-dim subspace + N(0, 0.1^2) noise, seed = rank), top l={ell} right singular vectors with "
+                    f"s={s} (16 oversampling columns), Gaussian Omega",
+        "l2": f"inputs larger than L2 (A is {n * d * 4 / 1e6:.0f} MB)",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "rooflines": rooflines, "quality": quality, "cpu_baseline": cpu, "e2e": e2e,
+                 "gpu_launches": R["launches"], "clocks": R["clocks"], "kernels_ms": kernels_ms(prof)})
+    return line
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The FP64 CPU oracle timed on the host cores, on bounded samples of the same workload."""
@@ -1187,7 +1303,19 @@ def run_reference(args, rank, world):
     cores = oracle.set_threads(os.cpu_count() or 1)
     budget = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
     wl = args.workload
-    if wl in ("small", "batch"):
+    if wl == "svd":
+        n, d, ell, s_ = svd_shape(args)
+        A, _ = svd_piece(n, d, 0)
+        Om = synth.gaussian_sketch(d, s_, seed=0)
+        vals, dts = [], []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = oracle_svd_rate(A, Om, ell, budget)
+            if i >= args.warmup:
+                vals.append(r["value"])
+                dts.append(time.perf_counter() - t0)
+        val, sample, cores = statistics.median(vals), r["sample"], r["cores"]
+    elif wl in ("small", "batch"):
         if wl == "small":
             X = mixture(10_000, 64, 10, 0)
             runs = [(X, 10, synth.seed_uniforms(10, 0))]
@@ -1269,6 +1397,8 @@ def main():
         line = run_stream((env, args))
     elif args.workload == "batch":
         line = run_batch((env, args))
+    elif args.workload == "svd":
+        line = run_svd(env, args)
     else:
         line = run_learned(env, args)
     if env.rank == 0:

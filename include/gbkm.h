@@ -139,6 +139,27 @@ int kmeans_ingest(gbkm_ctx *ctx, const float *X_src, int64_t n, int64_t d, float
 
 /* ------------------------------------------------------------------ A2: block projection */
 
+/* Randomised truncated SVD of a piece (Section 2.2: the best-fit subspace of
+ * dimension ell is spanned by the top ell right singular vectors; computed, as in
+ * the paper, by the randomised scheme of Halko, Martinsson and Tropp, which reduces
+ * the columns by a random matrix, then the rows, and decomposes the small rest;
+ * Section 2.3.2: weighted points enter as rows scaled by sqrt(w_i)):
+ *   A' = diag(sqrt(w)) A, Y = A' Omega, Q = orth(Y) (CholeskyQR, twice),
+ *   B = Q^T A' (s x d), V = the top ell right singular vectors of B.
+ *   A: n x d FP32 row-major; w: n FP32 >= 0 or NULL; Omega: d x s FP32 row-major
+ *   (the random matrix, e.g. independent N(0, 1) draws; s = ell + oversampling);
+ *   16 <= s <= 128, s % 16 == 0, 1 <= ell <= s <= min(n, d).
+ *   V: d x ell FP32 out, orthonormal columns in decreasing singular value, each
+ *   column's entry of largest magnitude (lowest row on ties) positive.
+ *   sigma: ell FP32 out (decreasing) or NULL.
+ *   info: 1 int32 (device) or NULL; bit 0: a Cholesky pivot had to be clamped (A'
+ *   of rank below s), bit 1: the Jacobi sweeps stopped at their cap.
+ * Arithmetic: FP32 products and sums for the passes over A, Gram matrices with
+ * double-float accumulation, Cholesky in FP64, one-sided Jacobi in FP32. */
+int kmeans_rsvd(gbkm_ctx *ctx, const float *A, int64_t n, int64_t d, const float *w,
+                const float *Omega, int64_t s, int64_t ell, float *V, float *sigma,
+                int32_t *info);
+
 /* Projection of a block of points onto the span of V (Section 2.2: the best-fit
  * subspace projection A_l = U D_l V^T; here V is given, d x r with orthonormal
  * columns, for example the top-r right singular vectors of a piece):

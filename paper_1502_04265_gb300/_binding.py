@@ -65,6 +65,7 @@ _SIGS = {
     "kmeans_ingest": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
     "kmeans_quantize": (ct.c_int, [_vp, _vp, _i64, _i64, _i32, _vp, _vp]),
     "kmeans_project_block": (ct.c_int, [_vp, _vp, _i32, _i64, _i64, _vp, _i64, _vp, _vp]),
+    "kmeans_rsvd": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "kmeans_seed_pp": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "kmeans_assign": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _vp, _i64,
                                  ct.POINTER(AssignOpts), _vp, _vp, _vp]),
@@ -311,6 +312,27 @@ def kmeans_ingest(X_src, X_dev=None, xnorm=None, Xq=None, resid=None, copy=True,
     c.check(load().kmeans_ingest(c.handle, ct.c_void_p(X_src.data_ptr()), n, d, _ptr(X_dev) if copy else None,
                                  _ptr(xnorm), _ptr(Xq) if quantize else None, _ptr(resid) if quantize else None))
     return (X_dev if copy else None), xnorm, (Xq if quantize else None), (resid if quantize else None)
+
+
+# ------------------------------------------------------------------ A2: the basis
+def kmeans_rsvd(A, Omega, ell, w=None, V=None, sigma=None, info=None, ctx=None):
+    """Top-ell right singular vectors (d x ell, sign-normalised) and singular values of
+    diag(sqrt(w)) A by the randomised scheme with the d x s random matrix Omega."""
+    _req(A, torch.float32, name="A")
+    _req(Omega, torch.float32, name="Omega")
+    n, d = A.shape
+    s = Omega.shape[1]
+    if Omega.shape[0] != d:
+        raise ValueError("Omega must be d x s")
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
+    V = V if V is not None else torch.empty((d, ell), dtype=torch.float32, device=A.device)
+    sigma = sigma if sigma is not None else torch.empty(ell, dtype=torch.float32, device=A.device)
+    info = info if info is not None else torch.zeros(1, dtype=torch.int32, device=A.device)
+    c = _ctx(ctx, A)
+    c.check(load().kmeans_rsvd(c.handle, _ptr(A), n, d, _ptr(w), _ptr(Omega), s, ell, _ptr(V), _ptr(sigma),
+                               _ptr(info)))
+    return V, sigma, info
 
 
 # ------------------------------------------------------------------ A2

@@ -111,6 +111,8 @@ uintptr_t host_block_of(const void *p, size_t bytes) {
 }  // namespace
 
 namespace gbkm {
+int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w, const float *Omega, int64_t s,
+              int64_t ell, float *V, float *sigma, int32_t *info);
 int launch_ingest(gbkm_ctx *c, const float *src, int64_t n, int64_t d, float *xdev, float *xnorm, void *xq,
                   float *resid);
 }
@@ -342,6 +344,20 @@ int kmeans_ingest(gbkm_ctx *c, const float *X_src, int64_t n, int64_t d, float *
     }
     prof_begin(c, "ingest");
     const int rc = gbkm::launch_ingest(c, src, n, d, X_dev, xnorm, Xq, resid);
+    prof_end(c);
+    return rc;
+}
+
+int kmeans_rsvd(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w, const float *Omega,
+                int64_t s, int64_t ell, float *V, float *sigma, int32_t *info) {
+    if (!c) return GBKM_EINVAL;
+    if (!A || !Omega || !V || n < 1 || d < 1) return set_error(c, GBKM_EINVAL, "rsvd: bad arguments");
+    if (s < 16 || s > 128 || s % 16 != 0 || ell < 1 || ell > s || s > n || s > d)
+        return set_error(c, GBKM_EINVAL, "rsvd: need 16 <= s <= 128, s %% 16 == 0, 1 <= ell <= s <= min(n, d)");
+    if (n >= ((int64_t)1 << 31) || d >= ((int64_t)1 << 31)) return set_error(c, GBKM_EUNSUPPORTED, "rsvd: n or d too large");
+    DeviceGuard g(c->device);
+    prof_begin(c, "rsvd");
+    const int rc = gbkm::rsvd_impl(c, A, n, d, w, Omega, s, ell, V, sigma, info);
     prof_end(c);
     return rc;
 }
