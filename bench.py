@@ -1247,7 +1247,7 @@ def run_svd(env, args):
                               2.0 * n * d * s, FFMA_PEAK_TFLOPS, R["total_s"], bound="alu", note=note)}
     roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
     Vh = V.cpu().numpy().astype(np.float64)
-    quality = {"info": int(info.item()),
+    quality = {"info": int(info.item()) & 0xFF, "jacobi_sweeps": int(info.item()) >> 8,
                "orthonormality": float(np.max(np.abs(Vh.T @ Vh - np.eye(ell)))),
                "planted_subspace_distance": float(np.linalg.norm(Vh @ Vh.T - Qp @ Qp.T, 2)),
                "sigma_first_last": [float(sig[0]), float(sig[-1])]}

@@ -153,7 +153,8 @@ int kmeans_ingest(gbkm_ctx *ctx, const float *X_src, int64_t n, int64_t d, float
  *   column's entry of largest magnitude (lowest row on ties) positive.
  *   sigma: ell FP32 out (decreasing) or NULL.
  *   info: 1 int32 (device) or NULL; bit 0: a Cholesky pivot had to be clamped (A'
- *   of rank below s), bit 1: the Jacobi sweeps stopped at their cap.
+ *   of rank below s), bit 1: the Jacobi sweeps stopped at their cap (30); bits 8-15:
+ *   the number of Jacobi sweeps run.
  * Arithmetic: FP32 products and sums for the passes over A, Gram matrices with
  * double-float accumulation, Cholesky in FP64, one-sided Jacobi in FP32. */
 int kmeans_rsvd(gbkm_ctx *ctx, const float *A, int64_t n, int64_t d, const float *w,

@@ -235,18 +235,24 @@ static int launch_gram(gbkm_ctx *c, const float *X, int64_t m, int64_t s, float2
 }
 
 // ---------------------------------------------------------------- Cholesky of G + shift I, R^-1
-// One CTA, the factor in shared memory (s^2 FP64).  G = R^T R with R upper triangular; shift =
-// shift_rel * trace(G) / s is added to the diagonal, and a pivot that still falls to or below
-// 1e-300 is clamped and flagged in *status.  R^-1 overwrites R in place, one column at a time:
-// X R = I gives X[i][j] = -(sum_{i <= q < j} X[i][q] R[q][j]) / R[j][j], which reads the finished
-// columns of X and the column j of R that is replaced next.  Outputs R, Rinv (FP64) and Rinv32.
+// One CTA, the factor in shared memory (s rows of s + 1 values of type W; FP64 here: an FP32
+// factor with the shift FP32 needs leaves Q's columns short by that shift, which lowers every
+// singular value by about 3e-4 relative).  G = R^T R, R upper triangular;
+// shift = shift_rel * trace(G) / s is added to the diagonal, and a pivot that still falls to or
+// below a tiny floor is clamped and flagged in *status.  R^-1 overwrites R in place, one column at
+// a time: X R = I gives X[i][j] = -(sum_{i <= q < j} X[i][q] R[q][j]) / R[j][j], which reads the
+// finished columns of X and the column j of R that is replaced next.  Outputs R and Rinv (FP64,
+// each optional) and Rinv32.
+template <typename W>
 __global__ void __launch_bounds__(256) k_chol(const double *__restrict__ G, int64_t s, double shift_rel,
                                               double *__restrict__ R, double *__restrict__ Rinv,
                                               float *__restrict__ Rinv32, int *status) {
-    extern __shared__ double Rs[];
+    extern __shared__ __align__(8) unsigned char chol_smem[];
+    W *Rs = reinterpret_cast<W *>(chol_smem);
     __shared__ double red[256];
-    __shared__ double inv_s;
-    const int tid = threadIdx.x, S = (int)s;
+    __shared__ W inv_s;
+    const W tiny = sizeof(W) == 4 ? (W)1e-30 : (W)1e-300;
+    const int tid = threadIdx.x, S = (int)s, L = S + 1;  // row stride S + 1: a column walk spreads over banks
     double tr = 0.0;
     for (int i = tid; i < S; i += 256) tr += G[i * S + i];
     red[tid] = tr;
@@ -258,49 +264,51 @@ __global__ void __launch_bounds__(256) k_chol(const double *__restrict__ G, int6
     const double shift = shift_rel * red[0] / (double)s;
     for (int e = tid; e < S * S; e += 256) {
         const int i = e / S, j = e - i * S;
-        Rs[e] = i <= j ? G[e] + (i == j ? shift : 0.0) : 0.0;
+        Rs[i * L + j] = (W)(i <= j ? G[e] + (i == j ? shift : 0.0) : 0.0);
     }
     __syncthreads();
     for (int k = 0; k < S; ++k) {
         if (tid == 0) {
-            double dk = Rs[k * S + k];
-            if (!(dk > 1e-300)) {
-                dk = 1e-300;
+            W dk = Rs[k * L + k];
+            if (!(dk > tiny)) {
+                dk = tiny;
                 atomicOr(status, 1);
             }
-            const double rkk = sqrt(dk);
-            Rs[k * S + k] = rkk;
-            inv_s = 1.0 / rkk;  // FP64 division and square root are long sequences: once per step
+            const W rkk = sqrt(dk);
+            Rs[k * L + k] = rkk;
+            inv_s = (W)1 / rkk;  // division and square root are long sequences: once per step
         }
         __syncthreads();
-        const double inv = inv_s;
-        for (int j = k + 1 + tid; j < S; j += 256) Rs[k * S + j] *= inv;
+        const W inv = inv_s;
+        for (int j = k + 1 + tid; j < S; j += 256) Rs[k * L + j] *= inv;
         __syncthreads();
         // trailing update of the upper triangle: row i = k + 1 + tid / 2 ... (threads stride rows)
         for (int i = k + 1 + (tid >> 3); i < S; i += 32) {
-            const double rki = Rs[k * S + i];
-            for (int j = i + (tid & 7); j < S; j += 8) Rs[i * S + j] -= rki * Rs[k * S + j];
+            const W rki = Rs[k * L + i];
+            for (int j = i + (tid & 7); j < S; j += 8) Rs[i * L + j] -= rki * Rs[k * L + j];
         }
         __syncthreads();
     }
-    for (int e = tid; e < S * S; e += 256) R[e] = Rs[e];
+    if (R)
+        for (int e = tid; e < S * S; e += 256) R[e] = (double)Rs[(e / S) * L + e % S];
     __syncthreads();
     for (int j = 0; j < S; ++j) {
-        if (tid == 0) inv_s = 1.0 / Rs[j * S + j];
+        if (tid == 0) inv_s = (W)1 / Rs[j * L + j];
         __syncthreads();
-        const double inv_jj = inv_s;
-        double t = 0.0;
+        const W inv_jj = inv_s;
+        W t = 0;
         const int i = tid;
         if (i < j)
-            for (int q = i; q < j; ++q) t += Rs[i * S + q] * Rs[q * S + j];
+            for (int q = i; q < j; ++q) t += Rs[i * L + q] * Rs[q * L + j];
         __syncthreads();
-        if (i < j) Rs[i * S + j] = -t * inv_jj;
-        if (i == j) Rs[j * S + j] = inv_jj;
+        if (i < j) Rs[i * L + j] = -t * inv_jj;
+        if (i == j) Rs[j * L + j] = inv_jj;
         __syncthreads();
     }
     for (int e = tid; e < S * S; e += 256) {
-        Rinv[e] = Rs[e];
-        Rinv32[e] = (float)Rs[e];
+        const W v = Rs[(e / S) * L + e % S];
+        if (Rinv) Rinv[e] = (double)v;
+        Rinv32[e] = (float)v;
     }
 }
 
@@ -506,7 +514,8 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double *__restrict__ R, c
         if (!rotated) break;
         __syncthreads();
     }
-    if (sweep == 30 && tid == 0) atomicOr(status, 2);
+    // bits 8-15: sweeps run (the sweep that found no pair to rotate included); bit 1: the cap
+    if (tid == 0) atomicOr(status, sweep == 30 ? (2 | (30 << 8)) : ((sweep + 1) << 8));
     for (int64_t cc = warp; cc < s; cc += 32) {
         float a = 0.f;
         for (int64_t r = lane; r < s; r += 32) a = fmaf(X[cc * s + r], X[cc * s + r], a);
@@ -600,8 +609,9 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
     if (cudaMemsetAsync(st, 0, sizeof(int), c->stream) != cudaSuccess) return cuda_check(c, cudaGetLastError(), "rsvd info");
     const size_t jsm = sizeof(float) * 2 * (size_t)s * (size_t)s + sizeof(int) * (size_t)s;
     if (jsm > 48 * 1024) cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
-    const size_t csm = sizeof(double) * (size_t)s * (size_t)s;
-    if (csm > 48 * 1024) cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    const size_t csm = sizeof(double) * (size_t)s * (size_t)(s + 1);
+    if (csm > 48 * 1024) cudaFuncSetAttribute(k_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+
     // 1. Y = A' Omega
     prof_begin(c, "rsvd_sketch");
     rc = launch_gemm_rows(c, A, Omega, w, n, d, s, Y);
@@ -610,11 +620,11 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
     // 2. CholeskyQR2: Y -> Q (via Q) -> Y
     prof_begin(c, "rsvd_qr");
     if ((rc = launch_gram(c, Y, n, s, gpart, G)) != GBKM_OK) return rc;
-    k_chol<<<1, 256, csm, c->stream>>>(G, s, 1e-6, R, Rinv, Rinv32, st);
+    k_chol<double><<<1, 256, csm, c->stream>>>(G, s, 1e-6, R, Rinv, Rinv32, st);
     GBKM_LAUNCHED(c);
     if ((rc = launch_gemm_rows(c, Y, Rinv32, nullptr, n, s, s, Q)) != GBKM_OK) return rc;
     if ((rc = launch_gram(c, Q, n, s, gpart, G)) != GBKM_OK) return rc;
-    k_chol<<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv, Rinv32, st);
+    k_chol<double><<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv, Rinv32, st);
     GBKM_LAUNCHED(c);
     if ((rc = launch_gemm_rows(c, Q, Rinv32, nullptr, n, s, s, Y)) != GBKM_OK) return rc;
     prof_end(c);
@@ -626,7 +636,7 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
     // 4. R_b from the Gram of Bt
     prof_begin(c, "rsvd_small");
     if ((rc = launch_gram(c, Bt, d, s, gpart, G)) != GBKM_OK) return rc;
-    k_chol<<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv, Rinv32, st);
+    k_chol<double><<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv, Rinv32, st);
     GBKM_LAUNCHED(c);
     // 5. singular values and T
     const float tol = (float)s * 1.2e-7f;

@@ -80,7 +80,7 @@ def test_rsvd_rank_deficient_recovers_exact_subspace(gb):
     V, sg, info = _run(gb, A, Om, 8)
     np.testing.assert_allclose(sg, sig[:8], rtol=1e-4)
     assert R.projector_distance(V, W[:, :8]) < 1e-3
-    assert info & ~1 == 0
+    assert 1 <= info >> 8 <= 30   # bits 8-15: the Jacobi sweeps run
 
 
 def test_rsvd_stream_piece_recovers_planted_basis(gb):
@@ -90,7 +90,7 @@ def test_rsvd_stream_piece_recovers_planted_basis(gb):
     A, _ = synth.subspace_mixture_chunk(Qp, 0, 16384, 500, 0)
     Om = synth.gaussian_sketch(2048, 80, seed=1)
     V, sg, info = _run(gb, A, Om, 64)
-    assert info == 0
+    assert (info & 0xFF) == 0
     _check(A, Om, 64, V, sg)
     assert R.projector_distance(V, Qp) < 0.1
 
