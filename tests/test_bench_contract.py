@@ -1,0 +1,28 @@
+"""The bench's reference arm (the FP64 oracle on the host cores) prints one JSON line with the
+contract's keys; run on tiny budgets, no GPU."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+        "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"}
+
+
+@pytest.mark.parametrize("workload", ["small", "svd"])
+def test_reference_arm_line(workload):
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--workload", workload, "--steps", "1",
+           "--warmup", "3", "--cpu-seconds", "0.2"]
+    if workload == "svd":
+        cmd += ["--n", "2048", "--d", "256"]
+    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert KEYS <= set(line)
+    assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None
