@@ -279,7 +279,7 @@ int kmeans_update(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const flo
  *    S = ceil(n/R) and R the smallest power of two >= R0 with k ceil(n/R) <= 2^23,
  *    R0 = 256 for k <= 2048 and 128 above.  A problem
  *    that needs more than GBKM_NOALLOC_SCRATCH_BYTES - 256 returns GBKM_ETOOBIG
- *    before anything is queued (n = 200,000, d = 1,024, k = 100 needs ~8 MB).
+ *    before anything is queued (n = 200,000, d = 1,024, k = 100 needs ~16.3 MB).
  *  - Labels must lie in [0, k); rows with other labels are left out of the sums
  *    (no status word is reported, since there is no context).
  * Returns GBKM_OK, GBKM_EINVAL, GBKM_EUNSUPPORTED, GBKM_ETOOBIG or GBKM_ECUDA. */
