@@ -274,18 +274,27 @@ int kmeans_update(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const flo
  *    the last call's contents (what must start at zero is cleared by the call
  *    itself).  Calls whose work overlaps on the GPU (two streams, two threads)
  *    race on the block and corrupt each other: serialise them.
- *  - Scratch needed (bytes, each term rounded up to 256): 8 k S + 4 ceil(kS/4096)
- *    + 8 (k+1) + 4 n + 8 (ceil(n/128) + k)(d + 2) + 8 k (2 + 2 ceil(d/256)), with
- *    S = ceil(n/R) and R the smallest power of two >= R0 with k ceil(n/R) <= 2^23,
- *    R0 = 256 for k <= 2048 and 128 above.  A problem
- *    that needs more than GBKM_NOALLOC_SCRATCH_BYTES - 256 returns GBKM_ETOOBIG
- *    before anything is queued (n = 200,000, d = 1,024, k = 100 needs ~16.3 MB).
+ *  - Scratch needed: kmeans_update_scratch_bytes(n, d, k) bytes, that is 256 plus these
+ *    terms, each rounded up to a multiple of 256: 4 kS (twice), 4 ceil(kS/4096),
+ *    4 (k+1) (twice), 4 n, 8 I d, 8 (ceil(I/32) + k) d, 16 I, 8 k (2 + 2 ceil(d/256)),
+ *    4 k and 4, with I = ceil(n/128) + k, S = ceil(n/R) and R the smallest power of two
+ *    >= R0 with k ceil(n/R) <= 2^23, R0 = 256 for k <= 2048 and 128 above.  A problem
+ *    that needs more than GBKM_NOALLOC_SCRATCH_BYTES returns GBKM_ETOOBIG before
+ *    anything is queued (n = 200,000, d = 1,024, k = 100 needs ~16.3 MB).
+ *  - The scratch block's address is resolved once per device and kept for the life of
+ *    the process: after cudaDeviceReset (which unloads the library's device image) this
+ *    entry point must not be called again in that process.
  *  - Labels must lie in [0, k); rows with other labels are left out of the sums
  *    (no status word is reported, since there is no context).
  * Returns GBKM_OK, GBKM_EINVAL, GBKM_EUNSUPPORTED, GBKM_ETOOBIG or GBKM_ECUDA. */
 int kmeans_update_noalloc(void *cuda_stream, const float *X, int64_t n, int64_t d, const float *w,
                           const int32_t *labels, int64_t k, const float *C_old, float *C_new,
                           double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
+
+/* Bytes of the fixed scratch block that kmeans_update_noalloc needs for an n x d update with
+ * k clusters (the formula above); -1 for sizes kmeans_update does not take.  Host
+ * arithmetic only: no device is touched.  No paper counterpart. */
+int64_t kmeans_update_scratch_bytes(int64_t n, int64_t d, int64_t k);
 
 /* ------------------------------------------------------------------ A8: batched problems */
 

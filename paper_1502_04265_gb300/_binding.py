@@ -73,6 +73,7 @@ _SIGS = {
     "kmeans_cost": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]),
     "kmeans_update_noalloc": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                          _vp, _vp]),
+    "kmeans_update_scratch_bytes": (ct.c_int64, [_i64, _i64, _i64]),
     "kmeans_batch_run": (ct.c_int, [_vp, ct.POINTER(Problem), _i64, _i64, _i64, _i32, _i32]),
     "kmeans_batch_replay": (ct.c_int, [_vp]),
     "kmeans_autotune": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32)]),
@@ -133,6 +134,44 @@ def _req(t, dtype, shape=None, name="tensor"):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
     return t
+
+
+def _same_device(ref, **tensors):
+    """Every given tensor (None skipped) must live on ref's device: the library reads them all
+    through one device's address space."""
+    for name, t in tensors.items():
+        if t is not None and t.device != ref.device:
+            raise ValueError(f"{name} is on {t.device}, but X is on {ref.device}")
+
+
+def _update_args(X, labels, C_old, w, C_new, counts, cost_old, cost_new, n_empty):
+    """Checks and default outputs shared by kmeans_update and kmeans_update_noalloc: a C_old that is
+    not k x d, or an output of the wrong shape, would make the kernels read or write past it."""
+    _req(X, torch.float32, name="X")
+    if X.dim() != 2:
+        raise ValueError("X must be n x d")
+    n, d = X.shape
+    _req(labels, torch.int32, (n,), "labels")
+    _req(C_old, torch.float32, name="C_old")
+    if C_old.dim() != 2 or C_old.shape[1] != d:
+        raise ValueError(f"C_old must be k x {d}, got {tuple(C_old.shape)}")
+    k = C_old.shape[0]
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
+    dev = X.device
+    C_new = C_new if C_new is not None else torch.empty_like(C_old)
+    counts = counts if counts is not None else torch.empty(k, dtype=torch.float64, device=dev)
+    cost_old = cost_old if cost_old is not None else torch.empty(1, dtype=torch.float64, device=dev)
+    cost_new = cost_new if cost_new is not None else torch.empty(1, dtype=torch.float64, device=dev)
+    n_empty = n_empty if n_empty is not None else torch.empty(1, dtype=torch.int64, device=dev)
+    _req(C_new, torch.float32, (k, d), "C_new")
+    _req(counts, torch.float64, (k,), "counts")
+    _req(cost_old, torch.float64, (1,), "cost_old")
+    _req(cost_new, torch.float64, (1,), "cost_new")
+    _req(n_empty, torch.int64, (1,), "n_empty")
+    _same_device(X, labels=labels, C_old=C_old, w=w, C_new=C_new, counts=counts, cost_old=cost_old,
+                 cost_new=cost_new, n_empty=n_empty)
+    return n, d, k, C_new, counts, cost_old, cost_new, n_empty
 
 
 class Context:
@@ -389,6 +428,15 @@ def kmeans_assign(X, C, Xop=None, Xop_scales=None, xnorm=None, compute="f32", en
     if xnorm is not None:
         _req(xnorm, torch.float32, (n,), "xnorm")
     labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=X.device)
+    _req(labels, torch.int32, (n,), "labels")
+    if min_d2 is not None:
+        _req(min_d2, torch.float32, (n,), "min_d2")
+    if compute == "fp8":
+        _req(Xop_scales, torch.float32, (n, (d + 127) // 128), "Xop_scales")
+    elif Xop_scales is not None:
+        _req(Xop_scales, torch.float32, (n,), "Xop_scales")
+    _same_device(X, C=C, Xop=Xop, Xop_scales=Xop_scales, xnorm=xnorm, labels=labels, min_d2=min_d2,
+                 n_rechecked=n_rechecked)
     opts = AssignOpts(DTYPES[compute], ENGINES[engine], 1 if recheck else 0, int(center_terms))
     c = _ctx(ctx, X)
     c.check(load().kmeans_assign(c.handle, _ptr(Xop), _ptr(Xop_scales), _ptr(X), _ptr(xnorm), n, d,
@@ -400,19 +448,8 @@ def kmeans_assign(X, C, Xop=None, Xop_scales=None, xnorm=None, compute="f32", en
 # ------------------------------------------------------------------ A6 + A7
 def kmeans_update(X, labels, C_old, w=None, C_new=None, counts=None, cost_old=None, cost_new=None,
                   n_empty=None, ctx=None):
-    _req(X, torch.float32, name="X")
-    n, d = X.shape
-    _req(labels, torch.int32, (n,), "labels")
-    _req(C_old, torch.float32, name="C_old")
-    k = C_old.shape[0]
-    if w is not None:
-        _req(w, torch.float32, (n,), "w")
-    dev = X.device
-    C_new = C_new if C_new is not None else torch.empty_like(C_old)
-    counts = counts if counts is not None else torch.empty(k, dtype=torch.float64, device=dev)
-    cost_old = cost_old if cost_old is not None else torch.empty(1, dtype=torch.float64, device=dev)
-    cost_new = cost_new if cost_new is not None else torch.empty(1, dtype=torch.float64, device=dev)
-    n_empty = n_empty if n_empty is not None else torch.empty(1, dtype=torch.int64, device=dev)
+    n, d, k, C_new, counts, cost_old, cost_new, n_empty = _update_args(
+        X, labels, C_old, w, C_new, counts, cost_old, cost_new, n_empty)
     c = _ctx(ctx, X)
     c.check(load().kmeans_update(c.handle, _ptr(X), n, d, _ptr(w), _ptr(labels), k, _ptr(C_old),
                                  _ptr(C_new), _ptr(counts), _ptr(cost_old), _ptr(cost_new),
@@ -442,21 +479,11 @@ def kmeans_update_noalloc(X, labels, C_old, w=None, C_new=None, counts=None, cos
     before the call; pass them in to allocate nothing at all.  Work is queued on torch's
     current stream of X's device, which must be the current device.
     """
-    _req(X, torch.float32, name="X")
-    n, d = X.shape
-    _req(labels, torch.int32, (n,), "labels")
-    _req(C_old, torch.float32, name="C_old")
-    k = C_old.shape[0]
-    if w is not None:
-        _req(w, torch.float32, (n,), "w")
+    n, d, k, C_new, counts, cost_old, cost_new, n_empty = _update_args(
+        X, labels, C_old, w, C_new, counts, cost_old, cost_new, n_empty)
     dev = X.device
     if dev.index != torch.cuda.current_device():
         raise ValueError("X must live on the current CUDA device")
-    C_new = C_new if C_new is not None else torch.empty_like(C_old)
-    counts = counts if counts is not None else torch.empty(k, dtype=torch.float64, device=dev)
-    cost_old = cost_old if cost_old is not None else torch.empty(1, dtype=torch.float64, device=dev)
-    cost_new = cost_new if cost_new is not None else torch.empty(1, dtype=torch.float64, device=dev)
-    n_empty = n_empty if n_empty is not None else torch.empty(1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
     rc = load().kmeans_update_noalloc(ct.c_void_p(stream), _ptr(X), n, d, _ptr(w), _ptr(labels), k,
                                       _ptr(C_old), _ptr(C_new), _ptr(counts), _ptr(cost_old),
@@ -466,6 +493,12 @@ def kmeans_update_noalloc(X, labels, C_old, w=None, C_new=None, counts=None, cos
                         (" (problem exceeds the fixed scratch block)" if rc == GBKM_ETOOBIG else ""))
     return {"C_new": C_new, "counts": counts, "cost_old": cost_old, "cost_new": cost_new,
             "n_empty": n_empty}
+
+
+def kmeans_update_scratch_bytes(n, d, k):
+    """Bytes of the fixed scratch block that kmeans_update_noalloc needs for an n x d, k-cluster
+    update (host arithmetic only; -1 for sizes the update does not take)."""
+    return int(load().kmeans_update_scratch_bytes(n, d, k))
 
 
 # ------------------------------------------------------------------ A8

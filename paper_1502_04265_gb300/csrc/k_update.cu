@@ -767,6 +767,12 @@ std::mutex g_noalloc_mu;
 void *g_noalloc_base[256] = {};  // device address of g_noalloc_scratch, per device ordinal
 }  // namespace
 
+extern "C" int64_t kmeans_update_scratch_bytes(int64_t n, int64_t d, int64_t k) {
+    if (n < 1 || d < 1 || k < 1 || k > 65536 || n >= ((int64_t)1 << 31)) return -1;
+    if ((uint64_t)n > (uint64_t)INT64_MAX / 64 / (uint64_t)d) return -1;
+    return (int64_t)gbkm::update_plan(n, d, k).bytes + 256;
+}
+
 extern "C" int kmeans_update_noalloc(void *cuda_stream, const float *X, int64_t n, int64_t d,
                                      const float *w, const int32_t *labels, int64_t k,
                                      const float *C_old, float *C_new, double *counts,

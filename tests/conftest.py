@@ -18,7 +18,7 @@ def orc():
     import oracle
 
     oracle.build()
-    oracle.set_threads(min(8, os.cpu_count() or 1))
+    oracle.set_threads(os.cpu_count() or 1)
     return oracle
 
 

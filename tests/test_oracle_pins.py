@@ -350,3 +350,70 @@ def test_e4m3_matches_torch_cast(orc):
     dec = orc.e4m3_decode(q) * np.repeat(s, 128, axis=1)[:, :300]
     big = np.abs(X) > np.repeat(s, 128, axis=1)[:, :300] * 2.0 ** -6
     assert np.all(np.abs(dec - X)[big] <= np.abs(X)[big] * 2.0 ** -4 + 1e-30)
+
+
+# --------------------------------------------------------------------------- row norms (Section 2.1)
+
+def test_row_norms_hand_example(orc):
+    """Hand-worked ||x||^2, including 2^32 + 1, which an FP32 accumulator would round to 2^32."""
+    g = _gold("row_norms_hand.json")
+    assert orc.row_norms(np.array(g["X"], np.float32)).tolist() == g["norms"]
+
+
+def test_row_norms_match_einsum(orc):
+    X, _ = synth.gaussian_mixture(3000, 257, 6, seed=41)
+    Xd = X.astype(np.float64)
+    np.testing.assert_allclose(orc.row_norms(X), np.einsum("ij,ij->i", Xd, Xd), rtol=1e-13, atol=0)
+    assert orc.row_norms(X[:0]).shape == (0,)
+
+
+# --------------------------------------------------------------------------- near-tie gap (the certified-tie rule)
+
+def _num(v):
+    return float("inf") if v == "inf" else float(v)
+
+
+def test_near_tie_gap_hand_cases(orc):
+    g = _gold("near_tie_gap_hand.json")
+    for c in g["cases"]:
+        got = orc.near_tie_gap(np.array([c["x"]], np.float32), np.array([_num(c["d1"])]),
+                               np.array([_num(c["d2"])]))[0]
+        want = _num(c["gap"])
+        if np.isinf(want):
+            assert np.isinf(got) and got > 0, c
+        else:
+            assert got == pytest.approx(want, rel=1e-15, abs=0), c
+
+
+def test_parity_checker_excuses_only_certified_ties(orc):
+    """A GPU label that picks the second-nearest center is excused only when the oracle's relative
+    top-2 gap is below 1e-5: planted points at gap 5e-6 pass, at 2e-5 (and exactly 1e-5) they fail."""
+    from parity_util import TIE_REL, assert_labels_match
+
+    C = np.array([[0.0, 0.0], [1000.0, 0.0]])
+
+    def planted(gap):
+        # x on the segment's perpendicular offset: d1 = a^2 + h^2, d2 = (1000 - a)^2 + h^2, with a set
+        # so that (d2 - d1) / d1 = gap, computed in FP64 and checked against the oracle's own gap
+        h = 300.0
+        lo, hi = 0.0, 500.0
+        for _ in range(200):
+            a = 0.5 * (lo + hi)
+            d1, d2 = a * a + h * h, (1000.0 - a) ** 2 + h * h
+            if (d2 - d1) / d1 > gap:
+                lo = a
+            else:
+                hi = a
+        return np.array([[a, h]], np.float32)
+
+    for gap, excused in [(5e-6, True), (2e-5, False), (4e-4, False)]:
+        X = planted(gap)
+        lab, d1, d2 = orc.assign(X, C)
+        real = orc.near_tie_gap(X, d1, d2)[0]
+        assert lab[0] == 0 and (real < TIE_REL) == excused, (gap, real)
+        wrong = np.array([1], np.int32)    # the second-nearest center
+        if excused:
+            assert_labels_match(orc, X, C, wrong)
+        else:
+            with pytest.raises(AssertionError):
+                assert_labels_match(orc, X, C, wrong)
