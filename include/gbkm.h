@@ -166,12 +166,31 @@ int kmeans_rsvd(gbkm_ctx *ctx, const float *A, int64_t n, int64_t d, const float
  * columns, for example the top-r right singular vectors of a piece):
  *   Y = X V         (n x r FP32, the r-dimensional coordinates)
  *   X_lift = Y V^T  (n x d FP32, the paper's d-dimensional A_l; NULL to skip).
- * X is n x d in dtype xt (GBKM_F32: the tensor cores read it as TF32;
- * GBKM_BF16: bfloat16) and V is d x r FP32 (rounded to xt's format for the
- * product).  Accumulation is FP32.  r must be a multiple of 16 and <= 256 for
- * the tensor-core engine; other r use the SIMT engine (FP32 X only). */
+ * X is n x d in dtype xt (GBKM_F32: the tensor cores take X and V in the 3xTF32
+ * form, each split into two TF32 terms and multiplied as hi.hi + hi.lo + lo.hi,
+ * which gives FP32-faithful products; GBKM_BF16: bfloat16 X against V rounded to
+ * bfloat16).  Accumulation is FP32.  r must be a multiple of 16 and <= 256 for
+ * the tensor-core engine; other r use the SIMT engine (FP32 X only).  The lift
+ * runs on the tensor cores in the 3xTF32 form when d % 16 == 0 and r % 4 == 0. */
 int kmeans_project_block(gbkm_ctx *ctx, const void *X, int32_t xt, int64_t n, int64_t d,
                          const float *V, int64_t r, float *Y, float *X_lift);
+
+/* Per-piece bases with the d-dimensional lift (Section 2.2, piecy: the input is read in pieces,
+ * each piece A_q is replaced by its projection A_q V_q V_q^T onto its own best-fit subspace of
+ * dimension ell, which keeps d coordinates; every piece adds up to ell dimensions to the point set
+ * as a whole).  Rows [q * piece_rows, (q + 1) * piece_rows) form piece q (the last may be shorter,
+ * but every piece needs at least s rows).  For each piece in order: kmeans_rsvd with the piece's
+ * rows (and weights), then kmeans_project_block of the piece onto V_q with the lift.
+ *   X: n x d FP32; w: n FP32 or NULL (the weighted SVD of Section 2.3.2; the lift needs no weights);
+ *   Omegas: pieces x d x s FP32, piece q's random matrix; s, ell: as in kmeans_rsvd;
+ *   X_lift: n x d FP32 out (may not alias X); V_out: pieces x d x ell FP32 out (piece q's basis);
+ *   sigma_out: pieces x ell FP32 or NULL; info_out: pieces int32 or NULL (kmeans_rsvd's info).
+ * The projection and the lift run on the tensor cores in the 3xTF32 form when ell % 16 == 0 and
+ * d % 16 == 0 (FP32-faithful products), else on the CUDA cores.  Allocates the coordinates of one
+ * piece (piece_rows x ell FP32) stream-ordered for the call. */
+int kmeans_piecy_lift(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const float *w, int64_t piece_rows,
+                      const float *Omegas, int64_t s, int64_t ell, float *X_lift, float *V_out, float *sigma_out,
+                      int32_t *info_out);
 
 /* ------------------------------------------------------------------ A3: k-means++ seeding */
 
@@ -413,6 +432,34 @@ int kmeans_learned_assign(gbkm_ctx *ctx, const gbkm_mlp *mlp, const float *X, co
  * C: k x d FP32; cost: 1 FP64 (device). */
 int kmeans_cost(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const float *w,
                 const float *C, int64_t k, double *cost);
+
+/* ------------------------------------------------------------------ BICO-style nearest-reference query */
+
+/* Batched weighted nearest-reference query against one snapshot of BICO's clustering features
+ * (Section 2.1: the feature (N_j, S_j, Q_j) of a point set holds its total weight, the weighted sum
+ * of its points and the weighted sum of their squared lengths, so it knows its centroid
+ * mu_j = S_j / N_j and its error c_j = Q_j - ||S_j||^2 / N_j; Section 2.3.1: a weighted point
+ * (x, w) stands for w copies of x, its nearest reference point is found once, and feature j
+ * takes
+ *     w' = w                                                if s ||x - mu_j||^2 - T + c_j <= 0,
+ *     w' = max(0, min(w, floor((s T - s c_j) / (s ||x - mu_j||^2 - T + c_j))))  otherwise,
+ * copies of it, s = N_j and T the threshold; the paper leaves c_j > T open, where this gives 0).
+ * The sequential tree that applies the answers is not part of the call: every point of the batch
+ * is answered against the same snapshot.
+ *   Xop, Xop_scales, X, xnorm, opts: as in kmeans_assign (X: n x d FP32 points; the operand form
+ *     of the distance GEMM; the reference search is the exact assignment step against R).
+ *   w: n FP32 weights (whole numbers in BICO's use) or NULL for 1.
+ *   R: m x d FP32 reference points (one per feature), m <= 65536.
+ *   N: m FP64 (> 0; a feature with N_j <= 0 is treated as empty: d2 = 0 and w' = w),
+ *   S: m x d FP64, Q: m FP64: the snapshot.  T: the threshold (>= 0, host value).
+ *   ref_out: n int32, the nearest reference (lowest index on ties, exact as kmeans_assign's labels).
+ *   d2_out: n FP64 or NULL, ||x_i - mu_j||^2 (FP64 direct differences).
+ *   take_out: n FP64, w' (whole copies when w is whole).
+ * Arithmetic after the search: FP64, each step of the rule above rounded once, in that order. */
+int kmeans_bico_query(gbkm_ctx *ctx, const void *Xop, const float *Xop_scales, const float *X,
+                      const float *xnorm, int64_t n, int64_t d, const float *w, const float *R,
+                      int64_t m, const double *N, const double *S, const double *Q, double T,
+                      const gbkm_assign_opts *opts, int32_t *ref_out, double *d2_out, double *take_out);
 
 #ifdef __cplusplus
 }

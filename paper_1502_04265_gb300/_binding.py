@@ -74,6 +74,9 @@ _SIGS = {
     "kmeans_update_noalloc": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                          _vp, _vp]),
     "kmeans_update_scratch_bytes": (ct.c_int64, [_i64, _i64, _i64]),
+    "kmeans_piecy_lift": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "kmeans_bico_query": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp,
+                                     ct.c_double, ct.POINTER(AssignOpts), _vp, _vp, _vp]),
     "kmeans_batch_run": (ct.c_int, [_vp, ct.POINTER(Problem), _i64, _i64, _i64, _i32, _i32]),
     "kmeans_batch_replay": (ct.c_int, [_vp]),
     "kmeans_autotune": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32)]),
@@ -396,6 +399,31 @@ def kmeans_project_block(X, V, Y=None, X_lift=None, lift=False, ctx=None):
     return (Y, X_lift) if X_lift is not None else Y
 
 
+def kmeans_piecy_lift(X, piece_rows, Omegas, ell, w=None, X_lift=None, ctx=None):
+    """Per-piece bases (randomised SVD with Omegas[q] for piece q) and the d-dimensional lift of every
+    piece onto its own basis.  Returns (X_lift n x d, V pieces x d x ell, sigma pieces x ell, info)."""
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    pieces = (n + piece_rows - 1) // piece_rows
+    _req(Omegas, torch.float32, name="Omegas")
+    if Omegas.dim() != 3 or Omegas.shape[0] != pieces or Omegas.shape[1] != d:
+        raise ValueError(f"Omegas must be {pieces} x {d} x s")
+    s = Omegas.shape[2]
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
+    dev = X.device
+    X_lift = X_lift if X_lift is not None else torch.empty((n, d), dtype=torch.float32, device=dev)
+    _req(X_lift, torch.float32, (n, d), "X_lift")
+    V = torch.empty((pieces, d, ell), dtype=torch.float32, device=dev)
+    sigma = torch.empty((pieces, ell), dtype=torch.float32, device=dev)
+    info = torch.zeros(pieces, dtype=torch.int32, device=dev)
+    _same_device(X, Omegas=Omegas, w=w, X_lift=X_lift)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_piecy_lift(c.handle, _ptr(X), n, d, _ptr(w), piece_rows, _ptr(Omegas), s, ell, _ptr(X_lift),
+                                     _ptr(V), _ptr(sigma), _ptr(info)))
+    return X_lift, V, sigma, info
+
+
 # ------------------------------------------------------------------ A3
 def kmeans_seed_pp(X, k, u, w=None, idx_out=None, C_out=None, ctx=None):
     _req(X, torch.float32, name="X")
@@ -613,3 +641,40 @@ def kmeans_learned_assign(net, X, Xh, C, s2, topm=32, labels=None, n_fallback=No
     c.check(load().kmeans_learned_assign(c.handle, ct.byref(m), _ptr(X), _ptr(Xh), n, d, _ptr(C), k, _ptr(s2), topm,
                                          _ptr(labels), _ptr(n_fallback), _ptr(cand_out)))
     return labels, n_fallback
+
+
+# ------------------------------------------------------------------ BICO-style query
+def kmeans_bico_query(X, R, N, S, Q, T, w=None, Xop=None, Xop_scales=None, xnorm=None, compute="f32",
+                      engine="auto", ref_out=None, d2_out=None, take_out=None, ctx=None):
+    """Nearest reference of every point (R: m x d) and the copies w' its feature takes under the
+    threshold T, against the snapshot N (m), S (m x d), Q (m) in FP64.  Returns (ref, d2, take)."""
+    _req(X, torch.float32, name="X")
+    n, d = X.shape
+    _req(R, torch.float32, name="R")
+    if R.dim() != 2 or R.shape[1] != d:
+        raise ValueError(f"R must be m x {d}")
+    m = R.shape[0]
+    _req(N, torch.float64, (m,), "N")
+    _req(S, torch.float64, (m, d), "S")
+    _req(Q, torch.float64, (m,), "Q")
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
+    if compute == "bf16":
+        _req(Xop, torch.bfloat16, (n, d), "Xop")
+    if xnorm is not None:
+        _req(xnorm, torch.float32, (n,), "xnorm")
+    dev = X.device
+    ref_out = ref_out if ref_out is not None else torch.empty(n, dtype=torch.int32, device=dev)
+    d2_out = d2_out if d2_out is not None else torch.empty(n, dtype=torch.float64, device=dev)
+    take_out = take_out if take_out is not None else torch.empty(n, dtype=torch.float64, device=dev)
+    _req(ref_out, torch.int32, (n,), "ref_out")
+    _req(d2_out, torch.float64, (n,), "d2_out")
+    _req(take_out, torch.float64, (n,), "take_out")
+    _same_device(X, R=R, N=N, S=S, Q=Q, w=w, Xop=Xop, Xop_scales=Xop_scales, xnorm=xnorm, ref_out=ref_out,
+                 d2_out=d2_out, take_out=take_out)
+    opts = AssignOpts(DTYPES[compute], ENGINES[engine], 1, 1)
+    c = _ctx(ctx, X)
+    c.check(load().kmeans_bico_query(c.handle, _ptr(Xop), _ptr(Xop_scales), _ptr(X), _ptr(xnorm), n, d, _ptr(w),
+                                     _ptr(R), m, _ptr(N), _ptr(S), _ptr(Q), float(T), ct.byref(opts),
+                                     _ptr(ref_out), _ptr(d2_out), _ptr(take_out)))
+    return ref_out, d2_out, take_out

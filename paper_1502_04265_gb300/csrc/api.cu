@@ -384,7 +384,13 @@ int kmeans_project_block(gbkm_ctx *c, const void *X, int32_t xt, int64_t n, int6
     prof_end(c);
     if (rc != GBKM_OK || !X_lift) return rc;
     // X_lift[n x d] = Y V^T: B = V as an N x K (d x r) row-major matrix
-    return gbkm::launch_gemm_simt_strided(c, Y, V, n, d, r, r, 1, X_lift);
+    prof_begin(c, "lift");
+    if (gbkm::tc_lift_supported(d, r) && aligned16(Y) && aligned16(X_lift))
+        rc = gbkm::launch_lift_tc(c, Y, n, r, V, d, X_lift);
+    else
+        rc = gbkm::launch_gemm_simt_strided(c, Y, V, n, d, r, r, 1, X_lift);
+    prof_end(c);
+    return rc;
 }
 
 int kmeans_seed_pp(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, int64_t k,

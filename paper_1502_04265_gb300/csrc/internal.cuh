@@ -275,6 +275,9 @@ int learned_assign(gbkm_ctx *c, const gbkm_mlp *m, const float *X, const void *X
 bool tc_project_supported(int dtype, int64_t d, int64_t r);
 int launch_project_tc(gbkm_ctx *c, int dtype, const void *X, int64_t n, int64_t d,
                       const float *V, int64_t r, float *Y);
+// X_lift = Y V^T on the tensor cores (3xTF32); d % 16 == 0, r % 4 == 0, Y and X_lift 16-byte aligned
+bool tc_lift_supported(int64_t d, int64_t r);
+int launch_lift_tc(gbkm_ctx *c, const float *Y, int64_t n, int64_t r, const float *V, int64_t d, float *X_lift);
 // ---------------------------------------------------------------- batched problems
 // device-side descriptor of one problem of a batched run (all pointers are device pointers)
 struct BProb {

@@ -1476,16 +1476,31 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
     return launch<F_TF32X3, E_ARGMIN>(c, tA, tB, tB2, a, p);
 }
 
-// V (d x r, FP32) -> V^T (r x d) in the operand format of the projection
-__global__ void k_vt(const float *__restrict__ V, int64_t d, int64_t r, int dtype, void *out) {
+// V (d x r, FP32) -> V^T (r x d) in the operand format of the projection: BF16, or FP32 split into
+// TF32 hi and lo parts (hi = the top 19 bits of v, lo = those of v - hi) for the 3xTF32 form
+__global__ void k_vt(const float *__restrict__ V, int64_t d, int64_t r, int dtype, void *out, float *out_lo) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= d * r) return;
     const int64_t q = e / d, t = e % d;  // out[q][t] = V[t][q]
     const float v = V[t * r + q];
-    if (dtype == GBKM_BF16)
+    if (dtype == GBKM_BF16) {
         static_cast<__nv_bfloat16 *>(out)[e] = __float2bfloat16_rn(v);
-    else
-        static_cast<float *>(out)[e] = v;
+    } else {
+        const float hi = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+        static_cast<float *>(out)[e] = hi;
+        out_lo[e] = __uint_as_float(__float_as_uint(__fsub_rn(v, hi)) & 0xffffe000u);
+    }
+}
+
+// V (d x r, FP32, row-major: already the N x K, K-major operand of the lift) split into TF32 hi / lo
+__global__ void k_split_tf32(const float *__restrict__ V, int64_t count, float *__restrict__ hi,
+                             float *__restrict__ lo) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const float v = V[e];
+    const float h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+    hi[e] = h;
+    lo[e] = __uint_as_float(__float_as_uint(__fsub_rn(v, h)) & 0xffffe000u);
 }
 
 bool tc_project_supported(int dtype, int64_t d, int64_t r) {
@@ -1496,32 +1511,67 @@ bool tc_project_supported(int dtype, int64_t d, int64_t r) {
     return false;
 }
 
+// a store-epilogue GEMM Out[M x N] = A[M x K] B^T (B: N x K) on the engine, operands already in place
+static int launch_store_gemm(gbkm_ctx *c, int form, const void *A, const void *B, const void *B_lo, int64_t M,
+                             int64_t N, int64_t K, float *Out) {
+    using namespace tc;
+    const uint32_t es = (form == F_BF16) ? 2 : 4;
+    const Plan p = plan(form, K, N);
+    const CUtensorMapDataType dt = (form == F_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUtensorMap tA, tB, tB2;
+    if (!make_tmap(&tA, dt, A, (uint64_t)K, (uint64_t)M, es, BM) ||
+        !make_tmap(&tB, dt, B, (uint64_t)K, (uint64_t)N, es, (uint32_t)p.bn))
+        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the projection operands");
+    tB2 = tB;
+    if (form == F_TF32X3 && !make_tmap(&tB2, dt, B_lo, (uint64_t)K, (uint64_t)N, es, (uint32_t)p.bn))
+        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the projection's low part");
+    Args a{};
+    a.n = M, a.d = K, a.k = N, a.k_pad = N;
+    a.n_chunks = p.n_chunks, a.bn = p.bn, a.kb = p.kb, a.stages = p.stages, a.tmem_cols = p.tmem_cols;
+    a.m_tiles = (int)ceil_div(M, BM);
+    a.a_bytes = p.a_bytes, a.b_bytes = p.b_bytes, a.stage_bytes = p.stage_bytes, a.tx_bytes = p.tx_bytes;
+    a.idesc = make_idesc(form, BM, p.bn);
+    a.Y = Out, a.ldy = N;
+    a.status = c->status;
+    if (form == F_BF16) return launch<F_BF16, E_STORE>(c, tA, tB, tB2, a, p);
+    return launch<F_TF32X3, E_STORE>(c, tA, tB, tB2, a, p);
+}
+
+// Y = X V: BF16 X against BF16 V, or FP32 X in the 3xTF32 form (the staged X tile split into TF32 hi
+// and lo in shared memory, V^T split in the workspace; three MMAs per step: FP32-faithful products)
 int launch_project_tc(gbkm_ctx *c, int dtype, const void *X, int64_t n, int64_t d, const float *V, int64_t r,
                       float *Y) {
     using namespace tc;
-    const int form = (dtype == GBKM_BF16) ? F_BF16 : F_TF32;
+    const int form = (dtype == GBKM_BF16) ? F_BF16 : F_TF32X3;
     const uint32_t es = (form == F_BF16) ? 2 : 4;
     int rc = GBKM_OK;
-    void *ws = ws_reserve(c, (size_t)r * d * es + 256, &rc);
+    WsPlan wp;
+    const size_t o_hi = wp.take<char>((size_t)r * d * es), o_lo = wp.take<float>(form == F_BF16 ? 0 : (size_t)r * d);
+    void *ws = ws_reserve(c, wp.off, &rc);
     if (!ws) return rc;
-    k_vt<<<(unsigned)ceil_div(r * d, 256), 256, 0, c->stream>>>(V, d, r, dtype, ws);
+    k_vt<<<(unsigned)ceil_div(r * d, 256), 256, 0, c->stream>>>(V, d, r, dtype, ws_at<void>(ws, o_hi),
+                                                                 ws_at<float>(ws, o_lo));
     GBKM_LAUNCHED(c);
-    const Plan p = plan(form, d, r);
-    const CUtensorMapDataType dt = (form == F_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    CUtensorMap tA, tB;
-    if (!make_tmap(&tA, dt, X, (uint64_t)d, (uint64_t)n, es, BM) ||
-        !make_tmap(&tB, dt, ws, (uint64_t)d, (uint64_t)r, es, (uint32_t)p.bn))
-        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the projection operands");
-    Args a{};
-    a.n = n, a.d = d, a.k = r, a.k_pad = r;
-    a.n_chunks = p.n_chunks, a.bn = p.bn, a.kb = p.kb, a.stages = p.stages, a.tmem_cols = p.tmem_cols;
-    a.m_tiles = (int)ceil_div(n, BM);
-    a.a_bytes = p.a_bytes, a.b_bytes = p.b_bytes, a.stage_bytes = p.stage_bytes, a.tx_bytes = p.tx_bytes;
-    a.idesc = make_idesc(form, BM, p.bn);
-    a.Y = Y, a.ldy = r;
-    a.status = c->status;
-    if (form == F_BF16) return launch<F_BF16, E_STORE>(c, tA, tB, tB, a, p);
-    return launch<F_TF32, E_STORE>(c, tA, tB, tB, a, p);
+    return launch_store_gemm(c, form, X, ws_at<void>(ws, o_hi), ws_at<void>(ws, o_lo), n, r, d, Y);
+}
+
+bool tc_lift_supported(int64_t d, int64_t r) {
+    return tc::encode_fn() && d % 16 == 0 && d >= 16 && r % 4 == 0 && r >= 4;
+}
+
+// X_lift = Y V^T (n x d) in the 3xTF32 form: A = Y (n x r, K = r), B = V itself (d x r row-major is the
+// N x K, K-major operand), split into TF32 hi / lo in the workspace
+int launch_lift_tc(gbkm_ctx *c, const float *Y, int64_t n, int64_t r, const float *V, int64_t d, float *X_lift) {
+    using namespace tc;
+    int rc = GBKM_OK;
+    WsPlan wp;
+    const size_t o_hi = wp.take<float>((size_t)d * r), o_lo = wp.take<float>((size_t)d * r);
+    void *ws = ws_reserve(c, wp.off, &rc);
+    if (!ws) return rc;
+    k_split_tf32<<<(unsigned)ceil_div(d * r, 256), 256, 0, c->stream>>>(V, d * r, ws_at<float>(ws, o_hi),
+                                                                        ws_at<float>(ws, o_lo));
+    GBKM_LAUNCHED(c);
+    return launch_store_gemm(c, F_TF32X3, Y, ws_at<void>(ws, o_hi), ws_at<void>(ws, o_lo), n, d, r, X_lift);
 }
 
 

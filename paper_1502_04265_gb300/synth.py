@@ -33,6 +33,8 @@ __all__ = [
     "subspace_mixture_chunk",
     "batch_problem_list",
     "mlp_init",
+    "bico_members",
+    "bico_batch",
 ]
 
 
@@ -173,3 +175,34 @@ def mlp_init(d_in: int, hidden: int, k: int, seed: int) -> np.ndarray:
         parts.append(rng.uniform(-bound, bound, size=fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+def bico_members(refs: np.ndarray, seed: int, max_members: int = 8):
+    """Member points of a snapshot of BICO-style features (Section 2.1), one feature per reference
+    row: feature j holds its reference point and N_j - 1 more points around it, N_j uniform in
+    {1, ..., max_members}, at a spread sigma_j log-uniform in [0.05, 1] (FP32).  Returns (P, f) with
+    f[i] the feature of member P[i]; the features' sums are left to the caller."""
+    refs = np.asarray(refs, dtype=np.float32)
+    m, d = refs.shape
+    rng = np.random.default_rng([seed, 0xB1C0])
+    cnt = rng.integers(1, max_members + 1, size=m)
+    sig = np.exp(rng.uniform(math.log(0.05), 0.0, size=m)).astype(np.float32)
+    f = np.repeat(np.arange(m, dtype=np.int32), cnt)
+    noise = rng.standard_normal((f.shape[0], d), dtype=np.float32)
+    first = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    noise[first] = 0.0
+    P = refs[f] + sig[f, None] * noise
+    return P.astype(np.float32), f
+
+
+def bico_batch(refs: np.ndarray, n: int, seed: int):
+    """A batch of n points arriving at a BICO-style summary: each lies near a reference row chosen
+    uniformly, at a spread of 0.01, 0.3 or 2 (equally likely), so that some points fit their feature
+    whole, some in part and some not at all.  FP32."""
+    refs = np.asarray(refs, dtype=np.float32)
+    m, d = refs.shape
+    rng = np.random.default_rng([seed, 0xB1C1])
+    j = rng.integers(0, m, size=n)
+    sp = np.array([0.01, 0.3, 2.0], np.float32)[rng.integers(0, 3, size=n)]
+    X = refs[j] + sp[:, None] * rng.standard_normal((n, d), dtype=np.float32)
+    return X.astype(np.float32)

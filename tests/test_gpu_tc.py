@@ -107,20 +107,44 @@ def test_tc_planted_ties(gb, orc):
         assert_labels_match(orc, X, C.astype(np.float64), lab)
 
 
+def _tf32(a):
+    """The top 19 bits of every FP32 value (what one TF32 term keeps)."""
+    a = np.ascontiguousarray(a, np.float32)
+    return (a.view(np.uint32) & np.uint32(0xffffe000)).view(np.float32).astype(np.float64)
+
+
 @pytest.mark.parametrize("xt", ["f32", "bf16"])
 @pytest.mark.parametrize("n,d,r", [(1000, 256, 64), (300, 2048, 64), (129, 64, 16), (200, 512, 256)])
-def test_tc_project(gb, orc, xt, n, d, r):
+def test_tc_project_and_lift(gb, orc, xt, n, d, r):
+    """Y = X V on the tensor cores (BF16, or FP32 X in the 3xTF32 form) and the lift Y V^T (3xTF32).
+
+    Worst-case bounds per element: BF16 |Y - Yr| <= (2u + d 2^-22) ||x|| (u = 2^-8, ||v_q|| = 1);
+    3xTF32 (3.01 2^-20 + 3d 2^-22) ||x||.  The FP32 form must also beat a single TF32 term: its error
+    is at most half the error that truncating X and V to TF32 gives on the same data (computed here
+    in FP64).  The lift is compared with the FP64 lift of the GPU's own Y, so that only its own
+    rounding counts, and must likewise beat a single TF32 term by 2x."""
     Q = synth.orthonormal_basis(d, min(r, 8), seed=d)
     X, _ = synth.subspace_mixture_chunk(Q, 0, n, 10, seed=r)
     V = synth.orthonormal_basis(d, r, seed=r + 1).astype(np.float32)
     Xg = T(X)
     Xin = Xg if xt == "f32" else gb.kmeans_quantize(Xg, "bf16")[0]
-    Y = H(gb.kmeans_project_block(Xin, T(V)))
-    Yr = orc.project(X, V.astype(np.float64))
+    Y, L = gb.kmeans_project_block(Xin, T(V), lift=True)
+    Y, L = H(Y), H(L)
+    V64 = V.astype(np.float64)
+    Yr = orc.project(X, V64)
     xn = np.sqrt(orc.row_norms(X))[:, None]
-    # per element |sum x_t v_t| error <= (2u + d 2^-22) sum |x_t v_t| <= (2u + d 2^-22) ||x|| (||v_q|| = 1)
-    u = 2.0 ** -8 if xt == "bf16" else 2.0 ** -10
-    assert np.all(np.abs(Y - Yr) <= (2 * u + d * 2.0 ** -22) * xn + 1e-5)
+    if xt == "bf16":
+        u = 2.0 ** -8
+        assert np.all(np.abs(Y - Yr) <= (2 * u + d * 2.0 ** -22) * xn + 1e-5)
+    else:
+        assert np.all(np.abs(Y - Yr) <= (3.01 * 2.0 ** -20 + 3 * d * 2.0 ** -22) * xn + 1e-6)
+        single = np.abs(_tf32(X) @ _tf32(V) - Yr).max()
+        assert np.abs(Y - Yr).max() <= 0.5 * single
+    Lg = Y.astype(np.float64) @ V64.T           # the exact lift of the GPU's Y
+    yn = np.sqrt((Y.astype(np.float64) ** 2).sum(1))[:, None]
+    assert np.all(np.abs(L - Lg) <= (3.01 * 2.0 ** -20 + 3 * r * 2.0 ** -22) * yn + 1e-6)
+    single = np.abs(_tf32(Y) @ _tf32(V).T - Lg).max()
+    assert np.abs(L - Lg).max() <= 0.5 * single
 
 
 @pytest.mark.parametrize("form", ["bf16", "f32", "fp8"])
