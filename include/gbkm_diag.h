@@ -33,6 +33,26 @@ int gbkm_profile_enable(struct gbkm_ctx *ctx, int enable);
  * negative gbkm_status. */
 int gbkm_profile_read(struct gbkm_ctx *ctx, char *buf, int64_t len);
 
+/* Failure detection without a GPU fault.
+ *
+ * gbkm_debug_set_wait_limit: every bounded device-side wait of the tensor-core kernels launched
+ * on ctx afterwards gives up after ns nanoseconds instead of the default 2 s (0 restores the
+ * default).  A wait that gives up makes its CTA stop issuing work, wait (at most 0.5 s) for its
+ * copies and tensor-core operations in flight, free its tensor memory and exit; the outputs of
+ * that call are then undefined, and the next gbkm_sync returns GBKM_ETIMEOUT and clears the
+ * status, after which the context is usable again.
+ *
+ * gbkm_debug_stall_loads: with on != 0, the tensor-core kernels launched on ctx afterwards issue
+ * none of their shared-memory copies, so the tensor-core issuer's first wait (for a copy that is
+ * never made) runs out after the wait limit and the whole launch takes the path above: the way a
+ * test makes a bounded wait give up without faulting the GPU.  0 turns it off.
+ *
+ * gbkm_debug_fail_alloc: the next `count` growths of ctx's workspace fail as a failed
+ * cudaMalloc would (GBKM_ENOMEM, nothing queued by that call); 0 clears it.  Host-side only. */
+int gbkm_debug_set_wait_limit(struct gbkm_ctx *ctx, uint64_t ns);
+int gbkm_debug_stall_loads(struct gbkm_ctx *ctx, int on);
+int gbkm_debug_fail_alloc(struct gbkm_ctx *ctx, int count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,9 @@ _SIGS = {
     "gbkm_version": (ct.c_int, []),
     "gbkm_profile_enable": (ct.c_int, [_vp, ct.c_int]),
     "gbkm_profile_read": (ct.c_int, [_vp, ct.c_char_p, _i64]),
+    "gbkm_debug_set_wait_limit": (ct.c_int, [_vp, ct.c_uint64]),
+    "gbkm_debug_fail_alloc": (ct.c_int, [_vp, ct.c_int]),
+    "gbkm_debug_stall_loads": (ct.c_int, [_vp, ct.c_int]),
     "kmeans_row_norms": (ct.c_int, [_vp, _vp, _i64, _i64, _vp]),
     "gbkm_host_alloc": (ct.c_int, [ct.c_size_t, ct.POINTER(ct.c_void_p)]),
     "gbkm_host_free": (ct.c_int, [_vp]),
@@ -229,6 +232,18 @@ class Context:
             name, n, ms = line.split()
             out[name] = (int(n), float(ms))
         return out
+
+    def set_wait_limit(self, ns: int):
+        """Limit of every bounded device wait of later tensor-core launches (0: the 2 s default)."""
+        self.check(load().gbkm_debug_set_wait_limit(self._h, int(ns)))
+
+    def stall_loads(self, on: bool):
+        """Make later tensor-core launches issue no copies, so that their bounded waits run out."""
+        self.check(load().gbkm_debug_stall_loads(self._h, 1 if on else 0))
+
+    def fail_next_allocs(self, count: int):
+        """Make the next `count` workspace growths fail as out of memory (host-side injection)."""
+        self.check(load().gbkm_debug_fail_alloc(self._h, int(count)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -39,6 +39,12 @@ void *ws_reserve(gbkm_ctx *c, size_t bytes, int *rc) {
     c->ws = nullptr;
     c->ws_bytes = 0;
     size_t want = bytes + (bytes >> 3) + (1 << 20);
+    if (c->fail_alloc > 0) {
+        // a failure injected by gbkm_debug_fail_alloc: the same path as a failed cudaMalloc
+        c->fail_alloc--;
+        *rc = set_error(c, GBKM_ENOMEM, "workspace of %zu bytes: allocation failure injected", want);
+        return nullptr;
+    }
     e = cudaMalloc(&c->ws, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -212,6 +218,24 @@ int gbkm_profile_read(gbkm_ctx *c, char *buf, int64_t len) {
         off += w;
     }
     return (int)acc.size();
+}
+
+int gbkm_debug_set_wait_limit(gbkm_ctx *c, uint64_t ns) {
+    if (!c) return GBKM_EINVAL;
+    c->wait_ns = ns;
+    return GBKM_OK;
+}
+
+int gbkm_debug_stall_loads(gbkm_ctx *c, int on) {
+    if (!c) return GBKM_EINVAL;
+    c->stall_loads = on != 0;
+    return GBKM_OK;
+}
+
+int gbkm_debug_fail_alloc(gbkm_ctx *c, int count) {
+    if (!c || count < 0) return GBKM_EINVAL;
+    c->fail_alloc = count;
+    return GBKM_OK;
 }
 
 int gbkm_destroy(gbkm_ctx *c) {

@@ -46,6 +46,9 @@ struct gbkm_ctx {
     uint64_t graph_epoch = 0;      // ws_epoch when graph_exec was recorded (its tables live in ws)
     cudaStream_t cap_stream = nullptr;  // private stream the batched run is recorded on
     int bn_cap = 0;                // center-chunk width of the tcgen05 assignment (0: 256); autotuner knob
+    uint64_t wait_ns = 0;          // limit of every bounded device wait (0: the default, 2 s)
+    int fail_alloc = 0;            // diagnostics: the next fail_alloc workspace growths fail as if out of memory
+    int stall_loads = 0;           // diagnostics: tensor-core launches issue no copies (their waits run out)
 };
 
 int set_error(gbkm_ctx *c, int code, const char *fmt, ...);

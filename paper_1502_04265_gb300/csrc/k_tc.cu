@@ -25,7 +25,8 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int MAX_STAGES = 8;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait unless the context sets another limit
+constexpr uint64_t DRAIN_LIMIT_NS = 500000000ull;  // 0.5 s for the copies in flight on the abort path
 constexpr int SMEM_BUDGET = 200 * 1024;      // stage ring of the batched kernel
 constexpr int MAX_DYN_SMEM = 227 * 1024;     // dynamic shared memory a CTA may use
 
@@ -80,6 +81,8 @@ struct Args {
     float *top_val;
     int topm;
     int *status;
+    uint64_t wait_ns;  // limit of every bounded wait (set by launch())
+    int stall_loads;   // diagnostics: the producer issues no copy, so the consumers' waits run out
 };
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
@@ -260,15 +263,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait for the phase of `parity`.  Gives up when the CTA's abort flag is raised, or after
-// WAIT_LIMIT_NS, in which case it raises the flag itself.  Returns false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// limit_ns, in which case it raises the flag itself.  Returns false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63) == 0) {
+        // the clock and the abort flag after 1, 2, 4, ... 32 polls, then every 64
+        if ((it & (it - 1)) == 0 || (it & 63) == 0) {
             if (*abort_flag) return false;
-            if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+            if (globaltimer_ns() - t0 > limit_ns) {
                 *abort_flag = 1;
                 return false;
             }
@@ -463,10 +468,11 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
             int s = 0;
             uint32_t ph = 0;
             uint32_t issued = 0, last_par = 0;  // per-stage: issued bit, parity of the last issue
+            if (a.stall_loads) goto producer_done;
             for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
                 for (int nc = 0; nc < units_per_tile; ++nc) {
                     for (int kb = 0; kb < a.kb; ++kb) {
-                        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) goto producer_done;
+                        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.wait_ns)) goto producer_done;
                         uint8_t *st = base + (size_t)s * a.stage_bytes;
                         mbar_expect_tx(&full[s], a.tx_bytes);
                         const int32_t kx =
@@ -486,7 +492,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                         if (a.bias_mma) {
                             // the bias block: the ones operand (the same tile for every row tile) and
                             // this chunk's rows of the bias operand
-                            if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) goto producer_done;
+                            if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.wait_ns)) goto producer_done;
                             uint8_t *st = base + (size_t)s * a.stage_bytes;
                             mbar_expect_tx(&full[s], a.tx_bytes);
                             tma_load_2d(st, &tmA2, &full[s], 0, 0);
@@ -505,7 +511,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
             if (*abort_flag) {
                 // let every bulk copy still in flight land before the CTA exits
                 for (int q = 0; q < a.stages; ++q)
-                    if (issued & (1u << q)) mbar_drain(&full[q], (last_par >> q) & 1, 500000000ull);
+                    if (issued & (1u << q)) mbar_drain(&full[q], (last_par >> q) & 1, DRAIN_LIMIT_NS);
             }
         }
     } else if (warp == 1) {
@@ -518,11 +524,11 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
             uint32_t last_parity = 0;
             for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
                 for (int nc = 0; nc < units_per_tile; ++nc) {
-                    if (!mbar_wait(&acce[ab], aph ^ 1, abort_flag)) goto mma_done;
+                    if (!mbar_wait(&acce[ab], aph ^ 1, abort_flag, a.wait_ns)) goto mma_done;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(ab * bn_alloc);
                     for (int kb = 0; kb < a.kb; ++kb) {
-                        if (!mbar_wait(X3 ? &tfull[s] : &full[s], ph, abort_flag)) goto mma_done;
+                        if (!mbar_wait(X3 ? &tfull[s] : &full[s], ph, abort_flag, a.wait_ns)) goto mma_done;
                         tc_fence_after();
                         uint8_t *st = base + (size_t)s * a.stage_bytes;
                         const uint64_t adesc = sw128_desc(st);
@@ -557,7 +563,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                     if constexpr (FORM == F_BF16) {
                         if (a.bias_mma) {
                             // one K = 16 step: ones x (bias head, bias tail, 0 ...) adds the bias
-                            if (!mbar_wait(&full[s], ph, abort_flag)) goto mma_done;
+                            if (!mbar_wait(&full[s], ph, abort_flag, a.wait_ns)) goto mma_done;
                             tc_fence_after();
                             uint8_t *st = base + (size_t)s * a.stage_bytes;
                             tc_mma<FORM>(d_tmem, sw128_desc(st), sw128_desc(st + a.a_bytes), a.idesc, 1u);
@@ -580,7 +586,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                 }
             }
         mma_done:
-            if (*abort_flag && committed && last_bar) mbar_drain(last_bar, last_parity, 500000000ull);
+            if (*abort_flag && committed && last_bar) mbar_drain(last_bar, last_parity, DRAIN_LIMIT_NS);
         }
     } else if (X3 && warp >= 8 && warp < 12) {
         // ------------------------------------------------ 3xTF32 split of the staged X tile
@@ -590,7 +596,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
         for (int tile = blockIdx.x; tile < m_tiles && !*abort_flag; tile += gridDim.x) {
             for (int nc = 0; nc < units_per_tile; ++nc) {
                 for (int kb = 0; kb < a.kb; ++kb) {
-                    if (!mbar_wait(&full[s], ph, abort_flag)) goto split_done;
+                    if (!mbar_wait(&full[s], ph, abort_flag, a.wait_ns)) goto split_done;
                     uint8_t *st = base + (size_t)s * a.stage_bytes;
                     uint4 *hi = reinterpret_cast<uint4 *>(st);
                     uint4 *lo = reinterpret_cast<uint4 *>(st + a.a_bytes);
@@ -691,11 +697,11 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                 // group 1 reuses its band list only after group 0 has merged the previous point's
                 if (eg == 1) {
                     uint64_t *xempty = reinterpret_cast<uint64_t *>(ex + NG * 2 * CAND_MAX * 128 * 4 + 128 * 16) + 4;
-                    if (!mbar_wait(&xempty[q], xph ^ 1, abort_flag)) goto epi_done;
+                    if (!mbar_wait(&xempty[q], xph ^ 1, abort_flag, a.wait_ns)) goto epi_done;
                 }
             }
             for (int nc = 0; nc < units_per_tile; ++nc) {
-                if (!mbar_wait(&accf[ab], aph, abort_flag)) goto epi_done;
+                if (!mbar_wait(&accf[ab], aph, abort_flag, a.wait_ns)) goto epi_done;
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * bn_alloc);
                 // W accumulator columns starting at chunk column c
@@ -956,7 +962,7 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                             const float *lvB = band.lv + 2 * CAND_MAX * 128;
                             const int32_t *liB = band.li + 2 * CAND_MAX * 128;
                             if (NG == 2) {
-                                if (!mbar_wait(&xfull[q], xph, abort_flag)) goto epi_done;
+                                if (!mbar_wait(&xfull[q], xph, abort_flag, a.wait_ns)) goto epi_done;
                                 const float4 o = xch[q * 32 + lane];
                                 vB = o.x, iB = __float_as_int(o.y), cB = __float_as_int(o.z), dB = o.w;
                             }
@@ -1055,7 +1061,8 @@ template <int FORM>
 __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
     k_tcb(const CUtensorMap *__restrict__ maps, const BProb *__restrict__ probs,
           const int32_t *__restrict__ tile_prob, int ntiles, int stages, uint32_t a_bytes, uint32_t b_bytes,
-          uint32_t stage_bytes, int32_t *__restrict__ flags, int32_t *__restrict__ flag_count, int *status) {
+          uint32_t stage_bytes, int32_t *__restrict__ flags, int32_t *__restrict__ flag_count, int *status,
+          uint64_t wait_ns) {
     constexpr bool X3 = (FORM == F_TF32X3);
     constexpr int BKE = 128 / (FORM == F_BF16 ? 2 : (FORM == F_FP8 ? 1 : 4));
     extern __shared__ uint8_t smem_raw[];
@@ -1103,7 +1110,7 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                 const CUtensorMap *tm = maps + 3 * p;
                 for (int nc = 0; nc < P.n_chunks; ++nc) {
                     for (int kb = 0; kb < P.kb; ++kb) {
-                        if (!mbar_wait(&empty[st], ph ^ 1, abort_flag)) goto producer_done;
+                        if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, wait_ns)) goto producer_done;
                         uint8_t *sb = base + (size_t)st * stage_bytes;
                         mbar_expect_tx(&full[st], P.tx_bytes);
                         tma_load_2d(sb, tm, &full[st], kb * BKE, ltile * BM);
@@ -1122,7 +1129,7 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
         producer_done:
             if (*abort_flag)
                 for (int q = 0; q < stages; ++q)
-                    if (issued & (1u << q)) mbar_drain(&full[q], (last_par >> q) & 1, 500000000ull);
+                    if (issued & (1u << q)) mbar_drain(&full[q], (last_par >> q) & 1, DRAIN_LIMIT_NS);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -1133,11 +1140,11 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
             for (int it = blockIdx.x; it < ntiles && !*abort_flag; it += gridDim.x) {
                 const BProb &P = probs[tile_prob[it]];
                 for (int nc = 0; nc < P.n_chunks; ++nc) {
-                    if (!mbar_wait(&acce[ab], aph ^ 1, abort_flag)) goto mma_done;
+                    if (!mbar_wait(&acce[ab], aph ^ 1, abort_flag, wait_ns)) goto mma_done;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(ab * BN_ALLOC);
                     for (int kb = 0; kb < P.kb; ++kb) {
-                        if (!mbar_wait(X3 ? &tfull[st] : &full[st], ph, abort_flag)) goto mma_done;
+                        if (!mbar_wait(X3 ? &tfull[st] : &full[st], ph, abort_flag, wait_ns)) goto mma_done;
                         tc_fence_after();
                         uint8_t *sb = base + (size_t)st * stage_bytes;
                         const uint64_t adesc = sw128_desc(sb);
@@ -1174,7 +1181,7 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                 }
             }
         mma_done:
-            if (*abort_flag && last_bar) mbar_drain(last_bar, last_parity, 500000000ull);
+            if (*abort_flag && last_bar) mbar_drain(last_bar, last_parity, DRAIN_LIMIT_NS);
         }
     } else if (X3 && warp >= 8) {
         const int t = threadIdx.x - 256;
@@ -1184,7 +1191,7 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
             const BProb &P = probs[tile_prob[it]];
             for (int nc = 0; nc < P.n_chunks; ++nc) {
                 for (int kb = 0; kb < P.kb; ++kb) {
-                    if (!mbar_wait(&full[st], ph, abort_flag)) goto split_done;
+                    if (!mbar_wait(&full[st], ph, abort_flag, wait_ns)) goto split_done;
                     uint8_t *sb = base + (size_t)st * stage_bytes;
                     uint4 *hi = reinterpret_cast<uint4 *>(sb);
                     uint4 *lo = reinterpret_cast<uint4 *>(sb + a_bytes);
@@ -1261,7 +1268,7 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                 band.reset(E2);
             };
             for (int nc = 0; nc < P.n_chunks; ++nc) {
-                if (!mbar_wait(&accf[ab], aph, abort_flag)) goto epi_done;
+                if (!mbar_wait(&accf[ab], aph, abort_flag, wait_ns)) goto epi_done;
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN_ALLOC);
                 auto process = [&](const uint32_t (&r)[16], int c) {
@@ -1405,6 +1412,8 @@ static int launch(gbkm_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const
     if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 smem attribute");
     const int threads = tc_threads<FORM, EPI>();
     const int grid = (int)std::min<int64_t>(c->sm_count, args.m_tiles);
+    args.wait_ns = c->wait_ns ? c->wait_ns : WAIT_LIMIT_NS;
+    args.stall_loads = c->stall_loads;
     kern<<<grid, threads, p.smem, c->stream>>>(A, B, B2, A2 ? *A2 : A, args);
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "tcgen05 kernel launch");
@@ -1611,19 +1620,20 @@ int launch_assign_tc_batched(gbkm_ctx *c, int dtype, const void *maps, const BPr
     const size_t smem = (size_t)stages * stage_bytes + 2048 + BCAND_MAX * 128 * 8;
     const int threads = x3 ? 384 : 256;
     const int grid = (int)std::min<int64_t>(c->sm_count, ntiles);
+    const uint64_t wait_ns = c->wait_ns ? c->wait_ns : WAIT_LIMIT_NS;
     cudaError_t e;
     if (x3) {
         e = cudaFuncSetAttribute(k_tcb<F_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_check(c, e, "batched smem attribute");
         k_tcb<F_TF32X3><<<grid, threads, smem, c->stream>>>(static_cast<const CUtensorMap *>(maps), probs, tile_prob,
                                                             (int)ntiles, stages, a_bytes, b_bytes, stage_bytes,
-                                                            flags, flag_count, c->status);
+                                                            flags, flag_count, c->status, wait_ns);
     } else {
         e = cudaFuncSetAttribute(k_tcb<F_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_check(c, e, "batched smem attribute");
         k_tcb<F_BF16><<<grid, threads, smem, c->stream>>>(static_cast<const CUtensorMap *>(maps), probs, tile_prob,
                                                           (int)ntiles, stages, a_bytes, b_bytes, stage_bytes,
-                                                          flags, flag_count, c->status);
+                                                          flags, flag_count, c->status, wait_ns);
     }
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "batched tcgen05 launch");
