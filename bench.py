@@ -54,8 +54,11 @@ METRICS = {
     "learned": "assign+update GFLOP/s, exact-method flops (learned assignment, 4M x 256, k=16384)",
     "swn": "assign+update GFLOP/s (Lloyd iteration, StructuredWithNoise 50 sets x 5000 points, d=1000, k=50)",
     "svd": "randomised truncated SVD GFLOP/s (one piece 65,536 x 2,048, l=64, s=80)",
+    "bico": "nearest-reference query GFLOP/s (1,000,000 x 128 points against 20,000 features)",
+    "piecy": "per-piece basis + lift GFLOP/s (8 pieces of 65,536 x 2,048, l=64, s=80)",
 }
-DEFAULT_STEPS = {"highdim": 30, "small": 20, "stream": 20, "batch": 5, "learned": 5, "swn": 30, "svd": 20}
+DEFAULT_STEPS = {"highdim": 30, "small": 20, "stream": 20, "batch": 5, "learned": 5, "swn": 30, "svd": 20,
+                 "bico": 10, "piecy": 5}
 SWN_X = 20   # signal dimensions per hidden set (Section 3 leaves the count open)
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -82,6 +85,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the compute-peak probes")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-compare", action="store_true", help="skip the other forms")
     a = ap.parse_args()
@@ -206,6 +210,16 @@ class Env:
         B.load(build_if_missing=True)
         self.ctx = B.Context(self.local)
         self.peaks = load_peaks()
+        # the compute peaks the copy + cuBLAS figures do not cover, probed on this GPU by the
+        # library's own kernels (tcgen05 kind::tf32 / kind::f8f6f4 at the engine's tile shape,
+        # CUDA-core FMA chains); every roofline takes the larger of a probe and its nominal ratio
+        self.peaks["probed"] = {}
+        if not args.no_probe:
+            for u in ("bf16", "tf32", "fp8", "ffma", "fp64"):
+                try:
+                    self.peaks["probed"][u] = self.ctx.probe_peak(u)
+                except Exception:
+                    self.peaks["probed"][u] = None
 
     @property
     def stream(self):
@@ -315,13 +329,35 @@ def bf16_peak(peaks, total_s):
     return peaks["bf16_tflops_sustained"] if total_s > 1.0 else peaks["bf16_tflops"]
 
 
+def _probed(peaks, unit):
+    return (peaks.get("probed") or {}).get(unit) or 0.0
+
+
+def ffma_peak(peaks):
+    """FP32 FMA peak: the larger of the probe and 152 SMs x 128 lanes x 2 x 2.07 GHz."""
+    return max(FFMA_PEAK_TFLOPS, _probed(peaks, "ffma"))
+
+
 def unit_peak(peaks, compute, engine_tc, total_s):
+    """Peak of the unit a form runs on: BF16 the measured cuBLAS figure; FP8 and 3xTF32 (three
+    kind::tf32 MMAs per product) the larger of the probe and the measured BF16 figure times the
+    nominal dense ratio; the SIMT form the FFMA peak."""
     b = bf16_peak(peaks, total_s)
     if compute == "bf16":
         return b
     if compute == "fp8":
-        return b * FP8_OVER_BF16
-    return b * TF32_OVER_BF16 / 3.0 if engine_tc else FFMA_PEAK_TFLOPS
+        return max(b * FP8_OVER_BF16, _probed(peaks, "fp8"))
+    return max(b * TF32_OVER_BF16, _probed(peaks, "tf32")) / 3.0 if engine_tc else ffma_peak(peaks)
+
+
+def peaks_report(peaks):
+    """The denominators in use, with their sources, for the JSON line."""
+    b = peaks["bf16_tflops"]
+    return {"hbm_gbs": peaks["hbm_gbs"], "bf16_tflops": b, "bf16_tflops_sustained": peaks["bf16_tflops_sustained"],
+            "source": peaks["source"], "probed_tflops": peaks.get("probed"),
+            "tf32_nominal_tflops": b * TF32_OVER_BF16, "fp8_nominal_tflops": b * FP8_OVER_BF16,
+            "ffma_nominal_tflops": FFMA_PEAK_TFLOPS,
+            "rule": "tf32 / fp8 / ffma peak = max(probe, nominal); 3xTF32 = tf32 / 3"}
 
 
 def gen_pool(jobs, fn, workers=None):
@@ -377,6 +413,7 @@ def base_line(env, workload, value, ms, steps, warmup, dtype, config):
     return {"metric": METRICS[workload], "value": value, "unit": UNIT, "n_gpus": env.world, "steps": steps,
             "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config,
+            "peaks": peaks_report(env.peaks),
             "kernel_timing": "per-kernel CUDA events on the launching stream, recorded by the library around "
                              "each kernel during a second pass of the same steps right after the timed one (the "
                              "timed pass runs without them: they add a few percent to a short step)"}
@@ -511,7 +548,7 @@ def run_highdim(env, args):
     roof = roofline(peaks, kname, kernel_avg_s(prof, kname), bytes_k, 2.0 * n * k * d,
                     unit_peak(peaks, form, tc, R["total_s"]), R["total_s"],
                     bound=None if form == "bf16" else ("tensor" if tc else "alu"),
-                    note=None if form == "bf16" else ("3xTF32: measured BF16 peak x nominal TF32/BF16 ratio / 3" if tc
+                    note=None if form == "bf16" else ("3xTF32: max(probed kind::tf32, measured BF16 x nominal TF32/BF16 ratio) / 3" if tc
                                                       else "FFMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"),
                     traffic=stored_traffic(f"{kname}/{form}/{n}x{d}_k{k}"))
     # the update's segmented sums: one FP32 read of X in cluster order (+ the permutation)
@@ -525,16 +562,23 @@ def run_highdim(env, args):
     # the roofline object is the dominant kernel's (the longest average launch)
     roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
     p_unit = unit_peak(peaks, form, tc, R["total_s"]) * 1e12
-    # one FP32 read of X is the least any assign + update pass can do; this design reads X twice
-    # (its BF16 copy in the assign, FP32 in the update)
-    B_min = n * d * 4 + k * d * 4 + n * 4 + k * (d + 2) * 8
-    B_design = B_min + n * d * es
-    t_roof = max(B_min / (peaks["hbm_gbs"] * 1e9), 2.0 * n * k * d / p_unit)
-    t_design = max(B_design / (peaks["hbm_gbs"] * 1e9), 2.0 * n * k * d / p_unit)
+    # the algorithmic floor of one iteration: one read of X at the operand dtype, the centers, the
+    # labels and the FP64 clustering features; for comparison, one FP32 read of X (what exact FP32
+    # centroid sums need at least) and this design's traffic (the operand copy in the assign, FP32
+    # in the update)
+    B_alg = n * d * es + k * d * 4 + n * 4 + k * (d + 2) * 8
+    B_f32 = n * d * 4 + k * d * 4 + n * 4 + k * (d + 2) * 8
+    B_design = B_f32 + n * d * es
+    hbm = peaks["hbm_gbs"] * 1e9
+    t_roof = max(B_alg / hbm, 2.0 * n * k * d / p_unit)
+    t_f32 = max(B_f32 / hbm, 2.0 * n * k * d / p_unit)
+    t_design = max(B_design / hbm, 2.0 * n * k * d / p_unit)
     step_roof = {"t_roof_ms": t_roof * 1e3, "frac": t_roof / (ms * 1e-3),
+                 "t_f32_read_ms": t_f32 * 1e3, "frac_f32_read": t_f32 / (ms * 1e-3),
                  "t_design_ms": t_design * 1e3, "frac_design": t_design / (ms * 1e-3),
-                 "note": "T_roof = max(bytes / HBM, flops / unit peak) over the whole iteration with one FP32 "
-                         "read of X; T_design counts the assign's read of the operand copy as well"}
+                 "note": "T_roof = max(bytes / HBM, flops / unit peak) over the whole iteration with one read of "
+                         "X at the operand dtype (the algorithmic floor); T_f32_read with one FP32 read; "
+                         "T_design with this design's two reads (operand copy in the assign, FP32 in the update)"}
 
     # the whole run (per-dataset preparation included): norms, operand copy, k-means++, 30 iterations
     iters = 30
@@ -809,7 +853,7 @@ def run_stream(env_args):
     roof = roofline(peaks, "assign_tc", kernel_avg_s(prof, "assign_tc"), n * r * es + k * r * es + n * 4,
                     2.0 * n * k * r, unit_peak(peaks, pf, True, R["total_s"]), R["total_s"],
                     bound=None if pf == "bf16" else "tensor",
-                    note=None if pf == "bf16" else "3xTF32: measured BF16 peak x nominal TF32/BF16 ratio / 3",
+                    note=None if pf == "bf16" else "3xTF32: max(probed kind::tf32, measured BF16 x nominal TF32/BF16 ratio) / 3",
                     traffic=stored_traffic(f"assign_tc/{pf}/{n}x{r}_k{k}"))
 
     def proj_roof(P, es):
@@ -1242,9 +1286,9 @@ def run_svd(env, args):
     note = "FFMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"
     rooflines = {
         "rsvd_sketch": roofline(env.peaks, "rsvd_sketch", kernel_avg_s(prof, "rsvd_sketch"), n * d * 4 + n * s * 4,
-                                2.0 * n * d * s, FFMA_PEAK_TFLOPS, R["total_s"], bound="alu", note=note),
+                                2.0 * n * d * s, ffma_peak(env.peaks), R["total_s"], bound="alu", note=note),
         "rsvd_rows": roofline(env.peaks, "rsvd_rows", kernel_avg_s(prof, "rsvd_rows"), n * d * 4 + n * s * 4,
-                              2.0 * n * d * s, FFMA_PEAK_TFLOPS, R["total_s"], bound="alu", note=note)}
+                              2.0 * n * d * s, ffma_peak(env.peaks), R["total_s"], bound="alu", note=note)}
     roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
     Vh = V.cpu().numpy().astype(np.float64)
     quality = {"info": int(info.item()) & 0xFF, "jacobi_sweeps": int(info.item()) >> 8,
@@ -1289,6 +1333,268 @@ def run_svd(env, args):
     return line
 
 
+# ---------------------------------------------------------------------------- BICO-style query
+BICO_N, BICO_D, BICO_M = 1_000_000, 128, 20_000
+
+
+def bico_inputs(seed, n=BICO_N):
+    """The features' reference points (a 100-component mixture in R^128, the shape of the paper's
+    Caltech128 SIFT vectors), their members and a batch of n arriving points with integer weights."""
+    from paper_1502_04265_gb300 import synth
+
+    refs, _ = synth.gaussian_mixture(BICO_M, BICO_D, 100, seed=seed)
+    P, f = synth.bico_members(refs, seed)
+    X = synth.bico_batch(refs, n, seed)
+    w = synth.integer_weights(n, seed=seed, max_w=20)
+    return refs, P, f, X, w
+
+
+def bico_snapshot_torch(torch, P, f, m, dev):
+    """The features' (N, S, Q) from their members, FP64 on the device (input preparation)."""
+    Pd = torch.from_numpy(P).to(dev).double()
+    fi = torch.from_numpy(f).to(dev).long()
+    N = torch.zeros(m, dtype=torch.float64, device=dev).index_add_(0, fi, torch.ones_like(fi, dtype=torch.float64))
+    S = torch.zeros((m, P.shape[1]), dtype=torch.float64, device=dev).index_add_(0, fi, Pd)
+    Q = torch.zeros(m, dtype=torch.float64, device=dev).index_add_(0, fi, (Pd * Pd).sum(1))
+    return N, S, Q
+
+
+def oracle_bico_rate(X, w, refs, N, S, Q, T, cpu_seconds):
+    """The FP64 oracle on a bounded sample of the batch: the nearest reference by the C full scan
+    (OpenMP over points), then the insertion rule per point (oracle/bico.py)."""
+    import numpy as np
+
+    import oracle
+    from oracle import bico as OB
+
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    m, d = refs.shape
+    cerr = np.array([OB.cf_error(N[j], S[j], Q[j]) for j in range(m)])
+    Rd = refs.astype(np.float64)
+    rows, t0, done = 256, time.perf_counter(), 0
+    while True:
+        Xs = X[done % X.shape[0]: done % X.shape[0] + rows]
+        j, _, _ = oracle.assign(Xs, Rd)
+        for i in range(Xs.shape[0]):
+            mu = S[j[i]] / N[j[i]]
+            diff = Xs[i].astype(np.float64) - mu
+            OB.insertable(N[j[i]], cerr[j[i]], T, float(diff @ diff), float(w[(done + i) % X.shape[0]]))
+        done += Xs.shape[0]
+        dt = time.perf_counter() - t0
+        if dt >= cpu_seconds:
+            break
+    flops = done * (2.0 * m * d + 3.0 * d)
+    return {"value": flops / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} points of the batch against all {m} features in chunks of {rows}: FP64 C full scan "
+                      f"(OpenMP over points) + the insertion rule per point, {dt:.1f} s"}
+
+
+def run_bico(env, args):
+    import numpy as np
+
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import driver
+
+    refs, P, f, X, w = bico_inputs(env.rank)
+    n, d, m = X.shape[0], BICO_D, BICO_M
+    dev = env.dev
+    N, S, Q = bico_snapshot_torch(torch, P, f, m, dev)
+    cerr = (Q - (S * S).sum(1) / N).cpu().numpy()
+    T = float(np.quantile(cerr, 0.8))
+    Xg, Rg, wg = torch.from_numpy(X).to(dev), torch.from_numpy(refs).to(dev), torch.from_numpy(w).to(dev)
+    ctx = env.ctx
+    xnorm = B.kmeans_row_norms(Xg, ctx=ctx)
+    ref = torch.empty(n, dtype=torch.int32, device=dev)
+    d2 = torch.empty(n, dtype=torch.float64, device=dev)
+    take = torch.empty(n, dtype=torch.float64, device=dev)
+    F = 2.0 * n * m * d + 3.0 * n * d
+
+    def run_form(form, steps, clocks):
+        Xop, Xr = B.kmeans_quantize(Xg, "bf16", ctx=ctx) if form == "bf16" else (None, None)
+
+        def step(i):
+            B.kmeans_bico_query(Xg, Rg, N, S, Q, T, w=wg, Xop=Xop, Xop_scales=Xr, xnorm=xnorm, compute=form,
+                                ref_out=ref, d2_out=d2, take_out=take, ctx=ctx)
+
+        return env.timed(step, steps, args.warmup, clocks=clocks)
+
+    form = primary_form(args.form, d)
+    R = run_form(form, args.steps, True)
+    ms, prof = R["ms"], R["prof"]
+    value = env.world * F / (ms * 1e-3) / 1e9
+    wn = w.astype(np.float64)
+    tk = take.cpu().numpy()
+    outcome = {"whole": int((tk == wn).sum()), "part": int(((tk > 0) & (tk < wn)).sum()), "none": int((tk == 0).sum()),
+               "threshold": T}
+    peaks = env.peaks
+    kname = assign_kernel(prof)
+    es = 2 if form == "bf16" else 4
+    rooflines = {kname: roofline(peaks, kname, kernel_avg_s(prof, kname), n * d * es + m * d * es + n * 4,
+                                 2.0 * n * m * d, unit_peak(peaks, form, kname == "assign_tc", R["total_s"]),
+                                 R["total_s"], bound="tensor",
+                                 note=None if form == "bf16" else
+                                 "3xTF32: max(probed kind::tf32, measured BF16 x nominal TF32/BF16 ratio) / 3"),
+                 "bico_take": roofline(peaks, "bico_take", kernel_avg_s(prof, "bico_take"),
+                                       n * d * 4 + n * (4 + 4 + 8 + 8) + m * d * 8 * 2, 0.0, 1.0, R["total_s"],
+                                       bound="hbm", note="the FP64 distance to the feature's centroid and the "
+                                                         "insertion rule (centroids read from L2 after the first)")}
+    roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
+    forms = {form: {"value": value, "ms_per_step": ms}}
+    if not args.no_compare:
+        other = "bf16" if form == "f32" else "f32"
+        R2 = run_form(other, max(3, args.steps // 2), False)
+        forms[other] = {"value": env.world * F / (R2["ms"] * 1e-3) / 1e9, "ms_per_step": R2["ms"],
+                        "note": "the same query in the other exact form (labels exact in both)"}
+
+    e2e = None
+    if not args.no_e2e:
+        hb = B.HostBlock((n, d))
+        hb.tensor.copy_(torch.from_numpy(X))
+        Xd = torch.empty_like(Xg)
+        take_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        ref_h = torch.empty(n, dtype=torch.int32).pin_memory()
+
+        def e2e_step(i):
+            B.kmeans_ingest(hb.tensor, X_dev=Xd, xnorm=xnorm, quantize=False, device=dev, ctx=ctx)
+            B.kmeans_bico_query(Xd, Rg, N, S, Q, T, w=wg, xnorm=xnorm, compute="f32" if form == "f32" else form,
+                                Xop=None if form == "f32" else B.kmeans_quantize(Xd, "bf16", ctx=ctx)[0],
+                                ref_out=ref, d2_out=d2, take_out=take, ctx=ctx)
+            take_h.copy_(take, non_blocking=True)
+            ref_h.copy_(ref, non_blocking=True)
+
+        E = env.timed(e2e_step, args.e2e_steps or 5, 3, profile=False)
+        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+               "d2h_bytes_per_step": int(n * (8 + 4)), "ms_per_step": E["ms"],
+               "note": "every step: the batch read from a mapped host block (kmeans_ingest), the query, and D2H of "
+                       "every point's reference and insertable count"}
+        del hb
+
+    cpu = None
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_bico_rate(X, w, refs, N.cpu().numpy(), S.cpu().numpy(), Q.cpu().numpy(), T, args.cpu_seconds)
+
+    line = base_line(env, "bico", value, ms, args.steps, args.warmup, form, {
+        "workload": f"a batch of n={n} weighted points (integer weights 1..20) arriving at a BICO-style summary of "
+                    f"m={m} features (200 k for k = 100) in d={d} (the shape of the paper's Caltech128 SIFT "
+                    f"vectors; references from a 100-component mixture, 1..8 members per feature), threshold T = "
+                    f"the 0.8 quantile of the features' errors; seed = rank",
+        "l2": f"inputs larger than L2 (X is {n * d * 4 / 1e6:.0f} MB)",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "rooflines": rooflines, "forms": forms, "outcome": outcome, "cpu_baseline": cpu,
+                 "e2e": e2e, "gpu_launches": R["launches"], "clocks": R["clocks"], "kernels_ms": kernels_ms(prof)})
+    return line
+
+
+# ---------------------------------------------------------------------------- per-piece bases + lift
+PIECY_PIECES, PIECY_ROWS, PIECY_D, PIECY_ELL, PIECY_S = 8, 65536, 2048, 64, 80
+
+
+def piecy_flops(pieces, rows, d, s, ell):
+    """Flops of the method: per piece the randomised SVD, the projection X V and the lift Y V^T."""
+    return pieces * (svd_flops(rows, d, s, ell) + 2.0 * rows * d * ell * 2)
+
+
+def run_piecy(env, args):
+    import numpy as np
+
+    torch, B = env.torch, env.B
+    from paper_1502_04265_gb300 import synth
+
+    P, rows, d, ell, s = PIECY_PIECES, PIECY_ROWS, PIECY_D, PIECY_ELL, PIECY_S
+    n = P * rows
+    Q = synth.orthonormal_basis(d, 64, env.rank)
+    Xg = torch.empty((n, d), dtype=torch.float32, device=env.dev)
+    for q in range(P):
+        Xq, _ = synth.subspace_mixture_chunk(Q, q * rows, rows, 500, env.rank)
+        Xg[q * rows:(q + 1) * rows].copy_(torch.from_numpy(Xq))
+    Om = torch.from_numpy(np.stack([synth.gaussian_sketch(d, s, seed=1000 * env.rank + q) for q in range(P)])).to(env.dev)
+    L = torch.empty_like(Xg)
+    ctx = env.ctx
+
+    def step(i):
+        B.kmeans_piecy_lift(Xg, rows, Om, ell, X_lift=L, ctx=ctx)
+
+    R = env.timed(step, args.steps, args.warmup, clocks=True)
+    ms, prof = R["ms"], R["prof"]
+    F = piecy_flops(P, rows, d, s, ell)
+    value = env.world * F / (ms * 1e-3) / 1e9
+    peaks = env.peaks
+    tf = unit_peak(peaks, "f32", True, R["total_s"])
+    note3 = "3xTF32: max(probed kind::tf32, measured BF16 x nominal TF32/BF16 ratio) / 3"
+    rooflines = {
+        "project": roofline(peaks, "project", kernel_avg_s(prof, "project"), rows * d * 4 + rows * ell * 4 + d * ell * 4,
+                            2.0 * rows * d * ell, tf, R["total_s"], note=note3),
+        "lift": roofline(peaks, "lift", kernel_avg_s(prof, "lift"), rows * d * 4 + rows * ell * 4 + d * ell * 4,
+                         2.0 * rows * d * ell, tf, R["total_s"], note=note3),
+        "rsvd_sketch": roofline(peaks, "rsvd_sketch", kernel_avg_s(prof, "rsvd_sketch"), rows * d * 4 + rows * s * 4,
+                                2.0 * rows * d * s, ffma_peak(peaks), R["total_s"], bound="alu"),
+        "rsvd_rows": roofline(peaks, "rsvd_rows", kernel_avg_s(prof, "rsvd_rows"), rows * d * 4 + rows * s * 4,
+                              2.0 * rows * d * s, ffma_peak(peaks), R["total_s"], bound="alu")}
+    rooflines = {k_: v for k_, v in rooflines.items() if k_ in prof or k_ in ("project", "lift")}
+    roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
+    # the intrinsic dimension the pieces add: the rank of the first two pieces' lifted rows
+    sub = L[: 2 * rows: 64].double().cpu().numpy()
+    sv = np.linalg.svd(sub, compute_uv=False)
+    quality = {"rank_first_two_pieces": int((sv > 1e-4 * sv[0]).sum()), "expected": 2 * ell}
+
+    cpu = None
+    if env.rank == 0 and env.world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_piecy_rate(Xg[:rows].cpu().numpy(), Om[0].cpu().numpy(), ell, args.cpu_seconds)
+
+    e2e = None
+    if not args.no_e2e:
+        hb = B.HostBlock((n, d))
+        hb.tensor.copy_(Xg.cpu())
+        Xd = torch.empty_like(Xg)
+        xn = torch.empty(n, dtype=torch.float32, device=env.dev)
+        Lh = torch.empty((n, d), dtype=torch.float32).pin_memory()
+
+        def e2e_step(i):
+            B.kmeans_ingest(hb.tensor, X_dev=Xd, xnorm=xn, quantize=False, device=env.dev, ctx=ctx)
+            B.kmeans_piecy_lift(Xd, rows, Om, ell, X_lift=L, ctx=ctx)
+            Lh.copy_(L, non_blocking=True)
+
+        E = env.timed(e2e_step, args.e2e_steps or 3, 3, profile=False)
+        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+               "d2h_bytes_per_step": int(n * d * 4), "ms_per_step": E["ms"],
+               "note": "every step: the pieces read from a mapped host block (kmeans_ingest), the per-piece bases "
+                       "and lifts, and D2H of the lifted points"}
+        del hb
+
+    line = base_line(env, "piecy", value, ms, args.steps, args.warmup, "f32", {
+        "workload": f"{P} pieces of {rows} rows of the rank-64-subspace workload (d={d}, 500-component mixture in a "
+                    f"random 64-dim subspace + N(0, 0.1^2) noise, seed = rank), each replaced by its projection onto "
+                    f"its own top l={ell} basis (randomised SVD, s={s}, one Gaussian Omega per piece), d-dim lift",
+        "l2": f"inputs larger than L2 (X is {n * d * 4 / 1e9:.1f} GB)",
+        "parallelism": "replicas" if env.world > 1 else "single GPU"})
+    line.update({"roofline": roof, "rooflines": rooflines, "quality": quality, "cpu_baseline": cpu, "e2e": e2e,
+                 "gpu_launches": R["launches"], "clocks": R["clocks"], "kernels_ms": kernels_ms(prof)})
+    return line
+
+
+def oracle_piecy_rate(A, Om, ell, cpu_seconds):
+    """The FP64 oracle (oracle/piecy.py: numpy QR and SVD as library steps) on row samples of one
+    piece, repeated for about cpu_seconds."""
+    import numpy as np
+
+    from oracle import piecy as OP
+
+    rows = 8192
+    s = Om.shape[1]
+    t0, reps = time.perf_counter(), 0
+    while True:
+        OP.lift_pieces(A[:rows], rows, [Om], ell)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= cpu_seconds:
+            break
+    F = reps * piecy_flops(1, rows, A.shape[1], s, ell)
+    return {"value": F / dt / 1e9, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"{reps} x one piece of {rows} rows x {A.shape[1]} (basis + lift, FP64 numpy with its "
+                      f"threaded BLAS / LAPACK), {dt:.1f} s"}
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The FP64 CPU oracle timed on the host cores, on bounded samples of the same workload."""
@@ -1303,7 +1609,33 @@ def run_reference(args, rank, world):
     cores = oracle.set_threads(os.cpu_count() or 1)
     budget = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
     wl = args.workload
-    if wl == "svd":
+    if wl == "bico":
+        import torch as _t
+
+        refs, P, f, X, w = bico_inputs(0, n=65536)
+        N, S, Q = (a.numpy() for a in bico_snapshot_torch(_t, P, f, BICO_M, "cpu"))
+        T = float(np.quantile(Q - (S * S).sum(1) / N, 0.8))
+        vals, dts = [], []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = oracle_bico_rate(X, w, refs, N, S, Q, T, budget)
+            if i >= args.warmup:
+                vals.append(r["value"])
+                dts.append(time.perf_counter() - t0)
+        val, sample, cores = statistics.median(vals), r["sample"], r["cores"]
+    elif wl == "piecy":
+        Qb = synth.orthonormal_basis(PIECY_D, 64, 0)
+        A, _ = synth.subspace_mixture_chunk(Qb, 0, 8192, 500, 0)
+        Om = synth.gaussian_sketch(PIECY_D, PIECY_S, seed=0)
+        vals, dts = [], []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = oracle_piecy_rate(A, Om, PIECY_ELL, budget)
+            if i >= args.warmup:
+                vals.append(r["value"])
+                dts.append(time.perf_counter() - t0)
+        val, sample, cores = statistics.median(vals), r["sample"], r["cores"]
+    elif wl == "svd":
         n, d, ell, s_ = svd_shape(args)
         A, _ = svd_piece(n, d, 0)
         Om = synth.gaussian_sketch(d, s_, seed=0)
@@ -1399,6 +1731,10 @@ def main():
         line = run_batch((env, args))
     elif args.workload == "svd":
         line = run_svd(env, args)
+    elif args.workload == "bico":
+        line = run_bico(env, args)
+    elif args.workload == "piecy":
+        line = run_piecy(env, args)
     else:
         line = run_learned(env, args)
     if env.rank == 0:

@@ -49,6 +49,15 @@ int gbkm_profile_read(struct gbkm_ctx *ctx, char *buf, int64_t len);
  *
  * gbkm_debug_fail_alloc: the next `count` growths of ctx's workspace fail as a failed
  * cudaMalloc would (GBKM_ENOMEM, nothing queued by that call); 0 clears it.  Host-side only. */
+/* Measured peak of one arithmetic unit on ctx's device, in TFLOP/s (host *tflops_out):
+ *   unit 0: tcgen05.mma kind::f16 (BF16 operands, FP32 accumulation), 1: kind::tf32, 2: kind::f8f6f4
+ *   (E4M3), each at the shape the library's tensor-core kernels issue (one CTA per SM,
+ *   cta_group::1, M = 128, N = 256, operands resident in shared memory);
+ *   3: FP32 FMA on the CUDA cores; 4: FP64 FMA.
+ * A 3xTF32 product costs three kind::tf32 MMAs, so its peak is unit 1's figure / 3.
+ * Runs a few tens of milliseconds of work and synchronises ctx's stream. */
+int gbkm_probe_peak(struct gbkm_ctx *ctx, int32_t unit, double *tflops_out);
+
 int gbkm_debug_set_wait_limit(struct gbkm_ctx *ctx, uint64_t ns);
 int gbkm_debug_stall_loads(struct gbkm_ctx *ctx, int on);
 int gbkm_debug_fail_alloc(struct gbkm_ctx *ctx, int count);

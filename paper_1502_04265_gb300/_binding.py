@@ -62,6 +62,7 @@ _SIGS = {
     "gbkm_debug_set_wait_limit": (ct.c_int, [_vp, ct.c_uint64]),
     "gbkm_debug_fail_alloc": (ct.c_int, [_vp, ct.c_int]),
     "gbkm_debug_stall_loads": (ct.c_int, [_vp, ct.c_int]),
+    "gbkm_probe_peak": (ct.c_int, [_vp, _i32, ct.POINTER(ct.c_double)]),
     "kmeans_row_norms": (ct.c_int, [_vp, _vp, _i64, _i64, _vp]),
     "gbkm_host_alloc": (ct.c_int, [ct.c_size_t, ct.POINTER(ct.c_void_p)]),
     "gbkm_host_free": (ct.c_int, [_vp]),
@@ -236,6 +237,16 @@ class Context:
     def set_wait_limit(self, ns: int):
         """Limit of every bounded device wait of later tensor-core launches (0: the 2 s default)."""
         self.check(load().gbkm_debug_set_wait_limit(self._h, int(ns)))
+
+    PROBE_UNITS = {"bf16": 0, "tf32": 1, "fp8": 2, "ffma": 3, "fp64": 4}
+
+    def probe_peak(self, unit: str) -> float:
+        """Measured TFLOP/s of one arithmetic unit ("bf16", "tf32", "fp8" tensor-core MMAs at the
+        engine's shape; "ffma", "fp64" CUDA-core FMAs).  Synchronises."""
+        self.bind_stream()
+        out = ct.c_double()
+        self.check(load().gbkm_probe_peak(self._h, self.PROBE_UNITS[unit], ct.byref(out)))
+        return float(out.value)
 
     def stall_loads(self, on: bool):
         """Make later tensor-core launches issue no copies, so that their bounded waits run out."""

@@ -1370,6 +1370,11 @@ static bool make_tmap(CUtensorMap *m, CUtensorMapDataType dt, const void *ptr, u
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+__device__ __forceinline__ uint32_t make_idesc_dev(int form) {
+    const uint32_t ab = (form == F_BF16 || form == F_BF16X2) ? 1u : (form == F_FP8 ? 0u : 2u);
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
 static uint32_t make_idesc(int form, int M, int N) {
     uint32_t ab = (form == F_BF16 || form == F_BF16X2) ? 1u : (form == F_FP8 ? 0u : 2u);
     uint32_t d = 0;
@@ -1417,6 +1422,89 @@ static int launch(gbkm_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const
     kern<<<grid, threads, p.smem, c->stream>>>(A, B, B2, A2 ? *A2 : A, args);
     GBKM_LAUNCHED(c);
     return cuda_check(c, cudaGetLastError(), "tcgen05 kernel launch");
+}
+
+// ---------------------------------------------------------------- peak probes (diagnostics)
+// Throughput of the tensor-core shape the engine issues (cta_group::1, M = 128, N = 256, one 32-byte
+// K step: K = 16 BF16, 8 TF32 or 32 E4M3 elements): one CTA per SM, operands a fixed pattern of
+// values in [0.5, 1) in shared memory, one thread issuing `iters` MMAs into two TMEM accumulators,
+// then one commit and a bounded wait.  Each CTA writes its elapsed %globaltimer nanoseconds.
+template <int FORM>
+__global__ void __launch_bounds__(128, 1) k_probe_mma(int iters, uint64_t *__restrict__ t_out, int *status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    constexpr uint32_t A_BYTES = 128 * 128, B_BYTES = 256 * 128;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + A_BYTES + B_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint32_t *w = reinterpret_cast<uint32_t *>(base);
+    for (uint32_t i = threadIdx.x; i < (A_BYTES + B_BYTES) / 4; i += blockDim.x) {
+        const uint32_t h = (i * 2654435761u) ^ (i >> 7);
+        uint32_t v;
+        if (FORM == F_BF16)
+            v = 0x3F003F00u | (h & 0x007F007Fu);        // two BF16 values in [0.5, 1)
+        else if (FORM == F_FP8)
+            v = 0x30303030u | (h & 0x07070707u);        // four E4M3 values in [0.5, 1)
+        else
+            v = 0x3F000000u | (h & 0x007FE000u);        // a TF32 value in [0.5, 1)
+        w[i] = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = make_idesc_dev(FORM);
+        const uint64_t adesc = sw128_desc(base), bdesc = sw128_desc(base + A_BYTES);
+        const uint64_t t0 = globaltimer_ns();
+        for (int it = 0; it < iters; ++it) {
+            const uint64_t off = (uint64_t)((it & 3) * 2);
+            tc_mma<FORM>(tmem + (uint32_t)((it & 1) * 256), adesc + off, bdesc + off, idesc, it >= 2 ? 1u : 0u);
+        }
+        tc_commit(bar);
+        const bool ok = mbar_wait(bar, 0, abort_flag, WAIT_LIMIT_NS);
+        const uint64_t t1 = globaltimer_ns();
+        t_out[blockIdx.x] = t1 - t0;
+        if (!ok) {
+            // the MMAs still read shared memory and write TMEM: let them finish before the exit
+            mbar_drain(bar, 0, DRAIN_LIMIT_NS);
+            status_raise(status, ST_TIMEOUT);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+// CUDA-core FMA throughput: CHAINS independent FMA chains per thread
+template <class T, int CHAINS>
+__global__ void __launch_bounds__(256) k_probe_fma(int iters, T *__restrict__ sink) {
+    T a[CHAINS];
+#pragma unroll
+    for (int i = 0; i < CHAINS; ++i) a[i] = (T)(threadIdx.x + 1) * (T)1e-3 + (T)i;
+    const T m = (T)0.999999, c = (T)1e-6;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < CHAINS; ++i) a[i] = fma(a[i], m, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < CHAINS; ++i) s += a[i];
+    if (s == (T)-1) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;  // never true; keeps the chains live
 }
 
 }  // namespace tc
@@ -1717,3 +1805,80 @@ int launch_gemm_bf16_tc(gbkm_ctx *c, const void *A, const void *B, int64_t M, in
 }
 
 }  // namespace gbkm
+
+// ---------------------------------------------------------------- peak probes: host entry
+extern "C" int gbkm_probe_peak(gbkm_ctx *c, int32_t unit, double *tflops_out) {
+    using namespace gbkm;
+    using namespace gbkm::tc;
+    if (!c || !tflops_out || unit < 0 || unit > 4) return GBKM_EINVAL;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+    int rc = GBKM_OK;
+    const int sms = c->sm_count;
+    void *buf = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&buf, sizeof(uint64_t) * (size_t)sms * 8 * 256);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = set_error(c, GBKM_ENOMEM, "probe: buffers");
+    }
+    double flops = 0.0, secs = 0.0;
+    if (rc == GBKM_OK && unit <= 2) {
+        const int form = unit == 0 ? F_BF16 : (unit == 1 ? F_TF32 : F_FP8);
+        const int kstep = unit == 0 ? 16 : (unit == 1 ? 8 : 32);
+        // about 100k MMAs of 1-2 MFLOP per SM: tens of milliseconds, well inside the wait limit
+        const int iters = 100000;
+        const size_t smem = 1024 + 128 * 128 + 256 * 128 + 64;
+        auto kern = form == F_BF16 ? k_probe_mma<F_BF16> : (form == F_TF32 ? k_probe_mma<F_TF32> : k_probe_mma<F_FP8>);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            kern<<<sms, 128, smem, c->stream>>>(iters / 10, static_cast<uint64_t *>(buf), c->status);  // warm-up
+            kern<<<sms, 128, smem, c->stream>>>(iters, static_cast<uint64_t *>(buf), c->status);
+            GBKM_LAUNCHED(c);
+            GBKM_LAUNCHED(c);
+            e = cudaStreamSynchronize(c->stream);
+        }
+        std::vector<uint64_t> t((size_t)sms);
+        if (e == cudaSuccess) e = cudaMemcpy(t.data(), buf, sizeof(uint64_t) * sms, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            rc = cuda_check(c, e, "probe: tensor-core launch");
+        } else {
+            uint64_t tmax = 0;
+            for (uint64_t v : t) tmax = std::max(tmax, v);
+            flops = 2.0 * 128 * 256 * kstep * (double)iters * sms;
+            secs = (double)tmax * 1e-9;
+        }
+    } else if (rc == GBKM_OK) {
+        const int blocks = sms * 8, iters = unit == 3 ? 20000 : 2000;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            // the first pass warms up, the second is timed
+            cudaEventRecord(e0, c->stream);
+            if (unit == 3)
+                k_probe_fma<float, 16><<<blocks, 256, 0, c->stream>>>(iters, static_cast<float *>(buf));
+            else
+                k_probe_fma<double, 8><<<blocks, 256, 0, c->stream>>>(iters, static_cast<double *>(buf));
+            GBKM_LAUNCHED(c);
+            cudaEventRecord(e1, c->stream);
+            e = cudaEventSynchronize(e1);
+        }
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_check(c, e, "probe: FMA launch");
+        } else {
+            flops = 2.0 * (unit == 3 ? 16 : 8) * (double)iters * blocks * 256;
+            secs = ms * 1e-3;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (buf) cudaFree(buf);
+    if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+    if (rc != GBKM_OK) return rc;
+    if (!(secs > 0.0)) return set_error(c, GBKM_ECUDA, "probe: no elapsed time");
+    *tflops_out = flops / secs * 1e-12;
+    return GBKM_OK;
+}
