@@ -232,10 +232,11 @@ int kmeans_seed_pp(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const fl
  * then take the direct recheck, scanning all k if needed).  Every label equals the
  * exact nearest center except where two centers' distances agree to within the
  * direct recheck's error ((ceil(d/128) + 10) 2^-24 relative).
- *   Xop_scales: per-row scales of an FP8 Xop (n x ceil(d/128)); for a BF16 Xop with
- *     one-term centers, optionally the rows' rounding residuals from kmeans_quantize
- *     (n FP32): the band then uses them and the centers' largest residual in place
- *     of the worst case u ||x||, u ||c|| (the bound stays certified); else NULL.
+ *   Xop_scales: per-row scales of an FP8 Xop (n x ceil(d/128)); for a BF16 Xop,
+ *     optionally the rows' rounding residuals from kmeans_quantize (n FP32): the band
+ *     then uses them in place of the worst case u ||x|| (and, with one-term centers,
+ *     the centers' largest residual in place of u ||c||; the bound stays certified);
+ *     else NULL.
  *   X: n x d FP32 (always required: recheck and bounds).
  *   xnorm: ||x_i||^2 FP32 from kmeans_row_norms, or NULL (then computed here).
  *   C: k x d FP32.  labels: n int32.  min_d2: n FP32 or NULL, the squared

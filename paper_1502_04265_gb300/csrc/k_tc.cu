@@ -648,7 +648,10 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
             {
                 const float xr = sqrtf(fmaxf(xn, 0.f)) * (1.f + 1.0e-6f);
                 if (a.pair_a > 0.f) {
-                    band.reset(a.pair_rel * xr * cm + a.pair_abs * cm * cm, a.pair_a * xr,
+                    // |2 dx.(c_j - c_0)| <= 2 ||dx|| (D_j + D_0): with the row's actual rounding residual
+                    // ||dx|| (rounded up) when the quantiser gave it, else its bound u ||x||
+                    const float A = a.xresid ? 2.f * (valid ? a.xresid[row] : 0.f) * (1.f + 1.0e-6f) : a.pair_a * xr;
+                    band.reset(a.pair_rel * xr * cm + a.pair_abs * cm * cm, A,
                                xn * (1.f + 2.4e-7f) + a.single_rel * xr * cm + a.single_abs * cm * cm);
                 } else if (FORM == F_BF16 && a.xresid) {
                     // with dx = x~ - x and e_j = c~_j - c_j: |x~.c~_j - x.c_j| <= ||dx|| (cmax + emax) +
@@ -1556,6 +1559,9 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
         a.err_u2 = (float)(2.0 * ldexp(1.0, -24) * (1 + 1e-6));
     }
     if (form == F_BF16X2) {
+        // the rows' rounding residuals ||x~ - x|| (kmeans_quantize's side data), when given, replace
+        // u ||x|| in the pair term of the band
+        if (Xscales) a.xresid = Xscales;
         // |x~ - x| <= u |x| with u = 2^-8 (BF16, nearest even), |c^ - c| <= u^2 |c| for hi + lo, FP32
         // accumulation of 2d products bounded by 2d 2^-22 relative (4x the textbook 2d 2^-24)
         const double u = ldexp(1.0, -8), g = 2.0 * (double)d * ldexp(1.0, -22) * (1 + u) * (1 + u);
