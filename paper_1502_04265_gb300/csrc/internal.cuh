@@ -280,6 +280,13 @@ int launch_project_tc(gbkm_ctx *c, int dtype, const void *X, int64_t n, int64_t 
                       const float *V, int64_t r, float *Y);
 // X_lift = Y V^T on the tensor cores (3xTF32); d % 16 == 0, r % 4 == 0, Y and X_lift 16-byte aligned
 bool tc_lift_supported(int64_t d, int64_t r);
+// the randomised SVD's two passes over a piece on the tensor cores (3xTF32)
+int launch_sketch_tc(gbkm_ctx *c, const float *A, const float *w, int64_t n, int64_t d, const float *Omega, int64_t s,
+                     float *omt, float *Y);
+bool tc_rows_supported(int64_t d, int64_t s);
+void tc_rows_shape(int64_t n, int64_t d, int sm_count, int *splits, int *kb_per_split);
+int launch_rows_tc(gbkm_ctx *c, const float *A, const float *w, int64_t n, int64_t d, const float *Q, int64_t s,
+                   float *qt, float *part, float *Bt);
 int launch_lift_tc(gbkm_ctx *c, const float *Y, int64_t n, int64_t r, const float *V, int64_t d, float *X_lift);
 // ---------------------------------------------------------------- batched problems
 // device-side descriptor of one problem of a batched run (all pointers are device pointers)

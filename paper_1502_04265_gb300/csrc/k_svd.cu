@@ -4,11 +4,13 @@
 // randomised scheme of Halko, Martinsson and Tropp that the paper adopts: the columns of A' are
 // reduced by a random d x s matrix Omega (s = l + oversampling), the rows by an orthonormal basis
 // of the result, and only the s x d matrix left over is decomposed.  All on the context's stream:
-//   1. k_gemm_rows   Y = A' Omega (n x s)                                  first read of A
+//   1. Y = A' Omega (n x s): the tensor cores' 3xTF32 store GEMM (k_tc), or k_gemm_rows on the CUDA
+//      cores where the shape does not allow TMA tiles                       first read of A
 //   2. CholeskyQR2   k_gram (Y^T Y, FP32 blocks of 8 rows added in double-float), k_chol (FP64
 //                    Cholesky with a small diagonal shift, R^-1), Y <- Y R^-1; twice -> Q
-//   3. k_gemm_tn     Bt = A'^T Q (d x s), split over row chunks, chunks added in fixed order
-//                                                                           second read of A
+//   3. Bt = A'^T Q (d x s): k_tn_tc on the tensor cores (A's tiles transposed in shared memory,
+//      3xTF32, split over row ranges, the splits added in fixed order), or k_gemm_tn on the CUDA
+//      cores, split over row chunks added in fixed order                   second read of A
 //   4. k_gram, k_chol  R_b with R_b^T R_b = Bt^T Bt, so Bt = Q_b R_b
 //   5. k_jacobi      one-sided Jacobi on R_b^T (one CTA): R_b^T J = W Sigma, singular values in
 //                    decreasing order, T = R_b^-1 J (first l columns of the order)
@@ -570,12 +572,15 @@ __global__ void __launch_bounds__(256) k_sign(float *__restrict__ V, int64_t d, 
 
 // ---------------------------------------------------------------- orchestration
 struct SvdPlan {
-    size_t o_y, o_q, o_gpart, o_g, o_r, o_rinv, o_rinv32, o_tpart, o_bt, o_t, o_sig, o_status, bytes;
+    size_t o_y, o_q, o_gpart, o_g, o_r, o_rinv, o_rinv32, o_tpart, o_bt, o_t, o_sig, o_status, o_omt, o_qt, o_rpart,
+        bytes;
+    bool tc;  // the two passes over the piece on the tensor cores
 };
 
-static SvdPlan svd_plan(int64_t n, int64_t d, int64_t s, int64_t ell) {
+static SvdPlan svd_plan(int64_t n, int64_t d, int64_t s, int64_t ell, int sm_count, bool tc) {
     SvdPlan P;
     WsPlan p;
+    P.tc = tc;
     const int nb = (int)ceil_div(s, (int64_t)GM_B);
     const int64_t gchunks = std::max<int64_t>(gram_chunks(n), gram_chunks(d));
     P.o_y = p.take<float>(n * s);
@@ -590,13 +595,20 @@ static SvdPlan svd_plan(int64_t n, int64_t d, int64_t s, int64_t ell) {
     P.o_t = p.take<float>(s * ell);
     P.o_sig = p.take<float>(ell);
     P.o_status = p.take<int>(1);
+    int splits = 1, kbs = 1;
+    if (tc) tc_rows_shape(n, d, sm_count, &splits, &kbs);
+    P.o_omt = p.take<float>(tc ? 2 * s * d : 0);
+    P.o_qt = p.take<float>(tc ? 2 * s * (ceil_div(n, (int64_t)4) * 4) : 0);
+    P.o_rpart = p.take<float>(tc ? (int64_t)splits * d * s : 0);
     P.bytes = p.off;
     return P;
 }
 
 int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w, const float *Omega, int64_t s,
               int64_t ell, float *V, float *sigma, int32_t *info) {
-    const SvdPlan P = svd_plan(n, d, s, ell);
+    // the passes over the piece run on the tensor cores (3xTF32) when the shapes allow TMA tiles
+    const bool tc = tc_rows_supported(d, s) && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    const SvdPlan P = svd_plan(n, d, s, ell, c->sm_count, tc);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, P.bytes, &rc);
     if (!ws) return rc;
@@ -614,7 +626,8 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
 
     // 1. Y = A' Omega
     prof_begin(c, "rsvd_sketch");
-    rc = launch_gemm_rows(c, A, Omega, w, n, d, s, Y);
+    rc = tc ? launch_sketch_tc(c, A, w, n, d, Omega, s, ws_at<float>(ws, P.o_omt), Y)
+            : launch_gemm_rows(c, A, Omega, w, n, d, s, Y);
     prof_end(c);
     if (rc != GBKM_OK) return rc;
     // 2. CholeskyQR2: Y -> Q (via Q) -> Y
@@ -630,7 +643,8 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
     prof_end(c);
     // 3. Bt = A'^T Q
     prof_begin(c, "rsvd_rows");
-    rc = launch_gemm_tn(c, A, Y, w, n, d, s, tpart, Bt);
+    rc = tc ? launch_rows_tc(c, A, w, n, d, Y, s, ws_at<float>(ws, P.o_qt), ws_at<float>(ws, P.o_rpart), Bt)
+            : launch_gemm_tn(c, A, Y, w, n, d, s, tpart, Bt);
     prof_end(c);
     if (rc != GBKM_OK) return rc;
     // 4. R_b from the Gram of Bt

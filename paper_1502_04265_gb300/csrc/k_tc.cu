@@ -68,6 +68,7 @@ struct Args {
     float *Y;
     int64_t ldy;
     const float *bias;
+    const float *row_w;  // store epilogue: every output row scaled by sqrt(max(row_w[row], 0)) (or null)
     int act;       // 0: none, 1: GELU (erf form)
     int out_bf16;
     float *Ypre;
@@ -761,6 +762,11 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                                 float v[16];
 #pragma unroll
                                 for (int g = 0; g < 16; ++g) v[g] = __uint_as_float(r[16 * h + g]);
+                                if (a.row_w) {
+                                    const float sc = sqrtf(fmaxf(a.row_w[row], 0.f));
+#pragma unroll
+                                    for (int g = 0; g < 16; ++g) v[g] *= sc;
+                                }
                                 if (a.bias) {
 #pragma unroll
                                     for (int g = 0; g < 4; ++g) {
@@ -1336,6 +1342,228 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
     }
 }
 
+// ---------------------------------------------------------------- transposed contraction over rows
+// part[ks] (d x s, FP32) = sum over the rows r of split ks of (sqrt(w_r) A[r, :])^T Q[r, :]: the
+// randomised SVD's row reduction Bt = A'^T Q, a contraction over the n rows of A (row-major n x d),
+// so A is the MN-major operand.  The tile is transposed in shared memory instead: the producer
+// loads a plain 32-row x 128-column box of A (no swizzle), warps 4-7 read it column-wise, scale each
+// row by sqrt(w_r), split the values into TF32 hi and lo and write them as the K-major, 128-byte
+// swizzled A operand (M = 128 columns of d, K = 32 rows of n); Q^T's hi / lo (s x n, K-major) are the
+// B operand.  3xTF32 as in k_tc (lo.hi + hi.lo + hi.hi), FP32 accumulation in TMEM over one split,
+// the splits then added in fixed order.  Units (split ks, column tile mt) go to CTAs round-robin;
+// two accumulators let the epilogue (warps 8-11, one TMEM lane quarter each) overlap the next unit.
+struct TnArgs {
+    int64_t n, d, s;
+    int mt_count, splits, kb_per_split, stages;
+    uint32_t raw_bytes, a_bytes, b_bytes, stage_bytes, tx_bytes, idesc;
+    const float *w;
+    float *part;
+    int *status;
+    uint64_t wait_ns;
+};
+
+__global__ void __launch_bounds__(384, 1)
+    k_tn_tc(const __grid_constant__ CUtensorMap tmRaw, const __grid_constant__ CUtensorMap tmQh,
+            const __grid_constant__ CUtensorMap tmQl, const TnArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + (size_t)a.stages * a.stage_bytes);
+    uint64_t *full = bars, *tfull = bars + MAX_STAGES, *empty = bars + 2 * MAX_STAGES;
+    uint64_t *accf = bars + 3 * MAX_STAGES, *acce = accf + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int units = a.mt_count * a.splits;
+    if ((int)blockIdx.x >= units) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // stage layout: [A hi | A lo | Q^T hi | Q^T lo | raw A box]
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < a.stages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&tfull[q], 4);
+            mbar_init(&empty[q], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int64_t rows_per_split = (int64_t)a.kb_per_split * 32;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0, issued = 0, last_par = 0;
+            for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+                const int ks = u / a.mt_count, mt = u % a.mt_count;
+                const int64_t r0 = (int64_t)ks * rows_per_split;
+                for (int kb = 0; kb < a.kb_per_split; ++kb) {
+                    const int64_t rr = r0 + (int64_t)kb * 32;
+                    if (rr >= a.n) break;
+                    if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, a.wait_ns)) goto producer_done;
+                    uint8_t *sb = base + (size_t)st * a.stage_bytes;
+                    mbar_expect_tx(&full[st], a.tx_bytes);
+                    tma_load_2d(sb + 2 * a.a_bytes + 2 * a.b_bytes, &tmRaw, &full[st], mt * 128, (int32_t)rr);
+                    tma_load_2d(sb + 2 * a.a_bytes, &tmQh, &full[st], (int32_t)rr, 0);
+                    tma_load_2d(sb + 2 * a.a_bytes + a.b_bytes, &tmQl, &full[st], (int32_t)rr, 0);
+                    issued |= 1u << st;
+                    last_par = (last_par & ~(1u << st)) | (ph << st);
+                    if (++st == a.stages) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+        producer_done:
+            if (*abort_flag)
+                for (int q = 0; q < a.stages; ++q)
+                    if (issued & (1u << q)) mbar_drain(&full[q], (last_par >> q) & 1, DRAIN_LIMIT_NS);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int st = 0, ab = 0;
+            uint32_t ph = 0, aph = 0;
+            uint64_t *last_bar = nullptr;
+            uint32_t last_parity = 0;
+            for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+                const int ks = u / a.mt_count;
+                const int64_t r0 = (int64_t)ks * rows_per_split;
+                if (!mbar_wait(&acce[ab], aph ^ 1, abort_flag, a.wait_ns)) goto mma_done;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(ab * 128);
+                for (int kb = 0; kb < a.kb_per_split; ++kb) {
+                    if (r0 + (int64_t)kb * 32 >= a.n) break;
+                    if (!mbar_wait(&tfull[st], ph, abort_flag, a.wait_ns)) goto mma_done;
+                    tc_fence_after();
+                    uint8_t *sb = base + (size_t)st * a.stage_bytes;
+                    const uint64_t ahi = sw128_desc(sb), alo = sw128_desc(sb + a.a_bytes);
+                    const uint64_t bhi = sw128_desc(sb + 2 * a.a_bytes), blo = sw128_desc(sb + 2 * a.a_bytes + a.b_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                        const uint64_t off = (uint64_t)(kk * 2);
+                        tc_mma<F_TF32X3>(d_tmem, alo + off, bhi + off, a.idesc, acc);
+                        tc_mma<F_TF32X3>(d_tmem, ahi + off, blo + off, a.idesc, 1u);
+                        tc_mma<F_TF32X3>(d_tmem, ahi + off, bhi + off, a.idesc, 1u);
+                    }
+                    tc_commit(&empty[st]);
+                    last_bar = &empty[st];
+                    last_parity = ph;
+                    if (++st == a.stages) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                }
+                tc_commit(&accf[ab]);
+                last_bar = &accf[ab];
+                last_parity = aph;
+                if (++ab == 2) {
+                    ab = 0;
+                    aph ^= 1;
+                }
+            }
+        mma_done:
+            if (*abort_flag && last_bar) mbar_drain(last_bar, last_parity, DRAIN_LIMIT_NS);
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // transposing split: thread t takes column mt * 128 + t of the box (one output row of the
+        // K-major operand); rows of the box beyond n were zero-filled by the copy
+        const int t = threadIdx.x - 128;
+        int st = 0;
+        uint32_t ph = 0;
+        for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+            const int ks = u / a.mt_count;
+            const int64_t r0 = (int64_t)ks * rows_per_split;
+            for (int kb = 0; kb < a.kb_per_split; ++kb) {
+                const int64_t rr = r0 + (int64_t)kb * 32;
+                if (rr >= a.n) break;
+                if (!mbar_wait(&full[st], ph, abort_flag, a.wait_ns)) goto split_done;
+                uint8_t *sb = base + (size_t)st * a.stage_bytes;
+                const float *raw = reinterpret_cast<const float *>(sb + 2 * a.a_bytes + 2 * a.b_bytes);
+                uint8_t *hi_row = sb + (t >> 3) * 1024 + (t & 7) * 128;
+                uint8_t *lo_row = hi_row + a.a_bytes;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float h4[4], l4[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int r = 4 * c + e;
+                        float v = raw[r * 128 + t];
+                        if (a.w) {
+                            const int64_t gr = rr + r;
+                            v *= gr < a.n ? sqrtf(fmaxf(__ldg(a.w + gr), 0.f)) : 0.f;
+                        }
+                        const float h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+                        h4[e] = h;
+                        l4[e] = __uint_as_float(__float_as_uint(__fsub_rn(v, h)) & 0xffffe000u);
+                    }
+                    const int pc = (c ^ (t & 7)) * 16;
+                    *reinterpret_cast<float4 *>(hi_row + pc) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                    *reinterpret_cast<float4 *>(lo_row + pc) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tfull[st]);
+                if (++st == a.stages) {
+                    st = 0;
+                    ph ^= 1;
+                }
+            }
+        }
+    split_done:;
+    } else if (warp >= 8) {
+        // epilogue: TMEM lane = column j of d; s accumulator columns per lane
+        const int q = warp & 3;
+        int ab = 0;
+        uint32_t aph = 0;
+        for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+            const int ks = u / a.mt_count, mt = u % a.mt_count;
+            if (!mbar_wait(&accf[ab], aph, abort_flag, a.wait_ns)) goto epi_done;
+            tc_fence_after();
+            const int64_t j = (int64_t)mt * 128 + q * 32 + lane;
+            const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * 128);
+            float *dst = a.part + ((int64_t)ks * a.d + j) * a.s;
+            for (int c = 0; c < (int)a.s; c += 16) {
+                uint32_t r[16];
+                tmem_ld16(tb + (uint32_t)c, r);
+                tmem_wait_ld(r);
+                if (j < a.d) {
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+                        reinterpret_cast<float4 *>(dst + c)[g] =
+                            make_float4(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]),
+                                        __uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[ab]);
+            if (++ab == 2) {
+                ab = 0;
+                aph ^= 1;
+            }
+        }
+    epi_done:;
+    }
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) status_raise(a.status, ST_TIMEOUT);
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(256u) : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -1376,6 +1604,21 @@ static bool make_tmap(CUtensorMap *m, CUtensorMapDataType dt, const void *ptr, u
 __device__ __forceinline__ uint32_t make_idesc_dev(int form) {
     const uint32_t ab = (form == F_BF16 || form == F_BF16X2) ? 1u : (form == F_FP8 ? 0u : 2u);
     return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// 2D FP32 tensor [outer x inner] with a row stride of stride_bytes (a multiple of 16), an arbitrary
+// box and swizzle; out-of-range elements read as zero
+static bool make_tmap_f32(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t outer, uint64_t stride_bytes,
+                          uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {stride_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static uint32_t make_idesc(int form, int M, int N) {
@@ -1616,7 +1859,7 @@ bool tc_project_supported(int dtype, int64_t d, int64_t r) {
 
 // a store-epilogue GEMM Out[M x N] = A[M x K] B^T (B: N x K) on the engine, operands already in place
 static int launch_store_gemm(gbkm_ctx *c, int form, const void *A, const void *B, const void *B_lo, int64_t M,
-                             int64_t N, int64_t K, float *Out) {
+                             int64_t N, int64_t K, float *Out, const float *row_w = nullptr) {
     using namespace tc;
     const uint32_t es = (form == F_BF16) ? 2 : 4;
     const Plan p = plan(form, K, N);
@@ -1635,9 +1878,20 @@ static int launch_store_gemm(gbkm_ctx *c, int form, const void *A, const void *B
     a.a_bytes = p.a_bytes, a.b_bytes = p.b_bytes, a.stage_bytes = p.stage_bytes, a.tx_bytes = p.tx_bytes;
     a.idesc = make_idesc(form, BM, p.bn);
     a.Y = Out, a.ldy = N;
+    a.row_w = row_w;
     a.status = c->status;
     if (form == F_BF16) return launch<F_BF16, E_STORE>(c, tA, tB, tB2, a, p);
     return launch<F_TF32X3, E_STORE>(c, tA, tB, tB2, a, p);
+}
+
+// The randomised SVD's sketch Y = diag(sqrt(w)) A Omega on the tensor cores (3xTF32): A (n x d) is
+// the K-major A operand, Omega^T (s x d, split into TF32 hi / lo by k_vt into omt, 2 s d floats of
+// workspace) the B operand; the row weights enter in the store epilogue.  d % 4 == 0, s % 16 == 0.
+int launch_sketch_tc(gbkm_ctx *c, const float *A, const float *w, int64_t n, int64_t d, const float *Omega, int64_t s,
+                     float *omt, float *Y) {
+    k_vt<<<(unsigned)ceil_div(s * d, 256), 256, 0, c->stream>>>(Omega, d, s, GBKM_F32, omt, omt + s * d);
+    GBKM_LAUNCHED(c);
+    return launch_store_gemm(c, tc::F_TF32X3, A, omt, omt + s * d, n, s, d, Y, w);
 }
 
 // Y = X V: BF16 X against BF16 V, or FP32 X in the 3xTF32 form (the staged X tile split into TF32 hi
@@ -1888,3 +2142,97 @@ extern "C" int gbkm_probe_peak(gbkm_ctx *c, int32_t unit, double *tflops_out) {
     *tflops_out = flops / secs * 1e-12;
     return GBKM_OK;
 }
+
+// ---------------------------------------------------------------- the SVD's row reduction on the tensor cores
+namespace gbkm {
+
+// Q (n x s, row-major) -> Q^T split into TF32 hi / lo, s x ld each (ld >= n, columns n..ld-1 zero)
+__global__ void __launch_bounds__(256) k_qt_split(const float *__restrict__ Q, int64_t n, int64_t s, int64_t ld,
+                                                  float *__restrict__ hi, float *__restrict__ lo) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t r = r0 + i, c = c0 + tx;
+        tile[i][tx] = (r < n && c < s) ? Q[r * s + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t c = c0 + i, r = r0 + tx;
+        if (c < s && r < ld) {
+            const float v = tile[tx][i];
+            const float h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+            hi[c * ld + r] = h;
+            lo[c * ld + r] = __uint_as_float(__float_as_uint(__fsub_rn(v, h)) & 0xffffe000u);
+        }
+    }
+}
+
+// Bt = the splits' partials added in split order, in double-float
+__global__ void __launch_bounds__(256) k_tn_reduce_f32(const float *__restrict__ part, int64_t ds, int splits,
+                                                       float *__restrict__ Bt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ds) return;
+    DF acc;
+    for (int g = 0; g < splits; ++g) acc.add(part[(int64_t)g * ds + e]);
+    Bt[e] = (float)acc.value();
+}
+
+bool tc_rows_supported(int64_t d, int64_t s) {
+    return tc::encode_fn() && d % 4 == 0 && s % 16 == 0 && s >= 16 && s <= 128;
+}
+
+// splits of the n rows: about four units per SM, 32-row K blocks
+void tc_rows_shape(int64_t n, int64_t d, int sm_count, int *splits, int *kb_per_split) {
+    const int64_t mt = ceil_div(d, (int64_t)128);
+    int64_t want = std::max<int64_t>(1, ceil_div(4 * (int64_t)sm_count, mt));
+    const int64_t kb_total = ceil_div(n, (int64_t)32);
+    const int64_t kbs = std::max<int64_t>(1, ceil_div(kb_total, want));
+    *kb_per_split = (int)kbs;
+    *splits = (int)ceil_div(kb_total, kbs);
+}
+
+// Bt (d x s) = (diag(sqrt(w)) A)^T Q on the tensor cores.  qt: 2 s ld floats (ld = n rounded up to 4),
+// part: splits x d x s floats, from tc_rows_shape.
+int launch_rows_tc(gbkm_ctx *c, const float *A, const float *w, int64_t n, int64_t d, const float *Q, int64_t s,
+                   float *qt, float *part, float *Bt) {
+    using namespace tc;
+    int splits = 0, kbs = 0;
+    tc_rows_shape(n, d, c->sm_count, &splits, &kbs);
+    const int64_t ld = ceil_div(n, (int64_t)4) * 4;
+    float *qhi = qt, *qlo = qt + s * ld;
+    k_qt_split<<<dim3((unsigned)ceil_div(ld, (int64_t)32), (unsigned)ceil_div(s, (int64_t)32)), 256, 0, c->stream>>>(
+        Q, n, s, ld, qhi, qlo);
+    GBKM_LAUNCHED(c);
+    CUtensorMap tRaw, tQh, tQl;
+    if (!make_tmap_f32(&tRaw, A, (uint64_t)d, (uint64_t)n, (uint64_t)d * 4, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+        !make_tmap_f32(&tQh, qhi, (uint64_t)n, (uint64_t)s, (uint64_t)ld * 4, 32, (uint32_t)s, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_tmap_f32(&tQl, qlo, (uint64_t)n, (uint64_t)s, (uint64_t)ld * 4, 32, (uint32_t)s, CU_TENSOR_MAP_SWIZZLE_128B))
+        return set_error(c, GBKM_ECUDA, "cuTensorMapEncodeTiled failed for the row reduction");
+    TnArgs a{};
+    a.n = n, a.d = d, a.s = s;
+    a.mt_count = (int)ceil_div(d, (int64_t)128);
+    a.splits = splits, a.kb_per_split = kbs;
+    a.a_bytes = 128 * 128;
+    a.b_bytes = (uint32_t)s * 128;
+    a.raw_bytes = 32 * 128 * 4;
+    a.stage_bytes = 2 * a.a_bytes + 2 * a.b_bytes + a.raw_bytes;
+    a.tx_bytes = a.raw_bytes + 2 * a.b_bytes;
+    a.stages = (int)std::min<int64_t>(MAX_STAGES, (MAX_DYN_SMEM - 2048) / a.stage_bytes);
+    a.idesc = make_idesc(F_TF32X3, 128, (int)s);
+    a.w = w;
+    a.part = part;
+    a.status = c->status;
+    a.wait_ns = c->wait_ns ? c->wait_ns : WAIT_LIMIT_NS;
+    const size_t smem = (size_t)a.stages * a.stage_bytes + 2048;
+    cudaError_t e = cudaFuncSetAttribute(k_tn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "row reduction smem attribute");
+    const int units = a.mt_count * splits;
+    k_tn_tc<<<(unsigned)std::min<int64_t>(c->sm_count, units), 384, smem, c->stream>>>(tRaw, tQh, tQl, a);
+    GBKM_LAUNCHED(c);
+    k_tn_reduce_f32<<<(unsigned)ceil_div(d * s, (int64_t)256), 256, 0, c->stream>>>(part, d * s, splits, Bt);
+    GBKM_LAUNCHED(c);
+    return cuda_check(c, cudaGetLastError(), "row reduction launch");
+}
+
+}  // namespace gbkm
