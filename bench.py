@@ -1269,6 +1269,20 @@ def oracle_svd_rate(A, Om, ell, cpu_seconds):
                       f"{dt:.1f} s"}
 
 
+def svd_rooflines(peaks, prof, n, d, s, total_s):
+    """The SVD's two passes over the piece (sketch Y = A' Omega, row reduction Bt = A'^T Q): 3xTF32
+    GEMMs on the tensor cores, one read of the piece each; the roofline takes the larger of the HBM
+    time and the 3xTF32 time."""
+    note = ("3xTF32 on tcgen05; peak max(probed kind::tf32, measured BF16 x nominal TF32/BF16 ratio) / 3; "
+            "bound = the larger of the HBM and tensor times")
+    out = {}
+    for name in ("rsvd_sketch", "rsvd_rows"):
+        if name in prof:
+            out[name] = roofline(peaks, name, kernel_avg_s(prof, name), n * d * 4 + n * s * 4, 2.0 * n * d * s,
+                                 unit_peak(peaks, "f32", True, total_s), total_s, note=note)
+    return out
+
+
 def run_svd(env, args):
     import numpy as np
 
@@ -1291,12 +1305,7 @@ def run_svd(env, args):
     ms, prof = R["ms"], R["prof"]
     F = svd_flops(n, d, s, ell)
     value = env.world * F / (ms * 1e-3) / 1e9
-    note = "FFMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"
-    rooflines = {
-        "rsvd_sketch": roofline(env.peaks, "rsvd_sketch", kernel_avg_s(prof, "rsvd_sketch"), n * d * 4 + n * s * 4,
-                                2.0 * n * d * s, ffma_peak(env.peaks), R["total_s"], bound="alu", note=note),
-        "rsvd_rows": roofline(env.peaks, "rsvd_rows", kernel_avg_s(prof, "rsvd_rows"), n * d * 4 + n * s * 4,
-                              2.0 * n * d * s, ffma_peak(env.peaks), R["total_s"], bound="alu", note=note)}
+    rooflines = svd_rooflines(env.peaks, prof, n, d, s, R["total_s"])
     roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
     Vh = V.cpu().numpy().astype(np.float64)
     quality = {"info": int(info.item()) & 0xFF, "jacobi_sweeps": int(info.item()) >> 8,
@@ -1535,10 +1544,7 @@ def run_piecy(env, args):
                             2.0 * rows * d * ell, tf, R["total_s"], note=note3),
         "lift": roofline(peaks, "lift", kernel_avg_s(prof, "lift"), rows * d * 4 + rows * ell * 4 + d * ell * 4,
                          2.0 * rows * d * ell, tf, R["total_s"], note=note3),
-        "rsvd_sketch": roofline(peaks, "rsvd_sketch", kernel_avg_s(prof, "rsvd_sketch"), rows * d * 4 + rows * s * 4,
-                                2.0 * rows * d * s, ffma_peak(peaks), R["total_s"], bound="alu"),
-        "rsvd_rows": roofline(peaks, "rsvd_rows", kernel_avg_s(prof, "rsvd_rows"), rows * d * 4 + rows * s * 4,
-                              2.0 * rows * d * s, ffma_peak(peaks), R["total_s"], bound="alu")}
+        **svd_rooflines(peaks, prof, rows, d, s, R["total_s"])}
     rooflines = {k_: v for k_, v in rooflines.items() if k_ in prof or k_ in ("project", "lift")}
     roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
     # the intrinsic dimension the pieces add: the rank of the first two pieces' lifted rows

@@ -18,7 +18,8 @@ struct gbkm_ctx;
 
 /* enable (1) or disable (0) event timing around the library's main kernels:
  * "row_norms", "quantize", "assign_simt", "assign_tc", "recheck", "escalate", "update" (part
- * "segsum": the segmented sums), "seed" (parts "seed_cc", "seed_d2", "seed_pick"), "project",
+ * "segsum": the segmented sums), "seed" (part "seed_d2": the rounds, each one launch), "project", "lift", "bico_take",
+ * "piecy_lift", "rsvd" (parts "rsvd_sketch", "rsvd_qr", "rsvd_rows", "rsvd_small"),
  * "center_prep", "gemm", "mlp_forward", "mlp_hidden", "mlp_topm", "mlp_logits", "mlp_train_step",
  * "learned_assign", "cand_check", "fallback", "batch_run" and, for a batched run
  * that is not recorded into a graph, "seed_batched", "assign_batched",

@@ -1,12 +1,14 @@
-// k_seed.cu -- A3 k-means++ D^2 seeding (Section 1): for each round, a fused D^2 update
-// with per-block FP64 sums, then a one-CTA two-level prefix-sum sampler that writes the chosen
-// row into the centers on the device.  No host synchronisation.
+// k_seed.cu -- A3 k-means++ D^2 seeding (Section 1): one launch per round.  Its blocks refresh D^2
+// against the newest center and write per-block FP64 sums; the block that finishes last (an atomic
+// ticket) samples the next center by a two-level prefix search, writes its row into the centers and
+// measures it against the earlier centers for the next round.  No host synchronisation.
 //
 // The D^2 update skips, exactly, every point the new center cannot reach: with a the point's
 // nearest chosen center and D its distance, ||x - c_new|| >= ||c_new - c_a|| - D, so when
 // ||c_new - c_a||^2 > 4 D^2 (with a margin far above the rounding of both double-float values) the
 // new distance exceeds D and min(D^2, ||x - c_new||^2) = D^2: the point's row is not read and D^2
-// keeps its bits.  The center-to-center distances of a round take one small kernel.
+// keeps its bits.  For the rows it does read, a plain FP32 distance with its error bound comes first;
+// only where that cannot show the new center to be farther is the double-float distance taken.
 #include "internal.cuh"
 #include "seed_util.cuh"
 
@@ -16,117 +18,6 @@ namespace {
 constexpr int SB = 128;    // rows per sampling block (one CTA of 8 warps, 16 rows per warp)
 constexpr int PICK_T = 1024;
 }  // namespace
-
-// p_i = w_i * D2_i summed per block of SB rows; D2 refreshed against the newest center c (round
-// j = index of c; init: D2 = distance to c), A = index of the nearest center so far, cc[a] =
-// ||c - c_a||^2 for the earlier centers (skip test above).  The block's threads test its rows in
-// parallel; the rows that need a distance go to a list that the 8 warps work through (one warp per
-// row); the block sum is a fixed tree over the rows.
-template <int VW>
-__global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, int64_t n, int64_t d,
-                                                   const float *__restrict__ w,
-                                                   const float *__restrict__ c, int64_t j,
-                                                   double *__restrict__ D2, int32_t *__restrict__ A,
-                                                   const double *__restrict__ cc, double *__restrict__ bsum,
-                                                   const int *__restrict__ stop) {
-    if (*stop) return;
-    __shared__ double nd_s[256];
-    __shared__ int list[SB];
-    __shared__ int nlist;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
-    if (tid == 0) nlist = 0;
-    __syncthreads();
-    if (tid < SB) {
-        const int64_t i = r0 + tid;
-        double od = 0.0;
-        if (i < r1) {
-            bool skip = false;
-            if (j > 0) {
-                od = D2[i];
-                skip = cc[A[i]] > 4.0 * od * (1.0 + 1e-6);
-            }
-            if (!skip) list[atomicAdd(&nlist, 1)] = tid;
-        }
-        nd_s[tid] = od;
-    } else {
-        nd_s[tid] = 0.0;
-    }
-    __syncthreads();
-    const int m = nlist;
-    // lpr lanes per listed row (32 / lpr rows per warp at a time), so that short rows keep the
-    // lanes busy and their sums take fewer butterfly steps
-    const int lpr = lanes_per_row(d, VW), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
-    for (int e0 = wid * rpw; e0 < m; e0 += 8 * rpw) {
-        const int e = e0 + sub;
-        const bool has = e < m;
-        const int t = has ? list[e] : 0;
-        const int64_t i = r0 + t;
-        DF acc;
-        if (has) {
-            const float *x = X + i * d;
-            if constexpr (VW == 4) {
-                const float4 *x4 = reinterpret_cast<const float4 *>(x);
-                const float4 *c4 = reinterpret_cast<const float4 *>(c);
-#pragma unroll 4
-                for (int64_t q = sl; q < d / 4; q += lpr) {
-                    float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
-                    acc.add_sqdiff(a.x, b.x);
-                    acc.add_sqdiff(a.y, b.y);
-                    acc.add_sqdiff(a.z, b.z);
-                    acc.add_sqdiff(a.w, b.w);
-                }
-            } else {
-                for (int64_t q = sl; q < d; q += lpr) acc.add_sqdiff(x[q], c[q]);
-            }
-        }
-        const double dist = group_sum_df(acc, lpr);
-        if (has && sl == 0 && (j == 0 || dist < nd_s[t])) {
-            nd_s[t] = dist;
-            D2[i] = dist;
-            A[i] = (int32_t)j;
-        }
-    }
-    __syncthreads();
-    double p = 0.0;
-    if (tid < SB && r0 + tid < r1) p = (w ? (double)w[r0 + tid] : 1.0) * nd_s[tid];
-    const double s = block_tree_sum_d(p, nd_s);
-    if (tid == 0) bsum[blockIdx.x] = s;
-}
-
-// cc[a] = ||C[j] - C[a]||^2 (double-float) for a < j: one warp per earlier center
-__global__ void __launch_bounds__(256) k_center_dist(const float *__restrict__ C, int64_t d, int64_t j,
-                                                     double *__restrict__ cc, const int *__restrict__ stop) {
-    if (*stop) return;
-    // lpr lanes per earlier center (32 / lpr centers per warp)
-    const int lpr = lanes_per_row(d, 1), sl = (threadIdx.x & 31) % lpr;
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t a = g / lpr;
-    if ((g & ~(int64_t)31) / lpr >= j) return;  // the whole warp is past the last center
-    const bool has = a < j;
-    const float *cj = C + j * d, *ca = C + a * d;
-    DF acc;
-    if (has)
-        for (int64_t t = sl; t < d; t += lpr) acc.add_sqdiff(cj[t], ca[t]);
-    const double v = group_sum_df(acc, lpr);
-    if (has && sl == 0) cc[a] = v;
-}
-
-// block sums of w (first center of a weighted run)
-__global__ void __launch_bounds__(256) k_wsum(const float *__restrict__ w, int64_t n,
-                                              double *__restrict__ bsum) {
-    __shared__ double sh[256];
-    const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
-    double s = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += 256) s += (double)w[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < 256; ++q) t += sh[q];
-        bsum[blockIdx.x] = t;
-    }
-}
 
 __device__ double block_incl_scan_d(double v, double *sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -157,25 +48,30 @@ __device__ double block_incl_scan_d(double v, double *sh) {
 // p_i = w_i * D2_i.  Blocks: prefix of the block sums; within the block: inclusive prefix in
 // row order.  Chosen = smallest i whose global inclusive prefix exceeds t = u_j * total; if
 // rounding leaves none, the last i with p_i > 0.  Writes idx_out[j], the center row, D2_i = 0.
-__global__ void __launch_bounds__(PICK_T) k_pick(const float *__restrict__ X, int64_t n, int64_t d,
-                                                 const float *__restrict__ w,
-                                                 double *__restrict__ D2, const double *__restrict__ bsum,
-                                                 int64_t nb, const double *__restrict__ u, int64_t j,
-                                                 int mode_w, int64_t *__restrict__ idx_out,
-                                                 float *__restrict__ C_out, int *stop, int *status) {
-    __shared__ double sh[32];
-    __shared__ int64_t s_block, s_idx;
-    __shared__ double s_base, s_t;
-    if (*stop) return;
-    const int tid = threadIdx.x;
+struct PickShared {
+    double sh[32];
+    int64_t s_block, s_idx;
+    double s_base, s_t;
+};
+
+// the pick by the whole CTA (blockDim.x threads, a multiple of 32 and at least SB); returns the
+// chosen row to every thread, or -1 when the run stops (fewer than k points with positive p_i)
+__device__ int64_t pick_center(const float *__restrict__ X, int64_t n, int64_t d, const float *__restrict__ w,
+                               double *__restrict__ D2, const double *__restrict__ bsum, int64_t nb,
+                               const double *__restrict__ u, int64_t j, int mode_w, int64_t *__restrict__ idx_out,
+                               float *__restrict__ C_out, int *stop, int *status, PickShared &ps) {
+    double *sh = ps.sh;
+    int64_t &s_block = ps.s_block, &s_idx = ps.s_idx;
+    double &s_base = ps.s_base, &s_t = ps.s_t;
+    const int tid = threadIdx.x, nt = blockDim.x;
     // 1. prefix over block sums, per thread over a contiguous range of blocks
-    const int64_t per = (nb + PICK_T - 1) / PICK_T;
+    const int64_t per = (nb + nt - 1) / nt;
     const int64_t b0 = (int64_t)tid * per, b1 = min(nb, b0 + per);
     double v = 0.0;
     for (int64_t b = b0; b < b1; ++b) v += bsum[b];
     const double incl = block_incl_scan_d(v, sh);
     const double excl = incl - v;
-    if (tid == PICK_T - 1) s_t = incl;  // total
+    if (tid == nt - 1) s_t = incl;  // total
     if (tid == 0) {
         s_block = INT64_MAX;
         s_idx = INT64_MAX;
@@ -187,7 +83,7 @@ __global__ void __launch_bounds__(PICK_T) k_pick(const float *__restrict__ X, in
             *stop = 1;
             status_raise(status, ST_DEGENERATE);
         }
-        return;
+        return -1;
     }
     const double t = u[j] * total;
     // 2. first block whose inclusive prefix exceeds t (recomputed with the same per-thread order)
@@ -251,13 +147,184 @@ __global__ void __launch_bounds__(PICK_T) k_pick(const float *__restrict__ X, in
             *stop = 1;
             status_raise(status, ST_DEGENERATE);
         }
-        return;
+        return -1;
     }
     if (tid == 0) {
         idx_out[j] = pick;
         D2[pick] = 0.0;
     }
-    for (int64_t q = tid; q < d; q += PICK_T) C_out[j * d + q] = X[pick * d + q];
+    for (int64_t q = tid; q < d; q += nt) C_out[j * d + q] = X[pick * d + q];
+    return pick;
+}
+
+// One CTA of PICK_T threads: the pick of round j as a kernel of its own (the weighted first center)
+__global__ void __launch_bounds__(PICK_T) k_pick(const float *__restrict__ X, int64_t n, int64_t d,
+                                                 const float *__restrict__ w,
+                                                 double *__restrict__ D2, const double *__restrict__ bsum,
+                                                 int64_t nb, const double *__restrict__ u, int64_t j,
+                                                 int mode_w, int64_t *__restrict__ idx_out,
+                                                 float *__restrict__ C_out, int *stop, int *status) {
+    __shared__ PickShared ps;
+    if (*stop) return;
+    pick_center(X, n, d, w, D2, bsum, nb, u, j, mode_w, idx_out, C_out, stop, status, ps);
+}
+
+// p_i = w_i * D2_i summed per block of SB rows; D2 refreshed against the newest center c (round
+// j = index of c; init: D2 = distance to c), A = index of the nearest center so far, cc[a] =
+// ||c - c_a||^2 for the earlier centers (skip test above).  The block's threads test its rows in
+// parallel; the rows that need a distance go to a list that the 8 warps work through (one warp per
+// row); the block sum is a fixed tree over the rows.
+// The last block to finish (an atomic ticket) then picks center jn with pick_center and measures it
+// against the earlier centers (cc for the next round's skip test), so a round is one launch.
+template <int VW>
+__global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, int64_t n, int64_t d,
+                                                   const float *__restrict__ w,
+                                                   const float *__restrict__ c, int64_t j,
+                                                   double *__restrict__ D2, int32_t *__restrict__ A,
+                                                   double *__restrict__ cc, double *__restrict__ bsum,
+                                                   int *__restrict__ stop, const double *__restrict__ u,
+                                                   int64_t jn, int64_t k, int64_t *__restrict__ idx_out,
+                                                   float *__restrict__ C_out, int *__restrict__ ticket,
+                                                   int *status) {
+    if (*stop) return;
+    __shared__ double nd_s[256];
+    __shared__ int list[SB];
+    __shared__ int nlist;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
+    if (tid == 0) nlist = 0;
+    __syncthreads();
+    if (tid < SB) {
+        const int64_t i = r0 + tid;
+        double od = 0.0;
+        if (i < r1) {
+            bool skip = false;
+            if (j > 0) {
+                od = D2[i];
+                skip = cc[A[i]] > 4.0 * od * (1.0 + 1e-6);
+            }
+            if (!skip) list[atomicAdd(&nlist, 1)] = tid;
+        }
+        nd_s[tid] = od;
+    } else {
+        nd_s[tid] = 0.0;
+    }
+    __syncthreads();
+    const int m = nlist;
+    // lpr lanes per listed row (32 / lpr rows per warp at a time), so that short rows keep the
+    // lanes busy and their sums take fewer butterfly steps
+    const int lpr = lanes_per_row(d, VW), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
+    // relative error bound of the plain FP32 distance below: each difference rounded once, each
+    // fma-accumulated square once, at most d terms per lane and five butterfly additions
+    const float g32 = (float)(d + 40) * 5.9604645e-8f;
+    for (int e0 = wid * rpw; e0 < m; e0 += 8 * rpw) {
+        const int e = e0 + sub;
+        const bool has = e < m;
+        const int t = has ? list[e] : 0;
+        const int64_t i = r0 + t;
+        // first a plain FP32 distance: when it shows, with its error bound, that the new center is
+        // farther than the current D^2, D^2 keeps its bits and the double-float distance is not
+        // needed (the update below would not change anything)
+        bool need = has;
+        if (j > 0) {
+            float a32 = 0.f;
+            if (has) {
+                const float *x = X + i * d;
+                if constexpr (VW == 4) {
+                    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+                    const float4 *c4 = reinterpret_cast<const float4 *>(c);
+#pragma unroll 4
+                    for (int64_t q = sl; q < d / 4; q += lpr) {
+                        const float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
+                        const float e0_ = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+                        a32 = fmaf(e0_, e0_, a32);
+                        a32 = fmaf(e1, e1, a32);
+                        a32 = fmaf(e2, e2, a32);
+                        a32 = fmaf(e3, e3, a32);
+                    }
+                } else {
+                    for (int64_t q = sl; q < d; q += lpr) {
+                        const float df = x[q] - c[q];
+                        a32 = fmaf(df, df, a32);
+                    }
+                }
+            }
+            for (int o = lpr >> 1; o > 0; o >>= 1) a32 += __shfl_xor_sync(0xffffffffu, a32, o);
+            need = has && !((double)a32 * (1.0 - (double)g32) > nd_s[t] * (1.0 + 1e-9));
+        }
+        if (!__any_sync(0xffffffffu, need)) continue;
+        DF acc;
+        if (need) {
+            const float *x = X + i * d;
+            if constexpr (VW == 4) {
+                const float4 *x4 = reinterpret_cast<const float4 *>(x);
+                const float4 *c4 = reinterpret_cast<const float4 *>(c);
+#pragma unroll 4
+                for (int64_t q = sl; q < d / 4; q += lpr) {
+                    float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
+                    acc.add_sqdiff(a.x, b.x);
+                    acc.add_sqdiff(a.y, b.y);
+                    acc.add_sqdiff(a.z, b.z);
+                    acc.add_sqdiff(a.w, b.w);
+                }
+            } else {
+                for (int64_t q = sl; q < d; q += lpr) acc.add_sqdiff(x[q], c[q]);
+            }
+        }
+        const double dist = group_sum_df(acc, lpr);
+        if (need && sl == 0 && (j == 0 || dist < nd_s[t])) {
+            nd_s[t] = dist;
+            D2[i] = dist;
+            A[i] = (int32_t)j;
+        }
+    }
+    __syncthreads();
+    double p = 0.0;
+    if (tid < SB && r0 + tid < r1) p = (w ? (double)w[r0 + tid] : 1.0) * nd_s[tid];
+    const double s = block_tree_sum_d(p, nd_s);
+    if (tid == 0) bsum[blockIdx.x] = s;
+    // ticket: the block that finishes last sees every block's D^2 and sum
+    __shared__ int last;
+    __shared__ PickShared ps;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int64_t pick = pick_center(X, n, d, w, D2, bsum, (int64_t)gridDim.x, u, jn, 0, idx_out, C_out, stop, status,
+                                     ps);
+    if (tid == 0) *ticket = 0;
+    if (pick < 0 || jn + 1 >= k) return;
+    __syncthreads();  // the new center's row in C_out
+    // cc[a] = ||C[jn] - C[a]||^2 (double-float) for a < jn: lpr1 lanes per earlier center
+    const int lpr1 = lanes_per_row(d, 1), cpw = 32 / lpr1, sl1 = lane % lpr1;
+    const float *cj = C_out + jn * d;
+    for (int64_t a0 = (int64_t)wid * cpw; a0 < jn; a0 += 8 * cpw) {
+        const int64_t a = a0 + lane / lpr1;
+        const bool has = a < jn;
+        DF acc;
+        if (has)
+            for (int64_t t = sl1; t < d; t += lpr1) acc.add_sqdiff(cj[t], C_out[a * d + t]);
+        const double v = group_sum_df(acc, lpr1);
+        if (has && sl1 == 0) cc[a] = v;
+    }
+}
+
+// block sums of w (first center of a weighted run)
+__global__ void __launch_bounds__(256) k_wsum(const float *__restrict__ w, int64_t n,
+                                              double *__restrict__ bsum) {
+    __shared__ double sh[256];
+    const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += 256) s += (double)w[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 256; ++q) t += sh[q];
+        bsum[blockIdx.x] = t;
+    }
 }
 
 // first center of an unweighted run: row floor(u0 * n)
@@ -276,14 +343,14 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     const int64_t nb = ceil_div(n, SB);
     WsPlan p;
     size_t o_d2 = p.take<double>(n), o_a = p.take<int32_t>(n), o_cc = p.take<double>(k), o_b = p.take<double>(nb),
-           o_stop = p.take<int>(1);
+           o_stop = p.take<int>(2);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
     double *D2 = ws_at<double>(ws, o_d2), *bsum = ws_at<double>(ws, o_b), *cc = ws_at<double>(ws, o_cc);
     int32_t *A = ws_at<int32_t>(ws, o_a);
-    int *stop = ws_at<int>(ws, o_stop);
-    cudaError_t e = cudaMemsetAsync(stop, 0, sizeof(int), c->stream);
+    int *stop = ws_at<int>(ws, o_stop), *ticket = stop + 1;
+    cudaError_t e = cudaMemsetAsync(stop, 0, 2 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(idx_out, 0xff, sizeof(int64_t) * k, c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "seed memset");
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
@@ -298,27 +365,19 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     }
     c->launches += 1;
     for (int64_t j = 1; j < k; ++j) {
-        // refresh D2 against center j - 1 (chosen in the previous round), then pick center j
+        // one launch: refresh D2 against center j - 1 (chosen in the previous round), then its last
+        // block picks center j and measures it against the earlier ones
         const int64_t jc = j - 1;
         const float *cprev = C_out + jc * d;
-        if (jc > 0) {
-            prof_begin(c, "seed_cc");
-            k_center_dist<<<(unsigned)ceil_div(jc * lanes_per_row(d, 1), 256), 256, 0, c->stream>>>(C_out, d, jc, cc,
-                                                                                                     stop);
-            prof_end(c);
-            c->launches += 1;
-        }
         prof_begin(c, "seed_d2");
         if (vec)
-            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop);
+            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, u, j, k,
+                                                                idx_out, C_out, ticket, c->status);
         else
-            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop);
+            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, u, j, k,
+                                                                idx_out, C_out, ticket, c->status);
         prof_end(c);
-        prof_begin(c, "seed_pick");
-        k_pick<<<1, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, 0, idx_out, C_out, stop,
-                                            c->status);
-        prof_end(c);
-        c->launches += 2;
+        c->launches += 1;
     }
     return cuda_check(c, cudaGetLastError(), "seed launch");
 }
