@@ -589,7 +589,9 @@ def run_highdim(env, args):
     def whole():
         # norms, BF16 copy and residuals in one read of X
         B.kmeans_ingest(Xg, copy=False, xnorm=xnorm, Xq=Xop, resid=Xr, quantize=form == "bf16", ctx=ctx)
-        B.kmeans_seed_pp(Xg, k, ug, C_out=Ca, ctx=ctx)
+        # k-means++ filters its rows through the BF16 copy where the form has one
+        B.kmeans_seed_pp(Xg, k, ug, C_out=Ca, Xq=Xop if form == "bf16" else None,
+                         xresid=Xr if form == "bf16" else None, ctx=ctx)
         cur, nxt = Ca, Cb
         for t in range(iters):
             B.kmeans_assign(Xg, cur, Xop=Xop, Xop_scales=Xr, xnorm=xnorm, compute=form, engine=engine,

@@ -210,6 +210,16 @@ int kmeans_piecy_lift(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const
 int kmeans_seed_pp(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const float *w,
                    int64_t k, const double *u, int64_t *idx_out, float *C_out);
 
+/* kmeans_seed_pp with the BF16 copy of X and its rows' rounding residuals at hand (kmeans_quantize
+ * or kmeans_ingest with resid): the same picks (bit-identical indices), found with less reading.  A
+ * row's distance to the new center is first bounded from below through its BF16 copy,
+ * ||x - c|| >= ||bf16(x) - c|| - ||bf16(x) - x|| (evaluated in FP32 with its error bound); when the
+ * bound already exceeds the row's D^2 the FP32 row is not read.  Xq: n x d bfloat16, 16-byte
+ * aligned, d % 8 == 0 (otherwise the call runs as kmeans_seed_pp); xresid: n FP32, the residuals
+ * rounded up.  Other arguments and results as kmeans_seed_pp. */
+int kmeans_seed_pp_q(gbkm_ctx *ctx, const float *X, const void *Xq, const float *xresid, int64_t n, int64_t d,
+                     const float *w, int64_t k, const double *u, int64_t *idx_out, float *C_out);
+
 /* ------------------------------------------------------------------ A4 + A5: assignment */
 
 /* Assignment step of Lloyd's algorithm (Section 1): labels[i] = argmin_j

@@ -71,6 +71,7 @@ _SIGS = {
     "kmeans_project_block": (ct.c_int, [_vp, _vp, _i32, _i64, _i64, _vp, _i64, _vp, _vp]),
     "kmeans_rsvd": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "kmeans_seed_pp": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp, _vp]),
+    "kmeans_seed_pp_q": (ct.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "kmeans_assign": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _vp, _i64,
                                  ct.POINTER(AssignOpts), _vp, _vp, _vp]),
     "kmeans_update": (ct.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -451,7 +452,9 @@ def kmeans_piecy_lift(X, piece_rows, Omegas, ell, w=None, X_lift=None, ctx=None)
 
 
 # ------------------------------------------------------------------ A3
-def kmeans_seed_pp(X, k, u, w=None, idx_out=None, C_out=None, ctx=None):
+def kmeans_seed_pp(X, k, u, w=None, idx_out=None, C_out=None, Xq=None, xresid=None, ctx=None):
+    """k-means++ seeding; with Xq (the BF16 copy) and xresid (its rows' residuals) the rounds filter
+    rows through the copy first (kmeans_seed_pp_q), with the same picks."""
     _req(X, torch.float32, name="X")
     n, d = X.shape
     _req(u, torch.float64, name="u")
@@ -459,10 +462,22 @@ def kmeans_seed_pp(X, k, u, w=None, idx_out=None, C_out=None, ctx=None):
         raise ValueError("u needs k uniforms")
     if w is not None:
         _req(w, torch.float32, (n,), "w")
+    if (Xq is None) != (xresid is None):
+        raise ValueError("Xq and xresid go together")
+    if Xq is not None:
+        _req(Xq, torch.bfloat16, (n, d), "Xq")
+        _req(xresid, torch.float32, (n,), "xresid")
     idx_out = idx_out if idx_out is not None else torch.empty(k, dtype=torch.int64, device=X.device)
     C_out = C_out if C_out is not None else torch.empty((k, d), dtype=torch.float32, device=X.device)
+    _req(idx_out, torch.int64, (k,), "idx_out")
+    _req(C_out, torch.float32, (k, d), "C_out")
+    _same_device(X, u=u, w=w, Xq=Xq, xresid=xresid, idx_out=idx_out, C_out=C_out)
     c = _ctx(ctx, X)
-    c.check(load().kmeans_seed_pp(c.handle, _ptr(X), n, d, _ptr(w), k, _ptr(u), _ptr(idx_out), _ptr(C_out)))
+    if Xq is None:
+        c.check(load().kmeans_seed_pp(c.handle, _ptr(X), n, d, _ptr(w), k, _ptr(u), _ptr(idx_out), _ptr(C_out)))
+    else:
+        c.check(load().kmeans_seed_pp_q(c.handle, _ptr(X), _ptr(Xq), _ptr(xresid), n, d, _ptr(w), k, _ptr(u),
+                                        _ptr(idx_out), _ptr(C_out)))
     return idx_out, C_out
 
 

@@ -429,6 +429,18 @@ int kmeans_seed_pp(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const floa
     return rc;
 }
 
+int kmeans_seed_pp_q(gbkm_ctx *c, const float *X, const void *Xq, const float *xresid, int64_t n, int64_t d,
+                     const float *w, int64_t k, const double *u, int64_t *idx_out, float *C_out) {
+    if (!c) return GBKM_EINVAL;
+    if (n < 1 || d < 1 || k < 1 || k > n || !X || !u || !idx_out || !C_out || !Xq || !xresid)
+        return set_error(c, GBKM_EINVAL, "seed_pp_q: bad arguments (need 1 <= k <= n, Xq and xresid)");
+    DeviceGuard g(c->device);
+    prof_begin(c, "seed");
+    int rc = gbkm::seed_impl(c, X, n, d, w, k, u, idx_out, C_out, Xq, xresid);
+    prof_end(c);
+    return rc;
+}
+
 int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const float *X,
                   const float *xnorm, int64_t n, int64_t d, const float *C, int64_t k,
                   const gbkm_assign_opts *opts, int32_t *labels, float *min_d2, int64_t *n_rechecked) {

@@ -254,7 +254,8 @@ int update_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *
                 const int32_t *labels, int64_t k, const float *C_old, float *C_new,
                 double *counts, double *cost_old, double *cost_new, int64_t *n_empty);
 int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, int64_t k,
-              const double *u, int64_t *idx_out, float *C_out);
+              const double *u, int64_t *idx_out, float *C_out, const void *Xq = nullptr,
+              const float *xresid = nullptr);
 // worst-case error coefficients of the distance scores of an operand format and engine
 void score_error_coeffs(int dtype, int engine_tc, int64_t d, float &err_rel, float &err_abs);
 bool tc_assign_supported(int dtype, int64_t d, int64_t k);

@@ -1,7 +1,7 @@
-// k_seed.cu -- A3 k-means++ D^2 seeding (Section 1): one launch per round.  Its blocks refresh D^2
-// against the newest center and write per-block FP64 sums; the block that finishes last (an atomic
-// ticket) samples the next center by a two-level prefix search, writes its row into the centers and
-// measures it against the earlier centers for the next round.  No host synchronisation.
+// k_seed.cu -- A3 k-means++ D^2 seeding (Section 1): two launches per round.  The first refreshes
+// D^2 against the newest center and writes per-block FP64 sums; then one CTA samples the next center
+// by a two-level prefix search, writes its row into the centers and measures it against the earlier
+// centers for the next round's skip test.  No host synchronisation.
 //
 // The D^2 update skips, exactly, every point the new center cannot reach: with a the point's
 // nearest chosen center and D its distance, ||x - c_new|| >= ||c_new - c_a|| - D, so when
@@ -67,8 +67,16 @@ __device__ int64_t pick_center(const float *__restrict__ X, int64_t n, int64_t d
     // 1. prefix over block sums, per thread over a contiguous range of blocks
     const int64_t per = (nb + nt - 1) / nt;
     const int64_t b0 = (int64_t)tid * per, b1 = min(nb, b0 + per);
+    // the block sums are loaded eight at a time and added in range order (the same sum as one by one)
     double v = 0.0;
-    for (int64_t b = b0; b < b1; ++b) v += bsum[b];
+    for (int64_t b = b0; b < b1; b += 8) {
+        double t8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t8[q] = b + q < b1 ? bsum[b + q] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (b + q < b1) v += t8[q];
+    }
     const double incl = block_incl_scan_d(v, sh);
     const double excl = incl - v;
     if (tid == nt - 1) s_t = incl;  // total
@@ -89,11 +97,20 @@ __device__ int64_t pick_center(const float *__restrict__ X, int64_t n, int64_t d
     // 2. first block whose inclusive prefix exceeds t (recomputed with the same per-thread order)
     {
         double run = excl;
-        for (int64_t b = b0; b < b1; ++b) {
-            run += bsum[b];
-            if (run > t) {
-                atomicMin((unsigned long long *)&s_block, (unsigned long long)b);
-                break;
+        bool found = false;
+        for (int64_t b = b0; b < b1 && !found; b += 8) {
+            double t8[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) t8[q] = b + q < b1 ? bsum[b + q] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (!found && b + q < b1) {
+                    run += t8[q];
+                    if (run > t) {
+                        atomicMin((unsigned long long *)&s_block, (unsigned long long)(b + q));
+                        found = true;
+                    }
+                }
             }
         }
     }
@@ -174,18 +191,14 @@ __global__ void __launch_bounds__(PICK_T) k_pick(const float *__restrict__ X, in
 // ||c - c_a||^2 for the earlier centers (skip test above).  The block's threads test its rows in
 // parallel; the rows that need a distance go to a list that the 8 warps work through (one warp per
 // row); the block sum is a fixed tree over the rows.
-// The last block to finish (an atomic ticket) then picks center jn with pick_center and measures it
-// against the earlier centers (cc for the next round's skip test), so a round is one launch.
 template <int VW>
-__global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, int64_t n, int64_t d,
+__global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ X, int64_t n, int64_t d,
                                                    const float *__restrict__ w,
                                                    const float *__restrict__ c, int64_t j,
                                                    double *__restrict__ D2, int32_t *__restrict__ A,
-                                                   double *__restrict__ cc, double *__restrict__ bsum,
-                                                   int *__restrict__ stop, const double *__restrict__ u,
-                                                   int64_t jn, int64_t k, int64_t *__restrict__ idx_out,
-                                                   float *__restrict__ C_out, int *__restrict__ ticket,
-                                                   int *status) {
+                                                   const double *__restrict__ cc, double *__restrict__ bsum,
+                                                   const int *__restrict__ stop, const __nv_bfloat16 *__restrict__ Xq,
+                                                   const float *__restrict__ xresid) {
     if (*stop) return;
     __shared__ double nd_s[256];
     __shared__ int list[SB];
@@ -227,8 +240,40 @@ __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, 
         // needed (the update below would not change anything)
         bool need = has;
         if (j > 0) {
+            if (Xq) {
+                // with the BF16 copy (d % 8 == 0): ||x - c|| >= ||x~ - c|| - ||x~ - x||, ||x~ - x|| <= the
+                // row's residual; when that lower bound already exceeds D, the FP32 row is not read
+                float a16 = 0.f;
+                if (has) {
+                    const uint4 *q8 = reinterpret_cast<const uint4 *>(Xq + i * d);
+                    const float4 *c4 = reinterpret_cast<const float4 *>(c);
+                    for (int64_t q = sl; q < d / 8; q += lpr) {
+                        const uint4 v = __ldg(q8 + q);
+                        const float4 b0 = __ldg(c4 + 2 * q), b1 = __ldg(c4 + 2 * q + 1);
+                        const float f0 = __uint_as_float(v.x << 16) - b0.x, f1 = __uint_as_float(v.x & 0xffff0000u) - b0.y;
+                        const float f2 = __uint_as_float(v.y << 16) - b0.z, f3 = __uint_as_float(v.y & 0xffff0000u) - b0.w;
+                        const float f4 = __uint_as_float(v.z << 16) - b1.x, f5 = __uint_as_float(v.z & 0xffff0000u) - b1.y;
+                        const float f6 = __uint_as_float(v.w << 16) - b1.z, f7 = __uint_as_float(v.w & 0xffff0000u) - b1.w;
+                        a16 = fmaf(f0, f0, a16);
+                        a16 = fmaf(f1, f1, a16);
+                        a16 = fmaf(f2, f2, a16);
+                        a16 = fmaf(f3, f3, a16);
+                        a16 = fmaf(f4, f4, a16);
+                        a16 = fmaf(f5, f5, a16);
+                        a16 = fmaf(f6, f6, a16);
+                        a16 = fmaf(f7, f7, a16);
+                    }
+                }
+                for (int o = lpr >> 1; o > 0; o >>= 1) a16 += __shfl_xor_sync(0xffffffffu, a16, o);
+                if (has) {
+                    const double lo = sqrt(fmax((double)a16 * (1.0 - (double)g32), 0.0)) * (1.0 - 1e-12) - (double)xresid[i];
+                    const double L = lo > 0.0 ? lo * lo * (1.0 - 1e-12) : 0.0;
+                    need = !(L * (1.0 - 1e-9) > nd_s[t]);
+                }
+                if (!__any_sync(0xffffffffu, need)) continue;
+            }
             float a32 = 0.f;
-            if (has) {
+            if (need) {
                 const float *x = X + i * d;
                 if constexpr (VW == 4) {
                     const float4 *x4 = reinterpret_cast<const float4 *>(x);
@@ -250,7 +295,7 @@ __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, 
                 }
             }
             for (int o = lpr >> 1; o > 0; o >>= 1) a32 += __shfl_xor_sync(0xffffffffu, a32, o);
-            need = has && !((double)a32 * (1.0 - (double)g32) > nd_s[t] * (1.0 + 1e-9));
+            need = need && !((double)a32 * (1.0 - (double)g32) > nd_s[t] * (1.0 + 1e-9));
         }
         if (!__any_sync(0xffffffffu, need)) continue;
         DF acc;
@@ -283,31 +328,32 @@ __global__ void __launch_bounds__(256) k_d2_update(const float *__restrict__ X, 
     if (tid < SB && r0 + tid < r1) p = (w ? (double)w[r0 + tid] : 1.0) * nd_s[tid];
     const double s = block_tree_sum_d(p, nd_s);
     if (tid == 0) bsum[blockIdx.x] = s;
-    // ticket: the block that finishes last sees every block's D^2 and sum
-    __shared__ int last;
+}
+
+// One CTA of PICK_T threads after each round's D^2 update: picks center j and measures it against the
+// earlier centers (cc, for the next round's skip test; double-float, lpr lanes per center)
+__global__ void __launch_bounds__(PICK_T) k_pick_cc(const float *__restrict__ X, int64_t n, int64_t d,
+                                                    const float *__restrict__ w, double *__restrict__ D2,
+                                                    const double *__restrict__ bsum, int64_t nb,
+                                                    const double *__restrict__ u, int64_t j, int64_t k,
+                                                    int64_t *__restrict__ idx_out, float *__restrict__ C_out,
+                                                    double *__restrict__ cc, int *stop, int *status) {
     __shared__ PickShared ps;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const int64_t pick = pick_center(X, n, d, w, D2, bsum, (int64_t)gridDim.x, u, jn, 0, idx_out, C_out, stop, status,
-                                     ps);
-    if (tid == 0) *ticket = 0;
-    if (pick < 0 || jn + 1 >= k) return;
+    if (*stop) return;
+    const int64_t pick = pick_center(X, n, d, w, D2, bsum, nb, u, j, 0, idx_out, C_out, stop, status, ps);
+    if (pick < 0 || j + 1 >= k) return;
     __syncthreads();  // the new center's row in C_out
-    // cc[a] = ||C[jn] - C[a]||^2 (double-float) for a < jn: lpr1 lanes per earlier center
-    const int lpr1 = lanes_per_row(d, 1), cpw = 32 / lpr1, sl1 = lane % lpr1;
-    const float *cj = C_out + jn * d;
-    for (int64_t a0 = (int64_t)wid * cpw; a0 < jn; a0 += 8 * cpw) {
-        const int64_t a = a0 + lane / lpr1;
-        const bool has = a < jn;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lpr = lanes_per_row(d, 1), cpw = 32 / lpr, sl = lane % lpr;
+    const float *cj = C_out + j * d;
+    for (int64_t a0 = (int64_t)wid * cpw; a0 < j; a0 += (int64_t)nw * cpw) {
+        const int64_t a = a0 + lane / lpr;
+        const bool has = a < j;
         DF acc;
         if (has)
-            for (int64_t t = sl1; t < d; t += lpr1) acc.add_sqdiff(cj[t], C_out[a * d + t]);
-        const double v = group_sum_df(acc, lpr1);
-        if (has && sl1 == 0) cc[a] = v;
+            for (int64_t t = sl; t < d; t += lpr) acc.add_sqdiff(cj[t], C_out[a * d + t]);
+        const double v = group_sum_df(acc, lpr);
+        if (has && sl == 0) cc[a] = v;
     }
 }
 
@@ -339,7 +385,7 @@ __global__ void k_pick_uniform(const float *__restrict__ X, int64_t n, int64_t d
 }
 
 int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w, int64_t k,
-              const double *u, int64_t *idx_out, float *C_out) {
+              const double *u, int64_t *idx_out, float *C_out, const void *Xq, const float *xresid) {
     const int64_t nb = ceil_div(n, SB);
     WsPlan p;
     size_t o_d2 = p.take<double>(n), o_a = p.take<int32_t>(n), o_cc = p.take<double>(k), o_b = p.take<double>(nb),
@@ -349,12 +395,15 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     if (!ws) return rc;
     double *D2 = ws_at<double>(ws, o_d2), *bsum = ws_at<double>(ws, o_b), *cc = ws_at<double>(ws, o_cc);
     int32_t *A = ws_at<int32_t>(ws, o_a);
-    int *stop = ws_at<int>(ws, o_stop), *ticket = stop + 1;
+    int *stop = ws_at<int>(ws, o_stop);
     cudaError_t e = cudaMemsetAsync(stop, 0, 2 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(idx_out, 0xff, sizeof(int64_t) * k, c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "seed memset");
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(C_out) & 15) == 0);
+    // the BF16 filter pass reads 16-byte groups of 8 elements of the copy
+    const __nv_bfloat16 *xq = (Xq && xresid && vec && (d & 7) == 0 && (reinterpret_cast<uintptr_t>(Xq) & 15) == 0)
+                                  ? static_cast<const __nv_bfloat16 *>(Xq) : nullptr;
     if (!w) {
         k_pick_uniform<<<1, 256, 0, c->stream>>>(X, n, d, u, idx_out, C_out);
     } else {
@@ -365,19 +414,22 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     }
     c->launches += 1;
     for (int64_t j = 1; j < k; ++j) {
-        // one launch: refresh D2 against center j - 1 (chosen in the previous round), then its last
-        // block picks center j and measures it against the earlier ones
+        // refresh D2 against center j - 1 (chosen in the previous round), then pick center j and
+        // measure it against the earlier ones
         const int64_t jc = j - 1;
         const float *cprev = C_out + jc * d;
         prof_begin(c, "seed_d2");
         if (vec)
-            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, u, j, k,
-                                                                idx_out, C_out, ticket, c->status);
+            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, xq,
+                                                                xresid);
         else
-            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, u, j, k,
-                                                                idx_out, C_out, ticket, c->status);
+            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, nullptr,
+                                                                nullptr);
         prof_end(c);
-        c->launches += 1;
+        prof_begin(c, "seed_pick");
+        k_pick_cc<<<1, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, k, idx_out, C_out, cc, stop, c->status);
+        prof_end(c);
+        c->launches += 2;
     }
     return cuda_check(c, cudaGetLastError(), "seed launch");
 }

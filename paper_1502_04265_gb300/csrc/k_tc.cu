@@ -45,6 +45,11 @@ struct Args {
     int n_chunks, bn, kb, stages, tmem_cols, m_tiles;
     uint32_t a_bytes, b_bytes, stage_bytes, tx_bytes;
     uint32_t idesc;
+    // 3xTF32 with bn <= 128: the centers' hi and lo tiles are adjacent in the stage, so one MMA of
+    // N = 2 bn (instruction descriptor idesc2) gives x.c_hi and x.c_lo side by side in the
+    // accumulator, and x_lo.c_hi is added to the first half; the epilogue adds the two halves
+    int stack;
+    uint32_t idesc2;
     // argmin epilogue
     const float *cnorm, *cscale, *xscale, *xnorm;
     const unsigned *cmax;
@@ -364,6 +369,16 @@ __device__ __forceinline__ void tmem_ld16_into32(uint32_t taddr, uint32_t (&r)[3
         : "r"(taddr)
         : "memory");
 }
+// 16 columns into the upper half of a 32-register buffer (the second half of a stacked accumulator)
+__device__ __forceinline__ void tmem_ld16_upper(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // wait for the thread's TMEM loads, with the loaded registers as operands so that no use of them
 // can be scheduled before the wait
@@ -540,10 +555,15 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                             const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes per MMA step
                             if constexpr (X3) {
                                 const uint64_t alo = sw128_desc(st + a.a_bytes);
-                                const uint64_t blo = sw128_desc(st + 2 * a.a_bytes + a.b_bytes);
-                                tc_mma<FORM>(d_tmem, alo + off, bdesc + off, a.idesc, acc);
-                                tc_mma<FORM>(d_tmem, adesc + off, blo + off, a.idesc, 1u);
-                                tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, 1u);
+                                if (a.stack) {
+                                    tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc2, acc);
+                                    tc_mma<FORM>(d_tmem, alo + off, bdesc + off, a.idesc, 1u);
+                                } else {
+                                    const uint64_t blo = sw128_desc(st + 2 * a.a_bytes + a.b_bytes);
+                                    tc_mma<FORM>(d_tmem, alo + off, bdesc + off, a.idesc, acc);
+                                    tc_mma<FORM>(d_tmem, adesc + off, blo + off, a.idesc, 1u);
+                                    tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, 1u);
+                                }
                             } else if constexpr (FORM == F_BF16X2) {
                                 const uint64_t blo = sw128_desc(st + a.a_bytes + a.b_bytes);
                                 tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, acc);
@@ -590,7 +610,9 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
             if (*abort_flag && committed && last_bar) mbar_drain(last_bar, last_parity, DRAIN_LIMIT_NS);
         }
     } else if (X3 && warp >= 8 && warp < 12) {
-        // ------------------------------------------------ 3xTF32 split of the staged X tile
+        // ------------------------------------------------ 3xTF32 split of the staged X tile: only the low
+        // part is written; the tensor cores read the staged FP32 tile itself as the high part (kind::tf32
+        // takes the top 19 bits of an FP32 operand, the same truncation as the mask here)
         const int t = threadIdx.x - 256;  // 0..127
         int s = 0;
         uint32_t ph = 0;
@@ -612,7 +634,6 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                         l.y = __float_as_uint(__fsub_rn(__uint_as_float(v.y), __uint_as_float(h.y))) & 0xffffe000u;
                         l.z = __float_as_uint(__fsub_rn(__uint_as_float(v.z), __uint_as_float(h.z))) & 0xffffe000u;
                         l.w = __float_as_uint(__fsub_rn(__uint_as_float(v.w), __uint_as_float(h.w))) & 0xffffe000u;
-                        hi[e] = h;
                         lo[e] = l;
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -910,14 +931,22 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                     // (the grouped top-m epilogue runs on chunk widths that are multiples of 32)
                     constexpr bool ONLY32 = EPI == E_TOPG;
                     auto load = [&](uint32_t (&r)[32], int cc) {
-                        if (ONLY32 || (UW == 32 && c_end - cc >= 32))
+                        if (ONLY32 || (UW == 32 && c_end - cc >= 32)) {
                             tmem_ld32(tbase + (uint32_t)cc, r);
-                        else
+                        } else {
                             tmem_ld16_into32(tbase + (uint32_t)cc, r);
+                            if (X3 && a.stack) tmem_ld16_upper(tbase + (uint32_t)(a.bn + cc), r);
+                        }
                     };
                     auto run = [&](const uint32_t (&r)[32], int cc) {
                         if constexpr (ONLY32) {
                             process(r, cc);
+                        } else if (X3 && a.stack) {
+                            uint32_t s16[16];
+#pragma unroll
+                            for (int g = 0; g < 16; ++g)
+                                s16[g] = __float_as_uint(__fadd_rn(__uint_as_float(r[g]), __uint_as_float(r[16 + g])));
+                            process(s16, cc);
                         } else {
                             if (UW == 32 && c_end - cc >= 32) {
                                 process(r, cc);
@@ -1215,7 +1244,6 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                         l.y = __float_as_uint(__fsub_rn(__uint_as_float(v.y), __uint_as_float(h.y))) & 0xffffe000u;
                         l.z = __float_as_uint(__fsub_rn(__uint_as_float(v.z), __uint_as_float(h.z))) & 0xffffe000u;
                         l.w = __float_as_uint(__fsub_rn(__uint_as_float(v.w), __uint_as_float(h.w))) & 0xffffe000u;
-                        hi[e] = h;
                         lo[e] = l;
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1655,6 +1683,16 @@ static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra
     return p;
 }
 
+// the stacked 3xTF32 MMA (x.[c_hi | c_lo] in one instruction of N = 2 bn) where a chunk has at most 128
+// centers: two accumulators of 2 bn columns each must fit the 512 TMEM columns
+static void set_stack(Args &a, int form, int bn) {
+    if (form == F_TF32X3 && bn <= 128) {
+        a.stack = 1;
+        a.idesc2 = make_idesc(F_TF32X3, BM, 2 * bn);
+        a.tmem_cols = (4 * bn <= 256) ? 256 : 512;
+    }
+}
+
 template <int FORM, int EPI>
 static int launch(gbkm_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &B2, Args &args,
                   const Plan &p, const CUtensorMap *A2 = nullptr) {
@@ -1816,6 +1854,7 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
     }
     a.labels = o.labels, a.min_d2 = o.min_d2, a.flag_list = o.flag_list, a.cand = o.cand, a.flag_count = o.flag_count;
     a.status = c->status;
+    set_stack(a, form, p.bn);
     if (form == F_BF16X2) return launch<F_BF16X2, E_ARGMIN>(c, tA, tB, tB2, a, p);
     if (form == F_BF16) return launch<F_BF16, E_ARGMIN>(c, tA, tB, tB2, a, p);
     if (form == F_FP8) return launch<F_FP8, E_ARGMIN>(c, tA, tB, tB2, a, p);
@@ -1880,6 +1919,7 @@ static int launch_store_gemm(gbkm_ctx *c, int form, const void *A, const void *B
     a.Y = Out, a.ldy = N;
     a.row_w = row_w;
     a.status = c->status;
+    set_stack(a, form, p.bn);
     if (form == F_BF16) return launch<F_BF16, E_STORE>(c, tA, tB, tB2, a, p);
     return launch<F_TF32X3, E_STORE>(c, tA, tB, tB2, a, p);
 }

@@ -38,14 +38,16 @@ def lloyd(X, k, iters, u, w=None, compute="f32", engine="auto", C0=None, ctx=Non
     if compute == "auto":
         compute = exact_form(d)
     idx = None
-    if C0 is None:
-        idx, C = B.kmeans_seed_pp(X, k, u, w=w, ctx=ctx)
-    else:
-        C = C0.clone()
     xnorm = B.kmeans_row_norms(X, ctx=ctx)
     Xop, scales = (None, None)
     if compute in ("bf16", "fp8"):
         Xop, scales = B.kmeans_quantize(X, compute, ctx=ctx)
+    if C0 is None:
+        # with a BF16 copy at hand, k-means++ filters its rows through it (the same picks)
+        bq = compute == "bf16"
+        idx, C = B.kmeans_seed_pp(X, k, u, w=w, Xq=Xop if bq else None, xresid=scales if bq else None, ctx=ctx)
+    else:
+        C = C0.clone()
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     C_next = torch.empty_like(C)
     trace = torch.empty((max(iters, 1), 2), dtype=torch.float64, device=dev)

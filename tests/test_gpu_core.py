@@ -276,6 +276,26 @@ def test_seed_pp_matches_oracle(gb, orc, n, d, k, weighted):
     assert np.array_equal(H(C), X[ref_idx])
 
 
+@pytest.mark.parametrize("n,d,k,weighted", [(5000, 64, 10, False), (3000, 40, 20, True), (2048, 256, 33, False),
+                                            (20000, 1024, 40, False)])
+def test_seed_pp_with_bf16_copy_matches_oracle(gb, orc, n, d, k, weighted):
+    """The variant that filters rows through the BF16 copy (kmeans_seed_pp_q) picks the same rows: the
+    copy's lower bound only decides which rows need their FP32 distance."""
+    X, _ = synth.gaussian_mixture(n, d, max(1, k), seed=n + d + 1)
+    u = synth.seed_uniforms(k, seed=n + 1)
+    w = synth.integer_weights(n, seed=d) if weighted else None
+    Xg = T(X)
+    Xq, xr = gb.kmeans_quantize(Xg, "bf16")
+    idx, C = gb.kmeans_seed_pp(Xg, k, T(u), w=T(w) if weighted else None, Xq=Xq, xresid=xr)
+    plain, _ = gb.kmeans_seed_pp(Xg, k, T(u), w=T(w) if weighted else None)
+    gb.gbkm_sync()
+    ref_idx, _, _, rc = orc.seed_pp(X, k, u, w=w)
+    assert rc == 0
+    assert np.array_equal(H(idx), ref_idx)
+    assert torch.equal(idx, plain)
+    assert np.array_equal(H(C), X[ref_idx])
+
+
 def test_seed_pp_degenerate_reports(gb):
     X = np.repeat(np.array([[0.0, 0.0], [3.0, 4.0]], np.float32), 50, axis=0)
     idx, C = gb.kmeans_seed_pp(T(X), 3, T(np.array([0.1, 0.5, 0.5])))

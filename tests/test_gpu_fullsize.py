@@ -25,13 +25,18 @@ def highdim():
 
 
 def test_highdim_seeding_matches_oracle(gb, orc, highdim):
+    """Both seeding calls (FP32 rows only, and with the BF16 copy as a filter) pick the oracle's rows."""
     X, u = highdim
     Xg = torch.from_numpy(X).to(DEV)
-    idx, C = gb.kmeans_seed_pp(Xg, 100, torch.from_numpy(u).to(DEV))
+    ug = torch.from_numpy(u).to(DEV)
+    idx, C = gb.kmeans_seed_pp(Xg, 100, ug)
+    Xq, xr = gb.kmeans_quantize(Xg, "bf16")
+    idx_q, _ = gb.kmeans_seed_pp(Xg, 100, ug, Xq=Xq, xresid=xr)
     gb.gbkm_sync()
     ref_idx, _, _, rc = orc.seed_pp(X, 100, u)
     assert rc == 0
     assert np.array_equal(idx.cpu().numpy(), ref_idx)
+    assert np.array_equal(idx_q.cpu().numpy(), ref_idx)
 
 
 @pytest.mark.parametrize("form", ["bf16", "f32"])
