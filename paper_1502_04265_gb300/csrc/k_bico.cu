@@ -40,31 +40,58 @@ __global__ void __launch_bounds__(256) k_bico_prep(const double *__restrict__ N,
     if (lane == 0) cerr[j] = s > 0.0 ? __dsub_rn(Q[j], __ddiv_rn(ss, s)) : 0.0;
 }
 
-// one warp per point: d2 = ||x_i - mu_j||^2 in FP64 with j = ref[i], then the copies feature j takes
+// 32 points per warp: each point's d2 = ||x_i - mu_j||^2 (FP64, j = ref[i]) is summed by the whole warp
+// (lane l takes columns l, l + 32, ...), the 32 partial sums of every lane are then reduced in one
+// transposing butterfly (31 exchanges; lane p ends with point p's sum, in a fixed order), and every
+// lane evaluates the insertion rule for its own point
 __global__ void __launch_bounds__(256) k_bico_take(const float *__restrict__ X, int64_t n, int64_t d,
                                                    const float *__restrict__ w, const int32_t *__restrict__ ref,
                                                    const double *__restrict__ N, const double *__restrict__ mu,
                                                    const double *__restrict__ cerr, int64_t m, double T,
                                                    double *__restrict__ d2_out, double *__restrict__ take_out,
                                                    int *status) {
-    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    const int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32;
+    if (base >= n) return;
+    double part[32];
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        const int64_t i = base + p;
+        double acc = 0.0;
+        if (i < n) {
+            const int32_t j = ref[i];
+            if (j >= 0 && (int64_t)j < m) {
+                const float *xi = X + i * d;
+                const double *mj = mu + (int64_t)j * d;
+                for (int64_t t = lane; t < d; t += 32) {
+                    const double df = __dsub_rn((double)xi[t], mj[t]);
+                    acc = __fma_rn(df, df, acc);
+                }
+            }
+        }
+        part[p] = acc;
+    }
+    // after the step of width o, element q of lane l holds the sum of point q + (the bits of l at o and
+    // above) over the lanes that agree with l below o
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < o; ++q) {
+            const double send = upper ? part[q] : part[q + o];
+            const double keep = upper ? part[q + o] : part[q];
+            part[q] = __dadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    const int64_t i = base + lane;
     if (i >= n) return;
     const int32_t j = ref[i];
     if (j < 0 || (int64_t)j >= m) {
         // a label outside the references cannot come from the assignment; skip the row
-        if (lane == 0) status_raise(status, ST_BOUNDS);
+        status_raise(status, ST_BOUNDS);
         return;
     }
-    const float *xi = X + i * d;
-    const double *mj = mu + (int64_t)j * d;
-    double acc = 0.0;
-    for (int64_t t = lane; t < d; t += 32) {
-        const double df = __dsub_rn((double)xi[t], mj[t]);
-        acc = __fma_rn(df, df, acc);
-    }
-    acc = warp_sum_d(acc);
-    if (lane != 0) return;
+    double acc = part[0];
     const double s = N[j], c = cerr[j];
     const double wi = w ? (double)w[i] : 1.0;
     double take;
@@ -122,8 +149,8 @@ extern "C" int kmeans_bico_query(gbkm_ctx *c, const void *Xop, const float *Xop_
     prof_begin(c, "bico_take");
     gbkm::k_bico_prep<<<(unsigned)ceil_div(m, 8), 256, 0, c->stream>>>(N, S, Q, m, d, mu, cerr);
     GBKM_LAUNCHED(c);
-    gbkm::k_bico_take<<<(unsigned)ceil_div(n, 8), 256, 0, c->stream>>>(X, n, d, w, ref_out, N, mu, cerr, m, T, d2_out,
-                                                                        take_out, c->status);
+    gbkm::k_bico_take<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(X, n, d, w, ref_out, N, mu, cerr, m, T,
+                                                                          d2_out, take_out, c->status);
     GBKM_LAUNCHED(c);
     prof_end(c);
     return cuda_check(c, cudaGetLastError(), "bico_query launch");

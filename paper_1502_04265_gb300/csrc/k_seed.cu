@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
     const int m = nlist;
     // lpr lanes per listed row (32 / lpr rows per warp at a time), so that short rows keep the
     // lanes busy and their sums take fewer butterfly steps
-    const int lpr = lanes_per_row(d, VW), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
+    const int lpr = lanes_per_row_d2(d, VW), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
     // relative error bound of the plain FP32 distance below: each difference rounded once, each
     // fma-accumulated square once, at most d terms per lane and five butterfly additions
     const float g32 = (float)(d + 40) * 5.9604645e-8f;
@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
                 if (has) {
                     const uint4 *q8 = reinterpret_cast<const uint4 *>(Xq + i * d);
                     const float4 *c4 = reinterpret_cast<const float4 *>(c);
+#pragma unroll 4
                     for (int64_t q = sl; q < d / 8; q += lpr) {
                         const uint4 v = __ldg(q8 + q);
                         const float4 b0 = __ldg(c4 + 2 * q), b1 = __ldg(c4 + 2 * q + 1);

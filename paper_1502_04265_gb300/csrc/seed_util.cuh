@@ -30,4 +30,13 @@ __host__ __device__ __forceinline__ int lanes_per_row(int64_t d, int vw) {
     return l;
 }
 
+// lanes per row of the D^2 update (rows read as float4 when vw == 4): a power of two giving each lane
+// about four vectors of its row, at most 32 lanes, so that a warp has several rows' loads in flight
+__host__ __device__ __forceinline__ int lanes_per_row_d2(int64_t d, int vw) {
+    const int64_t nv = vw == 4 ? d / 4 : d;
+    int l = 1;
+    while (l < 32 && 4 * l < nv) l <<= 1;
+    return l;
+}
+
 }  // namespace gbkm
