@@ -95,7 +95,14 @@ __device__ int64_t pick_center(const float *__restrict__ X, int64_t n, int64_t d
     }
     const double t = u[j] * total;
     // 2. first block whose inclusive prefix exceeds t (recomputed with the same per-thread order)
-    {
+    // a thread whose range ends clearly below t cannot hold the first block over t (the running sum
+    // rises monotonically and ends within rounding of incl); one whose range starts clearly above t
+    // holds it at its first block; only the thread(s) in between walk their range
+    if (b0 < b1 && incl < t * (1.0 - 1e-12)) {
+        // nothing in this range
+    } else if (b0 < b1 && excl > t * (1.0 + 1e-12)) {
+        atomicMin((unsigned long long *)&s_block, (unsigned long long)b0);
+    } else {
         double run = excl;
         bool found = false;
         for (int64_t b = b0; b < b1 && !found; b += 8) {
@@ -186,63 +193,61 @@ __global__ void __launch_bounds__(PICK_T) k_pick(const float *__restrict__ X, in
     pick_center(X, n, d, w, D2, bsum, nb, u, j, mode_w, idx_out, C_out, stop, status, ps);
 }
 
-// p_i = w_i * D2_i summed per block of SB rows; D2 refreshed against the newest center c (round
-// j = index of c; init: D2 = distance to c), A = index of the nearest center so far, cc[a] =
-// ||c - c_a||^2 for the earlier centers (skip test above).  The block's threads test its rows in
-// parallel; the rows that need a distance go to a list that the 8 warps work through (one warp per
-// row); the block sum is a fixed tree over the rows.
+// D2 refreshed against the newest center c (round j = index of c; round 0: D2 = distance to c), A =
+// the index of the nearest center so far.  Every test that only decides whether a row can change is
+// made in FP32 on shadow copies with margins that make it certified: D2f = D2 rounded up, ccf[a] =
+// ||c - c_a||^2 rounded down (skip test above), the FP32 (or BF16-copy) distance with its error bound.
+// FP64 work is left to the rows that may change (their double-float distance, compared with D2) and to
+// the blocks where a row did change: such a block recomputes p_i = w_i D2_i summed by a fixed tree,
+// the others keep their sum, whose bits a recomputation would give again.
 template <int VW>
 __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ X, int64_t n, int64_t d,
-                                                   const float *__restrict__ w,
-                                                   const float *__restrict__ c, int64_t j,
-                                                   double *__restrict__ D2, int32_t *__restrict__ A,
-                                                   const double *__restrict__ cc, double *__restrict__ bsum,
-                                                   const int *__restrict__ stop, const __nv_bfloat16 *__restrict__ Xq,
-                                                   const float *__restrict__ xresid) {
+                                                      const float *__restrict__ w,
+                                                      const float *__restrict__ c, int64_t j,
+                                                      double *__restrict__ D2, float *__restrict__ D2f,
+                                                      int32_t *__restrict__ A, const float *__restrict__ ccf,
+                                                      double *__restrict__ bsum, const int *__restrict__ stop,
+                                                      const __nv_bfloat16 *__restrict__ Xq,
+                                                      const float *__restrict__ xresid) {
     if (*stop) return;
-    __shared__ double nd_s[256];
+    __shared__ double sh[256];
     __shared__ int list[SB];
-    __shared__ int nlist;
+    __shared__ int nlist, changed;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
-    if (tid == 0) nlist = 0;
+    if (tid == 0) {
+        nlist = 0;
+        changed = j == 0;
+    }
     __syncthreads();
     if (tid < SB) {
         const int64_t i = r0 + tid;
-        double od = 0.0;
         if (i < r1) {
-            bool skip = false;
-            if (j > 0) {
-                od = D2[i];
-                skip = cc[A[i]] > 4.0 * od * (1.0 + 1e-6);
-            }
+            // ccf <= cc and D2f >= D2, so this implies cc > 4 D2 (1 + 1e-6)
+            const bool skip = j > 0 && ccf[A[i]] > 4.f * D2f[i] * (1.f + 4e-6f);
             if (!skip) list[atomicAdd(&nlist, 1)] = tid;
         }
-        nd_s[tid] = od;
-    } else {
-        nd_s[tid] = 0.0;
     }
     __syncthreads();
     const int m = nlist;
-    // lpr lanes per listed row (32 / lpr rows per warp at a time), so that short rows keep the
-    // lanes busy and their sums take fewer butterfly steps
+    // lpr lanes per listed row (32 / lpr rows per warp at a time)
     const int lpr = lanes_per_row_d2(d, VW), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
-    // relative error bound of the plain FP32 distance below: each difference rounded once, each
-    // fma-accumulated square once, at most d terms per lane and five butterfly additions
+    // relative error bound of the FP32 distances below (each difference rounded once, each
+    // fma-accumulated square once, at most d terms per lane, five butterfly additions), with room for
+    // the rounding of the product that applies it
     const float g32 = (float)(d + 40) * 5.9604645e-8f;
     for (int e0 = wid * rpw; e0 < m; e0 += 8 * rpw) {
         const int e = e0 + sub;
         const bool has = e < m;
         const int t = has ? list[e] : 0;
         const int64_t i = r0 + t;
-        // first a plain FP32 distance: when it shows, with its error bound, that the new center is
-        // farther than the current D^2, D^2 keeps its bits and the double-float distance is not
-        // needed (the update below would not change anything)
         bool need = has;
         if (j > 0) {
+            // above D2 whatever the rounding of the product
+            const float dold = has ? D2f[i] * (1.f + 2e-6f) : 0.f;
             if (Xq) {
-                // with the BF16 copy (d % 8 == 0): ||x - c|| >= ||x~ - c|| - ||x~ - x||, ||x~ - x|| <= the
-                // row's residual; when that lower bound already exceeds D, the FP32 row is not read
+                // ||x - c|| >= ||x~ - c|| - ||x~ - x|| with x~ the BF16 copy (d % 8 == 0) and ||x~ - x|| <= the
+                // row's residual: when that bound exceeds D the FP32 row is not read
                 float a16 = 0.f;
                 if (has) {
                     const uint4 *q8 = reinterpret_cast<const uint4 *>(Xq + i * d);
@@ -267,12 +272,15 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
                 }
                 for (int o = lpr >> 1; o > 0; o >>= 1) a16 += __shfl_xor_sync(0xffffffffu, a16, o);
                 if (has) {
-                    const double lo = sqrt(fmax((double)a16 * (1.0 - (double)g32), 0.0)) * (1.0 - 1e-12) - (double)xresid[i];
-                    const double L = lo > 0.0 ? lo * lo * (1.0 - 1e-12) : 0.0;
-                    need = !(L * (1.0 - 1e-9) > nd_s[t]);
+                    // a lower bound of ||x~ - c|| (sqrtf is correctly rounded; the factor covers it and the
+                    // product), then of ||x - c||^2
+                    const float lo = sqrtf(fmaxf(a16 * (1.f - g32), 0.f)) * (1.f - 2.4e-7f) - xresid[i];
+                    const float L = lo > 0.f ? lo * lo * (1.f - 1e-6f) : 0.f;
+                    need = !(L > dold);
                 }
                 if (!__any_sync(0xffffffffu, need)) continue;
             }
+            // the FP32 distance: when its lower bound exceeds D, D^2 keeps its bits
             float a32 = 0.f;
             if (need) {
                 const float *x = X + i * d;
@@ -296,7 +304,7 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
                 }
             }
             for (int o = lpr >> 1; o > 0; o >>= 1) a32 += __shfl_xor_sync(0xffffffffu, a32, o);
-            need = need && !((double)a32 * (1.0 - (double)g32) > nd_s[t] * (1.0 + 1e-9));
+            need = need && !(a32 * (1.f - g32) > dold);
         }
         if (!__any_sync(0xffffffffu, need)) continue;
         DF acc;
@@ -318,30 +326,34 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
             }
         }
         const double dist = group_sum_df(acc, lpr);
-        if (need && sl == 0 && (j == 0 || dist < nd_s[t])) {
-            nd_s[t] = dist;
+        if (need && sl == 0 && (j == 0 || dist < D2[i])) {
             D2[i] = dist;
+            D2f[i] = __double2float_ru(dist);
             A[i] = (int32_t)j;
+            changed = 1;
         }
     }
     __syncthreads();
+    if (!changed) return;
     double p = 0.0;
-    if (tid < SB && r0 + tid < r1) p = (w ? (double)w[r0 + tid] : 1.0) * nd_s[tid];
-    const double s = block_tree_sum_d(p, nd_s);
+    if (tid < SB && r0 + tid < r1) p = (w ? (double)w[r0 + tid] : 1.0) * D2[r0 + tid];
+    const double s = block_tree_sum_d(p, sh);
     if (tid == 0) bsum[blockIdx.x] = s;
 }
 
 // One CTA of PICK_T threads after each round's D^2 update: picks center j and measures it against the
-// earlier centers (cc, for the next round's skip test; double-float, lpr lanes per center)
+// earlier centers (ccf, rounded down, for the next round's skip test; double-float, lpr lanes per center)
 __global__ void __launch_bounds__(PICK_T) k_pick_cc(const float *__restrict__ X, int64_t n, int64_t d,
                                                     const float *__restrict__ w, double *__restrict__ D2,
                                                     const double *__restrict__ bsum, int64_t nb,
                                                     const double *__restrict__ u, int64_t j, int64_t k,
                                                     int64_t *__restrict__ idx_out, float *__restrict__ C_out,
-                                                    double *__restrict__ cc, int *stop, int *status) {
+                                                    float *__restrict__ D2f, float *__restrict__ ccf, int *stop,
+                                                    int *status) {
     __shared__ PickShared ps;
     if (*stop) return;
     const int64_t pick = pick_center(X, n, d, w, D2, bsum, nb, u, j, 0, idx_out, C_out, stop, status, ps);
+    if (pick >= 0 && threadIdx.x == 0) D2f[pick] = 0.f;
     if (pick < 0 || j + 1 >= k) return;
     __syncthreads();  // the new center's row in C_out
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -354,7 +366,7 @@ __global__ void __launch_bounds__(PICK_T) k_pick_cc(const float *__restrict__ X,
         if (has)
             for (int64_t t = sl; t < d; t += lpr) acc.add_sqdiff(cj[t], C_out[a * d + t]);
         const double v = group_sum_df(acc, lpr);
-        if (has && sl == 0) cc[a] = v;
+        if (has && sl == 0) ccf[a] = __double2float_rd(v);
     }
 }
 
@@ -389,12 +401,13 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
               const double *u, int64_t *idx_out, float *C_out, const void *Xq, const float *xresid) {
     const int64_t nb = ceil_div(n, SB);
     WsPlan p;
-    size_t o_d2 = p.take<double>(n), o_a = p.take<int32_t>(n), o_cc = p.take<double>(k), o_b = p.take<double>(nb),
-           o_stop = p.take<int>(2);
+    size_t o_d2 = p.take<double>(n), o_d2f = p.take<float>(n), o_a = p.take<int32_t>(n), o_cc = p.take<float>(k),
+           o_b = p.take<double>(nb), o_stop = p.take<int>(2);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
-    double *D2 = ws_at<double>(ws, o_d2), *bsum = ws_at<double>(ws, o_b), *cc = ws_at<double>(ws, o_cc);
+    double *D2 = ws_at<double>(ws, o_d2), *bsum = ws_at<double>(ws, o_b);
+    float *D2f = ws_at<float>(ws, o_d2f), *ccf = ws_at<float>(ws, o_cc);
     int32_t *A = ws_at<int32_t>(ws, o_a);
     int *stop = ws_at<int>(ws, o_stop);
     cudaError_t e = cudaMemsetAsync(stop, 0, 2 * sizeof(int), c->stream);
@@ -421,14 +434,15 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
         const float *cprev = C_out + jc * d;
         prof_begin(c, "seed_d2");
         if (vec)
-            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, xq,
+            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, D2f, A, ccf, bsum, stop, xq,
                                                                 xresid);
         else
-            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, A, cc, bsum, stop, nullptr,
-                                                                nullptr);
+            k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, D2f, A, ccf, bsum, stop,
+                                                                nullptr, nullptr);
         prof_end(c);
         prof_begin(c, "seed_pick");
-        k_pick_cc<<<1, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, k, idx_out, C_out, cc, stop, c->status);
+        k_pick_cc<<<1, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, k, idx_out, C_out, D2f, ccf, stop,
+                                               c->status);
         prof_end(c);
         c->launches += 2;
     }
