@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
                                                       double *__restrict__ D2, float *__restrict__ D2f,
                                                       int32_t *__restrict__ A, const float *__restrict__ ccf,
                                                       double *__restrict__ bsum, const int *__restrict__ stop,
+                                                      const int64_t *__restrict__ dirty,
                                                       const __nv_bfloat16 *__restrict__ Xq,
                                                       const float *__restrict__ xresid) {
     if (*stop) return;
@@ -217,7 +218,8 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
     const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
     if (tid == 0) {
         nlist = 0;
-        changed = j == 0;
+        // the block of the last pick had that row's D^2 set to 0 since its sum was taken
+        changed = j == 0 || *dirty == (int64_t)blockIdx.x;
     }
     __syncthreads();
     if (tid < SB) {
@@ -349,11 +351,14 @@ __global__ void __launch_bounds__(PICK_T) k_pick_cc(const float *__restrict__ X,
                                                     const double *__restrict__ u, int64_t j, int64_t k,
                                                     int64_t *__restrict__ idx_out, float *__restrict__ C_out,
                                                     float *__restrict__ D2f, float *__restrict__ ccf, int *stop,
-                                                    int *status) {
+                                                    int64_t *__restrict__ dirty, int *status) {
     __shared__ PickShared ps;
     if (*stop) return;
     const int64_t pick = pick_center(X, n, d, w, D2, bsum, nb, u, j, 0, idx_out, C_out, stop, status, ps);
-    if (pick >= 0 && threadIdx.x == 0) D2f[pick] = 0.f;
+    if (pick >= 0 && threadIdx.x == 0) {
+        D2f[pick] = 0.f;
+        *dirty = pick / SB;  // its block sum is refreshed in the next round
+    }
     if (pick < 0 || j + 1 >= k) return;
     __syncthreads();  // the new center's row in C_out
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -402,7 +407,7 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     const int64_t nb = ceil_div(n, SB);
     WsPlan p;
     size_t o_d2 = p.take<double>(n), o_d2f = p.take<float>(n), o_a = p.take<int32_t>(n), o_cc = p.take<float>(k),
-           o_b = p.take<double>(nb), o_stop = p.take<int>(2);
+           o_b = p.take<double>(nb), o_stop = p.take<int>(2), o_dirty = p.take<int64_t>(1);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
@@ -410,7 +415,9 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     float *D2f = ws_at<float>(ws, o_d2f), *ccf = ws_at<float>(ws, o_cc);
     int32_t *A = ws_at<int32_t>(ws, o_a);
     int *stop = ws_at<int>(ws, o_stop);
+    int64_t *dirty = ws_at<int64_t>(ws, o_dirty);
     cudaError_t e = cudaMemsetAsync(stop, 0, 2 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dirty, 0xff, sizeof(int64_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(idx_out, 0xff, sizeof(int64_t) * k, c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "seed memset");
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
@@ -434,15 +441,15 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
         const float *cprev = C_out + jc * d;
         prof_begin(c, "seed_d2");
         if (vec)
-            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, D2f, A, ccf, bsum, stop, xq,
-                                                                xresid);
+            k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, D2f, A, ccf, bsum, stop,
+                                                                dirty, xq, xresid);
         else
             k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, D2f, A, ccf, bsum, stop,
-                                                                nullptr, nullptr);
+                                                                dirty, nullptr, nullptr);
         prof_end(c);
         prof_begin(c, "seed_pick");
         k_pick_cc<<<1, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, k, idx_out, C_out, D2f, ccf, stop,
-                                               c->status);
+                                               dirty, c->status);
         prof_end(c);
         c->launches += 2;
     }
