@@ -589,9 +589,7 @@ def run_highdim(env, args):
     def whole():
         # norms, BF16 copy and residuals in one read of X
         B.kmeans_ingest(Xg, copy=False, xnorm=xnorm, Xq=Xop, resid=Xr, quantize=form == "bf16", ctx=ctx)
-        # k-means++ filters its rows through the BF16 copy where the form has one
-        B.kmeans_seed_pp(Xg, k, ug, C_out=Ca, Xq=Xop if form == "bf16" else None,
-                         xresid=Xr if form == "bf16" else None, ctx=ctx)
+        B.kmeans_seed_pp(Xg, k, ug, C_out=Ca, ctx=ctx)
         cur, nxt = Ca, Cb
         for t in range(iters):
             B.kmeans_assign(Xg, cur, Xop=Xop, Xop_scales=Xr, xnorm=xnorm, compute=form, engine=engine,
@@ -838,8 +836,7 @@ def run_stream(env_args):
     Y8, s8 = B.kmeans_quantize(Y, "fp8", ctx=ctx)
     idx = torch.empty(k, dtype=torch.int64, device=env.dev)
     C0 = torch.empty((k, r), dtype=torch.float32, device=env.dev)
-    # k-means++ filters its rows through the BF16 copy of the coordinates (the same picks)
-    S = env.once(lambda: B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=C0, Xq=Yb, xresid=Yr, ctx=ctx))
+    S = env.once(lambda: B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=C0, ctx=ctx))
     ctx.sync()
 
     F = 2.0 * n * k * r + n * r
@@ -911,9 +908,9 @@ def run_stream(env_args):
                 B.kmeans_quantize(Xg[r0:r1], "bf16", Xq=Xb[r0:r1], residuals=False, ctx=ctx)
                 B.kmeans_project_block(Xb[r0:r1], V, Y=Y[r0:r1], ctx=ctx)
         B.kmeans_row_norms(Y, xnorm=yn, ctx=ctx)
-        # the BF16 copy serves the seeding's row filter (and the BF16 form's assignment)
-        B.kmeans_quantize(Y, "bf16", Xq=Yb, scales=Yr, ctx=ctx)
-        B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=Ca, Xq=Yb, xresid=Yr, ctx=ctx)
+        if pf == "bf16":
+            B.kmeans_quantize(Y, "bf16", Xq=Yb, scales=Yr, ctx=ctx)
+        B.kmeans_seed_pp(Y, k, ug, idx_out=idx, C_out=Ca, ctx=ctx)
         cur, nxt = Ca, Cb
         for t in range(iters):
             B.kmeans_assign(Y, cur, Xop=Yb if pf == "bf16" else None, Xop_scales=Yr if pf == "bf16" else None,
@@ -928,9 +925,9 @@ def run_stream(env_args):
     pipeline = {"projection_bf16": proj_roof(P16, 2), "projection_tf32": proj_roof(P32, 4),
                 "seed_ms": S["ms"], "iterations": iters, "total_ms": W["ms"],
                 "gflops_whole_run": Fw / (W["ms"] * 1e-3) / 1e9,
-                "note": "whole run from device-resident BF16 points: 31 projections, norms, the BF16 copy of Y "
-                        "(the seeding's row filter and the BF16 form's operand), k-means++ (k=1000 rounds over Y), "
-                        "20 Lloyd iterations in the primary form; seeding time counted, its flops not"}
+                "note": "whole run from device-resident BF16 points: 31 projections, norms, (BF16 copy of Y for "
+                        "the BF16 form), k-means++ (k=1000 rounds over Y), 20 Lloyd iterations in the primary form; "
+                        "seeding time counted, its flops not"}
 
     e2e = None
     if not args.no_e2e:

@@ -216,7 +216,9 @@ int kmeans_seed_pp(gbkm_ctx *ctx, const float *X, int64_t n, int64_t d, const fl
  * ||x - c|| >= ||bf16(x) - c|| - ||bf16(x) - x|| (evaluated in FP32 with its error bound); when the
  * bound already exceeds the row's D^2 the FP32 row is not read.  Xq: n x d bfloat16, 16-byte
  * aligned, d % 8 == 0 (otherwise the call runs as kmeans_seed_pp); xresid: n FP32, the residuals
- * rounded up.  Other arguments and results as kmeans_seed_pp. */
+ * rounded up.  Other arguments and results as kmeans_seed_pp.  It pays where the bound decides most
+ * rows (clusters far apart compared with the rows' rounding); on the mixtures measured here, whose
+ * far distances differ by about the bound's slack, it was no faster than kmeans_seed_pp. */
 int kmeans_seed_pp_q(gbkm_ctx *ctx, const float *X, const void *Xq, const float *xresid, int64_t n, int64_t d,
                      const float *w, int64_t k, const double *u, int64_t *idx_out, float *C_out);
 
@@ -374,6 +376,18 @@ int kmeans_batch_replay(gbkm_ctx *ctx);
  * up to a power of two) for the life of the process and, when the environment
  * variable GBKM_TUNE_CACHE names a file, across processes.  Synchronises. */
 int kmeans_autotune(gbkm_ctx *ctx, int32_t compute, int64_t d, int64_t ncols, int32_t *bn_out);
+
+/* The autotuner for the single-problem assignment (no paper counterpart): times kmeans_assign of a
+ * synthetic 32,768-point problem of dimension d against k centers over the candidate configurations --
+ * the tcgen05 engine with center-chunk widths of 64, 128 and 256 columns (distinct chunkings only) and
+ * stage rings of 2, 3 or as many stages as fit in shared memory, and for GBKM_F32 the CUDA-core engine
+ * -- and keeps the fastest (host outputs, each may be NULL: *engine_out a gbkm_engine, *bn_out the
+ * chunk width, *stages_out the ring depth, 0 for as many as fit).  From then on, kmeans_assign with
+ * GBKM_ENGINE_AUTO on a shape of this (GPU, compute, d, k rounded up to a power of two) takes that
+ * configuration; labels are exact in every configuration.  Cached per process and, when GBKM_TUNE_CACHE
+ * names a file, across processes.  compute: GBKM_F32 or GBKM_BF16.  Synchronises. */
+int kmeans_autotune_assign(gbkm_ctx *ctx, int32_t compute, int64_t d, int64_t k, int32_t *engine_out,
+                           int32_t *bn_out, int32_t *stages_out);
 
 /* ------------------------------------------------------------------ A9: learned candidate proposal */
 

@@ -85,6 +85,8 @@ _SIGS = {
     "kmeans_batch_run": (ct.c_int, [_vp, ct.POINTER(Problem), _i64, _i64, _i64, _i32, _i32]),
     "kmeans_batch_replay": (ct.c_int, [_vp]),
     "kmeans_autotune": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32)]),
+    "kmeans_autotune_assign": (ct.c_int, [_vp, _i32, _i64, _i64, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
+                                          ct.POINTER(ct.c_int32)]),
     "kmeans_mlp_param_count": (ct.c_int64, [_i64, _i64, _i64]),
     "kmeans_gemm_bf16": (ct.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _i32, _i32, _vp, _i64]),
     "kmeans_mlp_forward": (ct.c_int, [_vp, ct.POINTER(MLP), _vp, _i64, _vp, _vp, _i32, _i32]),
@@ -612,6 +614,17 @@ def kmeans_autotune(d, ncols, compute="bf16", ctx=None):
     out = ct.c_int32()
     c.check(load().kmeans_autotune(c.handle, DTYPES[compute], d, ncols, ct.byref(out)))
     return int(out.value)
+
+
+def kmeans_autotune_assign(d, k, compute="f32", ctx=None):
+    """Tune the single-problem assignment for this shape (engine, chunk width, stage ring); later
+    kmeans_assign calls with engine="auto" on the shape use the choice.  Returns a dict."""
+    c = ctx or default_context()
+    c.bind_stream()
+    eng, bn, st = ct.c_int32(), ct.c_int32(), ct.c_int32()
+    c.check(load().kmeans_autotune_assign(c.handle, DTYPES[compute], d, k, ct.byref(eng), ct.byref(bn), ct.byref(st)))
+    names = {v: k_ for k_, v in ENGINES.items()}
+    return {"engine": names.get(int(eng.value), int(eng.value)), "bn": int(bn.value), "stages": int(st.value)}
 
 
 # ------------------------------------------------------------------ A9

@@ -468,6 +468,18 @@ int kmeans_assign(gbkm_ctx *c, const void *Xop, const float *Xop_scales, const f
         if (!use_tc && o.compute != GBKM_F32)
             return set_error(c, GBKM_EUNSUPPORTED, "assign: low-precision forms need the tcgen05 engine");
     }
+    // a configuration the autotuner chose for this shape (kmeans_autotune_assign) replaces the default
+    // one under GBKM_ENGINE_AUTO: the engine, the center-chunk width and the stage-ring depth
+    gbkm::TuneChoice tuned{0, 0, 0};
+    const bool has_tune = o.engine == GBKM_ENGINE_AUTO && gbkm::tuned_assign(c, o.compute, d, k, &tuned) &&
+                          (tuned.engine == GBKM_ENGINE_SIMT ? o.compute == GBKM_F32 : tc_ok);
+    if (has_tune) use_tc = tuned.engine == GBKM_ENGINE_TCGEN05;
+    struct CapGuard {
+        gbkm_ctx *c;
+        int bn, st;
+        ~CapGuard() { c->bn_cap = bn, c->stage_cap = st; }
+    } capg{c, c->bn_cap, c->stage_cap};
+    if (has_tune && use_tc) c->bn_cap = tuned.bn, c->stage_cap = tuned.stages;
     DeviceGuard g(c->device);
     const int64_t k_pad = use_tc ? ceil_div(k, 16) * 16 : k;
     // BF16 centers as two BF16 terms (hi + lo) on request: the near-tie bound then grows with the
@@ -639,6 +651,21 @@ int kmeans_autotune(gbkm_ctx *c, int32_t compute, int64_t d, int64_t ncols, int3
     int rc = gbkm::autotune_bn(c, compute, d, ncols, &bn);
     *bn_out = bn;
     return rc;
+}
+
+int kmeans_autotune_assign(gbkm_ctx *c, int32_t compute, int64_t d, int64_t k, int32_t *engine_out, int32_t *bn_out,
+                           int32_t *stages_out) {
+    if (!c) return GBKM_EINVAL;
+    if (d < 1 || k < 1 || k > 65536 || (compute != GBKM_F32 && compute != GBKM_BF16))
+        return set_error(c, GBKM_EINVAL, "autotune_assign: bad arguments (F32 or BF16, 1 <= k <= 65536)");
+    DeviceGuard g(c->device);
+    gbkm::TuneChoice t{0, 0, 0};
+    const int rc = gbkm::autotune_assign(c, compute, d, k, &t);
+    if (rc != GBKM_OK) return rc;
+    if (engine_out) *engine_out = t.engine;
+    if (bn_out) *bn_out = t.bn;
+    if (stages_out) *stages_out = t.stages;
+    return GBKM_OK;
 }
 
 int64_t kmeans_mlp_param_count(int64_t d_in, int64_t hidden, int64_t k) {

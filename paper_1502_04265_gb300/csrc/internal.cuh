@@ -46,6 +46,7 @@ struct gbkm_ctx {
     uint64_t graph_epoch = 0;      // ws_epoch when graph_exec was recorded (its tables live in ws)
     cudaStream_t cap_stream = nullptr;  // private stream the batched run is recorded on
     int bn_cap = 0;                // center-chunk width of the tcgen05 assignment (0: 256); autotuner knob
+    int stage_cap = 0;             // stage-ring depth cap of the tcgen05 assignment (0: as many as fit); autotuner knob
     uint64_t wait_ns = 0;          // limit of every bounded device wait (0: the default, 2 s)
     int fail_alloc = 0;            // diagnostics: the next fail_alloc workspace growths fail as if out of memory
     int stall_loads = 0;           // diagnostics: tensor-core launches issue no copies (their waits run out)
@@ -327,5 +328,14 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
               int flags, const int *bn_caps);
 // fastest center-chunk width (64, 128 or 256 columns) of the tcgen05 assignment for this shape
 int autotune_bn(gbkm_ctx *c, int dtype, int64_t d, int64_t ncols, int *bn_out);
+// the single-problem assignment's tuned configuration: engine (GBKM_ENGINE_SIMT or _TCGEN05), center-chunk
+// width and stage-ring depth (0: as many as fit)
+struct TuneChoice {
+    int engine, bn, stages;
+};
+// times the candidates for this shape (or returns the cached choice)
+int autotune_assign(gbkm_ctx *c, int dtype, int64_t d, int64_t ncols, TuneChoice *out);
+// the cached choice for this shape, without timing anything; false when the shape was never tuned
+bool tuned_assign(gbkm_ctx *c, int dtype, int64_t d, int64_t ncols, TuneChoice *out);
 int make_batch_tmaps(gbkm_ctx *c, int dtype, const BProb &P, void *host_maps3);
 }  // namespace gbkm

@@ -306,25 +306,8 @@ __device__ __forceinline__ float warp_direct_d2_rx(const float4 (&xr)[8], const 
     return v;
 }
 
-// the same distance with both the row and the center already in registers
-__device__ __forceinline__ float warp_direct_d2_rr(const float4 (&xr)[8], const float4 (&cv)[8]) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float e0 = xr[q].x - cv[q].x, e1 = xr[q].y - cv[q].y, e2 = xr[q].z - cv[q].z, e3 = xr[q].w - cv[q].w;
-        a0 = fmaf(e0, e0, a0);
-        a1 = fmaf(e1, e1, a1);
-        a2 = fmaf(e2, e2, a2);
-        a3 = fmaf(e3, e3, a3);
-    }
-    float v = (a0 + a1) + (a2 + a3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// (2 CTAs per SM: 16 warps, each with a flagged row and its first two candidates' loads in flight)
-__global__ void __launch_bounds__(256, 2) k_recheck(const float *__restrict__ X, int64_t d,
+// (3 CTAs per SM: 24 warps, each with one flagged row's loads in flight)
+__global__ void __launch_bounds__(256, 3) k_recheck(const float *__restrict__ X, int64_t d,
                                                  const float *__restrict__ C, int64_t k,
                                                  const int32_t *__restrict__ list,
                                                  const int32_t *__restrict__ cand,
@@ -376,32 +359,7 @@ __global__ void __launch_bounds__(256, 2) k_recheck(const float *__restrict__ X,
         };
         if (nc > 0 && nc <= CAND_MAX) {
             // the certified band holds these centers (increasing index): compare by (distance, index)
-            int q0 = 0;
-            if (cached && nc >= 2) {
-                // the first two candidates' rows are loaded together with the point's
-                const int ja = cf[1], jb = cf[2];
-                if (ja >= 0 && ja < k && jb >= 0 && jb < k) {
-                    const int nv = (int)(d / 4);
-                    const float4 *ca4 = reinterpret_cast<const float4 *>(C + (int64_t)ja * d);
-                    const float4 *cb4 = reinterpret_cast<const float4 *>(C + (int64_t)jb * d);
-                    float4 ca[8], cb[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const bool in = lane + 32 * q < nv;
-                        ca[q] = in ? __ldg(ca4 + lane + 32 * q) : xr[q];
-                        cb[q] = in ? __ldg(cb4 + lane + 32 * q) : xr[q];
-                    }
-                    const float va = warp_direct_d2_rr(xr, ca), vb = warp_direct_d2_rr(xr, cb);
-                    best = va;
-                    arg = ja;
-                    if (vb < best || (vb == best && jb < arg)) {
-                        best = vb;
-                        arg = jb;
-                    }
-                    q0 = 2;
-                }
-            }
-            for (int q = q0; q < nc; ++q) {
+            for (int q = 0; q < nc; ++q) {
                 const int j = cf[1 + q];
                 if (j < 0 || j >= k) {
                     if (lane == 0) status_raise(status, ST_BOUNDS);
@@ -432,7 +390,7 @@ __global__ void __launch_bounds__(256, 2) k_recheck(const float *__restrict__ X,
 
 int launch_recheck(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *C, int64_t k,
                    const AssignOut &o, int64_t *n_rechecked, const Escalation *esc, const int32_t *row_map) {
-    unsigned blocks = (unsigned)c->sm_count * 2;
+    unsigned blocks = (unsigned)c->sm_count * 3;
     Escalation e{};
     if (esc) e = *esc;
     k_recheck<<<blocks, 256, 0, c->stream>>>(X, d, C, k, o.flag_list, o.cand, o.flag_count, n, o.labels,

@@ -1666,7 +1666,8 @@ struct Plan {
     size_t smem;
 };
 
-static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra_smem = 0, int bn_align = 16) {
+static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra_smem = 0, int bn_align = 16,
+                 int stage_cap = 0) {
     Plan p;
     const int esize = (form == F_BF16 || form == F_BF16X2) ? 2 : (form == F_FP8 ? 1 : 4);
     p.n_chunks = (int)ceil_div(k_pad, bn_cap);
@@ -1678,6 +1679,7 @@ static Plan plan(int form, int64_t d, int64_t k_pad, int bn_cap = 256, int extra
     p.stage_bytes = (x3 ? 2 : 1) * p.a_bytes + (two_b ? 2 : 1) * p.b_bytes;
     p.tx_bytes = p.a_bytes + (two_b ? 2 : 1) * p.b_bytes;
     p.stages = (int)std::min<int64_t>(MAX_STAGES, (MAX_DYN_SMEM - 2048 - extra_smem) / p.stage_bytes);
+    if (stage_cap >= 2) p.stages = std::min(p.stages, stage_cap);
     p.tmem_cols = (2 * p.bn <= 256) ? 256 : 512;
     p.smem = (size_t)p.stages * p.stage_bytes + 1024 + 1024 + extra_smem;
     return p;
@@ -1810,7 +1812,7 @@ int launch_assign_tc(gbkm_ctx *c, int dtype, const void *Xop, const float *Xscal
     const int form = (dtype == GBKM_BF16) ? (cp.cop_lo ? F_BF16X2 : F_BF16)
                                           : (dtype == GBKM_FP8E4M3 ? F_FP8 : F_TF32X3);
     const bool bf = form == F_BF16 || form == F_BF16X2;
-    const Plan p = plan(form, d, k_pad, c->bn_cap > 0 ? c->bn_cap : 256, ARGMIN_EXTRA_SMEM);
+    const Plan p = plan(form, d, k_pad, c->bn_cap > 0 ? c->bn_cap : 256, ARGMIN_EXTRA_SMEM, 16, c->stage_cap);
     const CUtensorMapDataType dt = bf                ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                    : (form == F_FP8) ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;

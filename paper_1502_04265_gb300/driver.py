@@ -43,9 +43,7 @@ def lloyd(X, k, iters, u, w=None, compute="f32", engine="auto", C0=None, ctx=Non
     if compute in ("bf16", "fp8"):
         Xop, scales = B.kmeans_quantize(X, compute, ctx=ctx)
     if C0 is None:
-        # with a BF16 copy at hand, k-means++ filters its rows through it (the same picks)
-        bq = compute == "bf16"
-        idx, C = B.kmeans_seed_pp(X, k, u, w=w, Xq=Xop if bq else None, xresid=scales if bq else None, ctx=ctx)
+        idx, C = B.kmeans_seed_pp(X, k, u, w=w, ctx=ctx)
     else:
         C = C0.clone()
     labels = torch.empty(n, dtype=torch.int32, device=dev)

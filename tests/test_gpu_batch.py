@@ -115,3 +115,24 @@ def test_batch_replay_reproduces_the_run_and_is_invalidated_by_other_calls(gb):
         gb.kmeans_batch_replay(ctx=ctx)
     ctx.sync()
     ctx.close()
+
+
+@pytest.mark.parametrize("compute", ["f32", "bf16"])
+def test_autotune_assign_choice_keeps_labels_exact(gb, orc, compute):
+    """The single-problem tuner picks an engine, a chunk width and a stage ring for the shape; the
+    assignment under engine="auto" then runs in that configuration and its labels stay exact."""
+    d, k = 128, 300
+    choice = gb.kmeans_autotune_assign(d, k, compute)
+    assert choice["engine"] in ("simt", "tcgen05")
+    assert choice["bn"] in (0, 64, 128, 256) and choice["stages"] in (0, 2, 3)
+    if compute == "bf16":
+        assert choice["engine"] == "tcgen05"
+    assert gb.kmeans_autotune_assign(d, k, compute) == choice   # cached
+    X, _ = synth.gaussian_mixture(6000, d, 40, seed=31)
+    C = synth.gaussian_mixture(k, d, 40, seed=32)[0]
+    Xg, Cg = torch.from_numpy(X).to(DEV), torch.from_numpy(C).to(DEV)
+    Xop, sc = gb.kmeans_quantize(Xg, "bf16") if compute == "bf16" else (None, None)
+    lab = gb.kmeans_assign(Xg, Cg, Xop=Xop, Xop_scales=sc, compute=compute, engine="auto")
+    gb.gbkm_sync()
+    from parity_util import assert_labels_match
+    assert_labels_match(orc, X, C.astype(np.float64), lab.cpu().numpy())
