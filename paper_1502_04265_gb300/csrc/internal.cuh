@@ -307,7 +307,9 @@ struct BProb {
     int32_t *labels;         // seeds x n
     double *D2;              // seeds x n
     int32_t *A;              // seeds x n: nearest chosen center so far (k-means++ skip test)
-    double *cc;              // seeds x k: squared distances of the newest center to the earlier ones
+    float *D2f;              // seeds x n: D2 rounded up to FP32 (the certified tests' copy)
+    float *ccf;              // seeds x k: squared distances of the newest center to the earlier ones, rounded down
+    int64_t *dirty;          // seeds: the block of the last pick (its sum is refreshed in the next round)
     double *bsum;            // seeds x nb
     int32_t *stop;           // seeds
     const double *u;         // seeds x k uniforms

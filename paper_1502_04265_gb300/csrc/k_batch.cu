@@ -88,14 +88,19 @@ __global__ void k_b_seed_first(const BProb *__restrict__ probs, const int2 *__re
     if (i0 < 0) i0 = 0;
     float *c = P.C[0] + (int64_t)ps.y * P.k * P.d;
     for (int64_t t = threadIdx.x; t < P.d; t += blockDim.x) c[t] = P.X[i0 * P.d + t];
-    if (threadIdx.x == 0) P.stop[ps.y] = 0;
+    if (threadIdx.x == 0) {
+        P.stop[ps.y] = 0;
+        P.dirty[ps.y] = -1;
+    }
 }
 
 // round r >= 1: D^2 of every seed of the block's problem against that seed's center r-1, and the
-// block sum of D^2 per seed (a fixed tree over the rows).  A row whose nearest center a satisfies
-// ||c_{r-1} - c_a||^2 > 4 D^2 keeps D^2 without reading the row (k-means++ skip test, exact: the
-// new center cannot come closer); the block's threads test the rows in parallel and the 8 warps
-// work through the list of rows that need a distance (one warp per row).
+// block sum of D^2 per seed (a fixed tree over the rows).  As in the single-problem update, every test
+// that only decides whether a row can change is certified in FP32 on shadow copies (D2f = D2 rounded
+// up, ccf = the center distances rounded down): the skip test (a row whose nearest center a satisfies
+// ||c_{r-1} - c_a||^2 > 4 D^2 keeps D^2: the new center cannot come closer), then a plain FP32 distance
+// with its error bound.  Only rows that may change take the double-float distance, and only blocks
+// where a row changed (or the last pick's block) recompute their sum; the others keep the same bits.
 __global__ void __launch_bounds__(256) k_b_d2(const BProb *__restrict__ probs, const int2 *__restrict__ blocks,
                                               int r) {
     const int2 b = blocks[blockIdx.x];
@@ -103,49 +108,69 @@ __global__ void __launch_bounds__(256) k_b_d2(const BProb *__restrict__ probs, c
     if (r >= P.k) return;
     __shared__ double nd_s[256];
     __shared__ int list[RB];
-    __shared__ int nlist;
+    __shared__ int nlist, changed;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t blk = b.y / RB;
     const int64_t jc = r - 1;
     const int64_t r0 = b.y, r1 = min(P.n, (int64_t)b.y + RB);
+    const float g32 = (float)(P.d + 40) * 5.9604645e-8f;
     for (int s = 0; s < P.seeds; ++s) {
         if (P.stop[s]) continue;  // uniform over the block
         const float *c = P.C[0] + ((int64_t)s * P.k + jc) * P.d;
         double *D2 = P.D2 + (int64_t)s * P.n;
+        float *D2f = P.D2f + (int64_t)s * P.n;
         int32_t *A = P.A + (int64_t)s * P.n;
-        const double *cc = P.cc + (int64_t)s * P.k;
-        if (tid == 0) nlist = 0;
+        const float *ccf = P.ccf + (int64_t)s * P.k;
+        if (tid == 0) {
+            nlist = 0;
+            changed = jc == 0 || P.dirty[s] == blk;
+        }
         __syncthreads();
         if (tid < RB) {
             const int64_t i = r0 + tid;
-            double od = 0.0;
             if (i < r1) {
-                bool skip = false;
-                if (jc > 0) {
-                    od = D2[i];
-                    skip = cc[A[i]] > 4.0 * od * (1.0 + 1e-6);
-                }
+                const bool skip = jc > 0 && ccf[A[i]] > 4.f * D2f[i] * (1.f + 4e-6f);
                 if (!skip) list[atomicAdd(&nlist, 1)] = tid;
             }
-            nd_s[tid] = od;
-        } else {
-            nd_s[tid] = 0.0;
         }
         __syncthreads();
         const int m = nlist;
-        // lpr lanes per listed row (32 / lpr rows per warp at a time): short rows keep the lanes
-        // busy and their sums take fewer butterfly steps
         const bool v4 = (P.d % 4) == 0 && ((reinterpret_cast<uintptr_t>(P.X) & 15) == 0) &&
                         ((reinterpret_cast<uintptr_t>(c) & 15) == 0);
-        const int lpr = lanes_per_row(P.d, v4 ? 4 : 1), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
+        const int lpr = lanes_per_row_d2(P.d, v4 ? 4 : 1), rpw = 32 / lpr, sub = lane / lpr, sl = lane % lpr;
         for (int e0 = w * rpw; e0 < m; e0 += 8 * rpw) {
             const int e = e0 + sub;
             const bool has = e < m;
             const int t = has ? list[e] : 0;
             const int64_t i = r0 + t;
+            const float *x = P.X + i * P.d;
+            bool need = has;
+            if (jc > 0) {
+                float a32 = 0.f;
+                if (has) {
+                    if (v4) {
+                        for (int64_t q = sl; q < P.d / 4; q += lpr) {
+                            const float4 a4 = __ldg(reinterpret_cast<const float4 *>(x) + q);
+                            const float4 b4 = __ldg(reinterpret_cast<const float4 *>(c) + q);
+                            const float f0 = a4.x - b4.x, f1 = a4.y - b4.y, f2 = a4.z - b4.z, f3 = a4.w - b4.w;
+                            a32 = fmaf(f0, f0, a32);
+                            a32 = fmaf(f1, f1, a32);
+                            a32 = fmaf(f2, f2, a32);
+                            a32 = fmaf(f3, f3, a32);
+                        }
+                    } else {
+                        for (int64_t q = sl; q < P.d; q += lpr) {
+                            const float f = x[q] - c[q];
+                            a32 = fmaf(f, f, a32);
+                        }
+                    }
+                }
+                for (int o = lpr >> 1; o > 0; o >>= 1) a32 += __shfl_xor_sync(0xffffffffu, a32, o);
+                need = has && !(a32 * (1.f - g32) > D2f[i] * (1.f + 2e-6f));
+            }
+            if (!__any_sync(0xffffffffu, need)) continue;
             DF acc;
-            if (has) {
-                const float *x = P.X + i * P.d;
+            if (need) {
                 if (v4) {
                     for (int64_t q = sl; q < P.d / 4; q += lpr) {
                         const float4 a4 = __ldg(reinterpret_cast<const float4 *>(x) + q);
@@ -160,22 +185,25 @@ __global__ void __launch_bounds__(256) k_b_d2(const BProb *__restrict__ probs, c
                 }
             }
             const double dist = group_sum_df(acc, lpr);
-            if (has && sl == 0 && (jc == 0 || dist < nd_s[t])) {
-                nd_s[t] = dist;
+            if (need && sl == 0 && (jc == 0 || dist < D2[i])) {
                 D2[i] = dist;
+                D2f[i] = __double2float_ru(dist);
                 A[i] = (int32_t)jc;
+                changed = 1;
             }
         }
         __syncthreads();
-        const double v = (tid < RB && r0 + tid < r1) ? nd_s[tid] : 0.0;
-        const double tot = block_tree_sum_d(v, nd_s);
-        if (tid == 0) P.bsum[(int64_t)s * P.nb + blk] = tot;
+        if (changed) {
+            const double v = (tid < RB && r0 + tid < r1) ? D2[r0 + tid] : 0.0;
+            const double tot = block_tree_sum_d(v, nd_s);
+            if (tid == 0) P.bsum[(int64_t)s * P.nb + blk] = tot;
+        }
         __syncthreads();
     }
 }
 
-// round r >= 2: cc[s][a] = ||c_{r-1} - c_a||^2 (double-float) for a < r - 1, one warp per
-// (pair, earlier center); grid.y = pair
+// round r >= 2: ccf[s][a] = ||c_{r-1} - c_a||^2 (double-float, rounded down to FP32) for a < r - 1, one
+// warp per (pair, earlier center); grid.y = pair
 __global__ void __launch_bounds__(256) k_b_cc(const BProb *__restrict__ probs, const int2 *__restrict__ pairs, int r) {
     const int2 ps = pairs[blockIdx.y];
     const BProb &P = probs[ps.x];
@@ -193,7 +221,7 @@ __global__ void __launch_bounds__(256) k_b_cc(const BProb *__restrict__ probs, c
     if (has)
         for (int64_t t = sl; t < P.d; t += lpr) acc.add_sqdiff(C[jc * P.d + t], C[a * P.d + t]);
     const double v = group_sum_df(acc, lpr);
-    if (has && sl == 0) P.cc[(int64_t)ps.y * P.k + a] = v;
+    if (has && sl == 0) P.ccf[(int64_t)ps.y * P.k + a] = __double2float_rd(v);
 }
 
 __device__ double block_incl_scan_db(double v, double *sh) {
@@ -305,7 +333,11 @@ __global__ void __launch_bounds__(PICKB_T) k_b_pick(const BProb *__restrict__ pr
     }
     float *c = P.C[0] + ((int64_t)ps.y * P.k + r) * P.d;
     for (int64_t q = tid; q < P.d; q += PICKB_T) c[q] = P.X[pick * P.d + q];
-    if (tid == 0) const_cast<double *>(D2)[pick] = 0.0;
+    if (tid == 0) {
+        const_cast<double *>(D2)[pick] = 0.0;
+        P.D2f[(int64_t)ps.y * P.n + pick] = 0.f;
+        P.dirty[ps.y] = pick / RB;  // that block's sum is refreshed in the next round
+    }
 }
 
 // ---------------------------------------------------------------- per-iteration center preparation
@@ -780,9 +812,9 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         dmax = std::max(dmax, b.d);
         bn_max = std::max(bn_max, b.bn);
         // per-problem device buffers (sizes; carved below)
-        wbytes += 256 * 12 + b.n * 4 + (bf ? b.n * b.d * 2 : 0) + 2 * S * b.k * b.d * 4 + S * b.kps * 4 + 4 +
-                  S * b.kps * b.d * (bf ? 2 : 8) + S * b.n * 4 + S * b.n * 8 + S * b.n * 4 + S * b.k * 8 + 2 * 256 +
-                  S * b.nb * 8 + S * 4;
+        wbytes += 256 * 14 + b.n * 4 + (bf ? b.n * b.d * 2 : 0) + 2 * S * b.k * b.d * 4 + S * b.kps * 4 + 4 +
+                  S * b.kps * b.d * (bf ? 2 : 8) + S * b.n * 4 + S * b.n * 8 + S * b.n * 4 + S * b.n * 4 +
+                  S * b.k * 4 + S * 8 + 2 * 256 + S * b.nb * 8 + S * 4;
     }
     maxcb = std::max<int64_t>(1, ceil_div(dmax, 256));
     const int64_t npairs = count * S;
@@ -807,8 +839,10 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         b.cop_lo = bf ? nullptr : static_cast<void *>(carve<float>(cur, S * b.kps * b.d));
         b.labels = carve<int32_t>(cur, S * b.n);
         b.D2 = carve<double>(cur, S * b.n);
+        b.D2f = carve<float>(cur, S * b.n);
         b.A = carve<int32_t>(cur, S * b.n);
-        b.cc = carve<double>(cur, S * b.k);
+        b.ccf = carve<float>(cur, S * b.k);
+        b.dirty = carve<int64_t>(cur, S);
         b.bsum = carve<double>(cur, S * b.nb);
         b.stop = carve<int32_t>(cur, S);
     }
