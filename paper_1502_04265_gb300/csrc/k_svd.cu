@@ -6,8 +6,8 @@
 // of the result, and only the s x d matrix left over is decomposed.  All on the context's stream:
 //   1. Y = A' Omega (n x s): the tensor cores' 3xTF32 store GEMM (k_tc), or k_gemm_rows on the CUDA
 //      cores where the shape does not allow TMA tiles                       first read of A
-//   2. CholeskyQR2   k_gram (Y^T Y, FP32 blocks of 8 rows added in double-float), k_chol (FP64
-//                    Cholesky with a small diagonal shift, R^-1), Y <- Y R^-1; twice -> Q
+//   2. CholeskyQR2   k_gram (Y^T Y, FP32 blocks of 8 rows added in double-float), k_chol (double-
+//                    float Cholesky with a small diagonal shift, R^-1), Y <- Y R^-1; twice -> Q
 //   3. Bt = A'^T Q (d x s): k_tn_tc on the tensor cores (A's tiles transposed in shared memory,
 //      3xTF32, split over row ranges, the splits added in fixed order), or k_gemm_tn on the CUDA
 //      cores, split over row chunks added in fixed order                   second read of A
@@ -236,25 +236,66 @@ static int launch_gram(gbkm_ctx *c, const float *X, int64_t m, int64_t s, float2
     return cuda_check(c, cudaGetLastError(), "gram launch");
 }
 
+// ---------------------------------------------------------------- double-float arithmetic
+// A value is the unevaluated sum h + l of two FP32 numbers with |l| <= ulp(h) / 2 (Dekker 1971,
+// Knuth's TwoSum): about 48 significant bits on the FP32 pipe, which on this GPU runs 73 times
+// the FP64 rate.  Every step uses explicit round-to-nearest intrinsics, so nothing is contracted.
+struct F2 {
+    float h, l;
+};
+__device__ __forceinline__ F2 f2_quick(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    float s, e, t, f;
+    two_sum(a.h, b.h, s, e);
+    two_sum(a.l, b.l, t, f);
+    F2 r = f2_quick(s, __fadd_rn(e, t));
+    return f2_quick(r.h, __fadd_rn(r.l, f));
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return f2_quick(p, e);
+}
+__device__ __forceinline__ F2 f2_neg(F2 a) { return {-a.h, -a.l}; }
+// 1 / sqrt(d) for d > 0: rsqrtf's estimate and two Newton steps y <- y + y (1 - d y^2) / 2, the
+// residual 1 - d y^2 formed in double-float (its high part 1 - t.h is exact: t.h is near 1)
+__device__ __forceinline__ F2 f2_rsqrt(F2 d) {
+    F2 y = {rsqrtf(d.h), 0.f};
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const F2 t = f2_mul(f2_mul(d, y), y);
+        const float r = __fsub_rn(__fsub_rn(1.f, t.h), t.l);
+        y = f2_add(y, f2_quick(__fmul_rn(__fmul_rn(0.5f, y.h), r), 0.f));
+    }
+    return y;
+}
+
 // ---------------------------------------------------------------- Cholesky of G + shift I, R^-1
-// One CTA, the factor in shared memory (s rows of s + 1 values of type W; FP64 here: an FP32
-// factor with the shift FP32 needs leaves Q's columns short by that shift, which lowers every
-// singular value by about 3e-4 relative).  G = R^T R, R upper triangular;
-// shift = shift_rel * trace(G) / s is added to the diagonal, and a pivot that still falls to or
-// below a tiny floor is clamped and flagged in *status.  R^-1 overwrites R in place, one column at
-// a time: X R = I gives X[i][j] = -(sum_{i <= q < j} X[i][q] R[q][j]) / R[j][j], which reads the
-// finished columns of X and the column j of R that is replaced next.  Outputs R and Rinv (FP64,
-// each optional) and Rinv32.
-template <typename W>
+// One CTA in double-float.  G (s x s, FP64, symmetric) is first scaled by 2^-2e, a power of two that
+// brings its mean diagonal near 1 (so FP32's exponent range holds any FP64 Gram matrix of a piece),
+// and shift = shift_rel * trace(G) / s is added to the diagonal; R and R^-1 are scaled back by 2^e
+// and 2^-e, exactly.  G = R^T R with R upper triangular, right-looking: at pivot k every thread
+// forms y_k = 1 / sqrt(M_kk) itself (the same operations, the same bits), row k becomes R's row
+// (M_kj y_k), and the trailing matrix loses R_ki R_kj.  A pivot at or below a tiny floor is
+// clamped and flagged in *status.  Then X = R^-1, column by column: X_jj = y_j and
+// X_ij = -(sum_{i <= q < j} X_iq R_qj) y_j, the sums accumulated right-looking (when column q is
+// final its terms are added to every later column), one barrier per column.  Shared memory: hi and
+// lo planes of s rows of stride s + 1; R's strict upper triangle in place, X transposed into the
+// strict lower triangle, the diagonals of R and X in four vectors.  Outputs R (FP64, optional) and
+// Rinv32 = R^-1 in FP32.
 __global__ void __launch_bounds__(256) k_chol(const double *__restrict__ G, int64_t s, double shift_rel,
-                                              double *__restrict__ R, double *__restrict__ Rinv,
-                                              float *__restrict__ Rinv32, int *status) {
-    extern __shared__ __align__(8) unsigned char chol_smem[];
-    W *Rs = reinterpret_cast<W *>(chol_smem);
+                                              double *__restrict__ R, float *__restrict__ Rinv32, int *status) {
+    extern __shared__ __align__(16) float chol_smem[];
+    const int S = (int)s, L = S + 1, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float *H = chol_smem, *Lo = H + S * L;
+    float *rdh = Lo + S * L, *rdl = rdh + S, *yh = rdl + S, *yl = yh + S;
     __shared__ double red[256];
-    __shared__ W inv_s;
-    const W tiny = sizeof(W) == 4 ? (W)1e-30 : (W)1e-300;
-    const int tid = threadIdx.x, S = (int)s, L = S + 1;  // row stride S + 1: a column walk spreads over banks
+    const float tiny = 1e-30f;
     double tr = 0.0;
     for (int i = tid; i < S; i += 256) tr += G[i * S + i];
     red[tid] = tr;
@@ -263,57 +304,117 @@ __global__ void __launch_bounds__(256) k_chol(const double *__restrict__ G, int6
         if (tid < o) red[tid] += red[tid + o];
         __syncthreads();
     }
-    const double shift = shift_rel * red[0] / (double)s;
-    for (int e = tid; e < S * S; e += 256) {
-        const int i = e / S, j = e - i * S;
-        Rs[i * L + j] = (W)(i <= j ? G[e] + (i == j ? shift : 0.0) : 0.0);
+    const double mean = red[0] / (double)s;
+    int ex = 0;
+    if (mean > 0.0 && isfinite(mean)) frexp(mean, &ex);
+    const int e = ex >= 0 ? ex / 2 : -((1 - ex) / 2);  // floor(ex / 2): mean 2^-2e in [0.5, 2)
+    // the FP64 pipe is slow here: one exact scaling product, one sum and the splitting per entry of
+    // the upper triangle only
+    const double down = ldexp(1.0, -2 * e), shift = shift_rel * mean * down;
+    for (int i = ty; i < S; i += 16)
+        for (int j = i + ((tx - i) & 15); j < S; j += 16) {
+            const double g = G[i * S + j] * down + (i == j ? shift : 0.0);
+            const float h = __double2float_rn(g);
+            H[i * L + j] = h;
+            Lo[i * L + j] = __double2float_rn(g - (double)h);
+        }
+    __syncthreads();
+    // row 0 of R, then one barrier per pivot: in step k warp 0 brings row k + 1 up to date, forms its
+    // pivot and scales it into R's row (look-ahead), while warps 1-7 update rows k + 2 onwards with
+    // row k; nobody reads row k + 1 in step k
+    auto pivot = [&](int k, F2 dk, F2 &y) {
+        if (!(dk.h > tiny)) {
+            dk = {tiny, 0.f};
+            if ((tid & 31) == 0) atomicOr(status, 1);
+        }
+        y = f2_rsqrt(dk);
+        return f2_mul(dk, y);
+    };
+    if (tid < 32) {
+        F2 y;
+        const F2 r = pivot(0, {H[0], Lo[0]}, y);
+        for (int j = 1 + tid; j < S; j += 32) {
+            const F2 v = f2_mul({H[j], Lo[j]}, y);
+            H[j] = v.h, Lo[j] = v.l;
+        }
+        if (tid == 0) rdh[0] = r.h, rdl[0] = r.l, yh[0] = y.h, yl[0] = y.l;
     }
     __syncthreads();
-    for (int k = 0; k < S; ++k) {
-        if (tid == 0) {
-            W dk = Rs[k * L + k];
-            if (!(dk > tiny)) {
-                dk = tiny;
-                atomicOr(status, 1);
+    for (int k = 0; k + 1 < S; ++k) {
+        const float *rkh = H + k * L, *rkl = Lo + k * L;
+        if (tid < 32) {
+            const int i = k + 1;
+            const F2 a = {rkh[i], rkl[i]};
+            for (int j = i + tid; j < S; j += 32) {
+                const F2 v = f2_add({H[i * L + j], Lo[i * L + j]}, f2_neg(f2_mul(a, {rkh[j], rkl[j]})));
+                H[i * L + j] = v.h, Lo[i * L + j] = v.l;
             }
-            const W rkk = sqrt(dk);
-            Rs[k * L + k] = rkk;
-            inv_s = (W)1 / rkk;  // division and square root are long sequences: once per step
-        }
-        __syncthreads();
-        const W inv = inv_s;
-        for (int j = k + 1 + tid; j < S; j += 256) Rs[k * L + j] *= inv;
-        __syncthreads();
-        // trailing update of the upper triangle: row i = k + 1 + tid / 2 ... (threads stride rows)
-        for (int i = k + 1 + (tid >> 3); i < S; i += 32) {
-            const W rki = Rs[k * L + i];
-            for (int j = i + (tid & 7); j < S; j += 8) Rs[i * L + j] -= rki * Rs[k * L + j];
+            __syncwarp();
+            F2 y;
+            const F2 r = pivot(i, {H[i * L + i], Lo[i * L + i]}, y);
+            for (int j = i + 1 + tid; j < S; j += 32) {
+                const F2 v = f2_mul({H[i * L + j], Lo[i * L + j]}, y);
+                H[i * L + j] = v.h, Lo[i * L + j] = v.l;
+            }
+            if (tid == 0) rdh[i] = r.h, rdl[i] = r.l, yh[i] = y.h, yl[i] = y.l;
+        } else {
+            const int u = tid - 32, uy = u >> 4;  // 14 row lanes x 16 column lanes
+            for (int i = k + 2 + uy; i < S; i += 14) {
+                const F2 a = {rkh[i], rkl[i]};
+                for (int j = i + ((tx - i) & 15); j < S; j += 32) {  // j >= i, j = tx (mod 16), two at a time
+                    const bool two = j + 16 < S;
+                    F2 m0 = {H[i * L + j], Lo[i * L + j]}, b0 = {rkh[j], rkl[j]}, m1 = {0.f, 0.f}, b1 = {0.f, 0.f};
+                    if (two) m1 = {H[i * L + j + 16], Lo[i * L + j + 16]}, b1 = {rkh[j + 16], rkl[j + 16]};
+                    m0 = f2_add(m0, f2_neg(f2_mul(a, b0)));
+                    m1 = f2_add(m1, f2_neg(f2_mul(a, b1)));
+                    H[i * L + j] = m0.h, Lo[i * L + j] = m0.l;
+                    if (two) H[i * L + j + 16] = m1.h, Lo[i * L + j + 16] = m1.l;
+                }
+            }
         }
         __syncthreads();
     }
-    if (R)
-        for (int e = tid; e < S * S; e += 256) R[e] = (double)Rs[(e / S) * L + e % S];
+    for (int q = tid; q < S * S; q += 256) {  // the strict lower triangle holds X's sums: start at 0
+        const int i = q / S, j = q - i * S;
+        if (i > j) H[i * L + j] = Lo[i * L + j] = 0.f;
+    }
     __syncthreads();
-    for (int j = 0; j < S; ++j) {
-        if (tid == 0) inv_s = (W)1 / Rs[j * L + j];
-        __syncthreads();
-        const W inv_jj = inv_s;
-        W t = 0;
-        const int i = tid;
-        if (i < j)
-            for (int q = i; q < j; ++q) t += Rs[i * L + q] * Rs[q * L + j];
-        __syncthreads();
-        if (i < j) Rs[i * L + j] = -t * inv_jj;
-        if (i == j) Rs[j * L + j] = inv_jj;
+    for (int q = 0; q + 1 < S; ++q) {
+        for (int i = ty; i <= q; i += 16) {
+            const F2 xiq = i == q ? F2{yh[q], yl[q]} : F2{H[q * L + i], Lo[q * L + i]};
+            for (int j = q + 1 + tx; j < S; j += 32) {  // two at a time
+                const bool two = j + 16 < S;
+                F2 a0 = {H[j * L + i], Lo[j * L + i]}, b0 = {H[q * L + j], Lo[q * L + j]}, a1 = {0.f, 0.f},
+                   b1 = {0.f, 0.f};
+                if (two) a1 = {H[(j + 16) * L + i], Lo[(j + 16) * L + i]}, b1 = {H[q * L + j + 16], Lo[q * L + j + 16]};
+                a0 = f2_add(a0, f2_mul(xiq, b0));
+                a1 = f2_add(a1, f2_mul(xiq, b1));
+                if (j == q + 1) a0 = f2_neg(f2_mul(a0, {yh[j], yl[j]}));
+                H[j * L + i] = a0.h, Lo[j * L + i] = a0.l;
+                if (two) H[(j + 16) * L + i] = a1.h, Lo[(j + 16) * L + i] = a1.l;
+            }
+        }
         __syncthreads();
     }
-    for (int e = tid; e < S * S; e += 256) {
-        const W v = Rs[(e / S) * L + e % S];
-        if (Rinv) Rinv[e] = (double)v;
-        Rinv32[e] = (float)v;
+    // R in FP64 (scaled back by 2^e, exactly), R^-1 in FP32 (h + l rounded, scaled by 2^-e in FP32: exact
+    // unless it leaves FP32's range, where the FP32 copy could not hold it anyway)
+    const double up = ldexp(1.0, e);
+    const float rinv_scale = __double2float_rn(ldexp(1.0, -e));
+    for (int q = tid; q < S * S; q += 256) {
+        const int i = q / S, j = q - i * S;
+        float x = 0.f;
+        if (i < j) {
+            if (R) R[q] = ((double)H[i * L + j] + (double)Lo[i * L + j]) * up;
+            x = __fadd_rn(H[j * L + i], Lo[j * L + i]);
+        } else if (i == j) {
+            if (R) R[q] = ((double)rdh[i] + (double)rdl[i]) * up;
+            x = __fadd_rn(yh[i], yl[i]);
+        } else if (R) {
+            R[q] = 0.0;
+        }
+        Rinv32[q] = x * rinv_scale;
     }
 }
-
 // ---------------------------------------------------------------- Bt = A'^T Q
 // A: n x d, Q: n x s (s <= 128, s % 16 == 0), w: n or null.  CTA (column block jb, row chunk g):
 // columns [64 jb, 64 jb + 64) of d, rows of chunk g; thread (tx, ty) owns columns tx + 16 q and
@@ -445,51 +546,61 @@ static int launch_gemm_tn(gbkm_ctx *c, const float *A, const float *Q, const flo
 // X = R_b^T (s x s, column c of X = row c of R_b) is orthogonalised by plane rotations applied on
 // the right, accumulated in J: X J = W Sigma with orthogonal columns whose norms are the singular
 // values.  Rounds follow the circle method (s - 1 rounds of s / 2 disjoint pairs per sweep); each
-// half-warp rotates one pair of a round (1,024 threads: 64 half-warps >= s / 2).  Sweeps stop
-// when no pair has |x_p . x_q| > tol ||x_p|| ||x_q|| (or after 30, flagged in *status).  Then the
-// singular values are ranked (decreasing, lower index first on ties), sigma[0..l) written, and
-// T = R_b^-1 J[:, order[0..l)] (s x l, FP32).  Dynamic shared memory: 2 s^2 floats + s ints.
+// half-warp rotates one pair of a round (8 s threads: s is a multiple of 16), its lanes holding rows
+// gl, gl + 16, ... of both columns in registers for the round.  A pair is rotated when
+// |x_p . x_q| > tol ||x_p|| ||x_q||; sweeps stop when no pair is (or after 30, flagged in *status).
+// A rotation built as c = 1 / sqrt(1 + t^2), s = c t is orthogonal to rounding whatever the accuracy
+// of its angle t, so the angle's quotient and root take the fast forms.  Then the singular values are
+// ranked (decreasing, lower index first on ties), sigma[0..l) written, and T = R_b^-1 J[:, order[0..l)]
+// (s x l, FP32) from R_b^-1 staged, transposed, in X's place.  Dynamic shared memory: 2 s^2 floats +
+// s ints.
+constexpr int JAC_ROWS = 8;  // rows per lane of a half-warp: s <= 128
 __global__ void __launch_bounds__(1024) k_jacobi(const double *__restrict__ R, const float *__restrict__ Rinv32,
                                                  int64_t s, int64_t ell, float tol, float *__restrict__ sigma,
                                                  float *__restrict__ T, int *status) {
     extern __shared__ float js[];
-    float *X = js;               // column-major: X[c * s + r]
-    float *J = js + s * s;       // column-major
-    int *order = reinterpret_cast<int *>(js + 2 * s * s);
-    __shared__ int rotated;
+    const int S = (int)s, nt = (int)blockDim.x;
+    float *X = js;      // column-major: X[c * s + r]
+    float *J = js + S * S;  // column-major
+    int *order = reinterpret_cast<int *>(js + 2 * S * S);
     __shared__ float nrm[128];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = tid >> 4, gl = tid & 15, S = (int)s;
-    for (int e = tid; e < S * S; e += 1024) {
+    const int g = tid >> 4, gl = tid & 15;
+    for (int e = tid; e < S * S; e += nt) {
         const int cc = e / S, r = e - cc * S;
         X[e] = (float)R[e];
         J[e] = cc == r ? 1.f : 0.f;
     }
     __syncthreads();
     const int half = S / 2, rounds = S - 1;
+    const bool act = g < half;
     int sweep = 0;
     for (; sweep < 30; ++sweep) {
-        if (tid == 0) rotated = 0;
-        __syncthreads();
+        bool any = false;
         for (int t = 0; t < rounds; ++t) {
-            const bool act = g < half;
-            const int m = act ? g : 0;
             int p = S - 1, q = t;
-            if (m != 0) {
-                p = t + m;
+            if (g != 0) {
+                p = t + g;
                 if (p >= S - 1) p -= S - 1;
-                q = t - m;
+                q = t - g;
                 if (q < 0) q += S - 1;
             }
             float *xp = X + p * S, *xq = X + q * S;
+            float a[JAC_ROWS], b[JAC_ROWS];
             float al = 0.f, be = 0.f, ga = 0.f;
-            if (act)
-                for (int r = gl; r < S; r += 16) {
-                    const float a = xp[r], b = xq[r];
-                    al = fmaf(a, a, al);
-                    be = fmaf(b, b, be);
-                    ga = fmaf(a, b, ga);
-                }
+#pragma unroll
+            for (int u = 0; u < JAC_ROWS; ++u) {
+                const int r = gl + 16 * u;
+                const bool in = act && r < S;
+                a[u] = in ? xp[r] : 0.f;
+                b[u] = in ? xq[r] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < JAC_ROWS; ++u) {
+                al = fmaf(a[u], a[u], al);
+                be = fmaf(b[u], b[u], be);
+                ga = fmaf(a[u], b[u], ga);
+            }
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) {  // sums within each half-warp
                 al += __shfl_xor_sync(0xffffffffu, al, o);
@@ -497,48 +608,54 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double *__restrict__ R, c
                 ga += __shfl_xor_sync(0xffffffffu, ga, o);
             }
             if (act && fabsf(ga) > tol * sqrtf(al * be) && ga != 0.f) {
-                const float zeta = (be - al) / (2.f * ga);
-                const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                const float cs = 1.f / sqrtf(1.f + tt * tt), sn = cs * tt;
+                const float zeta = __fdividef(be - al, 2.f * ga);
+                const float tt = copysignf(__fdividef(1.f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
+                const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
                 float *jp = J + p * S, *jq = J + q * S;
-                for (int r = gl; r < S; r += 16) {
-                    const float a = xp[r], b = xq[r];
-                    xp[r] = cs * a - sn * b;
-                    xq[r] = sn * a + cs * b;
-                    const float ja = jp[r], jb = jq[r];
-                    jp[r] = cs * ja - sn * jb;
-                    jq[r] = sn * ja + cs * jb;
+#pragma unroll
+                for (int u = 0; u < JAC_ROWS; ++u) {
+                    const int r = gl + 16 * u;
+                    if (r < S) {
+                        const float ja = jp[r], jb = jq[r];
+                        xp[r] = cs * a[u] - sn * b[u];
+                        xq[r] = sn * a[u] + cs * b[u];
+                        jp[r] = cs * ja - sn * jb;
+                        jq[r] = sn * ja + cs * jb;
+                    }
                 }
-                if (gl == 0) rotated = 1;
+                any = true;
             }
             __syncthreads();
         }
-        if (!rotated) break;
-        __syncthreads();
+        if (!__syncthreads_or(any)) break;  // the same verdict on every thread
     }
     // bits 8-15: sweeps run (the sweep that found no pair to rotate included); bit 1: the cap
     if (tid == 0) atomicOr(status, sweep == 30 ? (2 | (30 << 8)) : ((sweep + 1) << 8));
-    for (int64_t cc = warp; cc < s; cc += 32) {
+    for (int cc = warp; cc < S; cc += nt >> 5) {
         float a = 0.f;
-        for (int64_t r = lane; r < s; r += 32) a = fmaf(X[cc * s + r], X[cc * s + r], a);
+        for (int r = lane; r < S; r += 32) a = fmaf(X[cc * S + r], X[cc * S + r], a);
         a = warp_sum_f(a);
         if (lane == 0) nrm[cc] = sqrtf(a);
     }
     __syncthreads();
-    for (int64_t cc = tid; cc < s; cc += 1024) {
+    for (int cc = tid; cc < S; cc += nt) {
         int rank = 0;
-        for (int64_t o = 0; o < s; ++o) rank += (nrm[o] > nrm[cc]) || (nrm[o] == nrm[cc] && o < cc);
-        order[rank] = (int)cc;
+        for (int o = 0; o < S; ++o) rank += (nrm[o] > nrm[cc]) || (nrm[o] == nrm[cc] && o < cc);
+        order[rank] = cc;
+    }
+    for (int e = tid; e < S * S; e += nt) {  // X <- (R_b^-1)^T: Xt[k * s + r] = R_b^-1[r][k]
+        const int k = e / S, r = e - k * S;
+        X[e] = Rinv32[r * S + k];
     }
     __syncthreads();
-    for (int64_t m = tid; m < ell; m += 1024) sigma[m] = nrm[order[m]];
-    // T = R_b^-1 J[:, order[m]]
-    for (int64_t e = tid; e < s * ell; e += 1024) {
-        const int64_t r = e / ell, m = e % ell;
-        const float *jc = J + (int64_t)order[m] * s;
+    for (int64_t m = tid; m < ell; m += nt) sigma[m] = nrm[order[m]];
+    // T[r][m] = sum_k R_b^-1[r][k] J[k][order[m]] (R_b^-1 is upper triangular: the zeros add nothing)
+    for (int e = tid; e < S * (int)ell; e += nt) {
+        const int m = e / S, r = e - m * S;
+        const float *jc = J + order[m] * S;
         float acc = 0.f;
-        for (int64_t k = r; k < s; ++k) acc = fmaf(Rinv32[r * s + k], jc[k], acc);
-        T[r * ell + m] = acc;
+        for (int k = 0; k < S; ++k) acc = fmaf(X[k * S + r], jc[k], acc);
+        T[(int64_t)r * ell + m] = acc;
     }
 }
 
@@ -572,7 +689,7 @@ __global__ void __launch_bounds__(256) k_sign(float *__restrict__ V, int64_t d, 
 
 // ---------------------------------------------------------------- orchestration
 struct SvdPlan {
-    size_t o_y, o_q, o_gpart, o_g, o_r, o_rinv, o_rinv32, o_tpart, o_bt, o_t, o_sig, o_status, o_omt, o_qt, o_rpart,
+    size_t o_y, o_q, o_gpart, o_g, o_r, o_rinv32, o_tpart, o_bt, o_t, o_sig, o_status, o_omt, o_qt, o_rpart,
         bytes;
     bool tc;  // the two passes over the piece on the tensor cores
 };
@@ -588,7 +705,6 @@ static SvdPlan svd_plan(int64_t n, int64_t d, int64_t s, int64_t ell, int sm_cou
     P.o_gpart = p.take<float2>(gchunks * (nb * (nb + 1) / 2) * GM_B * GM_B);
     P.o_g = p.take<double>(s * s);
     P.o_r = p.take<double>(s * s);
-    P.o_rinv = p.take<double>(s * s);
     P.o_rinv32 = p.take<float>(s * s);
     P.o_tpart = p.take<float2>((int64_t)TN_CHUNKS * d * s);
     P.o_bt = p.take<float>(d * s);
@@ -614,15 +730,15 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
     if (!ws) return rc;
     float *Y = ws_at<float>(ws, P.o_y), *Q = ws_at<float>(ws, P.o_q);
     float2 *gpart = ws_at<float2>(ws, P.o_gpart), *tpart = ws_at<float2>(ws, P.o_tpart);
-    double *G = ws_at<double>(ws, P.o_g), *R = ws_at<double>(ws, P.o_r), *Rinv = ws_at<double>(ws, P.o_rinv);
+    double *G = ws_at<double>(ws, P.o_g), *R = ws_at<double>(ws, P.o_r);
     float *Rinv32 = ws_at<float>(ws, P.o_rinv32), *Bt = ws_at<float>(ws, P.o_bt), *T = ws_at<float>(ws, P.o_t);
     int *st = info ? reinterpret_cast<int *>(info) : ws_at<int>(ws, P.o_status);
     if (!sigma) sigma = ws_at<float>(ws, P.o_sig);
     if (cudaMemsetAsync(st, 0, sizeof(int), c->stream) != cudaSuccess) return cuda_check(c, cudaGetLastError(), "rsvd info");
     const size_t jsm = sizeof(float) * 2 * (size_t)s * (size_t)s + sizeof(int) * (size_t)s;
     if (jsm > 48 * 1024) cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
-    const size_t csm = sizeof(double) * (size_t)s * (size_t)(s + 1);
-    if (csm > 48 * 1024) cudaFuncSetAttribute(k_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    const size_t csm = sizeof(float) * (2 * (size_t)s * (size_t)(s + 1) + 4 * (size_t)s);
+    if (csm > 48 * 1024) cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
 
     // 1. Y = A' Omega
     prof_begin(c, "rsvd_sketch");
@@ -633,11 +749,11 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
     // 2. CholeskyQR2: Y -> Q (via Q) -> Y
     prof_begin(c, "rsvd_qr");
     if ((rc = launch_gram(c, Y, n, s, gpart, G)) != GBKM_OK) return rc;
-    k_chol<double><<<1, 256, csm, c->stream>>>(G, s, 1e-6, R, Rinv, Rinv32, st);
+    k_chol<<<1, 256, csm, c->stream>>>(G, s, 1e-6, R, Rinv32, st);
     GBKM_LAUNCHED(c);
     if ((rc = launch_gemm_rows(c, Y, Rinv32, nullptr, n, s, s, Q)) != GBKM_OK) return rc;
     if ((rc = launch_gram(c, Q, n, s, gpart, G)) != GBKM_OK) return rc;
-    k_chol<double><<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv, Rinv32, st);
+    k_chol<<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv32, st);
     GBKM_LAUNCHED(c);
     if ((rc = launch_gemm_rows(c, Q, Rinv32, nullptr, n, s, s, Y)) != GBKM_OK) return rc;
     prof_end(c);
@@ -650,11 +766,11 @@ int rsvd_impl(gbkm_ctx *c, const float *A, int64_t n, int64_t d, const float *w,
     // 4. R_b from the Gram of Bt
     prof_begin(c, "rsvd_small");
     if ((rc = launch_gram(c, Bt, d, s, gpart, G)) != GBKM_OK) return rc;
-    k_chol<double><<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv, Rinv32, st);
+    k_chol<<<1, 256, csm, c->stream>>>(G, s, 1e-9, R, Rinv32, st);
     GBKM_LAUNCHED(c);
     // 5. singular values and T
     const float tol = (float)s * 1.2e-7f;
-    k_jacobi<<<1, 1024, jsm, c->stream>>>(R, Rinv32, s, ell, tol, sigma, T, st);
+    k_jacobi<<<1, (unsigned)(8 * s), jsm, c->stream>>>(R, Rinv32, s, ell, tol, sigma, T, st);
     GBKM_LAUNCHED(c);
     prof_end(c);
     // 6. V = Bt T, 7. signs
