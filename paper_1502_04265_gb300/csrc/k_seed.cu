@@ -16,7 +16,7 @@ namespace gbkm {
 
 namespace {
 constexpr int SB = 128;    // rows per sampling block (one CTA of 8 warps, 16 rows per warp)
-constexpr int PICK_T = 1024;
+constexpr int PICK_T = 256;   // threads of a pick CTA: the FP64 scans cost in proportion
 }  // namespace
 
 __device__ double block_incl_scan_d(double v, double *sh) {
@@ -47,7 +47,7 @@ __device__ double block_incl_scan_d(double v, double *sh) {
 // One CTA: choose the row for round j.  mode_w: p_i = w_i (weighted first center), else
 // p_i = w_i * D2_i.  Blocks: prefix of the block sums; within the block: inclusive prefix in
 // row order.  Chosen = smallest i whose global inclusive prefix exceeds t = u_j * total; if
-// rounding leaves none, the last i with p_i > 0.  Writes idx_out[j], the center row, D2_i = 0.
+// rounding leaves none, the last i with p_i > 0.  CTA 0 writes idx_out[j] and the center row.
 struct PickShared {
     double sh[32];
     int64_t s_block, s_idx;
@@ -173,11 +173,12 @@ __device__ int64_t pick_center(const float *__restrict__ X, int64_t n, int64_t d
         }
         return -1;
     }
-    if (tid == 0) {
-        idx_out[j] = pick;
-        D2[pick] = 0.0;
+    // (D2 of the pick is left as it is: other CTAs making the same pick may still read it, and the next
+    // round's update sets it to 0, the exact distance of the row to itself)
+    if (blockIdx.x == 0) {
+        if (tid == 0) idx_out[j] = pick;
+        for (int64_t q = tid; q < d; q += nt) C_out[j * d + q] = X[pick * d + q];
     }
-    for (int64_t q = tid; q < d; q += nt) C_out[j * d + q] = X[pick * d + q];
     return pick;
 }
 
@@ -207,7 +208,6 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
                                                       double *__restrict__ D2, float *__restrict__ D2f,
                                                       int32_t *__restrict__ A, const float *__restrict__ ccf,
                                                       double *__restrict__ bsum, const int *__restrict__ stop,
-                                                      const int64_t *__restrict__ dirty,
                                                       const __nv_bfloat16 *__restrict__ Xq,
                                                       const float *__restrict__ xresid) {
     if (*stop) return;
@@ -218,8 +218,7 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
     const int64_t r0 = (int64_t)blockIdx.x * SB, r1 = min(n, r0 + SB);
     if (tid == 0) {
         nlist = 0;
-        // the block of the last pick had that row's D^2 set to 0 since its sum was taken
-        changed = j == 0 || *dirty == (int64_t)blockIdx.x;
+        changed = j == 0;
     }
     __syncthreads();
     if (tid < SB) {
@@ -350,21 +349,16 @@ __global__ void __launch_bounds__(PICK_T) k_pick_cc(const float *__restrict__ X,
                                                     const double *__restrict__ bsum, int64_t nb,
                                                     const double *__restrict__ u, int64_t j, int64_t k,
                                                     int64_t *__restrict__ idx_out, float *__restrict__ C_out,
-                                                    float *__restrict__ D2f, float *__restrict__ ccf, int *stop,
-                                                    int64_t *__restrict__ dirty, int *status) {
+                                                    float *__restrict__ ccf, int *stop, int *status) {
     __shared__ PickShared ps;
     if (*stop) return;
     const int64_t pick = pick_center(X, n, d, w, D2, bsum, nb, u, j, 0, idx_out, C_out, stop, status, ps);
-    if (pick >= 0 && threadIdx.x == 0) {
-        D2f[pick] = 0.f;
-        *dirty = pick / SB;  // its block sum is refreshed in the next round
-    }
     if (pick < 0 || j + 1 >= k) return;
-    __syncthreads();  // the new center's row in C_out
+    // this CTA's share of the earlier centers, against the new one's row of X
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int lpr = lanes_per_row(d, 1), cpw = 32 / lpr, sl = lane % lpr;
-    const float *cj = C_out + j * d;
-    for (int64_t a0 = (int64_t)wid * cpw; a0 < j; a0 += (int64_t)nw * cpw) {
+    const float *cj = X + pick * d;
+    for (int64_t a0 = ((int64_t)blockIdx.x * nw + wid) * cpw; a0 < j; a0 += (int64_t)gridDim.x * nw * cpw) {
         const int64_t a = a0 + lane / lpr;
         const bool has = a < j;
         DF acc;
@@ -407,7 +401,7 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     const int64_t nb = ceil_div(n, SB);
     WsPlan p;
     size_t o_d2 = p.take<double>(n), o_d2f = p.take<float>(n), o_a = p.take<int32_t>(n), o_cc = p.take<float>(k),
-           o_b = p.take<double>(nb), o_stop = p.take<int>(2), o_dirty = p.take<int64_t>(1);
+           o_b = p.take<double>(nb), o_stop = p.take<int>(2);
     int rc = GBKM_OK;
     void *ws = ws_reserve(c, p.off, &rc);
     if (!ws) return rc;
@@ -415,9 +409,7 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
     float *D2f = ws_at<float>(ws, o_d2f), *ccf = ws_at<float>(ws, o_cc);
     int32_t *A = ws_at<int32_t>(ws, o_a);
     int *stop = ws_at<int>(ws, o_stop);
-    int64_t *dirty = ws_at<int64_t>(ws, o_dirty);
     cudaError_t e = cudaMemsetAsync(stop, 0, 2 * sizeof(int), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dirty, 0xff, sizeof(int64_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(idx_out, 0xff, sizeof(int64_t) * k, c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "seed memset");
     const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
@@ -442,14 +434,18 @@ int seed_impl(gbkm_ctx *c, const float *X, int64_t n, int64_t d, const float *w,
         prof_begin(c, "seed_d2");
         if (vec)
             k_d2_update<4><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, D2f, A, ccf, bsum, stop,
-                                                                dirty, xq, xresid);
+                                                                xq, xresid);
         else
             k_d2_update<1><<<(unsigned)nb, 256, 0, c->stream>>>(X, n, d, w, cprev, jc, D2, D2f, A, ccf, bsum, stop,
-                                                                dirty, nullptr, nullptr);
+                                                                nullptr, nullptr);
         prof_end(c);
         prof_begin(c, "seed_pick");
-        k_pick_cc<<<1, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, k, idx_out, C_out, D2f, ccf, stop,
-                                               dirty, c->status);
+        // every CTA makes the same pick (the same data, the same operations) and measures its share
+        // of the earlier centers against it; CTA 0 records it
+        const int lpr = lanes_per_row(d, 1), per_cta = (PICK_T / 32) * (32 / lpr);
+        const unsigned g = j + 1 < k ? (unsigned)std::min<int64_t>(ceil_div(j, (int64_t)per_cta), 64) : 1u;
+        k_pick_cc<<<g, PICK_T, 0, c->stream>>>(X, n, d, w, D2, bsum, nb, u, j, k, idx_out, C_out, ccf, stop,
+                                               c->status);
         prof_end(c);
         c->launches += 2;
     }
