@@ -237,101 +237,142 @@ __global__ void __launch_bounds__(256, 4) k_d2_update(const float *__restrict__ 
     // fma-accumulated square once, at most d terms per lane, five butterfly additions), with room for
     // the rounding of the product that applies it
     const float g32 = (float)(d + 40) * 5.9604645e-8f;
-    for (int e0 = wid * rpw; e0 < m; e0 += 8 * rpw) {
-        const int e = e0 + sub;
-        const bool has = e < m;
-        const int t = has ? list[e] : 0;
-        const int64_t i = r0 + t;
-        bool need = has;
-        if (j > 0) {
+    // two listed rows per lane group at a time: both rows' loads are issued before either is summed,
+    // so a warp keeps twice the bytes in flight (the distance passes wait on DRAM, not on arithmetic)
+    constexpr int NR = 2;
+    for (int e0 = wid * rpw * NR; e0 < m; e0 += 8 * rpw * NR) {
+        int64_t ii[NR];
+        bool hh[NR], need[NR];
+        float dold[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int e = e0 + r * rpw + sub;
+            hh[r] = e < m;
+            ii[r] = r0 + (hh[r] ? list[e] : 0);
+            need[r] = hh[r];
             // above D2 whatever the rounding of the product
-            const float dold = has ? D2f[i] * (1.f + 2e-6f) : 0.f;
+            dold[r] = (j > 0 && hh[r]) ? D2f[ii[r]] * (1.f + 2e-6f) : 0.f;
+        }
+        if (j > 0) {
             if (Xq) {
                 // ||x - c|| >= ||x~ - c|| - ||x~ - x|| with x~ the BF16 copy (d % 8 == 0) and ||x~ - x|| <= the
                 // row's residual: when that bound exceeds D the FP32 row is not read
-                float a16 = 0.f;
-                if (has) {
-                    const uint4 *q8 = reinterpret_cast<const uint4 *>(Xq + i * d);
-                    const float4 *c4 = reinterpret_cast<const float4 *>(c);
+                float a16[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) a16[r] = 0.f;
+                const uint4 *q8[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) q8[r] = reinterpret_cast<const uint4 *>(Xq + ii[r] * d);
+                const float4 *c4 = reinterpret_cast<const float4 *>(c);
 #pragma unroll 4
-                    for (int64_t q = sl; q < d / 8; q += lpr) {
-                        const uint4 v = __ldg(q8 + q);
-                        const float4 b0 = __ldg(c4 + 2 * q), b1 = __ldg(c4 + 2 * q + 1);
-                        const float f0 = __uint_as_float(v.x << 16) - b0.x, f1 = __uint_as_float(v.x & 0xffff0000u) - b0.y;
-                        const float f2 = __uint_as_float(v.y << 16) - b0.z, f3 = __uint_as_float(v.y & 0xffff0000u) - b0.w;
-                        const float f4 = __uint_as_float(v.z << 16) - b1.x, f5 = __uint_as_float(v.z & 0xffff0000u) - b1.y;
-                        const float f6 = __uint_as_float(v.w << 16) - b1.z, f7 = __uint_as_float(v.w & 0xffff0000u) - b1.w;
-                        a16 = fmaf(f0, f0, a16);
-                        a16 = fmaf(f1, f1, a16);
-                        a16 = fmaf(f2, f2, a16);
-                        a16 = fmaf(f3, f3, a16);
-                        a16 = fmaf(f4, f4, a16);
-                        a16 = fmaf(f5, f5, a16);
-                        a16 = fmaf(f6, f6, a16);
-                        a16 = fmaf(f7, f7, a16);
+                for (int64_t q = sl; q < d / 8; q += lpr) {
+                    uint4 v[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) v[r] = hh[r] ? __ldg(q8[r] + q) : make_uint4(0u, 0u, 0u, 0u);
+                    const float4 b0 = __ldg(c4 + 2 * q), b1 = __ldg(c4 + 2 * q + 1);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const float f0 = __uint_as_float(v[r].x << 16) - b0.x, f1 = __uint_as_float(v[r].x & 0xffff0000u) - b0.y;
+                        const float f2 = __uint_as_float(v[r].y << 16) - b0.z, f3 = __uint_as_float(v[r].y & 0xffff0000u) - b0.w;
+                        const float f4 = __uint_as_float(v[r].z << 16) - b1.x, f5 = __uint_as_float(v[r].z & 0xffff0000u) - b1.y;
+                        const float f6 = __uint_as_float(v[r].w << 16) - b1.z, f7 = __uint_as_float(v[r].w & 0xffff0000u) - b1.w;
+                        float a = a16[r];
+                        a = fmaf(f0, f0, a);
+                        a = fmaf(f1, f1, a);
+                        a = fmaf(f2, f2, a);
+                        a = fmaf(f3, f3, a);
+                        a = fmaf(f4, f4, a);
+                        a = fmaf(f5, f5, a);
+                        a = fmaf(f6, f6, a);
+                        a = fmaf(f7, f7, a);
+                        a16[r] = a;
                     }
                 }
-                for (int o = lpr >> 1; o > 0; o >>= 1) a16 += __shfl_xor_sync(0xffffffffu, a16, o);
-                if (has) {
-                    // a lower bound of ||x~ - c|| (sqrtf is correctly rounded; the factor covers it and the
-                    // product), then of ||x - c||^2
-                    const float lo = sqrtf(fmaxf(a16 * (1.f - g32), 0.f)) * (1.f - 2.4e-7f) - xresid[i];
-                    const float L = lo > 0.f ? lo * lo * (1.f - 1e-6f) : 0.f;
-                    need = !(L > dold);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    for (int o = lpr >> 1; o > 0; o >>= 1) a16[r] += __shfl_xor_sync(0xffffffffu, a16[r], o);
+                    if (hh[r]) {
+                        // a lower bound of ||x~ - c|| (sqrtf is correctly rounded; the factor covers it and the
+                        // product), then of ||x - c||^2
+                        const float lo = sqrtf(fmaxf(a16[r] * (1.f - g32), 0.f)) * (1.f - 2.4e-7f) - xresid[ii[r]];
+                        const float L = lo > 0.f ? lo * lo * (1.f - 1e-6f) : 0.f;
+                        need[r] = !(L > dold[r]);
+                    }
                 }
-                if (!__any_sync(0xffffffffu, need)) continue;
+                if (!__any_sync(0xffffffffu, need[0] || need[1])) continue;
             }
             // the FP32 distance: when its lower bound exceeds D, D^2 keeps its bits
-            float a32 = 0.f;
-            if (need) {
+            float a32[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) a32[r] = 0.f;
+            if constexpr (VW == 4) {
+                const float4 *x4[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) x4[r] = reinterpret_cast<const float4 *>(X + ii[r] * d);
+                const float4 *c4 = reinterpret_cast<const float4 *>(c);
+#pragma unroll 4
+                for (int64_t q = sl; q < d / 4; q += lpr) {
+                    float4 a[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) a[r] = need[r] ? __ldg(x4[r] + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 b = __ldg(c4 + q);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const float e0_ = a[r].x - b.x, e1 = a[r].y - b.y, e2 = a[r].z - b.z, e3 = a[r].w - b.w;
+                        float s = a32[r];
+                        s = fmaf(e0_, e0_, s);
+                        s = fmaf(e1, e1, s);
+                        s = fmaf(e2, e2, s);
+                        s = fmaf(e3, e3, s);
+                        a32[r] = s;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    if (need[r]) {
+                        const float *x = X + ii[r] * d;
+                        for (int64_t q = sl; q < d; q += lpr) {
+                            const float df = x[q] - c[q];
+                            a32[r] = fmaf(df, df, a32[r]);
+                        }
+                    }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                for (int o = lpr >> 1; o > 0; o >>= 1) a32[r] += __shfl_xor_sync(0xffffffffu, a32[r], o);
+                need[r] = need[r] && !(a32[r] * (1.f - g32) > dold[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (!__any_sync(0xffffffffu, need[r])) continue;
+            const int64_t i = ii[r];
+            DF acc;
+            if (need[r]) {
                 const float *x = X + i * d;
                 if constexpr (VW == 4) {
                     const float4 *x4 = reinterpret_cast<const float4 *>(x);
                     const float4 *c4 = reinterpret_cast<const float4 *>(c);
-#pragma unroll 4
+#pragma unroll 2
                     for (int64_t q = sl; q < d / 4; q += lpr) {
-                        const float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
-                        const float e0_ = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
-                        a32 = fmaf(e0_, e0_, a32);
-                        a32 = fmaf(e1, e1, a32);
-                        a32 = fmaf(e2, e2, a32);
-                        a32 = fmaf(e3, e3, a32);
+                        float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
+                        acc.add_sqdiff(a.x, b.x);
+                        acc.add_sqdiff(a.y, b.y);
+                        acc.add_sqdiff(a.z, b.z);
+                        acc.add_sqdiff(a.w, b.w);
                     }
                 } else {
-                    for (int64_t q = sl; q < d; q += lpr) {
-                        const float df = x[q] - c[q];
-                        a32 = fmaf(df, df, a32);
-                    }
+                    for (int64_t q = sl; q < d; q += lpr) acc.add_sqdiff(x[q], c[q]);
                 }
             }
-            for (int o = lpr >> 1; o > 0; o >>= 1) a32 += __shfl_xor_sync(0xffffffffu, a32, o);
-            need = need && !(a32 * (1.f - g32) > dold);
-        }
-        if (!__any_sync(0xffffffffu, need)) continue;
-        DF acc;
-        if (need) {
-            const float *x = X + i * d;
-            if constexpr (VW == 4) {
-                const float4 *x4 = reinterpret_cast<const float4 *>(x);
-                const float4 *c4 = reinterpret_cast<const float4 *>(c);
-#pragma unroll 4
-                for (int64_t q = sl; q < d / 4; q += lpr) {
-                    float4 a = __ldg(x4 + q), b = __ldg(c4 + q);
-                    acc.add_sqdiff(a.x, b.x);
-                    acc.add_sqdiff(a.y, b.y);
-                    acc.add_sqdiff(a.z, b.z);
-                    acc.add_sqdiff(a.w, b.w);
-                }
-            } else {
-                for (int64_t q = sl; q < d; q += lpr) acc.add_sqdiff(x[q], c[q]);
+            const double dist = group_sum_df(acc, lpr);
+            if (need[r] && sl == 0 && (j == 0 || dist < D2[i])) {
+                D2[i] = dist;
+                D2f[i] = __double2float_ru(dist);
+                A[i] = (int32_t)j;
+                changed = 1;
             }
-        }
-        const double dist = group_sum_df(acc, lpr);
-        if (need && sl == 0 && (j == 0 || dist < D2[i])) {
-            D2[i] = dist;
-            D2f[i] = __double2float_ru(dist);
-            A[i] = (int32_t)j;
-            changed = 1;
         }
     }
     __syncthreads();
