@@ -22,7 +22,6 @@ namespace gbkm {
 
 namespace {
 constexpr int GR_BM = 128, GR_BK = 16;   // k_gemm_rows tile
-constexpr int GM_B = 64, GM_RS = 32;     // k_gram: 64 x 64 output blocks, 32-row stages
 constexpr int TN_BJ = 64, TN_RS = 32;    // k_gemm_tn: 64 columns of d per CTA, 32-row stages
 constexpr int TN_CHUNKS = 16;            // row chunks of k_gemm_tn (partials added in order)
 
@@ -123,87 +122,93 @@ static int launch_gemm_rows(gbkm_ctx *c, const float *In, const float *W, const 
 }
 
 // ---------------------------------------------------------------- Gram matrix X^T X
-// X: m x s row-major.  CTA (block pair p, row chunk g) sums rows [g * rows, (g + 1) * rows) into
-// the 64 x 64 block (bi, bj), bi <= bj, of the Gram matrix: FP32 products summed over 8 rows, each
-// 8-row sum added into a double-float accumulator.  part[(g * npairs + p) * 4096 + local] = (hi, lo).
+// X: m x s row-major (s % 4 == 0, s <= 128, rows 16-byte aligned).  CTA g sums the rows
+// [g * rows, (g + 1) * rows) into the upper triangle of the s x s Gram matrix: the triangle's 4 x 4
+// tiles (p, q), p <= q, are dealt to the threads (tile e to thread e mod 256), each row's 16 products
+// of a tile summed in FP32 over 8 rows and each 8-row sum added into a double-float accumulator.
+// part[(g * s + i) * s + j] = (hi, lo) for i <= j (and for the lower half of a diagonal tile).
+constexpr int GM_RS = 32;  // rows per shared-memory stage
+template <int TPT>         // tiles per thread: s (s + 4) / 32 <= 256 TPT
 __global__ void __launch_bounds__(256) k_gram(const float *__restrict__ X, int64_t m, int64_t s, int64_t rows,
                                               float2 *__restrict__ part) {
-    __shared__ float Xi[GM_RS][GM_B + 1];
-    __shared__ float Xj[GM_RS][GM_B + 1];
-    const int nb = (int)((s + GM_B - 1) / GM_B);
-    int p = blockIdx.x, bi = 0;
-    while (p >= nb - bi) {  // pair index -> (bi, bj), bi <= bj
-        p -= nb - bi;
-        ++bi;
+    __shared__ __align__(16) float Xs[GM_RS][128];
+    const int tid = threadIdx.x, S4 = (int)(s >> 2), ntiles = S4 * (S4 + 1) / 2;
+    int tp[TPT], tq[TPT];
+    bool own[TPT];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+        const int e = tid + 256 * u;
+        own[u] = e < ntiles;
+        int p = 0, rem = own[u] ? e : 0;
+        while (rem >= S4 - p) rem -= S4 - p++;  // row-major order of the upper triangle
+        tp[u] = p, tq[u] = p + rem;
     }
-    const int bj = bi + p;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t r0 = (int64_t)blockIdx.y * rows, r1 = min(m, r0 + rows);
-    float hi[4][4], lo[4][4];
+    float hi[TPT][16], lo[TPT][16];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int u = 0; u < TPT; ++u)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.f;
+        for (int e = 0; e < 16; ++e) hi[u][e] = lo[u][e] = 0.f;
+    const int64_t r0 = (int64_t)blockIdx.x * rows, r1 = min(m, r0 + rows);
     for (int64_t base = r0; base < r1; base += GM_RS) {
-        for (int e = tid; e < GM_RS * GM_B; e += 256) {
-            const int rr = e / GM_B, cc = e % GM_B;
-            const int64_t r = base + rr, ci = (int64_t)bi * GM_B + cc, cj = (int64_t)bj * GM_B + cc;
-            Xi[rr][cc] = (r < r1 && ci < s) ? X[r * s + ci] : 0.f;
-            Xj[rr][cc] = (r < r1 && cj < s) ? X[r * s + cj] : 0.f;
+        for (int e = tid; e < GM_RS * S4; e += 256) {
+            const int rr = e / S4, c4 = e - rr * S4;
+            const int64_t r = base + rr;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < r1) v = __ldg(reinterpret_cast<const float4 *>(X + r * s) + c4);
+            *reinterpret_cast<float4 *>(&Xs[rr][4 * c4]) = v;
         }
         __syncthreads();
 #pragma unroll
         for (int g8 = 0; g8 < GM_RS; g8 += 8) {
-            float acc[4][4];
+            float acc[TPT][16];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int u = 0; u < TPT; ++u)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+                for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
 #pragma unroll
             for (int rr = g8; rr < g8 + 8; ++rr) {
-                float x[4], y[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) x[a] = Xi[rr][ty + 16 * a];
+                for (int u = 0; u < TPT; ++u) {
+                    if (!own[u]) continue;
+                    const float4 a = *reinterpret_cast<const float4 *>(&Xs[rr][4 * tp[u]]);
+                    const float4 b = *reinterpret_cast<const float4 *>(&Xs[rr][4 * tq[u]]);
+                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int b = 0; b < 4; ++b) y[b] = Xj[rr][tx + 16 * b];
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(x[a], y[b], acc[a][b]);
+                        for (int j = 0; j < 4; ++j) acc[u][4 * i + j] = fmaf(av[i], bv[j], acc[u][4 * i + j]);
+                }
             }
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int u = 0; u < TPT; ++u)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) df_add_f(hi[a][b], lo[a][b], acc[a][b]);
+                for (int e = 0; e < 16; ++e) df_add_f(hi[u][e], lo[u][e], acc[u][e]);
         }
         __syncthreads();
     }
-    const int npairs = nb * (nb + 1) / 2;
-    float2 *o = part + ((int64_t)blockIdx.y * npairs + blockIdx.x) * (GM_B * GM_B);
+    float2 *o = part + (int64_t)blockIdx.x * s * s;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int u = 0; u < TPT; ++u) {
+        if (!own[u]) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) o[(ty + 16 * a) * GM_B + tx + 16 * b] = make_float2(hi[a][b], lo[a][b]);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                o[(int64_t)(4 * tp[u] + i) * s + 4 * tq[u] + j] = make_float2(hi[u][4 * i + j], lo[u][4 * i + j]);
+    }
 }
 
-// the chunks' partial blocks added (double-float) into the full symmetric FP64 G: one warp per
-// entry of the upper triangle, lane l taking chunks l, l + 32, ..., then a fixed butterfly
+// the chunks' partials added (double-float) into the full symmetric FP64 G: one warp per entry of the
+// upper triangle, lane l taking chunks l, l + 32, ..., then a fixed butterfly
 __global__ void __launch_bounds__(256) k_gram_reduce(const float2 *__restrict__ part, int64_t s, int chunks,
                                                      double *__restrict__ G) {
     const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, S = (int)s;
     if (e >= S * S) return;
     const int i = e / S, j = e - i * S;
     if (i > j) return;
-    const int nb = (S + GM_B - 1) / GM_B;
-    const int bi = i / GM_B, bj = j / GM_B;
-    int pidx = 0;
-    for (int q = 0; q < bi; ++q) pidx += nb - q;
-    pidx += bj - bi;
-    const int npairs = nb * (nb + 1) / 2;
-    const int loc = (i % GM_B) * GM_B + (j % GM_B);
     float hi = 0.f, lo = 0.f;
     for (int g = lane; g < chunks; g += 32) {
-        const float2 v = part[((int64_t)g * npairs + pidx) * (GM_B * GM_B) + loc];
+        const float2 v = part[((int64_t)g * S + i) * S + j];
         df_add_f(hi, lo, v.x);
         df_add_f(hi, lo, v.y);
     }
@@ -224,13 +229,21 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const float2 *__restrict__ 
     }
 }
 
-static int gram_chunks(int64_t m) { return (int)std::min<int64_t>(96, std::max<int64_t>(1, ceil_div(m, 256))); }
+// row chunks: about two CTAs per SM, at least 64 rows each
+static int gram_chunks(int64_t m, int sm_count) {
+    return (int)std::min<int64_t>(2 * (int64_t)sm_count, std::max<int64_t>(1, ceil_div(m, (int64_t)64)));
+}
 
 static int launch_gram(gbkm_ctx *c, const float *X, int64_t m, int64_t s, float2 *part, double *G) {
-    const int chunks = gram_chunks(m);
+    const int chunks = gram_chunks(m, c->sm_count);
     const int64_t rows = ceil_div(m, (int64_t)chunks);
-    const int nb = (int)ceil_div(s, (int64_t)GM_B);
-    k_gram<<<dim3((unsigned)(nb * (nb + 1) / 2), (unsigned)chunks), 256, 0, c->stream>>>(X, m, s, rows, part);
+    const int64_t ntiles = (s / 4) * (s / 4 + 1) / 2;
+    if (ntiles <= 256)
+        k_gram<1><<<(unsigned)chunks, 256, 0, c->stream>>>(X, m, s, rows, part);
+    else if (ntiles <= 512)
+        k_gram<2><<<(unsigned)chunks, 256, 0, c->stream>>>(X, m, s, rows, part);
+    else
+        k_gram<3><<<(unsigned)chunks, 256, 0, c->stream>>>(X, m, s, rows, part);
     k_gram_reduce<<<(unsigned)ceil_div(s * s * 32, (int64_t)256), 256, 0, c->stream>>>(part, s, chunks, G);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "gram launch");
@@ -698,11 +711,10 @@ static SvdPlan svd_plan(int64_t n, int64_t d, int64_t s, int64_t ell, int sm_cou
     SvdPlan P;
     WsPlan p;
     P.tc = tc;
-    const int nb = (int)ceil_div(s, (int64_t)GM_B);
-    const int64_t gchunks = std::max<int64_t>(gram_chunks(n), gram_chunks(d));
+    const int64_t gchunks = std::max<int64_t>(gram_chunks(n, sm_count), gram_chunks(d, sm_count));
     P.o_y = p.take<float>(n * s);
     P.o_q = p.take<float>(n * s);
-    P.o_gpart = p.take<float2>(gchunks * (nb * (nb + 1) / 2) * GM_B * GM_B);
+    P.o_gpart = p.take<float2>(gchunks * s * s);
     P.o_g = p.take<double>(s * s);
     P.o_r = p.take<double>(s * s);
     P.o_rinv32 = p.take<float>(s * s);
