@@ -136,6 +136,49 @@ def stored_traffic(key):
     return e["dram_bytes_per_launch"]
 
 
+class Ranks:
+    """The rank bookkeeping of a replicated run (one process per GPU, launched by torchrun): the
+    launcher's RANK / LOCAL_RANK / WORLD_SIZE, a barrier and the maximum of a host value over the
+    ranks.  The bench uses NCCL tensors on each rank's GPU; the same logic runs on gloo and CPU
+    tensors for the multi-process tests."""
+
+    def __init__(self, backend="nccl", device=None):
+        import torch.distributed as dist
+
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = device
+        if self.world > 1 and not dist.is_initialized():
+            if backend == "nccl":
+                dist.init_process_group(backend, device_id=device)
+            else:
+                dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max_over_ranks(self, v):
+        if self.world == 1:
+            return v
+        import torch
+
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def whole_job(self, work_per_rank, ms):
+        """Throughput of all ranks' work (each rank does work_per_rank units) in the slowest rank's
+        time: the weak-scaling value of the JSON line."""
+        return self.world * work_per_rank / (ms * 1e-3)
+
+    def close(self):
+        if self.world > 1 and self.dist.is_initialized():
+            self.dist.destroy_process_group()
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -200,13 +243,11 @@ class Env:
 
         self.args = args
         self.torch, self.dist, self.B = torch, dist, B
-        self.world = int(os.environ.get("WORLD_SIZE", "1"))
-        self.rank = int(os.environ.get("RANK", "0"))
-        self.local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(self.local)
-        self.dev = torch.device("cuda", self.local)
-        if self.world > 1:
-            dist.init_process_group("nccl", device_id=self.dev)
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        self.dev = torch.device("cuda", local)
+        self.ranks = Ranks("nccl", self.dev)
+        self.world, self.rank, self.local = self.ranks.world, self.ranks.rank, self.ranks.local
         B.load(build_if_missing=True)
         self.ctx = B.Context(self.local)
         self.peaks = load_peaks()
@@ -226,15 +267,10 @@ class Env:
         return self.torch.cuda.current_stream(self.dev)
 
     def barrier(self):
-        if self.world > 1:
-            self.dist.barrier()
+        self.ranks.barrier()
 
     def max_over_ranks(self, v):
-        if self.world == 1:
-            return v
-        t = self.torch.tensor([v], dtype=self.torch.float64, device=self.dev)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return float(t.item())
+        return self.ranks.max_over_ranks(v)
 
     def event(self):
         return self.torch.cuda.Event(enable_timing=True)
@@ -539,7 +575,7 @@ def run_highdim(env, args):
     R = lloyd_timed(env, Xg, Xop, Xr, xnorm, C0, form, engine, args.steps, args.warmup, clocks=True,
                     center_terms=args.center_terms if form == "bf16" else 1)
     ms, prof = R["ms"], R["prof"]
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     peaks = env.peaks
     kname = assign_kernel(prof)
     tc = kname == "assign_tc"
@@ -634,10 +670,12 @@ def run_highdim(env, args):
         co2 = torch.empty(2, dtype=torch.float64, device=env.dev)
         st = {"C": Ce, "Cn": Cen}
 
-        def lloyd_and_readback():
-            B.kmeans_assign(Xd, st["C"], Xop=Xb2, Xop_scales=Xr2, xnorm=xn2, compute=form, engine=engine,
+        def lloyd_and_readback(Xs=None, xns=None, Xbs=None, Xrs=None):
+            Xs = Xd if Xs is None else Xs
+            xns, Xbs, Xrs = (xn2, Xb2, Xr2) if xns is None else (xns, Xbs, Xrs)
+            B.kmeans_assign(Xs, st["C"], Xop=Xbs, Xop_scales=Xrs, xnorm=xns, compute=form, engine=engine,
                             labels=lab2, ctx=ctx)
-            B.kmeans_update(Xd, lab2, st["C"], C_new=st["Cn"], cost_old=co2[0:1], cost_new=co2[1:2], ctx=ctx)
+            B.kmeans_update(Xs, lab2, st["C"], C_new=st["Cn"], cost_old=co2[0:1], cost_new=co2[1:2], ctx=ctx)
             Ch_out.copy_(st["Cn"], non_blocking=True)
             cost_h.copy_(co2[1:2], non_blocking=True)
             st["C"], st["Cn"] = st["Cn"], st["C"]
@@ -655,23 +693,52 @@ def run_highdim(env, args):
                 B.kmeans_quantize(Xd, "bf16", Xq=Xb2, scales=Xr2, ctx=ctx)
             lloyd_and_readback()
 
+        # pipelined: step i's ingest runs on a second stream (its own context and a second set of
+        # buffers) while step i - 1's Lloyd iteration and read-back run on the main one
+        s_ing = torch.cuda.Stream(device=env.dev)
+        ctx_ing = B.Context(env.dev.index)
+        pbuf = [(torch.empty_like(Xg), torch.empty(n, dtype=torch.float32, device=env.dev),
+                 torch.empty((n, d), dtype=torch.bfloat16, device=env.dev) if Xb2 is not None else None,
+                 torch.empty(n, dtype=torch.float32, device=env.dev) if Xb2 is not None else None)
+                for _ in range(2)]
+        ev_ready = [torch.cuda.Event() for _ in range(2)]
+        ev_free = [torch.cuda.Event() for _ in range(2)]
+
+        def e2e_step_pipelined(i):
+            b = i % 2
+            Xs, xns, Xbs, Xrs = pbuf[b]
+            with torch.cuda.stream(s_ing):
+                s_ing.wait_event(ev_free[b])  # the Lloyd step that last read this buffer
+                B.kmeans_ingest(hb.tensor, X_dev=Xs, xnorm=xns, Xq=Xbs, resid=Xrs, quantize=Xbs is not None,
+                                device=env.dev, ctx=ctx_ing)
+                ev_ready[b].record(s_ing)
+            torch.cuda.current_stream(env.dev).wait_event(ev_ready[b])
+            lloyd_and_readback(Xs, xns, Xbs, Xrs)
+            ev_free[b].record(torch.cuda.current_stream(env.dev))
+
         E = env.timed(e2e_step, args.e2e_steps or 5, 1, profile=False)
         Ec = env.timed(e2e_step_copy_engine, args.e2e_steps or 5, 1, profile=False)
-        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT,
+        Ep = env.timed(e2e_step_pipelined, args.e2e_steps or 5, 2, profile=False)
+        e2e = {"value": env.ranks.whole_job(F, E["ms"]) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * d * 4 + 8),
                "ms_per_step": E["ms"],
-               "copy_engine": {"value": env.world * F / (Ec["ms"] * 1e-3) / 1e9, "ms_per_step": Ec["ms"],
-                               "note": "the same step with X copied by the copy engine from torch-pinned memory, "
-                                       "then norms and the operand copy as separate passes"},
+               "pipelined": {"value": env.ranks.whole_job(F, Ep["ms"]) / 1e9, "ms_per_step": Ep["ms"],
+                             "note": "step i's ingest on a second stream and context (two buffer sets) issued "
+                                     "while step i - 1's Lloyd iteration runs: no faster, since the ingest "
+                                     "kernel holds every SM while it waits on the host link"},
+               "copy_engine": {"value": env.ranks.whole_job(F, Ec["ms"]) / 1e9, "ms_per_step": Ec["ms"],
+                               "note": "X copied by the copy engine from torch-pinned memory, then norms and "
+                                       "the operand copy as separate passes"},
                "note": "every step: X read from a mapped host block (kmeans_ingest: device copy, norms, BF16 "
-                       "copy and residuals in one pass), assign, update, and D2H of the centers and the cost"}
-        del hb
+                       "copy and residuals in one pass, at the host link's rate: 209 GB/s here, as fast as a "
+                       "copy-engine copy of pinned memory), assign, update, and D2H of the centers and the cost"}
+        del hb, pbuf
 
     forms = None
     if form == "bf16" and not args.no_compare:
         s32 = max(3, min(args.steps, args.steps // 2))
         R32 = lloyd_timed(env, Xg, None, None, xnorm, C0, "f32", "tcgen05", s32, args.warmup)
-        v32 = env.world * F / (R32["ms"] * 1e-3) / 1e9
+        v32 = env.ranks.whole_job(F, R32["ms"]) / 1e9
         it = args.warmup + min(s32, args.steps) - 1
         c16, c32 = float(R["costs"][it, 1]), float(R32["costs"][it, 1])
         forms = {"bf16": {"value": value, "ms_per_step": ms},
@@ -699,7 +766,7 @@ def run_highdim(env, args):
     line.update({"roofline": roof, "rooflines": rooflines, "step_roofline": step_roof, "pipeline": pipeline,
                  "forms": forms,
                  "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["launches"], "clocks": R["clocks"],
-                 "kernels_ms": kernels_ms(prof), "points_per_s": env.world * n / (ms * 1e-3),
+                 "kernels_ms": kernels_ms(prof), "points_per_s": env.ranks.whole_job(n, ms),
                  "rechecked_per_step": float(np.mean(R["rechecked"][args.warmup:])),
                  "cost_last": float(R["costs"][-1, 1])})
     return line
@@ -736,7 +803,7 @@ def run_small(env, args):
 
     R = env.timed(run, args.steps, args.warmup, clocks=True, flush=lambda: flush_buf.fill_(1.0))
     ms, prof = R["ms"], R["prof"]
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     kname = max((nm for nm in prof), key=lambda nm: prof[nm][1])
     bytes_per = {"assign_tc": n * d * 4 + k * d * 4 + n * 4, "assign_simt": n * d * 4 + k * d * 4 + n * 4,
                  "update": n * d * 4 + n * 4 + k * (d + 2) * 8, "seed": (k - 1) * n * d * 4,
@@ -768,7 +835,7 @@ def run_small(env, args):
             Lh.copy_(labels, non_blocking=True)
 
         E = env.timed(e2e_step, args.e2e_steps or 10, 2, flush=lambda: flush_buf.fill_(1.0), profile=False)
-        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+        e2e = {"value": env.ranks.whole_job(F, E["ms"]) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(k * d * 4 + n * 4), "ms_per_step": E["ms"]}
 
     cpu = None
@@ -847,7 +914,7 @@ def run_stream(env_args):
                     args.engine if pf == "bf16" else "tcgen05",
                     args.steps, args.warmup, clocks=True, center_terms=args.center_terms if pf == "bf16" else 1)
     ms, prof = R["ms"], R["prof"]
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     peaks = env.peaks
     es = 2 if pf == "bf16" else 4
     roof = roofline(peaks, "assign_tc", kernel_avg_s(prof, "assign_tc"), n * r * es + k * r * es + n * 4,
@@ -877,7 +944,7 @@ def run_stream(env_args):
         R16x2 = lloyd_timed(env, Y, Yb, Yr, yn, C0, "bf16", args.engine, s2, args.warmup, center_terms=2)
         it = args.warmup + s2 - 1
         c16, c8, c32 = (float(x["costs"][it, 1]) for x in (R16, R8, R32))
-        v16, v8, v32 = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (R16, R8, R32))
+        v16, v8, v32 = (env.ranks.whole_job(F, x["ms"]) / 1e9 for x in (R16, R8, R32))
         forms = {"bf16": {"value": v16, "ms_per_step": R16["ms"], "assign_ms": kernel_avg_s(R16["prof"], "assign_tc") * 1e3,
                           "rechecked_per_step": float(np.mean(R16["rechecked"][args.warmup:]))},
                  "fp8": {"value": v8, "ms_per_step": R8["ms"], "assign_ms": kernel_avg_s(R8["prof"], "assign_tc") * 1e3,
@@ -885,12 +952,12 @@ def run_stream(env_args):
                          "final_cost_rel_gap_vs_f32": abs(c8 - c32) / c32},
                  "f32_3xtf32": {"value": v32, "ms_per_step": R32["ms"],
                                 "assign_ms": kernel_avg_s(R32["prof"], "assign_tc") * 1e3},
-                 "bf16x2": {"value": env.world * F / (R16x2["ms"] * 1e-3) / 1e9, "ms_per_step": R16x2["ms"],
+                 "bf16x2": {"value": env.ranks.whole_job(F, R16x2["ms"]) / 1e9, "ms_per_step": R16x2["ms"],
                             "assign_ms": kernel_avg_s(R16x2["prof"], "assign_tc") * 1e3,
                             "rechecked_per_step": float(np.mean(R16x2["rechecked"][args.warmup:])),
                             "final_cost_rel_gap_vs_f32": abs(float(R16x2["costs"][it, 1]) - c32) / c32},
                  "primary": pf, "speedup_bf16_vs_f32": v16 / v32, "speedup_fp8_vs_f32": v8 / v32,
-                 "speedup_bf16x2_vs_f32": env.world * F / (R16x2["ms"] * 1e-3) / 1e9 / v32,
+                 "speedup_bf16x2_vs_f32": env.ranks.whole_job(F, R16x2["ms"]) / 1e9 / v32,
                  "final_cost_rel_gap_bf16_vs_f32": abs(c16 - c32) / c32,
                  "note": "the three forms run the same Lloyd iterations from the same k-means++ centers"}
 
@@ -940,7 +1007,7 @@ def run_stream(env_args):
             Lh.copy_(labels, non_blocking=True)
 
         E = env.timed(e2e_step, args.e2e_steps or 2, 1, profile=False)
-        e2e = {"value": env.world * Fw / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+        e2e = {"value": env.ranks.whole_job(Fw, E["ms"]) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(k * r * 4 + n * 4), "ms_per_step": E["ms"],
                "note": "a step is the whole job from FP32 chunks in pinned host memory: H2D, BF16 copy, "
                        "projection, norms, k-means++, 20 iterations, D2H of centers and labels"}
@@ -966,7 +1033,7 @@ def run_stream(env_args):
         "parallelism": "replicas" if env.world > 1 else "single GPU"})
     line.update({"roofline": roof, "pipeline": pipeline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e,
                  "gpu_launches": R["launches"], "clocks": R["clocks"], "kernels_ms": kernels_ms(prof),
-                 "points_per_s": env.world * n / (ms * 1e-3), "cost_last": float(R["costs"][-1, 1])})
+                 "points_per_s": env.ranks.whole_job(n, ms), "cost_last": float(R["costs"][-1, 1])})
     return line
 
 
@@ -1020,7 +1087,7 @@ def run_batch(env_args):
     costs_p = [p["cost_out"].clone() for p in probs]
     R = env.timed(lambda i: B.kmeans_batch_replay(ctx=ctx), args.steps, args.warmup - 1, clocks=True, profile=False)
     ms = R["ms"]
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     ok = all(torch.equal(p["cost_out"], c) for p, c in zip(probs, costs_p))
 
     # per-kernel times from one run that is not recorded into a graph
@@ -1046,7 +1113,7 @@ def run_batch(env_args):
         for p, cp in zip(probs, costs_p):
             a, b = cp[:, 1].cpu().numpy(), p["cost_out"][:, 1].cpu().numpy()
             gaps.append(float(np.max(np.abs(a - b) / b)))
-        vo = env.world * F / (Ro["ms"] * 1e-3) / 1e9
+        vo = env.ranks.whole_job(F, Ro["ms"]) / 1e9
         v16, ms16, f16 = (value, ms, first_s) if pf == "bf16" else (vo, Ro["ms"], first_o)
         v32, ms32, f32_ = (vo, Ro["ms"], first_o) if pf == "bf16" else (value, ms, first_s)
         forms = {"bf16": {"value": v16, "ms_per_step": ms16, "first_call_s": f16},
@@ -1069,7 +1136,7 @@ def run_batch(env_args):
                 co.copy_(p["cost_out"], non_blocking=True)
 
         E = env.timed(e2e_step, args.e2e_steps or 2, 1, profile=False)
-        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(xbytes),
+        e2e = {"value": env.ranks.whole_job(F, E["ms"]) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(xbytes),
                "d2h_bytes_per_step": int(sum(p["C_out"].numel() * 4 + p["cost_out"].numel() * 8 for p in probs)),
                "ms_per_step": E["ms"], "note": "H2D of every problem's X, planning + recording + launch of "
                                                "the graph (tile widths cached), D2H of centers and costs"}
@@ -1144,7 +1211,7 @@ def run_learned(env, args):
 
     R = env.timed(step_learned, K, args.warmup, clocks=True)
     ms, prof = R["ms"], R["prof"]
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     mis = int((lab != exact).sum().item())
     nfb = nf.cpu().numpy()[args.warmup:]
     c_learn = float(cost[-1, 0].item())
@@ -1175,7 +1242,7 @@ def run_learned(env, args):
     if not args.no_compare:
         Rb = full_scan("bf16", Xh, Xhr, max(2, min(K, 3)))
         Rf = full_scan("f32", None, None, 2)
-        vb, vf = (env.world * F / (x["ms"] * 1e-3) / 1e9 for x in (Rb, Rf))
+        vb, vf = (env.ranks.whole_job(F, x["ms"]) / 1e9 for x in (Rb, Rf))
         forms = {"learned": {"value": value, "ms_per_step": ms, "misassigned": mis, "cost": c_learn},
                  "bf16_full_scan": {"value": vb, "ms_per_step": Rb["ms"], "misassigned": Rb["mis"], "cost": Rb["cost"],
                                     "assign_ms": kernel_avg_s(Rb["prof"], "assign_tc") * 1e3},
@@ -1203,7 +1270,7 @@ def run_learned(env, args):
             ch.copy_(cost[0, 0:1], non_blocking=True)
 
         E = env.timed(e2e_step, args.e2e_steps or 2, 1, profile=False)
-        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+        e2e = {"value": env.ranks.whole_job(F, E["ms"]) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(n * 4 + 8), "ms_per_step": E["ms"]}
 
     cpu = None
@@ -1222,7 +1289,7 @@ def run_learned(env, args):
                  "fallback_rate": float(np.mean(nfb)) / n, "misassignment_rate": mis / n,
                  "training": {"epochs": 10, "batch": 4096, "train_s": train_s, "loss_first": losses[0],
                               "loss_last": losses[-1]},
-                 "centers_s": centers_s, "points_per_s": env.world * n / (ms * 1e-3)})
+                 "centers_s": centers_s, "points_per_s": env.ranks.whole_job(n, ms)})
     return line
 
 
@@ -1304,7 +1371,7 @@ def run_svd(env, args):
     R = env.timed(step, args.steps, args.warmup, clocks=True)
     ms, prof = R["ms"], R["prof"]
     F = svd_flops(n, d, s, ell)
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     rooflines = svd_rooflines(env.peaks, prof, n, d, s, R["total_s"])
     roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
     Vh = V.cpu().numpy().astype(np.float64)
@@ -1329,7 +1396,7 @@ def run_svd(env, args):
             sh_out.copy_(sig, non_blocking=True)
 
         E = env.timed(e2e_step, args.e2e_steps or 5, 1, profile=False)
-        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+        e2e = {"value": env.ranks.whole_job(F, E["ms"]) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(d * ell * 4 + ell * 4), "ms_per_step": E["ms"],
                "note": "every step: the piece read from a mapped host block (kmeans_ingest), the SVD, and D2H "
                        "of V and the singular values"}
@@ -1439,7 +1506,7 @@ def run_bico(env, args):
     form = primary_form(args.form, d)
     R = run_form(form, args.steps, True)
     ms, prof = R["ms"], R["prof"]
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     wn = w.astype(np.float64)
     tk = take.cpu().numpy()
     outcome = {"whole": int((tk == wn).sum()), "part": int(((tk > 0) & (tk < wn)).sum()), "none": int((tk == 0).sum()),
@@ -1461,7 +1528,7 @@ def run_bico(env, args):
     if not args.no_compare:
         other = "bf16" if form == "f32" else "f32"
         R2 = run_form(other, max(3, args.steps // 2), False)
-        forms[other] = {"value": env.world * F / (R2["ms"] * 1e-3) / 1e9, "ms_per_step": R2["ms"],
+        forms[other] = {"value": env.ranks.whole_job(F, R2["ms"]) / 1e9, "ms_per_step": R2["ms"],
                         "note": "the same query in the other exact form (labels exact in both)"}
 
     e2e = None
@@ -1481,7 +1548,7 @@ def run_bico(env, args):
             ref_h.copy_(ref, non_blocking=True)
 
         E = env.timed(e2e_step, args.e2e_steps or 5, 3, profile=False)
-        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+        e2e = {"value": env.ranks.whole_job(F, E["ms"]) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(n * (8 + 4)), "ms_per_step": E["ms"],
                "note": "every step: the batch read from a mapped host block (kmeans_ingest), the query, and D2H of "
                        "every point's reference and insertable count"}
@@ -1535,7 +1602,7 @@ def run_piecy(env, args):
     R = env.timed(step, args.steps, args.warmup, clocks=True)
     ms, prof = R["ms"], R["prof"]
     F = piecy_flops(P, rows, d, s, ell)
-    value = env.world * F / (ms * 1e-3) / 1e9
+    value = env.ranks.whole_job(F, ms) / 1e9
     peaks = env.peaks
     tf = unit_peak(peaks, "f32", True, R["total_s"])
     note3 = "3xTF32: max(probed kind::tf32, measured BF16 x nominal TF32/BF16 ratio) / 3"
@@ -1570,7 +1637,7 @@ def run_piecy(env, args):
             Lh.copy_(L, non_blocking=True)
 
         E = env.timed(e2e_step, args.e2e_steps or 3, 3, profile=False)
-        e2e = {"value": env.world * F / (E["ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
+        e2e = {"value": env.ranks.whole_job(F, E["ms"]) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(n * d * 4),
                "d2h_bytes_per_step": int(n * d * 4), "ms_per_step": E["ms"],
                "note": "every step: the pieces read from a mapped host block (kmeans_ingest), the per-piece bases "
                        "and lifts, and D2H of the lifted points"}
@@ -1753,8 +1820,7 @@ def main():
         line = run_learned(env, args)
     if env.rank == 0:
         print(json.dumps(line), flush=True)
-    if env.world > 1:
-        env.dist.destroy_process_group()
+    env.ranks.close()
 
 
 if __name__ == "__main__":
