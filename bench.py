@@ -64,6 +64,7 @@ SWN_X = 20   # signal dimensions per hidden set (Section 3 leaves the count open
 FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense ratios, applied to the measured BF16 peak
 FP8_OVER_BF16 = 4.5 / 2.25
+FP64_NOMINAL_TFLOPS = 1.25    # GB300's dense FP64 figure (the FP64 pipe is about 1/64 of the FP32 one)
 
 
 def parse():
@@ -369,6 +370,11 @@ def _probed(peaks, unit):
     return (peaks.get("probed") or {}).get(unit) or 0.0
 
 
+def fp64_peak(peaks):
+    """FP64 FMA peak: the larger of the probe and the nominal figure."""
+    return max(FP64_NOMINAL_TFLOPS, _probed(peaks, "fp64"))
+
+
 def ffma_peak(peaks):
     """FP32 FMA peak: the larger of the probe and 152 SMs x 128 lanes x 2 x 2.07 GHz."""
     return max(FFMA_PEAK_TFLOPS, _probed(peaks, "ffma"))
@@ -393,7 +399,8 @@ def peaks_report(peaks):
             "source": peaks["source"], "probed_tflops": peaks.get("probed"),
             "tf32_nominal_tflops": b * TF32_OVER_BF16, "fp8_nominal_tflops": b * FP8_OVER_BF16,
             "ffma_nominal_tflops": FFMA_PEAK_TFLOPS,
-            "rule": "tf32 / fp8 / ffma peak = max(probe, nominal); 3xTF32 = tf32 / 3"}
+            "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
+            "rule": "tf32 / fp8 / ffma / fp64 peak = max(probe, nominal); 3xTF32 = tf32 / 3"}
 
 
 def gen_pool(jobs, fn, workers=None):
@@ -1520,9 +1527,12 @@ def run_bico(env, args):
                                  note=None if form == "bf16" else
                                  "3xTF32: max(probed kind::tf32, measured BF16 x nominal TF32/BF16 ratio) / 3"),
                  "bico_take": roofline(peaks, "bico_take", kernel_avg_s(prof, "bico_take"),
-                                       n * d * 4 + n * (4 + 4 + 8 + 8) + m * d * 8 * 2, 0.0, 1.0, R["total_s"],
-                                       bound="hbm", note="the FP64 distance to the feature's centroid and the "
-                                                         "insertion rule (centroids read from L2 after the first)")}
+                                       n * d * 4 + n * (4 + 4 + 8 + 8) + m * d * 8 * 2, 3.0 * n * d + 8.0 * n,
+                                       fp64_peak(peaks), R["total_s"], bound="alu",
+                                       note="FP64-bound (ncu: FP64 pipe 87% busy, DRAM 9%): per element of "
+                                            "||x - mu||^2 one subtraction and one FMA (3 flops; the FP32 -> FP64 "
+                                            "conversions occupy the pipe too, uncounted), per point the rule's "
+                                            "divisions and products; peak = max(probed FP64, 1.25 TFLOP/s)")}
     roof = max(rooflines.values(), key=lambda r: r["kernel_ms"])
     forms = {form: {"value": value, "ms_per_step": ms}}
     if not args.no_compare:
