@@ -51,8 +51,10 @@ def _low_rank(n, d, r, top, seed, noise):
     return A.astype(np.float32)
 
 
+# s spans the Gram kernel's three tilings (up to 88, 96-124 and 128 columns)
 @pytest.mark.parametrize("n,d,r,s,ell", [(3000, 300, 40, 48, 32), (1000, 203, 30, 32, 5), (257, 64, 20, 16, 16),
-                                         (5000, 512, 100, 128, 100)])
+                                         (5000, 512, 100, 128, 100), (2400, 256, 70, 96, 64),
+                                         (1700, 320, 90, 112, 80)])
 def test_rsvd_matches_oracle(gb, n, d, r, s, ell):
     A = _low_rank(n, d, r, 100.0, seed=n + d, noise=1e-3)
     Om = synth.gaussian_sketch(d, s, seed=s)
