@@ -544,26 +544,46 @@ __global__ void __launch_bounds__(tc_threads<FORM, EPI>(), 1)
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(ab * bn_alloc);
                     for (int kb = 0; kb < a.kb; ++kb) {
-                        if (!mbar_wait(X3 ? &tfull[s] : &full[s], ph, abort_flag, a.wait_ns)) goto mma_done;
+                        // 3xTF32: the products of the staged tile itself (x.c_hi and x.c_lo) need only the
+                        // copies, so they are issued first and the split's low part overlaps them
+                        if (!mbar_wait(&full[s], ph, abort_flag, a.wait_ns)) goto mma_done;
                         tc_fence_after();
                         uint8_t *st = base + (size_t)s * a.stage_bytes;
                         const uint64_t adesc = sw128_desc(st);
                         const uint64_t bdesc = sw128_desc(st + (X3 ? 2 : 1) * a.a_bytes);
+                        if constexpr (X3) {
+                            const uint64_t blo = sw128_desc(st + 2 * a.a_bytes + a.b_bytes);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                                const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes per MMA step
+                                if (a.stack) {
+                                    tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc2, acc);
+                                } else {
+                                    tc_mma<FORM>(d_tmem, adesc + off, blo + off, a.idesc, acc);
+                                    tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, 1u);
+                                }
+                            }
+                            if (!mbar_wait(&tfull[s], ph, abort_flag, a.wait_ns)) {
+                                // the products above are in flight: commit them so the abort path drains them
+                                tc_commit(&empty[s]);
+                                committed = true;
+                                last_bar = &empty[s];
+                                last_parity = ph;
+                                goto mma_done;
+                            }
+                            tc_fence_after();
+                            const uint64_t alo = sw128_desc(st + a.a_bytes);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                tc_mma<FORM>(d_tmem, alo + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), a.idesc, 1u);
+                        }
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
                             const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes per MMA step
                             if constexpr (X3) {
-                                const uint64_t alo = sw128_desc(st + a.a_bytes);
-                                if (a.stack) {
-                                    tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc2, acc);
-                                    tc_mma<FORM>(d_tmem, alo + off, bdesc + off, a.idesc, 1u);
-                                } else {
-                                    const uint64_t blo = sw128_desc(st + 2 * a.a_bytes + a.b_bytes);
-                                    tc_mma<FORM>(d_tmem, alo + off, bdesc + off, a.idesc, acc);
-                                    tc_mma<FORM>(d_tmem, adesc + off, blo + off, a.idesc, 1u);
-                                    tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, 1u);
-                                }
+                                (void)acc;  // issued above
                             } else if constexpr (FORM == F_BF16X2) {
                                 const uint64_t blo = sw128_desc(st + a.a_bytes + a.b_bytes);
                                 tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, a.idesc, acc);
@@ -1182,7 +1202,8 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(ab * BN_ALLOC);
                     for (int kb = 0; kb < P.kb; ++kb) {
-                        if (!mbar_wait(X3 ? &tfull[st] : &full[st], ph, abort_flag, wait_ns)) goto mma_done;
+                        // 3xTF32: the two products of the staged tile itself go first, the split's low part after
+                        if (!mbar_wait(&full[st], ph, abort_flag, wait_ns)) goto mma_done;
                         tc_fence_after();
                         uint8_t *sb = base + (size_t)st * stage_bytes;
                         const uint64_t adesc = sw128_desc(sb);
@@ -1192,14 +1213,26 @@ __global__ void __launch_bounds__(FORM == F_TF32X3 ? 384 : 256, 1)
                             const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
                             const uint64_t off = (uint64_t)(kk * 2);
                             if constexpr (X3) {
-                                const uint64_t alo = sw128_desc(sb + a_bytes);
                                 const uint64_t blo = sw128_desc(sb + 2 * a_bytes + b_bytes);
-                                tc_mma<FORM>(d_tmem, alo + off, bdesc + off, P.idesc, acc);
-                                tc_mma<FORM>(d_tmem, adesc + off, blo + off, P.idesc, 1u);
+                                tc_mma<FORM>(d_tmem, adesc + off, blo + off, P.idesc, acc);
                                 tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, P.idesc, 1u);
                             } else {
                                 tc_mma<FORM>(d_tmem, adesc + off, bdesc + off, P.idesc, acc);
                             }
+                        }
+                        if constexpr (X3) {
+                            if (!mbar_wait(&tfull[st], ph, abort_flag, wait_ns)) {
+                                // the products above are in flight: commit them so the abort path drains them
+                                tc_commit(&empty[st]);
+                                last_bar = &empty[st];
+                                last_parity = ph;
+                                goto mma_done;
+                            }
+                            tc_fence_after();
+                            const uint64_t alo = sw128_desc(sb + a_bytes);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                tc_mma<FORM>(d_tmem, alo + (uint64_t)(kk * 2), bdesc + (uint64_t)(kk * 2), P.idesc, 1u);
                         }
                         tc_commit(&empty[st]);
                         last_bar = &empty[st];
