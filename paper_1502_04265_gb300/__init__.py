@@ -10,8 +10,10 @@ __all__ = [
     "kmeans_row_norms", "kmeans_quantize", "kmeans_project_block", "kmeans_seed_pp",
     "kmeans_assign", "kmeans_update", "kmeans_cost", "gbkm_sync", "gbkm_version",
     "Context", "default_context", "GbkmError", "lloyd", "kmeans_batch_run", "kmeans_batch_replay", "kmeans_autotune",
+    "kmeans_autotune_assign",
     "kmeans_update_noalloc", "kmeans_update_scratch_bytes", "kmeans_ingest", "HostBlock", "kmeans_rsvd",
-    "kmeans_piecy_lift", "kmeans_bico_query",
+    "kmeans_piecy_lift", "kmeans_bico_query", "kmeans_center_separation", "kmeans_gemm_bf16",
+    "kmeans_learned_assign", "kmeans_mlp_forward", "kmeans_mlp_param_count", "kmeans_mlp_train_step",
 ]
 
 
