@@ -196,6 +196,12 @@ struct Band {
             bool found = !(m < v0);
             if (!found && v0 <= tn) list_push(v0, i0);
             t = tn;
+            if (!found && (le & (le - 1)) == 0) {
+                // a new best that is the group's only member (m <= tn, so the one member is m)
+                v0 = m;
+                i0 = j0 + __ffs(le) - 1;
+                return;
+            }
             // the members in index order: the first one equal to a new best m becomes the best
             // (lowest index on ties), the others enter the list
             while (le) {
