@@ -151,7 +151,7 @@ def _same_device(ref, **tensors):
     through one device's address space."""
     for name, t in tensors.items():
         if t is not None and t.device != ref.device:
-            raise ValueError(f"{name} is on {t.device}, but X is on {ref.device}")
+            raise ValueError(f"{name} is on {t.device}, but the input is on {ref.device}")
 
 
 def _update_args(X, labels, C_old, w, C_new, counts, cost_old, cost_new, n_empty):
@@ -301,6 +301,8 @@ def kmeans_row_norms(X, xnorm=None, ctx=None):
     n, d = X.shape
     if xnorm is None:
         xnorm = torch.empty(n, dtype=torch.float32, device=X.device)
+    _req(xnorm, torch.float32, (n,), "xnorm")
+    _same_device(X, xnorm=xnorm)
     c = _ctx(ctx, X)
     c.check(load().kmeans_row_norms(c.handle, _ptr(X), n, d, _ptr(xnorm)))
     return xnorm
@@ -322,6 +324,10 @@ def kmeans_quantize(X, dtype="bf16", Xq=None, scales=None, residuals=True, ctx=N
         scales = scales if scales is not None else torch.empty((n, nb), dtype=torch.float32, device=X.device)
     else:
         raise ValueError("dtype must be 'bf16' or 'fp8'")
+    _req(Xq, torch.bfloat16 if dtype == "bf16" else torch.uint8, (n, d), "Xq")
+    if scales is not None:
+        _req(scales, torch.float32, (n,) if dtype == "bf16" else (n, (d + 127) // 128), "scales")
+    _same_device(X, Xq=Xq, scales=scales)
     c = _ctx(ctx, X)
     c.check(load().kmeans_quantize(c.handle, _ptr(X), n, d, DTYPES[dtype], _ptr(Xq), _ptr(scales)))
     return Xq, scales
@@ -379,6 +385,13 @@ def kmeans_ingest(X_src, X_dev=None, xnorm=None, Xq=None, resid=None, copy=True,
     if quantize:
         Xq = Xq if Xq is not None else torch.empty((n, d), dtype=torch.bfloat16, device=dev)
         resid = resid if resid is not None else torch.empty(n, dtype=torch.float32, device=dev)
+        _req(Xq, torch.bfloat16, (n, d), "Xq")
+        _req(resid, torch.float32, (n,), "resid")
+    if copy:
+        _req(X_dev, torch.float32, (n, d), "X_dev")
+    _req(xnorm, torch.float32, (n,), "xnorm")
+    _same_device(xnorm, X_dev=X_dev if copy else None, Xq=Xq if quantize else None,
+                 resid=resid if quantize else None, X_src=X_src if X_src.is_cuda else None)
     c = _ctx(ctx, xnorm)
     c.check(load().kmeans_ingest(c.handle, ct.c_void_p(X_src.data_ptr()), n, d, _ptr(X_dev) if copy else None,
                                  _ptr(xnorm), _ptr(Xq) if quantize else None, _ptr(resid) if quantize else None))
@@ -400,6 +413,10 @@ def kmeans_rsvd(A, Omega, ell, w=None, V=None, sigma=None, info=None, ctx=None):
     V = V if V is not None else torch.empty((d, ell), dtype=torch.float32, device=A.device)
     sigma = sigma if sigma is not None else torch.empty(ell, dtype=torch.float32, device=A.device)
     info = info if info is not None else torch.zeros(1, dtype=torch.int32, device=A.device)
+    _req(V, torch.float32, (d, ell), "V")
+    _req(sigma, torch.float32, (ell,), "sigma")
+    _req(info, torch.int32, (1,), "info")
+    _same_device(A, Omega=Omega, w=w, V=V, sigma=sigma, info=info)
     c = _ctx(ctx, A)
     c.check(load().kmeans_rsvd(c.handle, _ptr(A), n, d, _ptr(w), _ptr(Omega), s, ell, _ptr(V), _ptr(sigma),
                                _ptr(info)))
@@ -423,6 +440,10 @@ def kmeans_project_block(X, V, Y=None, X_lift=None, lift=False, ctx=None):
         Y = torch.empty((n, r), dtype=torch.float32, device=X.device)
     if lift and X_lift is None:
         X_lift = torch.empty((n, d), dtype=torch.float32, device=X.device)
+    _req(Y, torch.float32, (n, r), "Y")
+    if X_lift is not None:
+        _req(X_lift, torch.float32, (n, d), "X_lift")
+    _same_device(X, V=V, Y=Y, X_lift=X_lift)
     c = _ctx(ctx, X)
     c.check(load().kmeans_project_block(c.handle, _ptr(X), xt, n, d, _ptr(V), r, _ptr(Y), _ptr(X_lift)))
     return (Y, X_lift) if X_lift is not None else Y
@@ -533,7 +554,13 @@ def kmeans_cost(X, C, w=None, cost=None, ctx=None):
     _req(X, torch.float32, name="X")
     n, d = X.shape
     _req(C, torch.float32, name="C")
+    if C.dim() != 2 or C.shape[1] != d:
+        raise ValueError(f"C must be k x {d}")
+    if w is not None:
+        _req(w, torch.float32, (n,), "w")
     cost = cost if cost is not None else torch.empty(1, dtype=torch.float64, device=X.device)
+    _req(cost, torch.float64, (1,), "cost")
+    _same_device(X, C=C, w=w, cost=cost)
     c = _ctx(ctx, X)
     c.check(load().kmeans_cost(c.handle, _ptr(X), n, d, _ptr(w), _ptr(C), C.shape[0], _ptr(cost)))
     return cost
@@ -591,6 +618,11 @@ def kmeans_batch_run(problems, seeds, iters, compute="bf16", graph=True, autotun
         pr.setdefault("C_out", torch.empty((seeds, k, d), dtype=torch.float32, device=dev))
         pr.setdefault("labels_out", torch.empty((seeds, n), dtype=torch.int32, device=dev))
         pr.setdefault("cost_out", torch.empty((seeds, 2), dtype=torch.float64, device=dev))
+        _req(pr["C_out"], torch.float32, (seeds, k, d), "C_out")
+        _req(pr["labels_out"], torch.int32, (seeds, n), "labels_out")
+        _req(pr["cost_out"], torch.float64, (seeds, 2), "cost_out")
+        _same_device(problems[0]["X"], X=X, u=u, C_out=pr["C_out"], labels_out=pr["labels_out"],
+                     cost_out=pr["cost_out"])
         arr[i] = Problem(X.data_ptr(), n, d, k, u.data_ptr(), _ptr(pr["C_out"]).value,
                          _ptr(pr["labels_out"]).value, _ptr(pr["cost_out"]).value)
         keep.append(pr)
@@ -637,11 +669,17 @@ def kmeans_gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Y=None, ctx=None):
     _req(A, torch.bfloat16, name="A")
     _req(B, torch.bfloat16, name="B")
     M, K = A.shape
+    if B.dim() != 2 or B.shape[1] != K:
+        raise ValueError(f"B must be N x {K}")
     N = B.shape[0]
     if Y is None:
         Y = torch.empty((M, N), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=A.device)
+    _req(Y, torch.bfloat16 if out_bf16 else torch.float32, name="Y")
+    if Y.dim() != 2 or Y.shape[0] != M or Y.shape[1] < N:
+        raise ValueError(f"Y must be {M} x (at least {N})")
     if bias is not None:
         _req(bias, torch.float32, (N,), "bias")
+    _same_device(A, B=B, bias=bias, Y=Y)
     c = _ctx(ctx, A)
     c.check(load().kmeans_gemm_bf16(c.handle, _ptr(A), _ptr(B), M, N, K, _ptr(bias), act, 1 if out_bf16 else 0,
                                     _ptr(Y), Y.shape[1]))
@@ -657,7 +695,14 @@ def _mlp_struct(net):
 
 def kmeans_mlp_forward(net, Xh, logits=None, top_idx=None, topm=32, group=1, ctx=None):
     _req(Xh, torch.bfloat16, name="Xh")
+    if Xh.dim() != 2 or Xh.shape[1] != net.d_in:
+        raise ValueError(f"Xh must be n x {net.d_in}")
     n = Xh.shape[0]
+    if logits is not None:
+        _req(logits, torch.float32, (n, net.k), "logits")
+    if top_idx is not None:
+        _req(top_idx, torch.int32, (n, topm), "top_idx")
+    _same_device(Xh, params=net.params, logits=logits, top_idx=top_idx)
     m = _mlp_struct(net)
     c = _ctx(ctx, Xh)
     c.check(load().kmeans_mlp_forward(c.handle, ct.byref(m), _ptr(Xh), n, _ptr(logits), _ptr(top_idx), topm, int(group)))
@@ -666,8 +711,15 @@ def kmeans_mlp_forward(net, Xh, logits=None, top_idx=None, topm=32, group=1, ctx
 
 def kmeans_mlp_train_step(net, Xh, labels, lr, wd=0.0, loss_rows=None, grad_out=None, ctx=None):
     _req(Xh, torch.bfloat16, name="Xh")
-    _req(labels, torch.int32, name="labels")
+    if Xh.dim() != 2 or Xh.shape[1] != net.d_in:
+        raise ValueError(f"Xh must be B x {net.d_in}")
     B = Xh.shape[0]
+    _req(labels, torch.int32, (B,), "labels")
+    if loss_rows is not None:
+        _req(loss_rows, torch.float32, (B,), "loss_rows")
+    if grad_out is not None:
+        _req(grad_out, torch.float32, (net.params.numel(),), "grad_out")
+    _same_device(Xh, params=net.params, labels=labels, loss_rows=loss_rows, grad_out=grad_out)
     m = _mlp_struct(net)
     c = _ctx(ctx, Xh)
     c.check(load().kmeans_mlp_train_step(c.handle, ct.byref(m), _ptr(Xh), _ptr(labels), B, lr, wd,
@@ -679,6 +731,8 @@ def kmeans_center_separation(C, s2=None, ctx=None):
     _req(C, torch.float32, name="C")
     k, d = C.shape
     s2 = s2 if s2 is not None else torch.empty(k, dtype=torch.float32, device=C.device)
+    _req(s2, torch.float32, (k,), "s2")
+    _same_device(C, s2=s2)
     c = _ctx(ctx, C)
     c.check(load().kmeans_center_separation(c.handle, _ptr(C), k, d, _ptr(s2)))
     return s2
@@ -687,9 +741,20 @@ def kmeans_center_separation(C, s2=None, ctx=None):
 def kmeans_learned_assign(net, X, Xh, C, s2, topm=32, labels=None, n_fallback=None, cand_out=None, ctx=None):
     _req(X, torch.float32, name="X")
     n, d = X.shape
+    if d != net.d_in:
+        raise ValueError(f"X must be n x {net.d_in} (the network's input width)")
+    _req(Xh, torch.bfloat16, (n, d), "Xh")
+    _req(C, torch.float32, (net.k, d), "C")
     k = C.shape[0]
+    _req(s2, torch.float32, (k,), "s2")
     labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=X.device)
     n_fallback = n_fallback if n_fallback is not None else torch.zeros(1, dtype=torch.int64, device=X.device)
+    _req(labels, torch.int32, (n,), "labels")
+    _req(n_fallback, torch.int64, (1,), "n_fallback")
+    if cand_out is not None:
+        _req(cand_out, torch.int32, (n, topm), "cand_out")
+    _same_device(X, params=net.params, Xh=Xh, C=C, s2=s2, labels=labels, n_fallback=n_fallback,
+                 cand_out=cand_out)
     m = _mlp_struct(net)
     c = _ctx(ctx, X)
     c.check(load().kmeans_learned_assign(c.handle, ct.byref(m), _ptr(X), _ptr(Xh), n, d, _ptr(C), k, _ptr(s2), topm,
