@@ -1166,7 +1166,7 @@ def run_batch(env_args):
         "l2": f"inputs larger than L2 ({xbytes / 1e9:.1f} GB FP32 points)",
         "parallelism": "replicas" if env.world > 1 else "single GPU"})
     line.update({"roofline": roof, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["launches"],
-                 "gpu_launches_note": "one graph launch per step; the graph holds the run's kernels",
+                 "gpu_launches_note": "the kernels recorded in the graph, counted at every replay (one graph launch per step)",
                  "clocks": R["clocks"], "kernels_ms_outside_graph": per_iter, "first_call_s": first_s,
                  "replay_deterministic": bool(ok), "points_per_s": env.world * n_tot * S * iters / (ms * 1e-3)})
     return line

@@ -640,6 +640,7 @@ int kmeans_batch_replay(gbkm_ctx *c) {
     prof_begin(c, "batch_run");
     cudaError_t e = cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, c->stream);
     prof_end(c);
+    if (e == cudaSuccess) c->launches += c->graph_launches;  // every recorded kernel runs again
     return cuda_check(c, e, "graph launch");
 }
 

@@ -44,6 +44,7 @@ struct gbkm_ctx {
     void *graph_exec = nullptr;    // last instantiated batched-run graph (cudaGraphExec_t)
     uint64_t ws_epoch = 0;         // bumped by every ws_reserve (any call that writes the workspace)
     uint64_t graph_epoch = 0;      // ws_epoch when graph_exec was recorded (its tables live in ws)
+    int64_t graph_launches = 0;    // kernels recorded into graph_exec (counted again at every replay)
     cudaStream_t cap_stream = nullptr;  // private stream the batched run is recorded on
     int bn_cap = 0;                // center-chunk width of the tcgen05 assignment (0: 256); autotuner knob
     int stage_cap = 0;             // stage-ring depth cap of the tcgen05 assignment (0: as many as fit); autotuner knob

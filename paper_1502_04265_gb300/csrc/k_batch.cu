@@ -947,6 +947,7 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
     const bool graph = flags & 1;
     cudaGraph_t g = nullptr;
     const cudaStream_t user_stream = c->stream;
+    const int64_t launches0 = c->launches;  // the kernels recorded below are counted as they are queued
     if (graph) {
         if (!c->cap_stream) {
             e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -1041,9 +1042,9 @@ int batch_run(gbkm_ctx *c, const gbkm_problem *up, int64_t count, int64_t seeds,
         if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
         c->graph_exec = ex;
         c->graph_epoch = c->ws_epoch;
+        c->graph_launches = c->launches - launches0;  // already counted once: this first launch
         e = cudaGraphLaunch(ex, st);
         if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
-        c->launches += 0;
         return GBKM_OK;
     }
     if (rc != GBKM_OK) return rc;

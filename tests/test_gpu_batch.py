@@ -98,15 +98,21 @@ def test_batch_replay_reproduces_the_run_and_is_invalidated_by_other_calls(gb):
     seeds, iters = 2, 3
     ctx = gb.Context(0)
     probs, _ = _problems(seeds, salt=11)
+    l0 = ctx.launch_count()
     gb.kmeans_batch_run(probs, seeds, iters, compute="bf16", graph=True, ctx=ctx)
     ctx.sync()
+    recorded = ctx.launch_count() - l0
+    assert recorded > 0
     first = [(p["C_out"].clone(), p["labels_out"].clone(), p["cost_out"].clone()) for p in probs]
     for p in probs:
         p["C_out"].zero_()
         p["labels_out"].fill_(-1)
         p["cost_out"].zero_()
+    l1 = ctx.launch_count()
     gb.kmeans_batch_replay(ctx=ctx)
     ctx.sync()
+    # every kernel recorded in the graph runs again and is counted again
+    assert 0 < ctx.launch_count() - l1 <= recorded
     for p, (C, L, c) in zip(probs, first):
         assert torch.equal(p["C_out"], C) and torch.equal(p["labels_out"], L) and torch.equal(p["cost_out"], c)
     X = probs[0]["X"]
