@@ -1,5 +1,6 @@
 """The bench's reference arm (the FP64 oracle on the host cores) prints one JSON line with the
-contract's keys; run on tiny budgets, no GPU."""
+contract's keys, and the stored DRAM-traffic table it reports from is consistent; run on tiny
+budgets, no GPU."""
 import json
 import os
 import subprocess
@@ -26,3 +27,29 @@ def test_reference_arm_line(workload):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
+
+
+def test_stored_traffic_entries_are_well_formed():
+    """Every DRAM-traffic figure the bench may report names an ncu summary that exists under
+    profiles/, kernel sources that exist, and a positive byte count; the lookup returns it only while
+    those sources are unchanged (their hash is recomputed here, as the bench does)."""
+    sys.path.insert(0, ROOT)
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    argv, sys.argv = sys.argv, ["bench.py"]
+    try:
+        spec.loader.exec_module(bench)
+    finally:
+        sys.argv = argv
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        table = json.load(f)
+    assert table
+    csrc = os.path.join(ROOT, "paper_1502_04265_gb300", "csrc")
+    for key, e in table.items():
+        assert e["dram_bytes_per_launch"] > 0, key
+        assert os.path.exists(os.path.join(ROOT, e["capture"])), (key, e["capture"])
+        assert all(os.path.exists(os.path.join(csrc, s)) for s in e["sources"]), key
+        valid = e["source_hash"] == bench.source_hash(e["sources"])
+        assert bench.stored_traffic(key) == (e["dram_bytes_per_launch"] if valid else None), key
